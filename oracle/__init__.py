@@ -1,0 +1,30 @@
+"""FP64 CPU oracle for the layered-medium elastic multiple-scattering mat-vec.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
+only `tests/`, `__graft_entry__.smoke()` and the `cpu_baseline` / reference leg of
+`bench.py` use it.  It shares no code with the CUDA library (no kernels, headers,
+tables or constants); the only common input is the seeded generator module
+`synthetic`, which holds none of the method's arithmetic.
+
+Everything here is plain, slow and direct: numpy complex128 arithmetic, scipy's
+Bessel/Hankel routines as library primitives, direct O(M^2) Graf sums, and the
+separable Sommerfeld quadrature sums written exactly as the paper states them.
+
+Modules and the passages they follow
+------------------------------------
+media       wavenumbers kp = w/sqrt(lam+2mu), ks = w/sqrt(mu)          (Sec. 2)
+waves       cylindrical waves u_n, v_n, Cartesian derivatives and traction  (Sec. 2 tracdef, Sec. 4.1)
+disc        closed-form disc scattering matrix per mode, rigid and traction-free (Sec. 4.1, Sec. 4.3 projection matrix)
+graf        M2L translation T^{ml} by Graf's addition theorem          (Sec. 4.2)
+sommerfeld  contour, branch of sqrt(xi^2-k^2), M2S (pts1/sed1/sed2), S2L (Jacobi-Anger, stm/c1/c2),
+            2x2 interface reflection by the plane-wave route and by the paper's A_xi route (Sec. 3, 5.1, 5.3, 5.4, 7.3)
+system      mat-vec y = gamma - S (T + R) gamma, plane-wave right-hand side, GMRES, dense LU,
+            receiver fields, boundary-condition residual                    (Sec. 4.2 mul2, Sec. 5.2 aequ/Schur, Sec. 7.3 bplan)
+
+Pins (tests/test_oracle_*.py, all `-m "not gpu"`) tie each function to something other
+than itself: scipy/DLMF identities, Graf pointwise evaluation, the Sommerfeld identities
+as quadrature, Jacobi-Anger on contour nodes, boundary-condition residuals of the disc
+matrices, two independent derivations of the reflection matrix, identical-media zero
+reflection, plane-wave energy balance, interface continuity of the assembled field,
+boundary-condition residuals of the solved multi-particle system and a dense-LU solve.
+"""

@@ -1,0 +1,298 @@
+"""Sommerfeld-integral part of the layered operator (Sec. 3, 5.1, 5.3, 5.4).
+
+Test infrastructure only (see oracle/__init__.py).
+
+Contour (Sec. 5.1): xi(t) = t - i tanh(t)/2 on [-t_max, t_max].  The paper uses a
+trapezoid rule; we use composite Gauss-Legendre panels (reading A5) and the same nodes
+for every part of the operator.  Weights W_q = w_q xi'(t_q), xi'(t) = 1 - (i/2) sech^2 t.
+
+Branch (Sec. 3 remark, reading A4): s_k(xi) = sqrt(xi^2 - k^2) with Re s >= 0, taken as
+-i * sqrt(k^2 - xi^2) with the principal root, which also gives the limiting-absorption
+value s = -i sqrt(k^2 - xi^2) on the real propagating interval.
+
+Plane-wave bases used by the textbook route:
+  lower, upgoing   P: grad(e^{i xi x - s'_p y}),  S: grad_perp(e^{i xi x - s'_s y})
+  lower, downgoing P: grad(e^{i xi x + s'_p y}),  S: grad_perp(e^{i xi x + s'_s y})
+  upper, upgoing   P: grad(e^{i xi x - s_p y}),   S: grad_perp(e^{i xi x - s_s y})
+  upper, downgoing P: grad(e^{i xi x + s_p y}),   S: grad_perp(e^{i xi x + s_s y})
+
+M2S (Sec. 5.4, pts1 / sed1 / sed2): above a particle centred at (x_l, y_l),
+  grad(H_n(k r) e^{in th}) = (-1)^n/(i pi) int grad(e^{i xi x - s y}) e^{s y_l - i xi x_l}/s ((s - xi)/(i k))^n dxi
+so the upgoing amplitudes are U_b(xi) = sum_l sum_n gamma^l_{b,n} (-1)^n/(i pi) e^{s y_l - i xi x_l}/s ((s-xi)/(ik))^n.
+
+S2L (Sec. 5.3, Jacobi-Anger ja / stm): about a centre (x_m, y_m),
+  e^{i xi x + s y} = e^{i xi x_m + s y_m} sum_n i^n e^{i n phi} J_n(k r_m) e^{i n th_m},
+with e^{i phi} := (xi - s)/k, the analytic continuation of phi = arccos(xi/k) (reading A3),
+so a downgoing amplitude D_b contributes D_b e^{i xi x_m + s y_m} i^n e^{i n phi} to the local
+coefficient of order n.
+
+Reflection: the 2x2 map R(xi): (U_P, U_S) -> (D_P, D_S) is computed two independent ways:
+  * plane-wave route: continuity of displacement and of the traction T_y (Sec. 3) across y = 0
+    for the four plane waves, solved per node;
+  * paper route: the 4x4 system A_xi sigma = b_xi of Sec. 3 (aa), with the particle field's
+    spectral displacement b1 and traction b2 of Sec. 5.4 on the right-hand side, then sigma_21,
+    sigma_22 mapped to local expansions by eee1 (through c1/c2) of Sec. 5.3.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .media import Layered
+
+
+def contour(n_panels: int, nodes_per_panel: int, t_max: float):
+    """Nodes xi_q and weights W_q = w_q xi'(t_q) of the composite Gauss-Legendre rule."""
+    g, gw = np.polynomial.legendre.leggauss(nodes_per_panel)
+    edges = np.linspace(-t_max, t_max, n_panels + 1)
+    t = []
+    w = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        t.append(0.5 * (b - a) * g + 0.5 * (a + b))
+        w.append(0.5 * (b - a) * gw)
+    t = np.concatenate(t)
+    w = np.concatenate(w)
+    xi = t - 0.5j * np.tanh(t)
+    dxi = 1.0 - 0.5j / np.cosh(t) ** 2
+    return xi, w * dxi
+
+
+def branch_s(xi, k):
+    """s = sqrt(xi^2 - k^2) with Re s >= 0 (limiting absorption on the real axis)."""
+    xi = np.asarray(xi, dtype=complex)
+    return -1j * np.sqrt(k * k - xi * xi)
+
+
+# ----------------------------------------------------------------------------- plane waves
+
+def _pw(kind: str, xi, d):
+    """Displacement amplitude of grad(e^{i xi x + d y}) (kind 'P') or grad_perp(.) (kind 'S')."""
+    if kind == "P":
+        return np.array([1j * xi, d])
+    return np.array([-d, 1j * xi])
+
+
+def _traction_y(u, xi, d, lam, mu):
+    """T_y of a plane wave u e^{i xi x + d y} (Sec. 3: (mu(du1/dy + du2/dx), (lam+2mu) du2/dy + lam du1/dx))."""
+    return np.array([mu * (d * u[0] + 1j * xi * u[1]), (lam + 2 * mu) * d * u[1] + lam * 1j * xi * u[0]])
+
+
+def interface_solve(xi: complex, L: Layered, U=(0.0, 0.0), I=(0.0, 0.0)):
+    """Plane-wave route.  Given upgoing lower amplitudes U and downgoing upper amplitudes I
+    at horizontal wavenumber xi, return (D, E): downgoing lower and upgoing upper amplitudes
+    that make displacement and traction continuous at y = 0."""
+    sp_l, ss_l = branch_s(xi, L.kp_l), branch_s(xi, L.ks_l)
+    sp_u, ss_u = branch_s(xi, L.kp_u), branch_s(xi, L.ks_u)
+
+    def col(kind, d, lam, mu):
+        u = _pw(kind, xi, d)
+        return np.concatenate([u, _traction_y(u, xi, d, lam, mu)])
+
+    lo = (L.lam_l, L.mu_l)
+    up = (L.lam_u, L.mu_u)
+    # unknowns: D_P, D_S (lower, +s y), E_P, E_S (upper, -s y); equation: lower - upper = 0
+    A = np.stack([col("P", sp_l, *lo), col("S", ss_l, *lo),
+                  -col("P", -sp_u, *up), -col("S", -ss_u, *up)], axis=1)
+    rhs = -(U[0] * col("P", -sp_l, *lo) + U[1] * col("S", -ss_l, *lo)) \
+        + (I[0] * col("P", sp_u, *up) + I[1] * col("S", ss_u, *up))
+    z = np.linalg.solve(A, rhs)
+    return z[:2], z[2:]
+
+
+def reflection_plane_wave(xi: complex, L: Layered):
+    """2x2 R with (D_P, D_S) = R (U_P, U_S), plane-wave route."""
+    R = np.empty((2, 2), dtype=complex)
+    R[:, 0] = interface_solve(xi, L, U=(1.0, 0.0))[0]
+    R[:, 1] = interface_solve(xi, L, U=(0.0, 1.0))[0]
+    return R
+
+
+def paper_A(xi: complex, L: Layered):
+    """The 4x4 matrix A_xi of Sec. 3 (aa), entry by entry as printed, with one reading.
+
+    Row 2 is the x2-displacement continuity.  The paper prints its lower-layer entry
+    lp' - ks'^2/ls' - ls' in column 3 (sigma_21).  The sigma_21 column of the lower spectral
+    Green tensor has x2-component i xi (e^{s'_s y} - e^{s'_p y}) / (4 pi omega^2), which vanishes
+    at y = 0, while the sigma_22 column has x2-component (ks'^2/s'_s + s'_s - s'_p)/(4 pi omega^2);
+    so the entry belongs in column 4 (reading A18).  Every other entry matches the columns of
+    the upper and lower spectral Green tensors as printed."""
+    ls, lp = branch_s(xi, L.ks_u), branch_s(xi, L.kp_u)
+    ls2, lp2 = branch_s(xi, L.ks_l), branch_s(xi, L.kp_l)
+    ks, kp, ks2, kp2 = L.ks_u, L.kp_u, L.ks_l, L.kp_l
+    lam, mu, lam2, mu2 = L.lam_u, L.mu_u, L.lam_l, L.mu_l
+    x2 = xi * xi
+    return np.array([
+        [ks**2 / ls - x2 / ls + x2 / lp, 0, x2 / ls2 - ks2**2 / ls2 - x2 / lp2, 0],
+        [0, ks**2 / ls + ls - lp, 0, lp2 - ks2**2 / ls2 - ls2],   # printed in column 3; see paper_A doc
+        [-mu * ks**2, 1j * mu * xi * (ks**2 / ls + 2 * ls - 2 * lp), -mu2 * ks2**2,
+         1j * mu2 * xi * (2 * lp2 - 2 * ls2 - ks2**2 / ls2)],
+        [1j * xi * (2 * mu * (ls - lp) + lam * kp**2 / lp), -(lam + 2 * mu) * kp**2,
+         1j * xi * (2 * mu2 * (lp2 - ls2) - lam2 * kp2**2 / lp2), -(lam2 + 2 * mu2) * kp2**2],
+    ], dtype=complex)
+
+
+# ----------------------------------------------------------------------------- M2S / S2L
+
+def m2s(xi, L: Layered, centres, gamma):
+    """Upgoing amplitudes U_P, U_S at every node: arrays (N_S, nrhs) (pts1/sed1/sed2, Sec. 5.4).
+
+    gamma: (M, 2, 2p+1, nrhs) outgoing coefficients (alpha = [:,0], beta = [:,1])."""
+    M, _, nc, nrhs = gamma.shape
+    p = (nc - 1) // 2
+    n = np.arange(-p, p + 1)
+    out = []
+    for b, k in ((0, L.kp_l), (1, L.ks_l)):
+        s = branch_s(xi, k)                                   # (Q,)
+        fac = (s - xi) / (1j * k)                             # (Q,)
+        powers = ((-1.0) ** n)[None, :] * fac[:, None] ** n[None, :]     # (Q, nc)
+        E = np.exp(s[:, None] * centres[None, :, 1] - 1j * xi[:, None] * centres[None, :, 0])  # (Q, M)
+        E = E / (1j * np.pi * s[:, None])
+        inner = np.einsum("qn,mnr->qmr", powers, gamma[:, b])  # (Q, M, nrhs)
+        out.append(np.einsum("qm,qmr->qr", E, inner))
+    return out[0], out[1]
+
+
+def s2l(xi, W, L: Layered, centres, D_P, D_S, p: int):
+    """Local (incoming) coefficients (M, 2, 2p+1, nrhs) of the downgoing field
+    int D_P grad(e^{i xi x + s'_p y}) + D_S grad_perp(e^{i xi x + s'_s y}) dxi  (Sec. 5.3, stm)."""
+    n = np.arange(-p, p + 1)
+    res = []
+    for D, k in ((D_P, L.kp_l), (D_S, L.ks_l)):
+        s = branch_s(xi, k)
+        eiphi = (xi - s) / k
+        powers = (1j ** n)[None, :] * eiphi[:, None] ** n[None, :]       # (Q, nc)
+        E = np.exp(1j * xi[:, None] * centres[None, :, 0] + s[:, None] * centres[None, :, 1])  # (Q, M)
+        res.append(np.einsum("qm,qn,qr->mnr", E * W[:, None], powers, D))
+    return np.stack(res, axis=1)
+
+
+def reflect_nodes(xi, L: Layered, U_P, U_S):
+    """(D_P, D_S) = R(xi_q) (U_P, U_S) per node, plane-wave route."""
+    D_P = np.empty_like(U_P)
+    D_S = np.empty_like(U_S)
+    for q in range(xi.size):
+        R = reflection_plane_wave(xi[q], L)
+        D_P[q] = R[0, 0] * U_P[q] + R[0, 1] * U_S[q]
+        D_S[q] = R[1, 0] * U_P[q] + R[1, 1] * U_S[q]
+    return D_P, D_S
+
+
+def layered_apply(xi, W, L: Layered, centres, gamma):
+    """Local coefficients of the interface-reflected field generated by gamma (plane-wave route)."""
+    U_P, U_S = m2s(xi, L, centres, gamma)
+    D_P, D_S = reflect_nodes(xi, L, U_P, U_S)
+    p = (gamma.shape[2] - 1) // 2
+    return s2l(xi, W, L, centres, D_P, D_S, p)
+
+
+def layered_apply_paper(xi, W, L: Layered, centres, gamma, x0: float = 0.0):
+    """Same operator by the paper's route: b1/b2 spectral values -> A_xi sigma = b -> eee1.
+
+    b1 gives the spectral displacement (f11, f12) of grad(H_n(kp' r)e^{in th}) and
+    (f21, f22) of grad_perp(H_n(ks' r)e^{in th}) at y = 0, scaled by 4 pi omega^2 e^{i xi x0};
+    b2 gives their tractions.  Continuity u_1^s - u_2^s = v and T u_1^s - T' u_2^s = T' v
+    (rows of aa) put them on the right-hand side.  eee1 maps sigma_21, sigma_22 to local
+    coefficients; a quadrature weight W_q multiplies each node (Sec. 5.1)."""
+    M, _, nc, nrhs = gamma.shape
+    p = (nc - 1) // 2
+    n = np.arange(-p, p + 1)
+    om2 = L.omega ** 2
+    lam2, mu2 = L.lam_l, L.mu_l
+    out = np.zeros((M, 2, nc, nrhs), dtype=complex)
+    for q in range(xi.size):
+        x = xi[q]
+        lp2, ls2 = branch_s(x, L.kp_l), branch_s(x, L.ks_l)
+        phase = np.exp(1j * x * (x0 - centres[:, 0]))                      # (M,)
+        powp = ((-1.0) ** n) * ((lp2 - x) / (1j * L.kp_l)) ** n              # (nc,)
+        pows = ((-1.0) ** n) * ((ls2 - x) / (1j * L.ks_l)) ** n
+        ep = np.exp(lp2 * centres[:, 1]) * phase
+        es = np.exp(ls2 * centres[:, 1]) * phase
+        f11 = 4 * om2 * x / lp2 * ep[:, None] * powp[None, :]
+        f12 = 4 * om2 * 1j * ep[:, None] * powp[None, :]
+        f21 = -4 * om2 * 1j * es[:, None] * pows[None, :]
+        f22 = 4 * om2 * x / ls2 * es[:, None] * pows[None, :]
+        t11 = mu2 * f11 * (-lp2) + mu2 * f12 * (1j * x)
+        t12 = (lam2 + 2 * mu2) * f12 * (-lp2) + lam2 * f11 * (1j * x)
+        t21 = mu2 * f21 * (-ls2) + mu2 * f22 * (1j * x)
+        t22 = (lam2 + 2 * mu2) * f22 * (-ls2) + lam2 * f21 * (1j * x)
+        al = gamma[:, 0]
+        be = gamma[:, 1]
+        rhs = np.stack([
+            np.einsum("mn,mnr->r", f11, al) + np.einsum("mn,mnr->r", f21, be),
+            np.einsum("mn,mnr->r", f12, al) + np.einsum("mn,mnr->r", f22, be),
+            np.einsum("mn,mnr->r", t11, al) + np.einsum("mn,mnr->r", t21, be),
+            np.einsum("mn,mnr->r", t12, al) + np.einsum("mn,mnr->r", t22, be)])
+        sig = np.linalg.solve(paper_A(x, L), rhs)                        # (4, nrhs)
+        s21, s22 = sig[2], sig[3]
+        eiphp = (x - lp2) / L.kp_l
+        eiphs = (x - ls2) / L.ks_l
+        base = W[q] / (4 * np.pi * om2) * np.exp(1j * x * (centres[:, 0] - x0))   # (M,)
+        inp = (1j ** n) * eiphp ** n
+        ins = (1j ** n) * eiphs ** n
+        cp = (base * np.exp(lp2 * centres[:, 1]))[:, None] * inp[None, :]        # (M, nc)
+        cs = (base * np.exp(ls2 * centres[:, 1]))[:, None] * ins[None, :]
+        out[:, 0] += cp[:, :, None] * (-1j * x / lp2 * s21 - s22)[None, None, :]
+        out[:, 1] += cs[:, :, None] * (s21 - 1j * x / ls2 * s22)[None, None, :]
+    return out
+
+
+# ----------------------------------------------------------------------------- field sums
+
+def downgoing_field(xi, W, L: Layered, D_P, D_S, X, Y):
+    """u and grad u of int D_P grad(e^{i xi x + s'_p y}) + D_S grad_perp(e^{i xi x + s'_s y}) dxi.
+
+    D_P, D_S: (Q,) amplitudes for one right-hand side; X, Y: point arrays (lower layer)."""
+    X = np.asarray(X, float)[..., None]
+    Y = np.asarray(Y, float)[..., None]
+    sp, ss = branch_s(xi, L.kp_l), branch_s(xi, L.ks_l)
+    ep = W * D_P * np.exp(1j * xi * X + sp * Y)
+    es = W * D_S * np.exp(1j * xi * X + ss * Y)
+    ix = 1j * xi
+    u1 = (ix * ep - ss * es).sum(-1)
+    u2 = (sp * ep + ix * es).sum(-1)
+    g = [[(ix * ix * ep - ss * ix * es).sum(-1), (ix * sp * ep - ss * ss * es).sum(-1)],
+         [(sp * ix * ep + ix * ix * es).sum(-1), (sp * sp * ep + ix * ss * es).sum(-1)]]
+    return u1, u2, g
+
+
+def upgoing_upper_field(xi, W, L: Layered, E_P, E_S, X, Y):
+    """u and grad u of int E_P grad(e^{i xi x - s_p y}) + E_S grad_perp(e^{i xi x - s_s y}) dxi (upper layer)."""
+    X = np.asarray(X, float)[..., None]
+    Y = np.asarray(Y, float)[..., None]
+    sp, ss = branch_s(xi, L.kp_u), branch_s(xi, L.ks_u)
+    ep = W * E_P * np.exp(1j * xi * X - sp * Y)
+    es = W * E_S * np.exp(1j * xi * X - ss * Y)
+    ix = 1j * xi
+    u1 = (ix * ep + ss * es).sum(-1)
+    u2 = (-sp * ep + ix * es).sum(-1)
+    g = [[(ix * ix * ep + ss * ix * es).sum(-1), (-ix * sp * ep - ss * ss * es).sum(-1)],
+         [(-sp * ix * ep + ix * ix * es).sum(-1), (sp * sp * ep - ix * ss * es).sum(-1)]]
+    return u1, u2, g
+
+
+# ----------------------------------------------------------------------------- incidence
+
+def plane_wave_incidence(kind: int, angle: float, L: Layered):
+    """Incident plane wave from the upper layer travelling along d = (cos t, -sin t) (reading A7).
+
+    P-wave u = d e^{i kp d.x} = (1/(i kp)) grad(e^{i kp d.x}); S-wave u = d_perp e^{i ks d.x}
+    = (1/(i ks)) grad_perp(e^{i ks d.x}).  Returns (xi, (D_P, D_S), (E_P, E_S), (I_P, I_S)):
+    the transmitted (lower, downgoing) and reflected (upper, upgoing) amplitudes of the
+    background field of Sec. 7.3 (bplan)."""
+    k = L.kp_u if kind == 0 else L.ks_u
+    xi = complex(k * np.cos(angle), 0.0)
+    I = (1.0 / (1j * k), 0.0) if kind == 0 else (0.0, 1.0 / (1j * k))
+    D, E = interface_solve(xi, L, U=(0.0, 0.0), I=I)
+    return xi, D, E, I
+
+
+def local_expansion_of_plane(xi: complex, D, L: Layered, centres, p: int):
+    """Incoming coefficients (M, 2, 2p+1) of D_P grad(e^{i xi x + s'_p y}) + D_S grad_perp(e^{i xi x + s'_s y})
+    about every centre, by Jacobi-Anger (Sec. 5.3 ja/stm)."""
+    n = np.arange(-p, p + 1)
+    out = np.empty((centres.shape[0], 2, 2 * p + 1), dtype=complex)
+    for b, k in ((0, L.kp_l), (1, L.ks_l)):
+        s = branch_s(xi, k)
+        eiphi = (xi - s) / k
+        e = np.exp(1j * xi * centres[:, 0] + s * centres[:, 1])
+        out[:, b] = D[b] * e[:, None] * ((1j ** n) * eiphi ** n)[None, :]
+    return out

@@ -1,0 +1,207 @@
+"""Seeded synthetic workloads shared by the oracle tests, the GPU tests and the bench.
+
+This module holds only input generation: particle placement, media constants,
+incidence angles, receiver lines and random coefficient blocks.  It contains none
+of the method's arithmetic (no wavenumbers, special functions, translations or
+Sommerfeld quadrature), so both the CPU oracle and the CUDA path may consume its
+outputs without sharing method code.
+
+Workloads follow the paper's setting (Sec. 2: particles buried in the lower
+half-space of a welded two-layer elastic medium, well separated, Sec. 7: the
+star/pear family r(t) = a1 + a2 cos(a3 t)).  Placement is random sequential
+addition with rejection: enclosing discs keep |x_l - x_m| >= 1.1 (R_l + R_m)
+(the "10 % of particle size" separation of Sec. 2) and y_m + 1.1 R_m <= 0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEP = 1.1  # separation factor between enclosing discs (Sec. 2 well-separatedness)
+
+
+@dataclasses.dataclass
+class Media:
+    """Lame constants of the upper (x2 > 0) and lower (x2 < 0) layers; rho = 1 (Sec. 2)."""
+    lam_u: float
+    mu_u: float
+    lam_l: float
+    mu_l: float
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    media: Media
+    omega: float
+    p: int
+    centres: np.ndarray      # (M, 2) float64
+    radius: np.ndarray       # (M,) enclosing radius
+    bc: np.ndarray           # (M,) int32: 0 rigid, 1 traction-free
+    shape: np.ndarray        # (M,) int32: 0 disc, 1 star
+    rotation: np.ndarray     # (M,) float64 radians
+    inc_kind: np.ndarray     # (nrhs,) int32: 0 P-wave, 1 S-wave
+    inc_angle: np.ndarray    # (nrhs,) float64 radians, direction (cos t, -sin t)
+    receivers: np.ndarray    # (R, 2) float64
+    n_panels: int = 32
+    nodes_per_panel: int = 16
+    t_max: float = 20.0
+    gmres_tol: float = 1e-12
+
+    @property
+    def M(self) -> int:
+        return int(self.centres.shape[0])
+
+    @property
+    def nrhs(self) -> int:
+        return int(self.inc_angle.shape[0])
+
+    @property
+    def nc(self) -> int:
+        return 2 * self.p + 1
+
+
+MEDIA_STD = Media(lam_u=1.0, mu_u=0.5, lam_l=2.0, mu_l=1.0)
+
+
+def place_particles(rng: np.random.Generator, M: int, box, rmin: float, rmax: float,
+                    max_tries: int = 200000):
+    """Random sequential addition of M enclosing discs inside box=(x0,x1,y0,y1).
+
+    Radii are drawn U[rmin, rmax] (a constant when rmin == rmax).  A candidate is
+    rejected if it violates the separation rule against any accepted disc or if
+    y + SEP*R > 0.  A uniform cell grid keeps the neighbour check O(1).
+    """
+    x0, x1, y0, y1 = box
+    cell = 2.0 * SEP * rmax
+    nx = max(1, int(math.ceil((x1 - x0) / cell)))
+    ny = max(1, int(math.ceil((y1 - y0) / cell)))
+    grid: dict[tuple[int, int], list[int]] = {}
+    cx = np.empty(M)
+    cy = np.empty(M)
+    rr = np.empty(M)
+    n = 0
+    tries = 0
+    while n < M:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError(f"placement failed after {max_tries} tries ({n}/{M} placed)")
+        r = rng.uniform(rmin, rmax) if rmax > rmin else rmin
+        x = rng.uniform(x0, x1)
+        y = rng.uniform(y0, y1)
+        if y + SEP * r > 0.0:
+            continue
+        gx = min(nx - 1, int((x - x0) / cell))
+        gy = min(ny - 1, int((y - y0) / cell))
+        ok = True
+        for ix in range(gx - 1, gx + 2):
+            for iy in range(gy - 1, gy + 2):
+                for j in grid.get((ix, iy), ()):
+                    if (x - cx[j]) ** 2 + (y - cy[j]) ** 2 < (SEP * (r + rr[j])) ** 2:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        cx[n], cy[n], rr[n] = x, y, r
+        grid.setdefault((gx, gy), []).append(n)
+        n += 1
+    return np.stack([cx, cy], axis=1), rr
+
+
+def receiver_line(R: int, x0: float, x1: float, y: float) -> np.ndarray:
+    xs = np.linspace(x0, x1, R)
+    return np.stack([xs, np.full(R, y)], axis=1)
+
+
+def config1(seed: int = 1002) -> Workload:
+    """16 rigid discs R=0.5 in [-10,10]x[-8,-1], omega=2, p=10, one P-wave at 30 degrees."""
+    rng = np.random.default_rng(seed)
+    c, r = place_particles(rng, 16, (-10, 10, -8, -1), 0.5, 0.5)
+    M = 16
+    return Workload("discs16_p10", MEDIA_STD, 2.0, 10, c, r,
+                    np.zeros(M, np.int32), np.zeros(M, np.int32), np.zeros(M),
+                    np.zeros(1, np.int32), np.array([math.radians(30.0)]),
+                    receiver_line(256, -12, 12, -0.5))
+
+
+def config2(seed: int = 1003, nrhs: int = 1) -> Workload:
+    """1000 particles, radius 1.2 a with a ~ U[0.3,0.6], alternating rigid / traction-free,
+    omega=4, p=16, in [-40,40]x[-30,-1].  Particles are discs until star scattering
+    matrices are supplied (shape flag records the intended star)."""
+    rng = np.random.default_rng(seed)
+    M = 1000
+    c, r = place_particles(rng, M, (-40, 40, -30, -1), 1.2 * 0.3, 1.2 * 0.6)
+    bc = (np.arange(M) % 2).astype(np.int32)
+    rot = rng.uniform(0, 2 * math.pi, M)
+    irng = np.random.default_rng(2003)
+    ang = np.full(nrhs, math.radians(30.0)) if nrhs == 1 else np.radians(irng.uniform(10, 170, nrhs))
+    return Workload("particles1000_p16", MEDIA_STD, 4.0, 16, c, r, bc,
+                    np.zeros(M, np.int32), rot, np.zeros(nrhs, np.int32), ang,
+                    receiver_line(256, -40, 40, -0.5))
+
+
+def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
+    """10^4 particles, enclosing radius U[0.2,0.5], packing fraction 0.2 by enclosing
+    area, omega=6, p=20, 64 plane waves (half P, half S) at angles U[10,170] degrees.
+    BC alternates rigid / traction-free.  `M` may be lowered for parity sub-cases; the
+    box then shrinks to keep the packing fraction."""
+    rng = np.random.default_rng(seed)
+    er2 = (0.5 ** 3 - 0.2 ** 3) / (3 * 0.3)       # E[R^2] for R ~ U[0.2,0.5]
+    area = M * math.pi * er2 / 0.2
+    side = math.sqrt(area)
+    c, r = place_particles(rng, M, (-side / 2, side / 2, -side - 1.0, -1.0), 0.2, 0.5)
+    bc = (np.arange(M) % 2).astype(np.int32)
+    rot = rng.uniform(0, 2 * math.pi, M)
+    irng = np.random.default_rng(2004)
+    ang = np.radians(irng.uniform(10, 170, nrhs))
+    kind = (np.arange(nrhs) >= nrhs // 2).astype(np.int32)
+    return Workload(f"particles{M}_p20_rhs{nrhs}", MEDIA_STD, 6.0, 20, c, r, bc,
+                    np.zeros(M, np.int32), rot, kind, ang,
+                    receiver_line(256, -side / 2, side / 2, -0.5))
+
+
+def config4(seed: int = 1005, M: int = 2000, nrhs: int = 32) -> Workload:
+    """2000 rigid discs R ~ U[0.2,0.5], packing 0.2, omega=4, p=16, 32 P-waves, 128 receivers."""
+    rng = np.random.default_rng(seed)
+    er2 = (0.5 ** 3 - 0.2 ** 3) / (3 * 0.3)
+    side = math.sqrt(M * math.pi * er2 / 0.2)
+    c, r = place_particles(rng, M, (-side / 2, side / 2, -side - 1.0, -1.0), 0.2, 0.5)
+    irng = np.random.default_rng(2005)
+    ang = np.radians(irng.uniform(10, 170, nrhs))
+    return Workload(f"discs{M}_p16_rhs{nrhs}", MEDIA_STD, 4.0, 16, c, r,
+                    np.zeros(M, np.int32), np.zeros(M, np.int32), np.zeros(M),
+                    np.zeros(nrhs, np.int32), ang, receiver_line(128, -side / 2, side / 2, -0.5))
+
+
+def small_case(seed: int, M: int, p: int, omega: float = 2.0, nrhs: int = 1,
+               media: Media = MEDIA_STD, box=(-6.0, 6.0, -5.0, -1.0), rmin=0.3, rmax=0.6,
+               mixed_bc: bool = True, n_panels: int = 32, nodes_per_panel: int = 16,
+               t_max: float = 20.0) -> Workload:
+    """A few particles for parity tests that the oracle finishes in seconds."""
+    rng = np.random.default_rng(seed)
+    c, r = place_particles(rng, M, box, rmin, rmax)
+    bc = (np.arange(M) % 2).astype(np.int32) if mixed_bc else np.zeros(M, np.int32)
+    irng = np.random.default_rng(seed + 1000)
+    ang = np.radians(irng.uniform(10, 170, nrhs))
+    kind = (np.arange(nrhs) % 2).astype(np.int32)
+    return Workload(f"small{M}_p{p}", media, omega, p, c, r, bc, np.zeros(M, np.int32),
+                    rng.uniform(0, 2 * math.pi, M), kind, ang,
+                    receiver_line(32, box[0], box[1], -0.5), n_panels, nodes_per_panel, t_max)
+
+
+def random_coeffs(seed: int, M: int, p: int, nrhs: int) -> np.ndarray:
+    """Random complex coefficient block in the library layout (M, 2, 2p+1, nrhs).
+
+    Entries are N(0,1)+iN(0,1) scaled by 2^-|n| so high orders carry the small
+    magnitudes that outgoing coefficients of well-resolved particles have."""
+    rng = np.random.default_rng(seed)
+    nc = 2 * p + 1
+    z = rng.standard_normal((M, 2, nc, nrhs)) + 1j * rng.standard_normal((M, 2, nc, nrhs))
+    n = np.abs(np.arange(-p, p + 1))
+    return z * (0.5 ** n)[None, None, :, None]

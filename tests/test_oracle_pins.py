@@ -1,0 +1,300 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks one oracle function against the paper's printed values, a closed-form
+identity evaluated independently (scipy Bessel routines, direct field sums), a physical
+conservation law or a second derivation, chosen so that a dropped term, a sign or index
+error or a transposed operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+import synthetic as syn
+from oracle import disc, graf, sommerfeld, system, waves
+from oracle.media import Layered, wavenumbers
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+L_STD = Layered(syn.MEDIA_STD, 2.0)
+
+
+def test_wavenumbers_match_paper_printed_values():
+    """Sec. 7 preamble prints kp, ks, kp', ks' for omega = 2 pi and the default Lame constants."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "paper_wavenumbers.txt"))
+    for lam, mu, om, kp, ks in rows:
+        got = wavenumbers(lam, mu, om)
+        assert got[0] == pytest.approx(kp, rel=1e-14)
+        assert got[1] == pytest.approx(ks, rel=1e-14)
+
+
+@pytest.mark.parametrize("k", [0.7, 2.0, 6.0])
+def test_graf_translation_pointwise(k):
+    """Sec. 4.2: the local expansion T gamma about x_m reproduces the outgoing potential of
+    particle l evaluated directly with Hankel functions."""
+    p, P = 8, 50
+    xl = np.array([0.3, -2.0])
+    xm = np.array([2.1, -4.5])
+    rng = np.random.default_rng(0)
+    g = rng.standard_normal(2 * p + 1) + 1j * rng.standard_normal(2 * p + 1)
+    a = graf.translation_matrix(p, k, xm, xl, p_out=P) @ g
+    for t in np.linspace(0, 2 * np.pi, 9)[:-1]:
+        x = xm + 0.5 * np.array([math.cos(t), math.sin(t)])
+        dl = x - xl
+        direct = sum(g[j + p] * special.hankel1(j, k * np.hypot(*dl)) * np.exp(1j * j * math.atan2(dl[1], dl[0]))
+                     for j in range(-p, p + 1))
+        dm = x - xm
+        loc = sum(a[i + P] * special.jv(i, k * np.hypot(*dm)) * np.exp(1j * i * math.atan2(dm[1], dm[0]))
+                  for i in range(-P, P + 1))
+        assert abs(direct - loc) <= 1e-12 * abs(direct)
+
+
+def test_graf_all_sources_matches_pairwise():
+    p = 5
+    rng = np.random.default_rng(3)
+    centres = rng.uniform(-5, 5, (6, 2))
+    T = graf.translation_all_sources(p, 1.3, centres[0], centres)
+    assert np.all(T[0] == 0)
+    for l in range(1, 6):
+        np.testing.assert_allclose(T[l], graf.translation_matrix(p, 1.3, centres[0], centres[l]), rtol=1e-14)
+
+
+def test_sommerfeld_identity_som1():
+    """Sec. 3 som1: (i/4) H_0(k|x-x0|) = (1/4pi) int e^{-s|y-y0|}/s e^{i xi (x-x0)} dxi on the contour."""
+    xi, W = sommerfeld.contour(64, 16, 40.0)
+    for k, dx, dy in ((1.0, 0.7, 1.2), (2.0, -1.5, -0.9), (3.0, 2.0, 2.5)):
+        s = sommerfeld.branch_s(xi, k)
+        quad = (W * np.exp(-s * abs(dy)) / s * np.exp(1j * xi * dx)).sum() / (4 * np.pi)
+        assert abs(quad - 0.25j * special.hankel1(0, k * math.hypot(dx, dy))) < 1e-9
+
+
+@pytest.mark.parametrize("n", [0, 1, -1, 3, -5, 10])
+def test_multipole_to_sommerfeld_pts1(n):
+    """Sec. 5.4 pts1 as quadrature on the contour equals H_n(k r) e^{i n theta} evaluated by scipy."""
+    xi, W = sommerfeld.contour(64, 16, 40.0)
+    k, xm, ym, x, y = 1.0, 0.4, -1.3, 1.1, -0.2
+    s = sommerfeld.branch_s(xi, k)
+    integ = ((-1.0) ** n / (1j * np.pi)) * np.exp(s * (ym - y)) / s * np.exp(1j * xi * (x - xm)) \
+        * ((s - xi) / (1j * k)) ** n
+    quad = (W * integ).sum()
+    ex = special.hankel1(n, k * math.hypot(x - xm, y - ym)) * np.exp(1j * n * math.atan2(y - ym, x - xm))
+    assert abs(quad - ex) <= 1e-8 * abs(ex)
+
+
+def test_m2s_reproduces_particle_field_above_centre():
+    """m2s amplitudes: the upgoing plane-wave sum equals the direct outgoing field (sed1/sed2)."""
+    xi, W = sommerfeld.contour(64, 16, 40.0)
+    p = 4
+    rng = np.random.default_rng(5)
+    centres = np.array([[0.2, -1.5]])
+    gam = (rng.standard_normal((1, 2, 2 * p + 1, 1)) + 1j * rng.standard_normal((1, 2, 2 * p + 1, 1)))
+    U_P, U_S = sommerfeld.m2s(xi, L_STD, centres, gam)
+    X = np.array([-0.5, 0.4, 1.0])
+    Y = np.array([-0.3, -0.1, 0.0])
+    sp, ss = sommerfeld.branch_s(xi, L_STD.kp_l), sommerfeld.branch_s(xi, L_STD.ks_l)
+    e_p = W * U_P[:, 0] * np.exp(1j * xi * X[:, None] - sp * Y[:, None])
+    e_s = W * U_S[:, 0] * np.exp(1j * xi * X[:, None] - ss * Y[:, None])
+    u1 = (1j * xi * e_p + ss * e_s).sum(-1)
+    u2 = (-sp * e_p + 1j * xi * e_s).sum(-1)
+    d1, d2, _ = waves.field_of_coeffs("H", gam[0, 0, :, 0], gam[0, 1, :, 0], p, L_STD.kp_l, L_STD.ks_l,
+                                      X - centres[0, 0], Y - centres[0, 1])
+    np.testing.assert_allclose(u1, d1, rtol=1e-8, atol=1e-8 * np.abs(d1).max())
+    np.testing.assert_allclose(u2, d2, rtol=1e-8, atol=1e-8 * np.abs(d2).max())
+
+
+def test_jacobi_anger_on_contour_nodes():
+    """Sec. 5.3 ja/stm: e^{i xi X + s Y} = sum_n i^n q^n J_n(k r) e^{i n theta}, q = (xi - s)/k, at contour nodes."""
+    xi, _ = sommerfeld.contour(32, 16, 20.0)
+    k, X, Y = 1.0, 0.08, -0.05
+    r, th = math.hypot(X, Y), math.atan2(Y, X)
+    n = np.arange(-80, 81)
+    for q_i in (3, 100, 255, 256, 400, 508):
+        x0 = xi[q_i]
+        s = sommerfeld.branch_s(x0, k)
+        q = (x0 - s) / k
+        rhs = np.sum((1j ** n) * q ** n * special.jv(n, k * r) * np.exp(1j * n * th))
+        lhs = np.exp(1j * x0 * X + s * Y)
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_branch_has_nonnegative_real_part_and_limiting_absorption():
+    xi, _ = sommerfeld.contour(32, 16, 20.0)
+    for k in (1.0, 2.0, 6.0):
+        s = sommerfeld.branch_s(xi, k)
+        assert np.all(s.real >= 0)
+        np.testing.assert_allclose(s * s, xi * xi - k * k, rtol=1e-12, atol=1e-12)
+        # real propagating xi: s = -i sqrt(k^2 - xi^2)
+        assert sommerfeld.branch_s(0.5 * k, k) == pytest.approx(-1j * math.sqrt(0.75) * k)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("R", [0.2, 0.5, 1.3])
+def test_disc_scattering_matrix_boundary_condition(bc, R):
+    """Sec. 4.1: incoming + S(incoming) satisfies the rigid (u = 0) or traction-free (sigma r-hat = 0)
+    condition on r = R; the field is evaluated with Cartesian derivative recurrences (DLMF 10.6)
+    and the traction of Sec. 2, independently of the polar formulas used to build S."""
+    p = 12
+    L = L_STD
+    S = disc.disc_smatrix(p, L.kp_l, L.ks_l, R, bc, L.lam_l, L.mu_l)
+    rng = np.random.default_rng(int(R * 10) + bc)
+    a = (rng.standard_normal((2, 2 * p + 1)) + 1j * rng.standard_normal((2, 2 * p + 1)))
+    out = np.einsum("nij,jn->in", S, a)
+    th = np.linspace(0, 2 * np.pi, 50, endpoint=False)
+    X, Y = R * np.cos(th), R * np.sin(th)
+    ui1, ui2, gi = waves.field_of_coeffs("J", a[0], a[1], p, L.kp_l, L.ks_l, X, Y)
+    uo1, uo2, go = waves.field_of_coeffs("H", out[0], out[1], p, L.kp_l, L.ks_l, X, Y)
+    if bc == 0:
+        scale = max(np.abs(ui1).max(), np.abs(ui2).max())
+        assert np.abs(ui1 + uo1).max() < 1e-12 * scale
+        assert np.abs(ui2 + uo2).max() < 1e-12 * scale
+    else:
+        g = [[gi[i][j] + go[i][j] for j in range(2)] for i in range(2)]
+        t1, t2 = waves.traction(g, np.cos(th), np.sin(th), L.lam_l, L.mu_l)
+        s1, s2 = waves.traction(gi, np.cos(th), np.sin(th), L.lam_l, L.mu_l)
+        scale = max(np.abs(s1).max(), np.abs(s2).max())
+        assert np.abs(t1).max() < 1e-11 * scale
+        assert np.abs(t2).max() < 1e-11 * scale
+
+
+def test_reflection_two_routes_agree():
+    """The paper's A_xi / b1 / b2 / eee1 route (Sec. 3, 5.3, 5.4) and the plane-wave continuity
+    route give the same interface-reflected local expansions."""
+    wl = syn.small_case(7, 3, 6, omega=2.0)
+    P = system.Problem(wl)
+    gam = syn.random_coeffs(3, P.M, P.p, 2)
+    a1 = sommerfeld.layered_apply(P.xi, P.W, P.L, P.centres, gam)
+    a2 = sommerfeld.layered_apply_paper(P.xi, P.W, P.L, P.centres, gam)
+    assert np.linalg.norm(a1 - a2) <= 1e-12 * np.linalg.norm(a1)
+
+
+def test_reflection_vanishes_for_identical_media():
+    L = Layered(syn.Media(2.0, 1.0, 2.0, 1.0), 2.0)
+    xi, _ = sommerfeld.contour(8, 8, 20.0)
+    for x in list(xi[::5]) + [0.3 + 0j, 1.7 + 0j]:
+        assert np.abs(sommerfeld.reflection_plane_wave(x, L)).max() < 1e-13
+
+
+@pytest.mark.parametrize("xi0", [0.05, 0.5, 0.95])
+@pytest.mark.parametrize("U", [(1.0, 0.0), (0.0, 1.0), (0.3, -0.7j)])
+def test_interface_energy_balance(xi0, U):
+    """Time-averaged vertical energy flux Im(conj(u).T_y u) of the incident wave equals the sum
+    over reflected and transmitted waves when all four waves propagate (|xi| < min k)."""
+    L = L_STD
+    x = complex(xi0, 0)
+
+    def flux(kind, d, lam, mu, amp):
+        u = amp * sommerfeld._pw(kind, x, d)
+        return np.imag(np.vdot(u, sommerfeld._traction_y(u, x, d, lam, mu)))
+
+    D, E = sommerfeld.interface_solve(x, L, U=U)
+    sp, ss = sommerfeld.branch_s(x, L.kp_l), sommerfeld.branch_s(x, L.ks_l)
+    spu, ssu = sommerfeld.branch_s(x, L.kp_u), sommerfeld.branch_s(x, L.ks_u)
+    fin = flux("P", -sp, L.lam_l, L.mu_l, U[0]) + flux("S", -ss, L.lam_l, L.mu_l, U[1])
+    fr = flux("P", sp, L.lam_l, L.mu_l, D[0]) + flux("S", ss, L.lam_l, L.mu_l, D[1])
+    ft = flux("P", -spu, L.lam_u, L.mu_u, E[0]) + flux("S", -ssu, L.lam_u, L.mu_u, E[1])
+    assert fin > 0 and fr <= 0 and ft > 0
+    assert abs(fin + fr - ft) < 1e-13 * fin
+
+
+@pytest.fixture(scope="module")
+def solved_small():
+    wl = syn.small_case(11, 3, 14, omega=2.0, nrhs=2)
+    P = system.Problem(wl)
+    b = P.rhs(wl.inc_kind, wl.inc_angle)
+    x, it = P.solve_gmres(b, tol=1e-13)
+    return wl, P, b, x
+
+
+def test_solved_system_satisfies_particle_boundary_conditions(solved_small):
+    """Total field (background + every particle's outgoing field + interface reflection), summed
+    directly on each particle's boundary, meets its boundary condition to truncation error."""
+    wl, P, b, x = solved_small
+    worst = 0.0
+    for m in range(P.M):
+        res, sc = P.boundary_residual(x, wl.inc_kind, wl.inc_angle, m, 32)
+        worst = max(worst, np.abs(res).max() / np.abs(sc).max())
+    assert worst < 1e-6
+
+
+def test_boundary_residual_decays_with_order():
+    res = []
+    for p in (6, 10):
+        wl = syn.small_case(11, 3, p, omega=2.0, nrhs=1)
+        P = system.Problem(wl)
+        x, _ = P.solve_gmres(P.rhs(wl.inc_kind, wl.inc_angle), tol=1e-13)
+        r, s = P.boundary_residual(x, wl.inc_kind, wl.inc_angle, 0, 32)
+        res.append(np.abs(r).max() / np.abs(s).max())
+    assert res[1] < 1e-2 * res[0]
+
+
+def test_interface_continuity_of_assembled_field(solved_small):
+    """Particle-induced field: lower side (direct multipole sums + downgoing Sommerfeld field) and
+    upper side (upgoing Sommerfeld field) agree in displacement and traction on y = 0 (Sec. 3)."""
+    wl, P, b, x = solved_small
+    X = np.linspace(-3, 3, 7)
+    Y = np.zeros_like(X)
+    _, (E_P, E_S) = P.interface_amplitudes(x[..., :1])
+    us, gs = P.scattered_field(x[..., :1], X, Y, with_gradient=True)
+    u1, u2, gu = sommerfeld.upgoing_upper_field(P.xi, P.W, P.L, E_P[:, 0], E_S[:, 0], X, Y)
+    lo = np.stack([us[0][0], us[0][1]])
+    assert np.abs(lo - np.stack([u1, u2])).max() < 1e-8 * np.abs(lo).max()
+    tl = np.stack(waves.traction(gs[0], 0.0, 1.0, P.L.lam_l, P.L.mu_l))
+    tu = np.stack(waves.traction(gu, 0.0, 1.0, P.L.lam_u, P.L.mu_u))
+    assert np.abs(tl - tu).max() < 1e-8 * np.abs(tl).max()
+
+
+def test_gmres_matches_dense_lu():
+    wl = syn.small_case(12, 3, 6, omega=2.0, nrhs=2)
+    P = system.Problem(wl)
+    b = P.rhs(wl.inc_kind, wl.inc_angle)
+    x, _ = P.solve_gmres(b, tol=1e-13)
+    xl = P.solve_lu(b)
+    assert np.linalg.norm(x - xl) <= 1e-11 * np.linalg.norm(xl)
+    assert np.linalg.norm(P.matvec(x) - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_rotated_prototype_matrix_of_a_disc_is_invariant():
+    """Rotating a disc prototype (Sec. 4.3 basis rotation) leaves its scattering matrix unchanged,
+    and rotating a dense prototype by 2 pi is the identity map."""
+    wl = syn.small_case(13, 2, 5)
+    P = system.Problem(wl)
+    S0 = P.dense_S(0)
+    P2 = system.Problem(wl, proto_S=S0[None], proto_index=np.array([0, 0]))
+    np.testing.assert_allclose(P2.dense_S(0), S0, atol=1e-15)
+    P2.rotation = np.array([2 * np.pi, 1.0])
+    rng = np.random.default_rng(1)
+    Sr = rng.standard_normal(S0.shape) + 1j * rng.standard_normal(S0.shape)
+    P3 = system.Problem(wl, proto_S=Sr[None], proto_index=np.array([0, 0]))
+    P3.rotation = np.array([2 * np.pi, 0.0])
+    np.testing.assert_allclose(P3.dense_S(0), Sr, atol=1e-12)
+
+
+# --------------------------------------------------------------------- planted mistakes
+# A plausible slip in the oracle must fail one of the pins above; these plant one at a time.
+
+def test_planted_graf_index_flip_is_caught(monkeypatch):
+    orig = graf.translation_matrix
+
+    def flipped(p, k, xm, xl, p_out=None):
+        return orig(p, k, xl, xm, p_out)          # x_l - x_m instead of x_m - x_l
+    monkeypatch.setattr(graf, "translation_matrix", flipped)
+    with pytest.raises(AssertionError):
+        test_graf_translation_pointwise(2.0)
+
+
+def test_planted_branch_sign_is_caught(monkeypatch):
+    orig = sommerfeld.branch_s
+    monkeypatch.setattr(sommerfeld, "branch_s", lambda xi, k: np.conj(orig(xi, k)))
+    with pytest.raises(AssertionError):
+        test_multipole_to_sommerfeld_pts1(3)
+
+
+def test_planted_traction_term_drop_is_caught(monkeypatch):
+    orig = disc.mode_matrix
+
+    def dropped(kind, n, kp, ks, R, bc, lam, mu):
+        return orig(kind, n, kp, ks, R, bc, 0.0, mu)     # lambda term dropped
+    monkeypatch.setattr(disc, "mode_matrix", dropped)
+    with pytest.raises(AssertionError):
+        test_disc_scattering_matrix_boundary_condition(1, 0.5)
