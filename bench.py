@@ -1,0 +1,301 @@
+#!/usr/bin/env python3
+"""Benchmark: 64-right-hand-side mat-vecs of the layered multiple-scattering operator.
+
+Workload: 10^4 particles (enclosing radius U[0.2, 0.5], packing fraction 0.2), omega = 6,
+expansion order p = 20, 512 Sommerfeld nodes, 64 right-hand sides (synthetic, seeded).  A step
+is one application y = x - S (T + R) x of the whole hot path (precision staging, free-space
+translation, multipole-to-Sommerfeld, reflection, Sommerfeld-to-local, scattering-matrix apply)
+to the 64-column block.  `value` is mat-vecs per second over all ranks with inputs resident in
+HBM; `e2e` repeats the step through the same C-ABI call with the block copied host->device and
+the result device->host inside the timed region.  Inputs (0.84 GB) exceed the 126 MB L2.
+
+Multi-GPU: right-hand-side blocks are independent, so each rank applies the operator to its own
+64-column block with no collective (weak scaling, replicas of the geometry).
+
+--impl reference times the FP64 CPU oracle on this host on a bounded sample of the same
+mat-vec (a few target particles of the direct sum plus the full spectral part) and extrapolates
+to one full mat-vec.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "matvecs/s (2D N=1e4, 64 RHS, mixed FP32 operator)"
+UNIT = "matvec/s"
+
+
+def workload():
+    import synthetic as syn
+    return syn.config3()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(wl, targets: int, nrhs: int):
+    """Time the FP64 oracle on `targets` target particles of the direct translation sum and the
+    full spectral (multipole-to-Sommerfeld, reflection, Sommerfeld-to-local) part for `nrhs`
+    columns; extrapolate to one full 64-column mat-vec.  Returns (matvecs/s, cores, sample text)."""
+    import synthetic as syn
+    from oracle import system
+    ref = system.Problem(wl)
+    x = syn.random_coeffs(99, wl.M, wl.p, nrhs)
+    idx = list(range(targets))
+    t0 = time.perf_counter()
+    ref.translate(x, targets=idx)
+    t1 = time.perf_counter()
+    ref.reflect(x, targets=idx)
+    t2 = time.perf_counter()
+    per_target = (t1 - t0) / targets
+    # the direct sum scales with targets and with columns; the spectral part with columns
+    t_full = (per_target * wl.M + (t2 - t1)) * (64 / nrhs)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"oracle FP64 numpy/scipy: direct Graf sum for {targets} of {wl.M} targets and the full "
+              f"spectral part, {nrhs} of 64 columns, extrapolated linearly to one 64-column mat-vec "
+              f"({t1 - t0:.1f} s + {t2 - t1:.1f} s measured)")
+    return 1.0 / t_full, cores, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload()
+    vals = []
+    cores = 0
+    sample = ""
+    for _ in range(args.warmup + args.steps):
+        v, cores, sample = oracle_sample(wl, targets=2, nrhs=64)
+        vals.append(v)
+    v = statistics.mean(vals[args.warmup:]) if args.steps else vals[-1]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "M": wl.M, "p": wl.p, "nrhs": 64,
+                                            "n_nodes": wl.n_panels * wl.nodes_per_panel},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2608_26875_b300 as P
+    import synthetic as syn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    wl = workload()
+    prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
+    solver = P.Solver.from_workload(wl)
+    nrhs = 64
+    x = torch.as_tensor(syn.random_coeffs(1000 + rank, wl.M, wl.p, nrhs), device="cuda")
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.apply(x, prec=prec, out=y)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(st)
+        for _ in range(args.steps):
+            solver.apply(x, prec=prec, out=y)
+        ev1.record(st)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world / (ms / 1000.0)
+
+    # dominant kernel: the direct near-pair Graf sum (k_translate on the near lists) timed alone
+    # through the operator-parts view; that call also runs the two precision-staging passes
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    solver.operator(x, P.MS_PART_T_NEAR, prec=prec)
+    torch.cuda.synchronize()
+    nT = max(1, min(args.steps, 3))
+    ev2.record(st)
+    for _ in range(nT):
+        solver.operator(x, P.MS_PART_T_NEAR, prec=prec)
+    ev3.record(st)
+    torch.cuda.synchronize()
+    t_near = ev2.elapsed_time(ev3) / nT / 1000.0
+    nc = 2 * wl.p + 1
+    pairs = solver.near_pairs
+    flops = pairs * 2 * nc * nc * nrhs * 8.0          # complex MAC = 8 real flops
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s of the FP32 CUDA-core pipes
+    achieved = flops / t_near / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "near_traffic.json")
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get("bytes_per_launch")
+
+    # end to end: host block in, host block out, through the same call
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    ev4 = torch.cuda.Event(enable_timing=True)
+    ev5 = torch.cuda.Event(enable_timing=True)
+    ne = max(1, min(args.steps, 3))
+    barrier()
+    ev4.record(st)
+    for _ in range(ne):
+        xd.copy_(xh, non_blocking=True)
+        solver.apply(xd, prec=prec, out=y)
+        yh.copy_(y, non_blocking=True)
+    ev5.record(st)
+    barrier()
+    e2e_ms = ev4.elapsed_time(ev5) / ne
+    te = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = world / (float(te.item()) / 1000.0)
+    nbytes = x.numel() * 16
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_sample(wl, targets=2, nrhs=64)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if prec == P.MS_PREC_FP32 else "f64", "data": "synthetic",
+                "config": {"workload": wl.name, "M": wl.M, "p": wl.p, "nrhs": nrhs,
+                           "n_nodes": wl.n_panels * wl.nodes_per_panel, "omega": wl.omega,
+                           "near_pairs": pairs, "fmm_levels": solver.fmm_levels,
+                           "l2": "inputs 0.84 GB > 126 MB L2, no flush",
+                           "parallelism": f"rhs-replicas x{world}"},
+                "roofline": {"bound": "alu", "kernel": "k_translate<float> near pairs (timed via ms_operator(T_NEAR))",
+                             "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": achieved / fp32_peak, "traffic": traffic,
+                             "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} clock)"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "gpu_launches": launches_per_step(solver) * args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def launches_per_step(solver):
+    """Kernels of one ms_apply: staging in/out, near sum (2 waves), FMM (per wave: P2M, M2M per
+    level, M2L per level, L2L per level, L2P), M2S, reflect, S2L, S-apply."""
+    L = solver.fmm_levels
+    fmm = 0 if L == 0 else 2 * (1 + (L - 2) + (L - 1) + (L - 2) + 1)
+    return 2 + 2 + fmm + 3 + 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * ms_b300.h - C ABI of the B300 layered-medium elastic multiple-scattering library.
+ *
+ * The library applies and solves the coupled multiple-scattering system of
+ * arxiv 2608.26875 for M rigid or traction-free particles buried in the lower
+ * half-space of a welded two-layer elastic medium (Sec. 2), with the layered
+ * response written as Sommerfeld integrals (Sec. 3, 5):
+ *
+ *     gamma^m = S_m ( a0^m + sum_{l != m} T^{ml} gamma^l + (R gamma)^m )      (mul2, Sec. 4.2;
+ *                                                                             Schur complement, Sec. 5.2)
+ *
+ *   S_m     single-particle scattering matrix (Sec. 4.1, 4.3)
+ *   T^{ml}  Graf multipole-to-local translation (Sec. 4.2)
+ *   R       interface-reflected operator: multipole-to-Sommerfeld (Sec. 5.4, pts1/sed1/sed2),
+ *           2x2 P/S reflection per quadrature node (Sec. 3, aa), Sommerfeld-to-local
+ *           (Sec. 5.3, ja/stm/eee1); it includes the self term l = m
+ *   a0      local expansion of the transmitted plane wave (Sec. 7.3, bplan)
+ *
+ * Conventions
+ *   - Every call returns an int status: MS_OK (0), a positive warning or a negative error.
+ *     No C++ exception crosses the ABI.
+ *   - Coefficient blocks are complex, interleaved (re, im) double, in the layout
+ *         x[((m * 2 + b) * nc + (n + p)) * nrhs + r]
+ *     m particle, b = 0 compressional (alpha / a) or 1 shear (beta / b), n in [-p, p],
+ *     r right-hand side; nc = 2p + 1.  The basis is the paper's unscaled one (scatspan, Sec. 4.1).
+ *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers are
+ *     ordinary host memory owned by the caller.  The handle owns its own tables and workspace.
+ *   - Work is ordered on the CUDA stream passed in (cudaStream_t as void*, NULL = default stream).
+ *     Calls that need host decisions (ms_solve) synchronise that stream.  A handle must not be
+ *     used from two threads at once.
+ */
+#ifndef MS_B300_H
+#define MS_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define MS_OK                    0
+#define MS_NOT_CONVERGED         1    /* warning: a column did not reach tol; info holds residuals */
+#define MS_ERR_ARG              -1    /* NULL pointer, non-positive size, unknown enum */
+#define MS_ERR_CUDA             -2    /* a CUDA runtime call failed; see ms_last_cuda_error */
+#define MS_ERR_OVERLAP          -3    /* two enclosing discs closer than 1.1 (R_l + R_m) (Sec. 2) */
+#define MS_ERR_NOT_BURIED       -4    /* a particle with y_m + 1.1 R_m > 0 (must lie in x2 < 0, Sec. 2) */
+#define MS_ERR_UNSUPPORTED      -5    /* request outside what this build implements */
+#define MS_ERR_RECEIVER_INSIDE  -6    /* a receiver inside some particle's enclosing disc, or above y = 0 */
+#define MS_ERR_ALLOC            -7    /* device allocation failed */
+#define MS_ERR_NONFINITE        -9    /* NaN or Inf met in a right-hand side or residual */
+#define MS_ERR_BREAKDOWN       -10    /* GMRES breakdown with a non-zero residual */
+
+/* ------------------------------------------------------------------ precision of an apply / solve */
+#define MS_PREC_FP64   0   /* every operator step in FP64 */
+#define MS_PREC_FP32   1   /* translations and spectral contractions in FP32 (scaled basis); solves
+                              use FP64 iterative refinement around an FP32 inner GMRES */
+
+/* ------------------------------------------------------------------ operator parts (ms_operator) */
+#define MS_PART_T      1   /* free-space particle-to-particle translation sum_{l != m} T^{ml} */
+#define MS_PART_R      2   /* interface-reflected operator R (includes l = m) */
+#define MS_PART_S      4   /* left-multiply the selected sum by the scattering matrices S_m */
+#define MS_PART_T_NEAR 8   /* only the directly summed near pairs of T (adjacent FMM leaves) */
+#define MS_PART_T_FAR 16   /* only the FMM far field of T (zero when the FMM is off) */
+
+/* ------------------------------------------------------------------ inputs */
+typedef struct {
+    int32_t        M;          /* number of particles (>= 1) */
+    const double*  centres;    /* host [M][2]: (x_m, y_m), y_m < 0 */
+    const double*  radius;     /* host [M]: enclosing radius R_m > 0 (Sec. 4.3) */
+    const int32_t* bc;         /* host [M]: 0 rigid, 1 traction-free (Sec. 2) */
+    const int32_t* proto;      /* host [M] or NULL: -1 = disc of radius R_m (closed-form S);
+                                  q >= 0 = dense prototype table q below */
+    const double*  rotation;   /* host [M] or NULL: rotation angle phi_m of prototype particles (Sec. 4.3) */
+    int32_t        n_proto;    /* number of prototype tables (0 if none) */
+    const double*  proto_S;    /* host [n_proto][2nc][2nc] complex interleaved, row (b,n) -> column (b',n'),
+                                  the unrotated prototype's scattering matrix in its own frame */
+} ms_geometry;
+
+typedef struct {
+    double lam_u, mu_u;        /* upper layer Lame constants (x2 > 0); density 1 (Sec. 2) */
+    double lam_l, mu_l;        /* lower layer Lame constants (x2 < 0) */
+} ms_media;
+
+typedef struct {
+    int32_t n_panels;          /* Gauss-Legendre panels on the contour (default 32) */
+    int32_t nodes_per_panel;   /* nodes per panel (default 16); N_S = n_panels * nodes_per_panel */
+    double  t_max;             /* contour xi(t) = t - i tanh(t)/2, |t| <= t_max (Sec. 5.1; default 20) */
+    int32_t restart;           /* GMRES restart length (default 50) */
+    int32_t max_iters;         /* total GMRES iteration cap per solve (default 2000) */
+    int32_t check_geometry;    /* 1 = validate separation / burial (default 1) */
+    int32_t use_fmm;           /* 1 = quadtree FMM for non-adjacent leaves when M is large enough
+                                  (default 1); 0 = direct Graf sum over every pair */
+    int32_t leaf_target;       /* FMM: target particles per leaf box (default 40) */
+} ms_options;
+
+typedef struct {
+    int32_t       nrhs;
+    const int32_t* kind;       /* host [nrhs]: 0 plane P-wave, 1 plane S-wave, from the upper layer */
+    const double*  angle;      /* host [nrhs]: direction (cos t, -sin t), t in (0, pi) (Sec. 7.3) */
+} ms_incidence;
+
+typedef struct {
+    int32_t iterations;        /* total inner GMRES iterations (max over columns) */
+    int32_t refinements;       /* FP64 refinement steps (MS_PREC_FP32 solves) */
+    int32_t matvecs;           /* operator applications */
+    double  max_rel_residual;  /* max over columns of ||b - A x|| / ||b|| in FP64 at exit */
+    double  seconds;           /* wall time of the solve */
+} ms_solve_info;
+
+typedef struct ms_handle ms_handle;
+
+/* Fill *o with the defaults listed above. */
+void ms_default_options(ms_options* o);
+
+/* Build a handle for one geometry, medium, frequency omega > 0 and expansion order p >= 0
+ * (truncation Z_p of Sec. 4.1): wavenumbers (Sec. 2), scattering matrices (closed-form discs,
+ * Sec. 4.1; caller prototypes, Sec. 4.3), the Sommerfeld contour and the 2x2 reflection table per
+ * node (Sec. 3, 5.1), and device workspace.  Errors: MS_ERR_ARG, MS_ERR_OVERLAP,
+ * MS_ERR_NOT_BURIED, MS_ERR_ALLOC, MS_ERR_CUDA.  On error *out is NULL. */
+int ms_setup(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
+             const ms_options* o, ms_handle** out);
+
+/* y = A x = x - S (T + R) x for nrhs columns (mul2 with the layered Schur complement).
+ * x, y: device [M][2][nc][nrhs] complex double; x and y must not overlap.
+ * prec: MS_PREC_FP64 or MS_PREC_FP32 (operator steps in FP32; input/output stay FP64). */
+int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream);
+
+/* Building block view of the same operator: y = [S] (T_sel + R_sel) x with parts a mask of
+ * MS_PART_T (or its halves MS_PART_T_NEAR, MS_PART_T_FAR) | MS_PART_R | MS_PART_S.  Without
+ * MS_PART_S the result is a block of local (incoming) coefficients.  Same layouts and errors as
+ * ms_apply. */
+int ms_operator(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, int32_t parts,
+                void* stream);
+
+/* b = S a0: right-hand side for plane-wave incidences from the upper layer (Sec. 7.3, bplan).
+ * b: device [M][2][nc][inc->nrhs] complex double. */
+int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stream);
+
+/* Solve A gamma = S a0 for the given incidences to relative residual tol (per column, 2-norm)
+ * with restarted GMRES (MS_PREC_FP64) or GMRES with FP64 iterative refinement around an FP32
+ * inner solve (MS_PREC_FP32).  gamma: device [M][2][nc][nrhs] complex double, overwritten.
+ * info may be NULL.  Returns MS_OK, MS_NOT_CONVERGED (positive) or an error. */
+int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
+             ms_solve_info* info, void* stream);
+
+/* Scattered displacement at R receivers in the lower layer (Sec. 5, total-field representation):
+ * direct outgoing sum of every particle plus the interface-reflected Sommerfeld field.
+ * gamma: device [M][2][nc][nrhs]; rx: device [R][2] double; u: device [nrhs][R][2] complex double.
+ * Errors: MS_ERR_RECEIVER_INSIDE if a receiver lies in an enclosing disc or at y >= 0. */
+int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
+              void* stream);
+
+/* Sizes of the handle: M, p, N_S, FMM levels (0 = direct sum over all pairs) and the number of
+ * ordered particle pairs summed directly.  Any output pointer may be NULL. */
+int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,
+            int64_t* near_pairs);
+
+/* Release every device buffer of the handle.  NULL is ignored. */
+void ms_destroy(ms_handle* h);
+
+/* Static string for a status code. */
+const char* ms_status_string(int status);
+
+/* Last CUDA error code (cudaError_t value) recorded by the handle, 0 if none. */
+int ms_last_cuda_error(const ms_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_B300_H */

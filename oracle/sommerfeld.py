@@ -132,10 +132,11 @@ def paper_A(xi: complex, L: Layered):
 
 # ----------------------------------------------------------------------------- M2S / S2L
 
-def m2s(xi, L: Layered, centres, gamma):
+def m2s(xi, L: Layered, centres, gamma, chunk: int = 512):
     """Upgoing amplitudes U_P, U_S at every node: arrays (N_S, nrhs) (pts1/sed1/sed2, Sec. 5.4).
 
-    gamma: (M, 2, 2p+1, nrhs) outgoing coefficients (alpha = [:,0], beta = [:,1])."""
+    gamma: (M, 2, 2p+1, nrhs) outgoing coefficients (alpha = [:,0], beta = [:,1]).  Particles are
+    summed in chunks; each chunk is one matrix product over the orders n."""
     M, _, nc, nrhs = gamma.shape
     p = (nc - 1) // 2
     n = np.arange(-p, p + 1)
@@ -144,24 +145,38 @@ def m2s(xi, L: Layered, centres, gamma):
         s = branch_s(xi, k)                                   # (Q,)
         fac = (s - xi) / (1j * k)                             # (Q,)
         powers = ((-1.0) ** n)[None, :] * fac[:, None] ** n[None, :]     # (Q, nc)
-        E = np.exp(s[:, None] * centres[None, :, 1] - 1j * xi[:, None] * centres[None, :, 0])  # (Q, M)
-        E = E / (1j * np.pi * s[:, None])
-        inner = np.einsum("qn,mnr->qmr", powers, gamma[:, b])  # (Q, M, nrhs)
-        out.append(np.einsum("qm,qmr->qr", E, inner))
+        U = np.zeros((xi.size, nrhs), dtype=complex)
+        for c0 in range(0, M, chunk):
+            c1 = min(M, c0 + chunk)
+            cc = centres[c0:c1]
+            E = np.exp(s[:, None] * cc[None, :, 1] - 1j * xi[:, None] * cc[None, :, 0])  # (Q, mc)
+            E = E / (1j * np.pi * s[:, None])
+            g = gamma[c0:c1, b].transpose(1, 0, 2).reshape(nc, -1)           # (nc, mc*nrhs)
+            inner = (powers @ g).reshape(xi.size, c1 - c0, nrhs)              # (Q, mc, nrhs)
+            U += np.einsum("qm,qmr->qr", E, inner)
+        out.append(U)
     return out[0], out[1]
 
 
-def s2l(xi, W, L: Layered, centres, D_P, D_S, p: int):
+def s2l(xi, W, L: Layered, centres, D_P, D_S, p: int, chunk: int = 512):
     """Local (incoming) coefficients (M, 2, 2p+1, nrhs) of the downgoing field
     int D_P grad(e^{i xi x + s'_p y}) + D_S grad_perp(e^{i xi x + s'_s y}) dxi  (Sec. 5.3, stm)."""
     n = np.arange(-p, p + 1)
+    M = centres.shape[0]
+    nc = 2 * p + 1
     res = []
     for D, k in ((D_P, L.kp_l), (D_S, L.ks_l)):
         s = branch_s(xi, k)
         eiphi = (xi - s) / k
         powers = (1j ** n)[None, :] * eiphi[:, None] ** n[None, :]       # (Q, nc)
-        E = np.exp(1j * xi[:, None] * centres[None, :, 0] + s[:, None] * centres[None, :, 1])  # (Q, M)
-        res.append(np.einsum("qm,qn,qr->mnr", E * W[:, None], powers, D))
+        out = np.empty((M, nc, D.shape[1]), dtype=complex)
+        for c0 in range(0, M, chunk):
+            c1 = min(M, c0 + chunk)
+            cc = centres[c0:c1]
+            E = np.exp(1j * xi[:, None] * cc[None, :, 0] + s[:, None] * cc[None, :, 1])  # (Q, mc)
+            A = (E * W[:, None])[:, :, None] * powers[:, None, :]                         # (Q, mc, nc)
+            out[c0:c1] = (A.reshape(xi.size, -1).T @ D).reshape(c1 - c0, nc, -1)
+        res.append(out)
     return np.stack(res, axis=1)
 
 

@@ -78,13 +78,23 @@ class Problem:
             for b, k in ((0, self.L.kp_l), (1, self.L.ks_l)):
                 T = graf.translation_all_sources(self.p, k, self.centres[m], self.centres)
                 T[m] = 0.0
-                out[i, b] = np.einsum("lij,ljr->ir", T, gamma[:, b])
+                # sum over sources l and orders j as one matrix product
+                nrhs = gamma.shape[3]
+                out[i, b] = T.transpose(1, 0, 2).reshape(self.nc, -1) @ gamma[:, b].reshape(-1, nrhs)
         return out
+
+    def reflection_table(self):
+        """R(xi_q) for every node (plane-wave route), computed once per problem."""
+        if getattr(self, "_R", None) is None:
+            self._R = np.stack([sommerfeld.reflection_plane_wave(x, self.L) for x in self.xi])
+        return self._R
 
     def reflect(self, gamma, targets=None):
         """(R gamma)^m: local coefficients of the interface-reflected field (Sec. 5.3-5.4)."""
         U_P, U_S = sommerfeld.m2s(self.xi, self.L, self.centres, gamma)
-        D_P, D_S = sommerfeld.reflect_nodes(self.xi, self.L, U_P, U_S)
+        R = self.reflection_table()
+        D_P = R[:, 0, 0, None] * U_P + R[:, 0, 1, None] * U_S
+        D_S = R[:, 1, 0, None] * U_P + R[:, 1, 1, None] * U_S
         c = self.centres if targets is None else self.centres[list(targets)]
         return sommerfeld.s2l(self.xi, self.W, self.L, c, D_P, D_S, self.p)
 

@@ -1,0 +1,167 @@
+"""B300-native layered-medium elastic multiple-scattering solver (arxiv 2608.26875).
+
+Python face of the C ABI in include/ms_b300.h.  `Solver` owns one library handle; its methods
+take and return torch CUDA tensors in the library layout (M, 2, 2p+1, nrhs) complex128, with
+b = 0 the compressional (alpha / a) and b = 1 the shear (beta / b) coefficients of order n = -p..p.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from ._native import (MS_PART_R, MS_PART_S, MS_PART_T, MS_PART_T_FAR, MS_PART_T_NEAR, MS_PREC_FP32,
+                      MS_PREC_FP64, MsError)
+
+__all__ = ["Solver", "MsError", "MS_PREC_FP64", "MS_PREC_FP32", "MS_PART_T", "MS_PART_R", "MS_PART_S",
+           "MS_PART_T_NEAR", "MS_PART_T_FAR", "default_options"]
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(nat.c_dp)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(nat.c_ip)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_options() -> nat.Options:
+    o = nat.Options()
+    nat.lib().ms_default_options(ctypes.byref(o))
+    return o
+
+
+class Solver:
+    """One geometry, medium, frequency omega and expansion order p (ms_setup)."""
+
+    def __init__(self, centres, radius, bc, media, omega: float, p: int, proto=None, rotation=None,
+                 proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
+                 restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
+                 use_fmm: bool = True, leaf_target: int = 40):
+        L = nat.lib()
+        self._keep = []
+        c = np.ascontiguousarray(centres, dtype=np.float64)
+        r = np.ascontiguousarray(radius, dtype=np.float64)
+        b = np.ascontiguousarray(bc, dtype=np.int32)
+        M = int(c.shape[0])
+        g = nat.Geometry()
+        g.M = M
+        g.centres, g.radius, g.bc = _dp(c), _dp(r), _ip(b)
+        self._keep += [c, r, b]
+        if proto is not None:
+            pr = np.ascontiguousarray(proto, dtype=np.int32)
+            g.proto = _ip(pr)
+            self._keep.append(pr)
+        if rotation is not None:
+            ro = np.ascontiguousarray(rotation, dtype=np.float64)
+            g.rotation = _dp(ro)
+            self._keep.append(ro)
+        if proto_S is not None:
+            ps = np.ascontiguousarray(np.asarray(proto_S, dtype=np.complex128)).view(np.float64)
+            g.n_proto = int(np.asarray(proto_S).shape[0])
+            g.proto_S = _dp(ps)
+            self._keep.append(ps)
+        md = nat.Media(float(media.lam_u), float(media.mu_u), float(media.lam_l), float(media.mu_l))
+        o = default_options()
+        o.n_panels, o.nodes_per_panel, o.t_max = n_panels, nodes_per_panel, float(t_max)
+        o.restart, o.max_iters, o.check_geometry = restart, max_iters, int(bool(check_geometry))
+        o.use_fmm, o.leaf_target = int(bool(use_fmm)), int(leaf_target)
+        h = ctypes.c_void_p()
+        nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
+                             ctypes.byref(h)), "ms_setup")
+        self._h = h
+        self.M, self.p, self.nc = M, int(p), 2 * int(p) + 1
+        nn, lev, npair = nat.c_int(), nat.c_int(), ctypes.c_int64()
+        L.ms_info(h, None, None, ctypes.byref(nn), ctypes.byref(lev), ctypes.byref(npair))
+        self.n_nodes = int(nn.value)
+        self.fmm_levels = int(lev.value)
+        self.near_pairs = int(npair.value)
+        self._keep = []
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        """Handle for a synthetic.Workload (closed-form discs unless prototypes are given)."""
+        return cls(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, wl.p, rotation=wl.rotation,
+                   n_panels=wl.n_panels, nodes_per_panel=wl.nodes_per_panel, t_max=wl.t_max, **kw)
+
+    # ------------------------------------------------------------------ helpers
+    def _check_vec(self, x: torch.Tensor, nrhs=None) -> int:
+        if not (x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous()):
+            raise ValueError("expected a contiguous complex128 CUDA tensor")
+        if x.dim() != 4 or tuple(x.shape[:3]) != (self.M, 2, self.nc):
+            raise ValueError(f"expected shape ({self.M}, 2, {self.nc}, nrhs), got {tuple(x.shape)}")
+        return int(x.shape[3])
+
+    def empty(self, nrhs: int, device=None) -> torch.Tensor:
+        return torch.empty((self.M, 2, self.nc, nrhs), dtype=torch.complex128, device=device or "cuda")
+
+    # ------------------------------------------------------------------ entry points
+    def apply(self, x: torch.Tensor, prec: int = MS_PREC_FP64, out=None, stream=None) -> torch.Tensor:
+        """y = x - S (T + R) x (ms_apply)."""
+        nrhs = self._check_vec(x)
+        y = out if out is not None else torch.empty_like(x)
+        nat.check(nat.lib().ms_apply(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                     nrhs, prec, _stream(stream)), "ms_apply")
+        return y
+
+    def operator(self, x: torch.Tensor, parts: int, prec: int = MS_PREC_FP64, stream=None) -> torch.Tensor:
+        """y = [S] (T_sel + R_sel) x (ms_operator)."""
+        nrhs = self._check_vec(x)
+        y = torch.empty_like(x)
+        nat.check(nat.lib().ms_operator(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        nrhs, prec, parts, _stream(stream)), "ms_operator")
+        return y
+
+    def _incidence(self, kinds, angles):
+        k = np.ascontiguousarray(kinds, dtype=np.int32)
+        a = np.ascontiguousarray(angles, dtype=np.float64)
+        inc = nat.Incidence(int(k.size), _ip(k), _dp(a))
+        return inc, (k, a)
+
+    def rhs(self, kinds, angles, stream=None) -> torch.Tensor:
+        """b = S a0 for plane-wave incidences from the upper layer (ms_rhs)."""
+        inc, keep = self._incidence(kinds, angles)
+        b = self.empty(inc.nrhs)
+        nat.check(nat.lib().ms_rhs(self._h, ctypes.byref(inc), ctypes.c_void_p(b.data_ptr()), _stream(stream)),
+                  "ms_rhs")
+        return b
+
+    def solve(self, kinds, angles, tol: float = 1e-12, prec: int = MS_PREC_FP64, stream=None, out=None):
+        """gamma solving A gamma = S a0 (ms_solve).  Returns (gamma, info dict, status)."""
+        inc, keep = self._incidence(kinds, angles)
+        g = out if out is not None else self.empty(inc.nrhs)
+        info = nat.SolveInfo()
+        st = nat.check(nat.lib().ms_solve(self._h, ctypes.byref(inc), float(tol), prec,
+                                          ctypes.c_void_p(g.data_ptr()), ctypes.byref(info), _stream(stream)),
+                       "ms_solve", allow_warning=True)
+        return g, {"iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
+                   "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
+
+    def fields(self, gamma: torch.Tensor, receivers, stream=None) -> torch.Tensor:
+        """Scattered displacement (nrhs, R, 2) complex128 at receivers (R, 2) in the lower layer (ms_fields)."""
+        nrhs = self._check_vec(gamma)
+        rx = torch.as_tensor(np.ascontiguousarray(receivers, dtype=np.float64), device=gamma.device)
+        R = int(rx.shape[0])
+        u = torch.empty((nrhs, R, 2), dtype=torch.complex128, device=gamma.device)
+        nat.check(nat.lib().ms_fields(self._h, ctypes.c_void_p(gamma.data_ptr()), nrhs,
+                                      ctypes.c_void_p(rx.data_ptr()), R, ctypes.c_void_p(u.data_ptr()),
+                                      _stream(stream)), "ms_fields")
+        return u
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            nat.lib().ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,204 @@
+// C ABI entry points other than setup and solve: apply, operator parts, right-hand side,
+// sizes, teardown and status strings.
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+
+typedef std::complex<double> cd;
+bool ms_plane_wave_transmission(const ms_handle* h, int kind, double angle, double* xi_out, cd D[2]);
+
+int ms_check(ms_handle* h, cudaError_t e) {
+    if (e == cudaSuccess) return MS_OK;
+    if (h) h->last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? MS_ERR_ALLOC : MS_ERR_CUDA;
+}
+
+static void dfree(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+template <typename X>
+static void dfree_t(X*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+int ms_ensure_workspace(ms_handle* h, int nrhs) {
+    if (h->ws_nrhs >= nrhs) return MS_OK;
+    dfree(h->ws_x);
+    dfree(h->ws_a);
+    dfree(h->ws_y);
+    dfree(h->ws_part);
+    dfree(h->ws_u);
+    h->ws_nrhs = 0;
+    size_t nvec = (size_t)h->M * 2 * h->nc * nrhs * sizeof(double2);
+    size_t npart = (size_t)64 * 2 * h->NS * nrhs * sizeof(double2);
+    size_t nu = (size_t)2 * h->NS * nrhs * sizeof(double2);
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->ws_x, nvec)) != cudaSuccess || (e = cudaMalloc(&h->ws_a, nvec)) != cudaSuccess ||
+        (e = cudaMalloc(&h->ws_y, nvec)) != cudaSuccess || (e = cudaMalloc(&h->ws_part, npart)) != cudaSuccess ||
+        (e = cudaMalloc(&h->ws_u, nu)) != cudaSuccess) {
+        h->last_cuda = (int)e;
+        return MS_ERR_ALLOC;
+    }
+    if (int rc = ms_fmm_workspace(h, nrhs)) return rc;
+    h->ws_nrhs = nrhs;
+    return MS_OK;
+}
+
+static int check_call(ms_handle* h, const void* x, void* y, int nrhs, int prec) {
+    if (!h || !x || !y || nrhs < 1) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+    return ms_ensure_workspace(h, nrhs);
+}
+
+static int apply_common(ms_handle* h, const void* x, void* y, int nrhs, int prec, int parts, bool identity,
+                        cudaStream_t st) {
+    int rc;
+    if ((rc = ms_to_scaled(h, x, h->ws_x, nrhs, prec, st))) return rc;
+    if (prec == MS_PREC_FP64)
+        rc = ms_apply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, parts, identity, st);
+    else
+        rc = ms_apply_scaled<float>(h, h->ws_x, h->ws_y, nrhs, parts, identity, st);
+    if (rc) return rc;
+    // without S the result is a local (incoming) block, scaled the other way
+    bool local = !(parts & MS_PART_S) && (parts & (MS_PART_T | MS_PART_R | MS_PART_T_NEAR | MS_PART_T_FAR));
+    return ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, local);
+}
+
+extern "C" int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
+    int rc = check_call(h, x, y, nrhs, prec);
+    if (rc) return rc;
+    return apply_common(h, x, y, nrhs, prec, MS_PART_T | MS_PART_R | MS_PART_S, true, (cudaStream_t)stream);
+}
+
+extern "C" int ms_operator(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, int32_t parts,
+                           void* stream) {
+    int rc = check_call(h, x, y, nrhs, prec);
+    if (rc) return rc;
+    if (parts & ~(MS_PART_T | MS_PART_R | MS_PART_S | MS_PART_T_NEAR | MS_PART_T_FAR)) return MS_ERR_ARG;
+    return apply_common(h, x, y, nrhs, prec, parts, false, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ plane-wave right-hand side
+// a~0[m,b,n,r] = 2^{a_{m,b,n}} D_b(r) e^{i xi_r x_m + s_{b,r} y_m} i^n q_{b,r}^n  (Jacobi-Anger about x_m)
+__global__ void k_incident(double2* __restrict__ as, const double2* __restrict__ centre, const int* __restrict__ expo,
+                           const double* __restrict__ xi, const double2* __restrict__ amp,
+                           const double2* __restrict__ s, const double2* __restrict__ q, int M, int p, int nrhs) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nc = 2 * p + 1;
+    long long total = (long long)M * 2 * nc * nrhs;
+    if (i >= total) return;
+    int r = (int)(i % nrhs);
+    long long row = i / nrhs;
+    int ni = (int)(row % nc);
+    int b = (int)((row / nc) % 2);
+    int m = (int)(row / (2 * nc));
+    int n = ni - p;
+    double2 c = centre[m];
+    double2 sb = s[r * 2 + b], qb = q[r * 2 + b];
+    double re = sb.x * c.y;
+    double im = xi[r] * c.x + sb.y * c.y;
+    double mag = exp(re), sn, cs;
+    sincos(im, &sn, &cs);
+    double2 v = cmul(amp[r * 2 + b], make_double2(mag * cs, mag * sn));
+    // i^n q^n by repeated multiplication (|n| <= 30)
+    double2 f = make_double2(1.0, 0.0);
+    double2 iq = cmul(make_double2(0.0, 1.0), qb);
+    if (n < 0) iq = cdiv(make_double2(1.0, 0.0), iq);
+    int an = n < 0 ? -n : n;
+    for (int k = 0; k < an; ++k) f = cmul(f, iq);
+    double sc = pow2d(expo[row]);
+    v = cmul(v, f);
+    as[i] = make_double2(v.x * sc, v.y * sc);
+}
+
+extern "C" int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stream) {
+    if (!h || !inc || !b || !inc->kind || !inc->angle) return MS_ERR_ARG;
+    const int nrhs = inc->nrhs;
+    int rc = check_call(h, b, b, nrhs, MS_PREC_FP64);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> xi(nrhs);
+    std::vector<double2> amp(nrhs * 2), s(nrhs * 2), q(nrhs * 2);
+    for (int r = 0; r < nrhs; ++r) {
+        if ((inc->kind[r] != 0 && inc->kind[r] != 1) || !(inc->angle[r] > 0) || !(inc->angle[r] < M_PI))
+            return MS_ERR_ARG;
+        cd D[2];
+        if (!ms_plane_wave_transmission(h, inc->kind[r], inc->angle[r], &xi[r], D)) return MS_ERR_ARG;
+        for (int bb = 0; bb < 2; ++bb) {
+            double k = bb ? h->ks_l : h->kp_l;
+            cd x(xi[r], 0.0);
+            cd sv = cd(0, -1) * std::sqrt(cd(k * k - xi[r] * xi[r], 0.0));
+            cd qv = (x - sv) / k;
+            amp[r * 2 + bb] = make_double2(D[bb].real(), D[bb].imag());
+            s[r * 2 + bb] = make_double2(sv.real(), sv.imag());
+            q[r * 2 + bb] = make_double2(qv.real(), qv.imag());
+        }
+    }
+    double *d_xi = nullptr;
+    double2 *d_amp = nullptr, *d_s = nullptr, *d_q = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_xi, nrhs * sizeof(double))) || (e = cudaMalloc(&d_amp, nrhs * 2 * sizeof(double2))) ||
+        (e = cudaMalloc(&d_s, nrhs * 2 * sizeof(double2))) || (e = cudaMalloc(&d_q, nrhs * 2 * sizeof(double2)))) {
+        cudaFree(d_xi); cudaFree(d_amp); cudaFree(d_s); cudaFree(d_q);
+        return ms_check(h, e);
+    }
+    cudaMemcpyAsync(d_xi, xi.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_amp, amp.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_s, s.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_q, q.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
+    long long total = (long long)h->M * 2 * h->nc * nrhs;
+    k_incident<<<(int)((total + 255) / 256), 256, 0, st>>>((double2*)h->ws_a, h->d.centre, h->d.expo, d_xi, d_amp, d_s,
+                                                          d_q, h->M, h->p, nrhs);
+    rc = ms_check(h, cudaGetLastError());
+    // b~ = S~ a~0 (identity off, S on, no operator part: the workspace a~ is used as is)
+    if (!rc) rc = ms_sapply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, false, true, st);
+    if (!rc) rc = ms_from_scaled(h, h->ws_y, b, nrhs, MS_PREC_FP64, st);
+    cudaStreamSynchronize(st);
+    cudaFree(d_xi); cudaFree(d_amp); cudaFree(d_s); cudaFree(d_q);
+    return rc;
+}
+
+extern "C" int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,
+                       int64_t* near_pairs) {
+    if (!h) return MS_ERR_ARG;
+    if (M) *M = h->M;
+    if (p) *p = h->p;
+    if (n_nodes) *n_nodes = h->NS;
+    if (fmm_levels) *fmm_levels = h->fmm_levels;
+    if (near_pairs) *near_pairs = h->nnz_near;
+    return MS_OK;
+}
+
+extern "C" void ms_destroy(ms_handle* h) {
+    if (!h) return;
+    dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);
+    dfree_t(h->d.proto); dfree_t(h->d.rot); dfree_t(h->d.sproto); dfree_t(h->d.node); dfree_t(h->d.wq);
+    dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
+    ms_fmm_free(h);
+    dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u);
+    delete h;
+}
+
+extern "C" const char* ms_status_string(int s) {
+    switch (s) {
+        case MS_OK: return "ok";
+        case MS_NOT_CONVERGED: return "not converged";
+        case MS_ERR_ARG: return "invalid argument";
+        case MS_ERR_CUDA: return "CUDA error";
+        case MS_ERR_OVERLAP: return "enclosing discs closer than 1.1 (R_l + R_m)";
+        case MS_ERR_NOT_BURIED: return "particle not buried below the interface";
+        case MS_ERR_UNSUPPORTED: return "unsupported request";
+        case MS_ERR_RECEIVER_INSIDE: return "receiver inside an enclosing disc or not below the interface";
+        case MS_ERR_ALLOC: return "device allocation failed";
+        case MS_ERR_NONFINITE: return "non-finite value";
+        case MS_ERR_BREAKDOWN: return "GMRES breakdown";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int ms_last_cuda_error(const ms_handle* h) { return h ? h->last_cuda : 0; }

@@ -1,0 +1,675 @@
+// Free-space particle-to-particle translation: direct Graf sum for near pairs (row a2) and a
+// quadtree fast multipole method for the rest (row a3), Sec. 4.2 (FMM cited there, O(M p^2)).
+//
+// Every translation in this file has the same Toeplitz form (Graf's addition theorem,
+// DLMF 10.23.7, for H and J):
+//     dst[i] += sum_j Z_{j-i}(k |v|) e^{i (j-i) arg v} src[j],   v = c_dst - c_src,
+// with Z = H^(1) from outgoing to local (particle near pairs, M2L) and Z = J for shifts of
+// outgoing expansions (P2M, M2M) and of local expansions (L2L, L2P).  The sequences
+// h_k = Z_k(k|v|) e^{ik arg v}, |k| <= K = P_dst + P_src, are computed once per geometry in FP64
+// on the device and stored in HBM (an FP32 mantissa / binary-exponent copy serves the FP32 path).
+// Coefficients live in the scaled basis: outgoing x~ = x / tau, local a~ = a tau, tau = 2^a, so
+// the entry applied is  h_{j-i} 2^{s_dst a_dst,i + s_src a_src,j}  with the signs s of each side.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+
+namespace {
+
+// ------------------------------------------------------------------ sequence generation
+// h[K + k] = Z_k(x) e^{ik phi}, k in [-K, K], Z = J (kind 0) or H^(1) (kind 1).  The recurrences
+// are those of bessel.cuh, run in place in the output row: first (J_k, Y_k) are written at
+// h[K + k], k >= 0, then phases are applied and negative orders filled from Z_{-k} = (-1)^k Z_k.
+__device__ void zseq_inplace(int K, double x, double ux, double uy, int kind, double2* h) {
+    double2* o = h + K;
+    // Y upward (stable), kept in .y
+    if (kind == 1) {
+        o[0].y = y0(x);
+        if (K >= 1) o[1].y = y1(x);
+        for (int k = 1; k < K; ++k) o[k + 1].y = (2.0 * k / x) * o[k].y - o[k - 1].y;
+    }
+    if (x > (double)K) {
+        o[0].x = j0(x);
+        if (K >= 1) o[1].x = j1(x);
+        for (int k = 1; k < K; ++k) o[k + 1].x = (2.0 * k / x) * o[k].x - o[k - 1].x;
+    } else {
+        int ns = K + 16 + (int)ceil(x) + (int)sqrt(40.0 * K);
+        ns += ns & 1;
+        double jp1 = 0.0, j = 1e-300;
+        for (int k = ns; k >= 1; --k) {
+            double jm1 = (2.0 * k / x) * j - jp1;
+            jp1 = j;
+            j = jm1;
+            if (k - 1 <= K) o[k - 1].x = jm1;
+            if (fabs(j) > 1e250) {
+                j *= 1e-250;
+                jp1 *= 1e-250;
+                for (int i = k - 1; i <= K; ++i) o[i].x *= 1e-250;
+            }
+        }
+        double j0s = o[0].x, j1s = K >= 1 ? o[1].x : jp1;
+        double c = (fabs(j0s) > fabs(j1s)) ? j0(x) / j0s : j1(x) / j1s;
+        for (int k = 0; k <= K; ++k) o[k].x *= c;
+    }
+    if (kind == 0)
+        for (int k = 0; k <= K; ++k) o[k].y = 0.0;
+    // phases; walk k downward so that the (J, Y) pairs at o[k] are read before h[K - k] is written
+    // (h[K - k] for k > 0 lies below o[0]).
+    double2 u = make_double2(ux, uy);
+    // e^{iK phi} by repeated squaring would lose nothing here; plain powers are accurate to ~K ulp
+    double2 eK = make_double2(1.0, 0.0);
+    for (int k = 0; k < K; ++k) eK = cmul(eK, u);
+    double2 e = eK;
+    double2 ub = cconj(u);
+    for (int k = K; k >= 0; --k) {
+        double2 Z = o[k];
+        o[k] = cmul(Z, e);
+        if (k > 0) {
+            double2 w = cmul(Z, cconj(e));
+            if (k & 1) w = make_double2(-w.x, -w.y);
+            h[K - k] = w;
+        }
+        e = cmul(e, ub);
+    }
+}
+
+struct SeqSpec {
+    double vx, vy, k;
+    int K, kind;
+    long long off;
+};
+
+__global__ void k_gen_seq(const SeqSpec* __restrict__ spec, int n, double2* __restrict__ seq) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    SeqSpec s = spec[i];
+    double d = sqrt(s.vx * s.vx + s.vy * s.vy);
+    double ux = d > 0 ? s.vx / d : 1.0, uy = d > 0 ? s.vy / d : 0.0;
+    if (d == 0.0) {
+        // zero shift: J_k(0) = delta_k0 (only J sequences are ever asked for at d = 0)
+        for (int k = -s.K; k <= s.K; ++k) seq[s.off + s.K + k] = make_double2(k == 0 ? 1.0 : 0.0, 0.0);
+        return;
+    }
+    zseq_inplace(s.K, s.k * d, ux, uy, s.kind, seq + s.off);
+}
+
+__global__ void k_split_seq(const double2* __restrict__ seq, float2* __restrict__ m, int* __restrict__ e,
+                            long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float2 mm;
+    int ee;
+    split_exp(seq[i], mm, ee);
+    m[i] = mm;
+    e[i] = ee;
+}
+
+// ------------------------------------------------------------------ generic translation
+constexpr int TR_IB = 3;
+constexpr int TR_RB = 8;
+constexpr int TR_ICH = 42;     // dst orders per CTA (14 x TR_IB)
+constexpr int TR_JCH = 48;     // src orders per staged tile
+constexpr int TR_THREADS = 128;
+
+template <typename T> struct SeqRef;
+template <> struct SeqRef<double> {
+    const double2* s;
+    __device__ double2 entry(long long idx, int scale) const {
+        double2 v = s[idx];
+        double f = pow2d(scale);
+        return make_double2(v.x * f, v.y * f);
+    }
+};
+template <> struct SeqRef<float> {
+    const float2* m;
+    const int* e;
+    __device__ float2 entry(long long idx, int scale) const {
+        float2 v = m[idx];
+        float f = pow2f(e[idx] + scale);
+        return make_float2(v.x * f, v.y * f);
+    }
+};
+
+// CTA = (dst entity d, dst order chunk).  For each task (src entity, sequence) of d and each chunk
+// of source orders, the CTA stages the scaled operator tile and the source block in shared
+// memory; each thread accumulates a TR_IB x TR_RB register tile over all tasks and chunks.
+template <typename T>
+__global__ void __launch_bounds__(TR_THREADS)
+k_translate(TransArgs a, SeqRef<T> seq) {
+    typedef typename CT<T>::c C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Eb = reinterpret_cast<C*>(smem_raw);          // [TR_ICH][TR_JCH]
+    C* Xb = Eb + TR_ICH * TR_JCH;                   // [TR_JCH][nrhs]
+    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1, K = a.K, nrhs = a.nrhs;
+    const int d = blockIdx.x;
+    const int ic0 = blockIdx.y * TR_ICH;
+    const int ni = min(TR_ICH, nd - ic0);
+    const int n_rb = (nrhs + TR_RB - 1) / TR_RB;
+    const int tile = threadIdx.x;
+    const bool act = tile < ((ni + TR_IB - 1) / TR_IB) * n_rb;
+    const int ib = act ? tile / n_rb : 0, rb = act ? tile % n_rb : 0;
+    const int i0 = ib * TR_IB, r0 = rb * TR_RB;
+    const int* ad = a.ad + (long long)d * a.ad_stride;
+    C acc[TR_IB][TR_RB];
+#pragma unroll
+    for (int u = 0; u < TR_IB; ++u)
+#pragma unroll
+        for (int v = 0; v < TR_RB; ++v) acc[u][v] = mk((T)0, (T)0);
+
+    const int t0 = a.dst_ptr[d], t1 = a.dst_ptr[d + 1];
+    for (int t = t0; t < t1; ++t) {
+        const int s = a.task_src[t];
+        const long long so = a.task_seq[t];
+        const C* src = reinterpret_cast<const C*>(a.src) + (long long)s * a.src_stride;
+        const int* as = a.as + (long long)s * a.as_stride;
+        for (int jc = 0; jc < ns; jc += TR_JCH) {
+            const int nj = min(TR_JCH, ns - jc);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nj * nrhs; e += blockDim.x) {
+                int jj = e / nrhs, r = e % nrhs;
+                Xb[jj * nrhs + r] = src[(long long)(jc + jj) * nrhs + r];
+            }
+            for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+                int ii = e / nj, jj = e % nj;
+                int i = ic0 + ii, j = jc + jj;
+                int sc = a.sd * ad[i] + a.ss * as[j];
+                // index j - i in dst / src order numbering (n = index - P)
+                int kk = (j - a.Ps) - (i - a.Pd);
+                Eb[ii * TR_JCH + jj] = seq.entry(so + K + kk, sc);
+            }
+            __syncthreads();
+            if (act) {
+                for (int jj = 0; jj < nj; ++jj) {
+                    C xv[TR_RB];
+#pragma unroll
+                    for (int v = 0; v < TR_RB; ++v) {
+                        int r = r0 + v;
+                        xv[v] = r < nrhs ? Xb[jj * nrhs + r] : mk((T)0, (T)0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < TR_IB; ++u) {
+                        int ii = i0 + u;
+                        C e = ii < ni ? Eb[ii * TR_JCH + jj] : mk((T)0, (T)0);
+#pragma unroll
+                        for (int v = 0; v < TR_RB; ++v) cfma(acc[u][v], e, xv[v]);
+                    }
+                }
+            }
+        }
+    }
+    if (act) {
+        C* dst = reinterpret_cast<C*>(a.dst) + (long long)d * a.dst_stride;
+#pragma unroll
+        for (int u = 0; u < TR_IB; ++u) {
+            int ii = i0 + u;
+            if (ii >= ni) continue;
+#pragma unroll
+            for (int v = 0; v < TR_RB; ++v) {
+                int r = r0 + v;
+                if (r >= nrhs) continue;
+                long long o = (long long)(ic0 + ii) * nrhs + r;
+                dst[o] = a.accumulate ? cadd(dst[o], acc[u][v]) : acc[u][v];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+static double fmm_order_tail(double k, double rho, double dist) {
+    // smallest P with |J_{P+1}(k rho)| |H_{P+1}(k (dist - rho))| < 1e-14 and |J_{P+1}(k rho)| < 1e-3
+    for (int P = 5; P < 1000; ++P) {
+        double j = fabs(jn(P + 1, k * rho));
+        double hx = k * (dist - rho);
+        double hy = hypot(jn(P + 1, hx), yn(P + 1, hx));
+        if (j * hy < 1e-14 && j < 1e-3) return P;
+    }
+    return 1000;
+}
+
+int ms_translate_launch(ms_handle* h, const TransArgs& a, int ndst, bool fp32, cudaStream_t st) {
+    if (ndst == 0) return MS_OK;
+    int nd = 2 * a.Pd + 1;
+    dim3 grid(ndst, (nd + TR_ICH - 1) / TR_ICH);
+    int tiles = 14 * ((a.nrhs + TR_RB - 1) / TR_RB);
+    int threads = std::max(32, std::min(TR_THREADS, (tiles + 31) / 32 * 32));
+    if (fp32) {
+        size_t smem = (size_t)TR_ICH * TR_JCH * sizeof(float2) + (size_t)TR_JCH * a.nrhs * sizeof(float2);
+        cudaFuncSetAttribute(k_translate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        SeqRef<float> s{h->d.seqm, h->d.seqe};
+        k_translate<float><<<grid, threads, smem, st>>>(a, s);
+    } else {
+        size_t smem = (size_t)TR_ICH * TR_JCH * sizeof(double2) + (size_t)TR_JCH * a.nrhs * sizeof(double2);
+        cudaFuncSetAttribute(k_translate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        SeqRef<double> s{h->d.seq64};
+        k_translate<double><<<grid, threads, smem, st>>>(a, s);
+    }
+    return ms_check(h, cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ host: tree and task lists
+namespace {
+
+struct HostList {
+    std::vector<int> ptr, src;
+    std::vector<long long> seq;
+};
+
+struct Builder {
+    ms_handle* h;
+    std::vector<SeqSpec> specs;
+    long long total = 0;
+    long long add(double vx, double vy, double k, int K, int kind) {
+        SeqSpec s{vx, vy, k, K, kind, total};
+        specs.push_back(s);
+        total += 2 * K + 1;
+        return s.off;
+    }
+};
+
+template <typename X>
+int up(ms_handle* h, X** dst, const std::vector<X>& v) {
+    if (v.empty()) { *dst = nullptr; return MS_OK; }
+    if (cudaMalloc((void**)dst, v.size() * sizeof(X)) != cudaSuccess) return MS_ERR_ALLOC;
+    return ms_check(h, cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
+}
+
+int upload_list(ms_handle* h, const HostList& L, DevList& D) {
+    D.ndst = (int)L.ptr.size() - 1;
+    D.ntask = (int)L.src.size();
+    int rc;
+    if ((rc = up(h, &D.ptr, L.ptr)) || (rc = up(h, &D.src, L.src)) || (rc = up(h, &D.seq, L.seq))) return rc;
+    return MS_OK;
+}
+
+}  // namespace
+
+// Build the near-field pair lists (all pairs when the FMM is off) and, with the FMM on, the
+// quadtree, interaction lists and translation sequences.  Called once from ms_setup.
+int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
+    const int M = h->M, p = h->p;
+    const double* c = h->h_centres.data();
+    double rmax = 0;
+    for (double r : h->h_radius) rmax = std::max(rmax, r);
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int m = 0; m < M; ++m) {
+        xmin = std::min(xmin, c[2 * m]); xmax = std::max(xmax, c[2 * m]);
+        ymin = std::min(ymin, c[2 * m + 1]); ymax = std::max(ymax, c[2 * m + 1]);
+    }
+    double S = std::max(xmax - xmin, ymax - ymin) * (1.0 + 1e-9) + 1e-9;
+    // leaf level: about leaf_target particles per leaf, >= 2, leaf width > 3.5 R_max (so that
+    // non-adjacent leaves are separated for the expansions, particle discs included)
+    int L = 0;
+    if (use_fmm) {
+        L = (int)lround(log((double)M / leaf_target) / log(4.0));
+        while (L >= 2 && S / (1 << L) <= 3.5 * rmax) --L;
+        if (L < 2) L = 0;
+    }
+    h->fmm_levels = L;
+    Builder B{h};
+    const double kb[2] = {h->kp_l, h->ks_l};
+
+    // leaf index of each particle (or a single leaf)
+    int nL = L ? (1 << L) : 1;
+    double wL = S / nL;
+    std::vector<int> leaf(M);
+    for (int m = 0; m < M; ++m) {
+        int ix = std::min(nL - 1, std::max(0, (int)((c[2 * m] - xmin) / wL)));
+        int iy = std::min(nL - 1, std::max(0, (int)((c[2 * m + 1] - ymin) / wL)));
+        leaf[m] = iy * nL + ix;
+    }
+    std::vector<int> lptr(nL * nL + 1, 0), lidx(M);
+    for (int m = 0; m < M; ++m) lptr[leaf[m] + 1]++;
+    for (int i = 0; i < nL * nL; ++i) lptr[i + 1] += lptr[i];
+    {
+        std::vector<int> fill(lptr.begin(), lptr.end() - 1);
+        for (int m = 0; m < M; ++m) lidx[fill[leaf[m]]++] = m;
+    }
+
+    // near lists: sources in the 3 x 3 leaves around the target's leaf (all pairs if one leaf)
+    HostList nearL;
+    nearL.ptr.assign(M + 1, 0);
+    std::vector<long long> seq_near[2];
+    for (int m = 0; m < M; ++m) {
+        nearL.ptr[m] = (int)nearL.src.size();
+        int ix = leaf[m] % nL, iy = leaf[m] / nL;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int jx = ix + dx, jy = iy + dy;
+                if (jx < 0 || jy < 0 || jx >= nL || jy >= nL) continue;
+                int bx = jy * nL + jx;
+                for (int t = lptr[bx]; t < lptr[bx + 1]; ++t) {
+                    int l = lidx[t];
+                    if (l == m) continue;
+                    nearL.src.push_back(l);
+                }
+            }
+    }
+    nearL.ptr[M] = (int)nearL.src.size();
+    h->nnz_near = (int)nearL.src.size();
+    for (int b = 0; b < 2; ++b) {
+        seq_near[b].resize(nearL.src.size());
+        for (int m = 0; m < M; ++m)
+            for (int t = nearL.ptr[m]; t < nearL.ptr[m + 1]; ++t) {
+                int l = nearL.src[t];
+                seq_near[b][t] = B.add(c[2 * m] - c[2 * l], c[2 * m + 1] - c[2 * l + 1], kb[b], 2 * p, 1);
+            }
+    }
+    int rc;
+    for (int b = 0; b < 2; ++b) {
+        HostList hl = nearL;
+        hl.seq = seq_near[b];
+        if ((rc = upload_list(h, hl, h->fmm.near[b]))) return rc;
+    }
+
+    if (L) {
+        // ---------------------------------------------------------- tree
+        FmmHost& F = h->fmm;
+        std::vector<std::vector<int>> nonempty(L + 1);
+        for (int lev = 0; lev <= L; ++lev) {
+            int n = 1 << lev;
+            F.nbox[lev] = n * n;
+            F.w[lev] = S / n;
+            nonempty[lev].assign(n * n, 0);
+        }
+        for (int m = 0; m < M; ++m) {
+            int ix = leaf[m] % nL, iy = leaf[m] / nL;
+            for (int lev = L; lev >= 0; --lev) {
+                int sh = L - lev;
+                nonempty[lev][(iy >> sh) * (1 << lev) + (ix >> sh)] = 1;
+            }
+        }
+        auto centre = [&](int lev, int id, double& cx, double& cy) {
+            int n = 1 << lev;
+            cx = xmin + ((id % n) + 0.5) * F.w[lev];
+            cy = ymin + ((id / n) + 0.5) * F.w[lev];
+        };
+        for (int b = 0; b < 2; ++b)
+            for (int lev = 2; lev <= L; ++lev) {
+                double rho = F.w[lev] * sqrt(2.0) / 2.0 + rmax;
+                int P = (int)fmm_order_tail(kb[b], rho, 2.0 * F.w[lev]);
+                P = std::min(P, 480);
+                F.P[b][lev] = P;
+                // scale exponents of the box expansions: round(log2((k rho / 2)^|n| / |n|!))
+                std::vector<int> e(2 * P + 1);
+                for (int i = 0; i <= 2 * P; ++i) {
+                    int n = abs(i - P);
+                    double l2 = n * log2(kb[b] * rho / 2.0) - lgamma(n + 1.0) / log(2.0);
+                    e[i] = (int)std::max(-900L, std::min(900L, lround(l2)));
+                }
+                if ((rc = up(h, &F.expo[b][lev], e))) return rc;
+            }
+        // ---------------------------------------------------------- lists per wave
+        for (int b = 0; b < 2; ++b) {
+            const double k = kb[b];
+            // P2M: leaf <- its particles, v = c_leaf - x_l
+            HostList p2m;
+            p2m.ptr.assign(nL * nL + 1, 0);
+            for (int bx = 0; bx < nL * nL; ++bx) {
+                p2m.ptr[bx] = (int)p2m.src.size();
+                double cx, cy;
+                centre(L, bx, cx, cy);
+                for (int t = lptr[bx]; t < lptr[bx + 1]; ++t) {
+                    int l = lidx[t];
+                    p2m.src.push_back(l);
+                    p2m.seq.push_back(B.add(cx - c[2 * l], cy - c[2 * l + 1], k, F.P[b][L] + p, 0));
+                }
+            }
+            p2m.ptr[nL * nL] = (int)p2m.src.size();
+            if ((rc = upload_list(h, p2m, F.p2m[b]))) return rc;
+            // L2P: particle <- its leaf, v = x_m - c_leaf
+            HostList l2p;
+            l2p.ptr.assign(M + 1, 0);
+            for (int m = 0; m < M; ++m) {
+                l2p.ptr[m] = m;
+                double cx, cy;
+                centre(L, leaf[m], cx, cy);
+                l2p.src.push_back(leaf[m]);
+                l2p.seq.push_back(B.add(c[2 * m] - cx, c[2 * m + 1] - cy, k, p + F.P[b][L], 0));
+            }
+            l2p.ptr[M] = M;
+            if ((rc = upload_list(h, l2p, F.l2p[b]))) return rc;
+            for (int lev = 2; lev <= L; ++lev) {
+                int n = 1 << lev;
+                double w = F.w[lev];
+                // M2L table: offsets (dx, dy) in [-3, 3]^2 with max(|dx|,|dy|) >= 2
+                long long tab[7][7];
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dx = -3; dx <= 3; ++dx)
+                        tab[dy + 3][dx + 3] = (std::max(abs(dx), abs(dy)) >= 2)
+                                                  ? B.add(dx * w, dy * w, k, 2 * F.P[b][lev], 1) : -1;
+                HostList m2l;
+                m2l.ptr.assign(n * n + 1, 0);
+                for (int id = 0; id < n * n; ++id) {
+                    m2l.ptr[id] = (int)m2l.src.size();
+                    if (!nonempty[lev][id]) continue;
+                    int ix = id % n, iy = id / n;
+                    int px = ix >> 1, py = iy >> 1;
+                    for (int qy = py - 1; qy <= py + 1; ++qy)
+                        for (int qx = px - 1; qx <= px + 1; ++qx) {
+                            if (qx < 0 || qy < 0 || qx >= n / 2 || qy >= n / 2) continue;
+                            for (int cyy = 0; cyy < 2; ++cyy)
+                                for (int cxx = 0; cxx < 2; ++cxx) {
+                                    int sx = 2 * qx + cxx, sy = 2 * qy + cyy;
+                                    int dx = ix - sx, dy = iy - sy;
+                                    if (std::max(abs(dx), abs(dy)) < 2) continue;
+                                    int sid = sy * n + sx;
+                                    if (!nonempty[lev][sid]) continue;
+                                    m2l.src.push_back(sid);
+                                    m2l.seq.push_back(tab[dy + 3][dx + 3]);
+                                }
+                        }
+                }
+                m2l.ptr[n * n] = (int)m2l.src.size();
+                if ((rc = upload_list(h, m2l, F.m2l[b][lev]))) return rc;
+                if (lev < L) {
+                    // M2M: parent (lev) <- children (lev+1); v = c_parent - c_child = (+-w/4, +-w/4)
+                    int nc2 = 2 * n;
+                    long long tabc[2][2], tabp[2][2];
+                    for (int cyy = 0; cyy < 2; ++cyy)
+                        for (int cxx = 0; cxx < 2; ++cxx) {
+                            // c_parent - c_child: the child centre sits (cxx - 1/2) child widths
+                            // from the parent centre
+                            double vx = (0.5 - cxx) * F.w[lev + 1];
+                            double vy = (0.5 - cyy) * F.w[lev + 1];
+                            tabc[cyy][cxx] = B.add(vx, vy, k, F.P[b][lev] + F.P[b][lev + 1], 0);
+                            tabp[cyy][cxx] = B.add(-vx, -vy, k, F.P[b][lev + 1] + F.P[b][lev], 0);
+                        }
+                    HostList m2m, l2l;
+                    m2m.ptr.assign(n * n + 1, 0);
+                    for (int id = 0; id < n * n; ++id) {
+                        m2m.ptr[id] = (int)m2m.src.size();
+                        int ix = id % n, iy = id / n;
+                        for (int cyy = 0; cyy < 2; ++cyy)
+                            for (int cxx = 0; cxx < 2; ++cxx) {
+                                int cid = (2 * iy + cyy) * nc2 + 2 * ix + cxx;
+                                if (!nonempty[lev + 1][cid]) continue;
+                                m2m.src.push_back(cid);
+                                m2m.seq.push_back(tabc[cyy][cxx]);
+                            }
+                    }
+                    m2m.ptr[n * n] = (int)m2m.src.size();
+                    l2l.ptr.assign(nc2 * nc2 + 1, 0);
+                    for (int cid = 0; cid < nc2 * nc2; ++cid) {
+                        l2l.ptr[cid] = (int)l2l.src.size();
+                        if (!nonempty[lev + 1][cid]) continue;
+                        int cx = cid % nc2, cy = cid / nc2;
+                        l2l.src.push_back((cy / 2) * n + cx / 2);
+                        l2l.seq.push_back(tabp[cy & 1][cx & 1]);
+                    }
+                    l2l.ptr[nc2 * nc2] = (int)l2l.src.size();
+                    if ((rc = upload_list(h, m2m, F.m2m[b][lev])) || (rc = upload_list(h, l2l, F.l2l[b][lev + 1])))
+                        return rc;
+                }
+            }
+        }
+    }
+
+    // ---------------------------------------------------------- sequences on the device
+    h->seq_len = B.total;
+    if (cudaMalloc(&h->d.seq64, B.total * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&h->d.seqm, B.total * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&h->d.seqe, B.total * sizeof(int)) != cudaSuccess)
+        return MS_ERR_ALLOC;
+    SeqSpec* dspec = nullptr;
+    const size_t chunk = 1 << 20;
+    if (cudaMalloc(&dspec, std::min(chunk, B.specs.size() + 1) * sizeof(SeqSpec)) != cudaSuccess) return MS_ERR_ALLOC;
+    for (size_t s0 = 0; s0 < B.specs.size(); s0 += chunk) {
+        size_t n = std::min(chunk, B.specs.size() - s0);
+        if ((rc = ms_check(h, cudaMemcpy(dspec, B.specs.data() + s0, n * sizeof(SeqSpec), cudaMemcpyHostToDevice)))) {
+            cudaFree(dspec);
+            return rc;
+        }
+        k_gen_seq<<<(int)((n + 127) / 128), 128>>>(dspec, (int)n, h->d.seq64);
+        if ((rc = ms_check(h, cudaGetLastError()))) { cudaFree(dspec); return rc; }
+    }
+    cudaFree(dspec);
+    k_split_seq<<<(int)((B.total + 255) / 256), 256>>>(h->d.seq64, h->d.seqm, h->d.seqe, B.total);
+    if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    return ms_check(h, cudaDeviceSynchronize());
+}
+
+// Translation part of the operator in the scaled basis: a~ (workspace) = T~ xs (written, not
+// accumulated).  Near pairs directly; with the FMM, far pairs through P2M, M2M, M2L, L2L, L2P.
+// `near` / `far` select the two halves (both for the full T).
+__global__ void k_zero_c(double2* a, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = make_double2(0, 0);
+}
+
+template <typename T>
+int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool far, cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const bool f32 = sizeof(T) == 4;
+    const int M = h->M, p = h->p, nc = h->nc;
+    int rc;
+    if (!near) {
+        // far field only: start from zero (sizeof(C) bytes per coefficient)
+        long long n = (long long)M * 2 * nc * nrhs * (long long)sizeof(C) / (long long)sizeof(double2);
+        k_zero_c<<<(int)((n + 255) / 256), 256, 0, st>>>((double2*)h->ws_a, n);
+        if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    }
+    for (int b = 0; b < 2 && near; ++b) {
+        TransArgs a{};
+        const DevList& nl = h->fmm.near[b];
+        a.dst_ptr = nl.ptr; a.task_src = nl.src; a.task_seq = nl.seq;
+        a.K = 2 * p; a.Pd = p; a.Ps = p;
+        a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
+        a.src = (const C*)xs + (long long)b * nc * nrhs; a.src_stride = 2LL * nc * nrhs;
+        a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;
+        a.as = h->d.expo + b * nc; a.as_stride = 2 * nc; a.ss = 1;
+        a.nrhs = nrhs; a.accumulate = 0;
+        if ((rc = ms_translate_launch(h, a, M, f32, st))) return rc;
+    }
+    const int L = h->fmm_levels;
+    if (!L || !far) return MS_OK;
+    FmmHost& F = h->fmm;
+    for (int b = 0; b < 2; ++b) {
+        auto mexp = [&](int lev) { return (C*)F.mexp[b][lev]; };
+        auto lexp = [&](int lev) { return (C*)F.lexp[b][lev]; };
+        auto ncl = [&](int lev) { return 2 * F.P[b][lev] + 1; };
+        // P2M
+        {
+            TransArgs a{};
+            a.dst_ptr = F.p2m[b].ptr; a.task_src = F.p2m[b].src; a.task_seq = F.p2m[b].seq;
+            a.Pd = F.P[b][L]; a.Ps = p; a.K = a.Pd + a.Ps;
+            a.dst = mexp(L); a.dst_stride = (long long)ncl(L) * nrhs;
+            a.src = (const C*)xs + (long long)b * nc * nrhs; a.src_stride = 2LL * nc * nrhs;
+            a.ad = F.expo[b][L]; a.ad_stride = 0; a.sd = -1;
+            a.as = h->d.expo + b * nc; a.as_stride = 2 * nc; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0;
+            if ((rc = ms_translate_launch(h, a, F.p2m[b].ndst, f32, st))) return rc;
+        }
+        // M2M upward
+        for (int lev = L - 1; lev >= 2; --lev) {
+            TransArgs a{};
+            a.dst_ptr = F.m2m[b][lev].ptr; a.task_src = F.m2m[b][lev].src; a.task_seq = F.m2m[b][lev].seq;
+            a.Pd = F.P[b][lev]; a.Ps = F.P[b][lev + 1]; a.K = a.Pd + a.Ps;
+            a.dst = mexp(lev); a.dst_stride = (long long)ncl(lev) * nrhs;
+            a.src = mexp(lev + 1); a.src_stride = (long long)ncl(lev + 1) * nrhs;
+            a.ad = F.expo[b][lev]; a.ad_stride = 0; a.sd = -1;
+            a.as = F.expo[b][lev + 1]; a.as_stride = 0; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0;
+            if ((rc = ms_translate_launch(h, a, F.m2m[b][lev].ndst, f32, st))) return rc;
+        }
+        // M2L and L2L downward
+        for (int lev = 2; lev <= L; ++lev) {
+            TransArgs a{};
+            a.dst_ptr = F.m2l[b][lev].ptr; a.task_src = F.m2l[b][lev].src; a.task_seq = F.m2l[b][lev].seq;
+            a.Pd = F.P[b][lev]; a.Ps = F.P[b][lev]; a.K = 2 * a.Pd;
+            a.dst = lexp(lev); a.dst_stride = (long long)ncl(lev) * nrhs;
+            a.src = mexp(lev); a.src_stride = (long long)ncl(lev) * nrhs;
+            a.ad = F.expo[b][lev]; a.ad_stride = 0; a.sd = 1;
+            a.as = F.expo[b][lev]; a.as_stride = 0; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0;
+            if ((rc = ms_translate_launch(h, a, F.m2l[b][lev].ndst, f32, st))) return rc;
+            if (lev > 2) {
+                TransArgs c{};
+                c.dst_ptr = F.l2l[b][lev].ptr; c.task_src = F.l2l[b][lev].src; c.task_seq = F.l2l[b][lev].seq;
+                c.Pd = F.P[b][lev]; c.Ps = F.P[b][lev - 1]; c.K = c.Pd + c.Ps;
+                c.dst = lexp(lev); c.dst_stride = (long long)ncl(lev) * nrhs;
+                c.src = lexp(lev - 1); c.src_stride = (long long)ncl(lev - 1) * nrhs;
+                c.ad = F.expo[b][lev]; c.ad_stride = 0; c.sd = 1;
+                c.as = F.expo[b][lev - 1]; c.as_stride = 0; c.ss = -1;
+                c.nrhs = nrhs; c.accumulate = 1;
+                if ((rc = ms_translate_launch(h, c, F.l2l[b][lev].ndst, f32, st))) return rc;
+            }
+        }
+        // L2P
+        {
+            TransArgs a{};
+            a.dst_ptr = F.l2p[b].ptr; a.task_src = F.l2p[b].src; a.task_seq = F.l2p[b].seq;
+            a.Pd = p; a.Ps = F.P[b][L]; a.K = a.Pd + a.Ps;
+            a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
+            a.src = lexp(L); a.src_stride = (long long)ncl(L) * nrhs;
+            a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;
+            a.as = F.expo[b][L]; a.as_stride = 0; a.ss = -1;
+            a.nrhs = nrhs; a.accumulate = 1;
+            if ((rc = ms_translate_launch(h, a, M, f32, st))) return rc;
+        }
+    }
+    return MS_OK;
+}
+
+template int ms_translate_scaled<double>(ms_handle*, const void*, int, bool, bool, cudaStream_t);
+template int ms_translate_scaled<float>(ms_handle*, const void*, int, bool, bool, cudaStream_t);
+
+// Expansion buffers for nrhs columns (called from the workspace allocator).
+int ms_fmm_workspace(ms_handle* h, int nrhs) {
+    FmmHost& F = h->fmm;
+    for (int b = 0; b < 2; ++b)
+        for (int lev = 0; lev <= 12; ++lev) {
+            if (F.mexp[b][lev]) cudaFree(F.mexp[b][lev]);
+            if (F.lexp[b][lev]) cudaFree(F.lexp[b][lev]);
+            F.mexp[b][lev] = F.lexp[b][lev] = nullptr;
+        }
+    for (int b = 0; b < 2; ++b)
+        for (int lev = 2; lev <= h->fmm_levels; ++lev) {
+            size_t n = (size_t)F.nbox[lev] * (2 * F.P[b][lev] + 1) * nrhs * sizeof(double2);
+            if (cudaMalloc(&F.mexp[b][lev], n) != cudaSuccess || cudaMalloc(&F.lexp[b][lev], n) != cudaSuccess)
+                return MS_ERR_ALLOC;
+            cudaMemset(F.mexp[b][lev], 0, n);
+            cudaMemset(F.lexp[b][lev], 0, n);
+        }
+    return MS_OK;
+}
+
+void ms_fmm_free(ms_handle* h) {
+    FmmHost& F = h->fmm;
+    auto fl = [](DevList& D) { cudaFree(D.ptr); cudaFree(D.src); cudaFree(D.seq); D = DevList{}; };
+    for (int b = 0; b < 2; ++b) {
+        fl(F.near[b]); fl(F.p2m[b]); fl(F.l2p[b]);
+        for (int lev = 0; lev <= 12; ++lev) {
+            fl(F.m2m[b][lev]); fl(F.m2l[b][lev]); fl(F.l2l[b][lev]);
+            cudaFree(F.expo[b][lev]); F.expo[b][lev] = nullptr;
+            cudaFree(F.mexp[b][lev]); cudaFree(F.lexp[b][lev]);
+            F.mexp[b][lev] = F.lexp[b][lev] = nullptr;
+        }
+    }
+    cudaFree(h->d.seq64); cudaFree(h->d.seqm); cudaFree(h->d.seqe);
+    h->d.seq64 = nullptr; h->d.seqm = nullptr; h->d.seqe = nullptr;
+}

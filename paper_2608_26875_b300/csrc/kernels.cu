@@ -1,0 +1,407 @@
+// Hot-path kernels of one mat-vec y = x - S (T + R) x, in the scaled basis.
+//
+// Scaled basis: every coefficient of particle m, wave b, order n carries an exact power-of-two
+// scale tau = 2^a, a = round(log2((k_b R_m / 2)^|n| / |n|!)).  Outgoing blocks are stored as
+// x~ = x / tau, local blocks as a~ = a * tau, so that the translation entries
+// tau_i H_{j-i}(k d) e^{i(j-i)theta} tau_j, the spectral factors and the scattering blocks
+// tau^-1 S tau^-1 all stay O(1) and fit FP32; in FP64 the scaling is exact.
+//
+// Kernels (one template per precision T = double or float):
+//   k_to_scaled / k_from_scaled  precision staging (row a1)
+//   (free-space translation, rows a2/a3, lives in fmm.cu)
+//   k_m2s                        multipole-to-Sommerfeld, split over source chunks (row a4, Sec. 5.4)
+//   k_reflect                    chunk reduction + 2x2 reflection per node (row a5, Sec. 3 / 5.2)
+//   k_s2l                        Sommerfeld-to-local (row a6, Sec. 5.3)
+//   k_sapply_disc / k_sapply_proto  scattering-matrix apply and combine (row a7, Sec. 4.2 mul2, 4.3)
+#include <algorithm>
+
+#include "bessel.cuh"
+#include "common.cuh"
+#include "handle.h"
+
+namespace {
+
+// ------------------------------------------------------------------ precision staging
+template <typename T>
+__global__ void k_to_scaled(const double2* __restrict__ x, typename CT<T>::c* __restrict__ xs,
+                            const int* __restrict__ expo, long long total, int nrhs) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int row = (int)(i / nrhs);
+    double s = pow2d(-expo[row]);
+    double2 v = x[i];
+    xs[i] = to_c<T>(make_double2(v.x * s, v.y * s));
+}
+
+// outgoing-type blocks: y = y~ 2^a (sign = +1); local-type blocks: a = a~ 2^-a (sign = -1)
+template <typename T>
+__global__ void k_from_scaled(const typename CT<T>::c* __restrict__ ys, double2* __restrict__ y,
+                              const int* __restrict__ expo, long long total, int nrhs, int sign) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int row = (int)(i / nrhs);
+    double s = pow2d(sign * expo[row]);
+    double2 v = to_d(ys[i]);
+    y[i] = make_double2(v.x * s, v.y * s);
+}
+
+// ------------------------------------------------------------------ multipole-to-Sommerfeld
+// part[chunk][b][q][r] = sum_{l in chunk} e^{s_b y_l - i xi_q x_l} sum_n Q_b(q,n) tau_{l,b,n} x~^l_{b,n,r}
+// with Q_b(q,n) = (-i)^n q_b^n / (i pi s_b) (pts1 / sed1 / sed2).  CTA = (b, tile of TQ nodes, chunk);
+// the generated factor F(q,l,n) is built in FP64 per source batch into shared memory.
+constexpr int M2S_TQ = 16;
+constexpr int M2S_LB = 4;
+constexpr int M2S_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(M2S_THREADS)
+k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
+      const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
+      const double2* __restrict__ sq, const double2* __restrict__ qpow, int M, int p, int NS, int nrhs,
+      int chunk_len) {
+    typedef typename CT<T>::c C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = 2 * p + 1;
+    C* F = reinterpret_cast<C*>(smem_raw);              // [TQ][LB][nc]
+    const int b = blockIdx.z;
+    const int q0 = blockIdx.x * M2S_TQ;
+    const int chunk = blockIdx.y;
+    const int l0 = chunk * chunk_len, l1 = min(M, l0 + chunk_len);
+    const int tq = threadIdx.x / 16, rl = threadIdx.x % 16;
+    const int q = q0 + tq;
+    constexpr int RMAX = 4;   // nrhs <= 64
+    C acc[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) acc[k] = mk((T)0, (T)0);
+
+    for (int lb = l0; lb < l1; lb += M2S_LB) {
+        const int nl = min(M2S_LB, l1 - lb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < M2S_TQ * nl * nc; e += blockDim.x) {
+            int n = e % nc, rest = e / nc;
+            int li = rest % nl, qi = rest / nl;
+            int qq_ = q0 + qi;
+            C val = mk((T)0, (T)0);
+            if (qq_ < NS) {
+                int l = lb + li;
+                double2 cl = centre[l];
+                double2 xi = node[qq_];
+                double2 s = sq[qq_ * 2 + b];
+                // s y_l - i xi x_l
+                double re = s.x * cl.y + xi.y * cl.x;
+                double im = s.y * cl.y - xi.x * cl.x;
+                double mag = exp(re);
+                double sn, cs;
+                sincos(im, &sn, &cs);
+                double2 E = make_double2(mag * cs, mag * sn);
+                double2 f = cmul(E, qpow[((size_t)b * NS + qq_) * nc + n]);
+                double sc = pow2d(expo[(l * 2 + b) * nc + n]);
+                val = to_c<T>(make_double2(f.x * sc, f.y * sc));
+            }
+            F[(qi * M2S_LB + li) * nc + n] = val;
+        }
+        __syncthreads();
+        if (q < NS) {
+            for (int li = 0; li < nl; ++li) {
+                const int l = lb + li;
+                const C* xl = xs + ((size_t)(l * 2 + b) * nc) * nrhs;
+                const C* f = F + (tq * M2S_LB + li) * nc;
+#pragma unroll
+                for (int k = 0; k < RMAX; ++k) {
+                    int r = rl + 16 * k;
+                    if (r < nrhs) {
+                        C s = acc[k];
+                        for (int n = 0; n < nc; ++n) cfma(s, f[n], xl[(size_t)n * nrhs + r]);
+                        acc[k] = s;
+                    }
+                }
+            }
+        }
+    }
+    if (q < NS) {
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            int r = rl + 16 * k;
+            if (r < nrhs) part[(((size_t)chunk * 2 + b) * NS + q) * nrhs + r] = to_d(acc[k]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reduce chunks + reflect
+// U_b(q,r) = sum_chunks part; D(q,r) = R(xi_q) U(q,r).  Output ud[b][q][r] holds D.
+__global__ void k_reflect(const double2* __restrict__ part, double2* __restrict__ ud,
+                          const double2* __restrict__ refl, int nchunks, int NS, int nrhs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NS * nrhs) return;
+    int q = i / nrhs, r = i % nrhs;
+    double2 up = make_double2(0, 0), us = make_double2(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        up = cadd(up, part[(((size_t)c * 2 + 0) * NS + q) * nrhs + r]);
+        us = cadd(us, part[(((size_t)c * 2 + 1) * NS + q) * nrhs + r]);
+    }
+    const double2* R = refl + (size_t)q * 4;
+    ud[(size_t)(0 * NS + q) * nrhs + r] = cadd(cmul(R[0], up), cmul(R[1], us));
+    ud[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(R[2], up), cmul(R[3], us));
+}
+
+// ------------------------------------------------------------------ Sommerfeld-to-local
+// a~^m_{b,n,r} (+)= tau_{m,b,n} sum_q e^{i xi_q x_m + s_b y_m} [i^n q_b^n W_q] D_b(q,r)  (ja / stm / eee1).
+// CTA = (target m, wave b); nodes in batches of QB with the generated factor in shared memory.
+constexpr int S2L_QB = 32;
+constexpr int S2L_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(S2L_THREADS)
+k_s2l(const double2* __restrict__ ud, typename CT<T>::c* __restrict__ as,
+      const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
+      const double2* __restrict__ sq, const double2* __restrict__ qpow, int p, int NS, int nrhs,
+      int accumulate) {
+    typedef typename CT<T>::c C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = 2 * p + 1;
+    C* G = reinterpret_cast<C*>(smem_raw);          // [QB][nc]
+    C* Ds = G + S2L_QB * nc;                        // [QB][nrhs]
+    const int m = blockIdx.x, b = blockIdx.y;
+    const double2 cm = centre[m];
+    const int nout = nc * nrhs;
+    constexpr int TMAX = 16;   // ceil(61*64/256): p <= 30, nrhs <= 64
+    C acc[TMAX];
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) acc[k] = mk((T)0, (T)0);
+
+    for (int qb = 0; qb < NS; qb += S2L_QB) {
+        const int nq = min(S2L_QB, NS - qb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
+            int n = e % nc, qi = e / nc;
+            int q = qb + qi;
+            double2 xi = node[q];
+            double2 s = sq[q * 2 + b];
+            // i xi x_m + s y_m
+            double re = -xi.y * cm.x + s.x * cm.y;
+            double im = xi.x * cm.x + s.y * cm.y;
+            double mag = exp(re);
+            double sn, cs;
+            sincos(im, &sn, &cs);
+            double2 g = cmul(make_double2(mag * cs, mag * sn), qpow[((size_t)b * NS + q) * nc + n]);
+            double sc = pow2d(expo[(m * 2 + b) * nc + n]);
+            G[qi * nc + n] = to_c<T>(make_double2(g.x * sc, g.y * sc));
+        }
+        for (int e = threadIdx.x; e < nq * nrhs; e += blockDim.x) {
+            int r = e % nrhs, qi = e / nrhs;
+            Ds[qi * nrhs + r] = to_c<T>(ud[((size_t)b * NS + qb + qi) * nrhs + r]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TMAX; ++k) {
+            int t = threadIdx.x + k * blockDim.x;
+            if (t < nout) {
+                int n = t / nrhs, r = t % nrhs;
+                C s = acc[k];
+                for (int qi = 0; qi < nq; ++qi) cfma(s, G[qi * nc + n], Ds[qi * nrhs + r]);
+                acc[k] = s;
+            }
+        }
+    }
+    C* out = as + ((size_t)(m * 2 + b) * nc) * nrhs;
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) {
+        int t = threadIdx.x + k * blockDim.x;
+        if (t < nout) out[t] = accumulate ? cadd(out[t], acc[k]) : acc[k];
+    }
+}
+
+// ------------------------------------------------------------------ scattering-matrix apply
+// y~ = (identity ? x~ : 0) - S~ a~ for disc particles: 2x2 per mode (Sec. 4.1).  With
+// negate = 0 the sign is + (plain S~ a~, used by the operator-parts view).
+template <typename T>
+__global__ void k_sapply_disc(const typename CT<T>::c* __restrict__ xs, const typename CT<T>::c* __restrict__ as,
+                              typename CT<T>::c* __restrict__ ys, const typename CT<T>::c* __restrict__ sd,
+                              const int* __restrict__ proto, int M, int nc, int nrhs, int identity,
+                              int apply_s) {
+    typedef typename CT<T>::c C;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)M * nc * nrhs;
+    if (i >= total) return;
+    int r = (int)(i % nrhs);
+    long long mn = i / nrhs;
+    int n = (int)(mn % nc), m = (int)(mn / nc);
+    if (proto[m] >= 0) return;
+    size_t ip = ((size_t)(m * 2 + 0) * nc + n) * nrhs + r;
+    size_t is = ((size_t)(m * 2 + 1) * nc + n) * nrhs + r;
+    C ap = as[ip], a2 = as[is];
+    C yp, y2;
+    if (apply_s) {
+        const C* S = sd + ((size_t)m * nc + n) * 4;
+        yp = cadd(cmul(S[0], ap), cmul(S[1], a2));
+        y2 = cadd(cmul(S[2], ap), cmul(S[3], a2));
+    } else {
+        yp = ap;
+        y2 = a2;
+    }
+    if (identity) {
+        ys[ip] = csub(xs[ip], yp);
+        ys[is] = csub(xs[is], y2);
+    } else {
+        ys[ip] = yp;
+        ys[is] = y2;
+    }
+}
+
+// Dense prototype particles (Sec. 4.3): S~_{(b,i),(b',j)} = 2^{-a_{m,b,i}} e^{-i (n_i - n_j) phi_m}
+// S_proto[(b,i),(b',j)] 2^{-a_{m,b',j}}, generated on the fly.  One CTA per prototype particle.
+template <typename T>
+__global__ void k_sapply_proto(const typename CT<T>::c* __restrict__ xs, const typename CT<T>::c* __restrict__ as,
+                               typename CT<T>::c* __restrict__ ys, const double2* __restrict__ sproto,
+                               const int* __restrict__ proto, const double* __restrict__ rot,
+                               const int* __restrict__ expo, int p, int nrhs, int identity, int apply_s) {
+    typedef typename CT<T>::c C;
+    const int m = blockIdx.x;
+    const int pi = proto[m];
+    if (pi < 0) return;
+    const int nc = 2 * p + 1, N2 = 2 * nc;
+    const double phi = rot[m];
+    const double2* S = sproto + (size_t)pi * N2 * N2;
+    const C* a = as + (size_t)m * N2 * nrhs;
+    for (int t = threadIdx.x; t < N2 * nrhs; t += blockDim.x) {
+        int row = t / nrhs, r = t % nrhs;
+        C y;
+        if (apply_s) {
+            int ni = row % nc - p;
+            int ai = expo[m * N2 + row];
+            C s = mk((T)0, (T)0);
+            for (int col = 0; col < N2; ++col) {
+                int nj = col % nc - p;
+                double sn, cs;
+                sincos(-(double)(ni - nj) * phi, &sn, &cs);
+                double2 v = cmul(S[(size_t)row * N2 + col], make_double2(cs, sn));
+                double sc = pow2d(-ai - expo[m * N2 + col]);
+                cfma(s, to_c<T>(make_double2(v.x * sc, v.y * sc)), a[(size_t)col * nrhs + r]);
+            }
+            y = s;
+        } else {
+            y = a[(size_t)row * nrhs + r];
+        }
+        size_t o = (size_t)m * N2 * nrhs + t;
+        ys[o] = identity ? csub(xs[o], y) : y;
+    }
+}
+
+template <typename T>
+__global__ void k_zero(typename CT<T>::c* a, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = mk((T)0, (T)0);
+}
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host launchers
+
+int ms_to_scaled(ms_handle* h, const void* x, void* xs, int nrhs, int prec, cudaStream_t st) {
+    long long total = (long long)h->M * 2 * h->nc * nrhs;
+    if (prec == MS_PREC_FP64)
+        k_to_scaled<double><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (double2*)xs, h->d.expo, total, nrhs);
+    else
+        k_to_scaled<float><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (float2*)xs, h->d.expo, total, nrhs);
+    return ms_check(h, cudaGetLastError());
+}
+
+int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st, bool local) {
+    long long total = (long long)h->M * 2 * h->nc * nrhs;
+    int sign = local ? -1 : 1;
+    if (prec == MS_PREC_FP64)
+        k_from_scaled<double><<<nblk(total, 256), 256, 0, st>>>((const double2*)ys, (double2*)y, h->d.expo, total, nrhs,
+                                                               sign);
+    else
+        k_from_scaled<float><<<nblk(total, 256), 256, 0, st>>>((const float2*)ys, (double2*)y, h->d.expo, total, nrhs,
+                                                              sign);
+    return ms_check(h, cudaGetLastError());
+}
+
+static int m2s_chunks(ms_handle* h) {
+    int chunks = (h->M + 63) / 64;
+    if (chunks > 64) chunks = 64;
+    return chunks;
+}
+
+// a~ (workspace) = (T~ + R~) xs for the parts selected (scaled basis); zero if none.
+template <typename T>
+int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const C* xs = (const C*)xs_;
+    C* as = (C*)h->ws_a;
+    const int M = h->M, p = h->p, nc = h->nc, NS = h->NS;
+    long long nall = (long long)M * 2 * nc * nrhs;
+    bool have = false;
+    if (parts & (MS_PART_T | MS_PART_T_NEAR | MS_PART_T_FAR)) {
+        bool near = (parts & (MS_PART_T | MS_PART_T_NEAR)) != 0;
+        bool far = (parts & (MS_PART_T | MS_PART_T_FAR)) != 0;
+        if (int rc = ms_translate_scaled<T>(h, xs_, nrhs, near, far, st)) return rc;
+        have = true;
+    }
+    if (parts & MS_PART_R) {
+        int chunks = m2s_chunks(h);
+        int chunk_len = (M + chunks - 1) / chunks;
+        chunks = (M + chunk_len - 1) / chunk_len;
+        dim3 g((NS + M2S_TQ - 1) / M2S_TQ, chunks, 2);
+        size_t smem = (size_t)M2S_TQ * M2S_LB * nc * sizeof(C);
+        cudaFuncSetAttribute(k_m2s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2s<T><<<g, M2S_THREADS, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, h->d.expo, h->d.node,
+                                               h->d.sq, h->d.qpow_m2s, M, p, NS, nrhs, chunk_len);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+        k_reflect<<<nblk((long long)NS * nrhs, 256), 256, 0, st>>>((const double2*)h->ws_part, (double2*)h->ws_u,
+                                                                   h->d.refl, chunks, NS, nrhs);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+        size_t smem2 = (size_t)S2L_QB * nc * sizeof(C) + (size_t)S2L_QB * nrhs * sizeof(C);
+        cudaFuncSetAttribute(k_s2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        k_s2l<T><<<dim3(M, 2), S2L_THREADS, smem2, st>>>((const double2*)h->ws_u, as, h->d.centre, h->d.expo,
+                                                         h->d.node, h->d.sq, h->d.qpow_s2l, p, NS, nrhs,
+                                                         have ? 1 : 0);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+        have = true;
+    }
+    if (!have) {
+        k_zero<T><<<nblk(nall, 256), 256, 0, st>>>(as, nall);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    }
+    return MS_OK;
+}
+
+// ys = [xs -] [S~] a~ with a~ the workspace (scaled basis).
+template <typename T>
+int ms_sapply_scaled(ms_handle* h, const void* xs_, void* ys_, int nrhs, bool identity, bool apply_s,
+                     cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const C* xs = (const C*)xs_;
+    C* ys = (C*)ys_;
+    const C* as = (const C*)h->ws_a;
+    const int M = h->M, p = h->p, nc = h->nc;
+    const C* sd = (const C*)(sizeof(T) == 8 ? (const void*)h->d.sdisc : (const void*)h->d.sdisc_f);
+    long long nd = (long long)M * nc * nrhs;
+    k_sapply_disc<T><<<nblk(nd, 256), 256, 0, st>>>(xs, as, ys, sd, h->d.proto, M, nc, nrhs, identity ? 1 : 0,
+                                                    apply_s ? 1 : 0);
+    if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    if (h->any_proto) {
+        k_sapply_proto<T><<<M, 256, 0, st>>>(xs, as, ys, h->d.sproto, h->d.proto, h->d.rot, h->d.expo, p, nrhs,
+                                             identity ? 1 : 0, apply_s ? 1 : 0);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    }
+    return MS_OK;
+}
+
+// ys = [xs -] [S~] (T~ + R~) xs for the parts selected (all in the scaled basis).
+template <typename T>
+int ms_apply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, int parts, bool identity, cudaStream_t st) {
+    int rc = ms_local_scaled<T>(h, xs, nrhs, parts, st);
+    if (rc) return rc;
+    return ms_sapply_scaled<T>(h, xs, ys, nrhs, identity, (parts & MS_PART_S) != 0, st);
+}
+
+template int ms_local_scaled<double>(ms_handle*, const void*, int, int, cudaStream_t);
+template int ms_local_scaled<float>(ms_handle*, const void*, int, int, cudaStream_t);
+template int ms_sapply_scaled<double>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t);
+template int ms_sapply_scaled<float>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t);
+template int ms_apply_scaled<double>(ms_handle*, const void*, void*, int, int, bool, cudaStream_t);
+template int ms_apply_scaled<float>(ms_handle*, const void*, void*, int, int, bool, cudaStream_t);

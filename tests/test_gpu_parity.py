@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances.  The FP64 path must match the oracle's mat-vec to round-off: relative l2 <= 1e-12
+and, element by element in the natural scaled norm |y_e| / tau_e with tau the order scale
+(k R / 2)^|n| / |n|!, within 1e-11 of the largest scaled entry.  Solutions: relative l2 <= 1e-10
+(FP64) and <= 1e-8 (FP32 inner solve with FP64 refinement), the targets of the method.  The FP32
+mat-vec itself is compared in the scaled norm at 2e-5 (single-precision operator entries and
+accumulation over up to ~10^3 terms).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_2608_26875_b300 as P  # noqa: E402
+
+
+def tau(wl):
+    """Order scale (k_b R_m / 2)^|n| / |n|! per (m, b, n): the natural size of outgoing coefficients."""
+    from oracle.media import Layered
+    L = Layered(wl.media, wl.omega)
+    n = np.abs(np.arange(-wl.p, wl.p + 1))
+    lg = np.array([math.lgamma(k + 1) for k in n])
+    out = np.empty((wl.M, 2, 2 * wl.p + 1))
+    for b, k in ((0, L.kp_l), (1, L.ks_l)):
+        out[:, b, :] = np.exp(n[None, :] * np.log(k * wl.radius[:, None] / 2) - lg[None, :])
+    return out
+
+
+def compare(got, want, wl, rel_l2, rel_el, targets=None):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    t = tau(wl)
+    if targets is not None:
+        t = t[list(targets)]
+    e = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert e <= rel_l2, f"relative l2 {e:.3e} > {rel_l2:.1e}"
+    sg = np.abs(got - want) / t[..., None]
+    sw = np.abs(want) / t[..., None]
+    el = sg.max() / sw.max()
+    assert el <= rel_el, f"scaled elementwise {el:.3e} > {rel_el:.1e}"
+    return e, el
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+CASES = [
+    # (seed, M, p, nrhs, omega)
+    (21, 1, 3, 1, 2.0),     # single particle: no pair, reflection self term only
+    (22, 2, 0, 1, 2.0),     # p = 0
+    (23, 5, 6, 3, 2.0),
+    (24, 12, 10, 37, 3.0),  # ragged nrhs
+    (25, 20, 8, 64, 4.0),   # full RHS block
+]
+
+
+@pytest.mark.parametrize("seed,M,p,nrhs,omega", CASES)
+def test_apply_fp64_matches_oracle(seed, M, p, nrhs, omega):
+    wl = syn.small_case(seed, M, p, omega=omega, nrhs=nrhs)
+    ref = system.Problem(wl)
+    x = syn.random_coeffs(seed + 7, M, p, nrhs)
+    want = ref.matvec(x)
+    s = P.Solver.from_workload(wl)
+    got = s.apply(dev(x)).cpu().numpy()
+    compare(got, want, wl, 1e-12, 1e-11)
+
+
+@pytest.mark.parametrize("parts", [P.MS_PART_T, P.MS_PART_R, P.MS_PART_T | P.MS_PART_S,
+                                   P.MS_PART_R | P.MS_PART_S, P.MS_PART_S])
+def test_operator_parts_fp64(parts):
+    wl = syn.small_case(31, 9, 7, omega=2.5, nrhs=5)
+    ref = system.Problem(wl)
+    x = syn.random_coeffs(32, wl.M, wl.p, 5)
+    a = np.zeros_like(x)
+    if parts & P.MS_PART_T:
+        a = a + ref.translate(x)
+    if parts & P.MS_PART_R:
+        a = a + ref.reflect(x)
+    want = ref.apply_S(a) if parts & P.MS_PART_S else a
+    got = P.Solver.from_workload(wl).operator(dev(x), parts).cpu().numpy()
+    if not np.any(want):
+        assert not np.any(got)
+        return
+    # local coefficients (no S) are large by 1/tau^2 relative to outgoing ones: compare in l2 only
+    e = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert e <= 1e-12
+
+
+def test_apply_fp32_matches_oracle_in_scaled_norm():
+    wl = syn.small_case(41, 16, 10, omega=3.0, nrhs=8)
+    ref = system.Problem(wl)
+    x = syn.random_coeffs(42, wl.M, wl.p, 8)
+    want = ref.matvec(x)
+    got = P.Solver.from_workload(wl).apply(dev(x), prec=P.MS_PREC_FP32).cpu().numpy()
+    t = tau(wl)[..., None]
+    el = (np.abs(got - want) / t).max() / (np.abs(want) / t).max()
+    assert el <= 2e-5
+
+
+def test_rhs_matches_oracle():
+    wl = syn.small_case(51, 10, 8, omega=2.0, nrhs=6)
+    ref = system.Problem(wl)
+    want = ref.rhs(wl.inc_kind, wl.inc_angle)
+    got = P.Solver.from_workload(wl).rhs(wl.inc_kind, wl.inc_angle).cpu().numpy()
+    compare(got, want, wl, 1e-12, 1e-11)
+
+
+def test_prototype_particles_dense_scattering_matrix():
+    """Dense prototype tables with per-particle rotation (Sec. 4.3), mixed with closed-form discs."""
+    wl = syn.small_case(61, 8, 5, omega=2.0, nrhs=3)
+    ref0 = system.Problem(wl)
+    rng = np.random.default_rng(62)
+    nc = 2 * wl.p + 1
+    protos = []
+    for q in range(2):
+        base = ref0.dense_S(q)     # a physical disc matrix, perturbed into a dense table
+        pert = (rng.standard_normal(base.shape) + 1j * rng.standard_normal(base.shape)) * 1e-3
+        nn = np.tile(np.abs(np.arange(-wl.p, wl.p + 1)), 2)
+        protos.append(base + pert * np.outer(0.3 ** nn, 0.3 ** nn))
+    protos = np.stack(protos)
+    pidx = np.array([0, 1, -1, 0, 1, -1, 0, -1])
+    ref = system.Problem(wl, proto_S=protos, proto_index=pidx)
+    x = syn.random_coeffs(63, wl.M, wl.p, 3)
+    want = ref.matvec(x)
+    s = P.Solver(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, wl.p, proto=pidx, rotation=wl.rotation,
+                 proto_S=protos)
+    got = s.apply(dev(x)).cpu().numpy()
+    compare(got, want, wl, 1e-12, 1e-11)
+    assert nc == protos.shape[1] // 2
+
+
+def test_config1_solve_fields_fp64():
+    """16 rigid discs, p = 10, one P-wave at 30 degrees, GMRES tol 1e-12, 256 receivers."""
+    wl = syn.config1()
+    ref = system.Problem(wl)
+    b = ref.rhs(wl.inc_kind, wl.inc_angle)
+    want, _ = ref.solve_gmres(b, tol=1e-13)
+    s = P.Solver.from_workload(wl)
+    got, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-12, prec=P.MS_PREC_FP64)
+    assert info["status"] == 0 and info["max_rel_residual"] <= 1e-12
+    e = np.linalg.norm(got.cpu().numpy() - want) / np.linalg.norm(want)
+    assert e <= 1e-10, e
+    u = s.fields(got, wl.receivers).cpu().numpy()
+    uw = ref.scattered_field(want, wl.receivers[:, 0], wl.receivers[:, 1])
+    eu = np.linalg.norm(u - uw) / np.linalg.norm(uw)
+    assert eu <= 1e-10, eu
+
+
+def test_config1_mixed_precision_solve():
+    wl = syn.config1()
+    ref = system.Problem(wl)
+    b = ref.rhs(wl.inc_kind, wl.inc_angle)
+    want, _ = ref.solve_gmres(b, tol=1e-13)
+    s = P.Solver.from_workload(wl)
+    got, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP32)
+    assert info["status"] == 0 and info["refinements"] >= 1
+    e = np.linalg.norm(got.cpu().numpy() - want) / np.linalg.norm(want)
+    assert e <= 1e-8, e
+
+
+def test_multi_rhs_solve_matches_oracle():
+    wl = syn.small_case(71, 10, 8, omega=3.0, nrhs=5)
+    ref = system.Problem(wl)
+    want, _ = ref.solve_gmres(ref.rhs(wl.inc_kind, wl.inc_angle), tol=1e-13)
+    s = P.Solver.from_workload(wl)
+    for prec, tol, bound in ((P.MS_PREC_FP64, 1e-12, 1e-10), (P.MS_PREC_FP32, 1e-10, 1e-8)):
+        got, info = s.solve(wl.inc_kind, wl.inc_angle, tol=tol, prec=prec)
+        assert info["status"] == 0
+        e = np.linalg.norm(got.cpu().numpy() - want) / np.linalg.norm(want)
+        assert e <= bound, (prec, e)
+
+
+def test_receiver_inside_is_rejected():
+    wl = syn.config1()
+    s = P.Solver.from_workload(wl)
+    g = torch.zeros((wl.M, 2, wl.nc, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(P.MsError) as e:
+        s.fields(g, wl.centres[:2])
+    assert e.value.status == P._native.MS_ERR_RECEIVER_INSIDE
+
+
+def test_config2_apply_sampled_targets():
+    """1000 particles, p = 16, omega = 4: the full-size mat-vec compared on sampled targets."""
+    wl = syn.config2()
+    x = syn.random_coeffs(81, wl.M, wl.p, 1)
+    s = P.Solver.from_workload(wl)
+    got = s.apply(dev(x)).cpu().numpy()
+    ref = system.Problem(wl)
+    targets = [0, 1, 137, 500, 998, 999]
+    want = ref.matvec(x, targets=targets)
+    compare(got[targets], want, wl, 1e-12, 1e-11, targets=targets)
+
+
+# --------------------------------------------------------------------- fast multipole far field
+def test_fmm_matches_direct_sum_on_sampled_targets():
+    """3000 particles with the quadtree FMM (row a3) against the oracle's direct Graf sum."""
+    wl = syn.config3(M=3000, nrhs=4)
+    x = syn.random_coeffs(91, wl.M, wl.p, 4)
+    s = P.Solver.from_workload(wl)
+    got = s.operator(dev(x), P.MS_PART_T | P.MS_PART_S).cpu().numpy()
+    ref = system.Problem(wl)
+    targets = [0, 17, 1500, 2999]
+    want = ref.apply_S(ref.translate(x, targets=targets), targets=targets)
+    compare(got[targets], want, wl, 1e-11, 1e-11, targets=targets)
+
+
+@pytest.mark.parametrize("prec,tol", [(P.MS_PREC_FP64, 1e-11), (P.MS_PREC_FP32, 2e-5)])
+def test_fmm_matches_gpu_direct_everywhere(prec, tol):
+    """FMM operator vs the direct all-pairs GPU sum (itself pinned to the oracle) on every target."""
+    wl = syn.config3(M=2500, nrhs=8)
+    x = dev(syn.random_coeffs(92, wl.M, wl.p, 8))
+    f = P.Solver.from_workload(wl).apply(x, prec=prec).cpu().numpy()
+    d = P.Solver.from_workload(wl, use_fmm=False).apply(x, prec=P.MS_PREC_FP64).cpu().numpy()
+    t = tau(wl)[..., None]
+    el = (np.abs(f - d) / t).max() / (np.abs(d) / t).max()
+    assert el <= tol, el
