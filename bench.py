@@ -282,6 +282,28 @@ def launches_per_step(solver):
     return 2 + 2 + fmm + 3 + 1
 
 
+def run_profile(args):
+    """Small case for ncu: M particles at the bench's density, 64 columns, `--part` of the operator
+    applied `--steps` times (near: direct near-pair sum; far: FMM far field; refl: spectral part;
+    all: the whole mat-vec)."""
+    import torch
+
+    import paper_2608_26875_b300 as P
+    import synthetic as syn
+    wl = syn.config3(M=args.M, nrhs=64)
+    prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
+    s = P.Solver.from_workload(wl)
+    x = torch.as_tensor(syn.random_coeffs(5, wl.M, wl.p, 64), device="cuda")
+    parts = {"near": P.MS_PART_T_NEAR, "far": P.MS_PART_T_FAR, "refl": P.MS_PART_R | P.MS_PART_S}
+    for _ in range(args.steps):
+        if args.part == "all":
+            s.apply(x, prec=prec)
+        else:
+            s.operator(x, parts[args.part], prec=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.part, "M": wl.M, "near_pairs": s.near_pairs, "fmm_levels": s.fmm_levels}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,8 +312,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small case for ncu (see run_profile)")
+    ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
+    ap.add_argument("--M", type=int, default=2500)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -151,3 +151,4 @@ extern "C" int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const do
                                                           h->d.wq, h->d.sq, (double2*)u, h->NS, nrhs, R);
     return ms_check(h, cudaGetLastError());
 }
+

@@ -511,6 +511,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
 
     // ---------------------------------------------------------- sequences on the device
     h->seq_len = B.total;
+    if (B.total == 0) return MS_OK;   // a single particle and no FMM: nothing to translate
     if (cudaMalloc(&h->d.seq64, B.total * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&h->d.seqm, B.total * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&h->d.seqe, B.total * sizeof(int)) != cudaSuccess)

@@ -4,10 +4,9 @@
 // Gram-Schmidt applied twice (CGS2) with FP64 accumulation of every inner product, whatever the
 // vector precision.  The small Hessenberg / Givens work runs on the host in FP64.
 //
-// MS_PREC_FP64: restarted GMRES on the unscaled FP64 system (residual in the ABI basis).
-// MS_PREC_FP32: iterative refinement.  The outer loop keeps x and r = b - A x in FP64 (operator
-// applied in FP64); each step solves A d = r approximately with FP32 GMRES in the scaled basis,
-// then x += d.
+// Both precisions use iterative refinement: the outer loop keeps x and r = b - A x in FP64 in
+// the ABI basis; each step solves the diagonally scaled system for the correction with
+// restarted GMRES in FP64 (MS_PREC_FP64, inner tolerance 1e-7) or FP32 (MS_PREC_FP32, 1e-5).
 #include <math.h>
 
 #include <chrono>
@@ -235,7 +234,7 @@ int gmres(Krylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x,
         std::fill(g.begin(), g.end(), cd(0));
         std::fill(H.begin(), H.end(), cd(0));
         for (int r = 0; r < nrhs; ++r) {
-            g[r] = done[r] ? 0.0 : beta[r];
+            g[(size_t)r * (m + 1)] = done[r] ? 0.0 : beta[r];   // g_0 of column r
             kcol[r] = 0;
         }
         int j = 0;
@@ -335,56 +334,78 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
             return r2;
         return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st);
     };
-    if (prec == MS_PREC_FP64) {
-        Krylov<double> K{h, st, N, nrhs, h->opt.restart};
-        if ((rc = K.init())) { cudaFree(b); return rc; }
-        rc = gmres<double>(K, op64, b, x, tol, h->opt.max_iters, iters, matvecs, relres);
-    } else {
-        // iterative refinement: FP64 residual, FP32 scaled inner GMRES
-        Krylov<double> K64{h, st, N, nrhs, 1};
-        Krylov<float> K32{h, st, N, nrhs, h->opt.restart};
-        double2* r = nullptr;
-        float2 *rs = nullptr, *ds = nullptr;
-        if ((rc = K64.init()) || (rc = K32.init()) || (rc = ms_check(h, cudaMalloc(&r, tot * sizeof(double2)))) ||
-            (rc = ms_check(h, cudaMalloc(&rs, tot * sizeof(float2)))) ||
-            (rc = ms_check(h, cudaMalloc(&ds, tot * sizeof(float2))))) {
-            cudaFree(b); cudaFree(r); cudaFree(rs); cudaFree(ds);
-            return rc ? rc : MS_ERR_ALLOC;
-        }
-        auto op32 = [&](const float2* in, float2* out) -> int {
-            return ms_apply_scaled<float>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
-        };
-        std::vector<double> bn, rn;
-        rc = K64.norms(b, bn);
-        const double inner_tol = 1e-5;
-        const int max_ref = 30;
-        int left = h->opt.max_iters;
-        while (!rc) {
-            // r = b - A x in FP64
-            if ((rc = op64(x, K64.w))) break;
-            ++matvecs;
-            k_sub<<<nb(tot, 256), 256, 0, st>>>(b, K64.w, r, tot);
-            if ((rc = K64.norms(r, rn))) break;
-            bool all = true;
-            relres.assign(nrhs, 0.0);
-            for (int c = 0; c < nrhs; ++c) {
-                if (!std::isfinite(rn[c])) { rc = MS_ERR_NONFINITE; break; }
-                relres[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
-                all = all && relres[c] <= tol;
-            }
-            if (rc || all || refinements >= max_ref || left <= 0) break;
-            k_scale_down_f<<<nb(tot, 256), 256, 0, st>>>(r, rs, h->d.expo, tot, nrhs);
-            if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * sizeof(float2), st)))) break;
-            int it = 0;
-            std::vector<double> inner_res;
-            if ((rc = gmres<float>(K32, op32, rs, ds, inner_tol, left, it, matvecs, inner_res))) break;
-            iters += it;
-            left -= it;
-            k_add_up_f<<<nb(tot, 256), 256, 0, st>>>(x, ds, h->d.expo, tot, nrhs);
-            ++refinements;
-        }
-        cudaFree(r); cudaFree(rs); cudaFree(ds);
+    // Iterative refinement.  The outer loop keeps x and r = b - A x in FP64 in the ABI basis, so
+    // the tolerance means what the caller reads.  Each step solves the diagonally scaled system
+    // D^-1 A D d~ = D^-1 r (D = diag(2^a), condition numbers many orders below A's) by GMRES in
+    // the inner precision, then x += D d~.
+    Krylov<double> K64{h, st, N, nrhs, 1};
+    double2* r = nullptr;
+    void *rs = nullptr, *ds = nullptr;
+    const size_t esz = prec == MS_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    if ((rc = K64.init()) || (rc = ms_check(h, cudaMalloc(&r, tot * sizeof(double2)))) ||
+        (rc = ms_check(h, cudaMalloc(&rs, tot * esz))) || (rc = ms_check(h, cudaMalloc(&ds, tot * esz)))) {
+        cudaFree(b); cudaFree(r); cudaFree(rs); cudaFree(ds);
+        return rc ? rc : MS_ERR_ALLOC;
     }
+    Krylov<double>* K64i = nullptr;
+    Krylov<float>* K32 = nullptr;
+    if (prec == MS_PREC_FP64) {
+        K64i = new Krylov<double>{h, st, N, nrhs, h->opt.restart};
+        rc = K64i->init();
+    } else {
+        K32 = new Krylov<float>{h, st, N, nrhs, h->opt.restart};
+        rc = K32->init();
+    }
+    auto op32 = [&](const float2* in, float2* out) -> int {
+        return ms_apply_scaled<float>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+    };
+    auto op64s = [&](const double2* in, double2* out) -> int {
+        return ms_apply_scaled<double>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+    };
+    std::vector<double> bn, rn;
+    if (!rc) rc = K64.norms(b, bn);
+    const double inner_tol = prec == MS_PREC_FP64 ? 1e-7 : 1e-5;
+    const int max_ref = 40;
+    int left = h->opt.max_iters;
+    while (!rc) {
+        if ((rc = op64(x, K64.w))) break;
+        ++matvecs;
+        k_sub<<<nb(tot, 256), 256, 0, st>>>(b, K64.w, r, tot);
+        if ((rc = K64.norms(r, rn))) break;
+        bool all = true;
+        relres.assign(nrhs, 0.0);
+        for (int c = 0; c < nrhs; ++c) {
+            if (!std::isfinite(rn[c])) { rc = MS_ERR_NONFINITE; break; }
+            relres[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+            all = all && relres[c] <= tol;
+        }
+        if (rc || all || refinements >= max_ref || left <= 0) break;
+        int it = 0;
+        std::vector<double> inner_res;
+        if (prec == MS_PREC_FP64) {
+            if ((rc = ms_to_scaled(h, r, rs, nrhs, MS_PREC_FP64, st))) break;
+            if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
+            if ((rc = gmres<double>(*K64i, op64s, (const double2*)rs, (double2*)ds, inner_tol, left, it, matvecs,
+                                    inner_res)))
+                break;
+            if ((rc = ms_from_scaled(h, ds, K64.w, nrhs, MS_PREC_FP64, st))) break;
+            std::vector<cd> one(nrhs, cd(1.0, 0.0));
+            if ((rc = K64.update(K64.w, 1, x, one, -1.0))) break;       // x += D d~
+        } else {
+            k_scale_down_f<<<nb(tot, 256), 256, 0, st>>>(r, (float2*)rs, h->d.expo, tot, nrhs);
+            if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
+            if ((rc = gmres<float>(*K32, op32, (const float2*)rs, (float2*)ds, inner_tol, left, it, matvecs,
+                                   inner_res)))
+                break;
+            k_add_up_f<<<nb(tot, 256), 256, 0, st>>>(x, (const float2*)ds, h->d.expo, tot, nrhs);
+        }
+        iters += it;
+        left -= it;
+        ++refinements;
+    }
+    delete K64i;
+    delete K32;
+    cudaFree(r); cudaFree(rs); cudaFree(ds);
     cudaStreamSynchronize(st);
     cudaFree(b);
     double worst = 0;
