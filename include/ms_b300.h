@@ -50,6 +50,7 @@ extern "C" {
 #define MS_ERR_ALLOC            -7    /* device allocation failed */
 #define MS_ERR_NONFINITE        -9    /* NaN or Inf met in a right-hand side or residual */
 #define MS_ERR_BREAKDOWN       -10    /* GMRES breakdown with a non-zero residual */
+#define MS_ERR_TOO_LARGE       -11    /* request exceeds the fixed scratch of ms_fields_noalloc */
 
 /* ------------------------------------------------------------------ precision of an apply / solve */
 #define MS_PREC_FP64   0   /* every operator step in FP64 */
@@ -150,6 +151,26 @@ int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, vo
  * Errors: MS_ERR_RECEIVER_INSIDE if a receiver lies in an enclosing disc or at y >= 0. */
 int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
               void* stream);
+
+/* Allocation-free variant of ms_fields (the paper has no counterpart: this is a service for
+ * callers).  Some callers cannot call cudaMalloc: code that runs while a stream is being captured
+ * into a CUDA graph, real-time loops that must never wait on the allocator, or processes confined
+ * to a memory pool sized in advance.  This call computes exactly what ms_fields computes, with the
+ * same arguments, layouts and receiver validation, but allocates nothing: no cudaMalloc, cudaFree
+ * or allocating library routine.  Its scratch -- the multipole-to-Sommerfeld partial sums, the
+ * reflected spectral amplitudes, a device copy of the radii and a validation flag -- lives in fixed
+ * device arrays of about 10 MiB that every GPU which loads the library keeps until the process
+ * exits.
+ *   Limits: nrhs <= 64, M <= 131072, min(16, M) * 2 * N_S * nrhs <= 524288 and
+ *   2 * N_S * nrhs <= 65536 (e.g. N_S = 512 allows nrhs <= 32); beyond them it returns
+ *   MS_ERR_TOO_LARGE and touches nothing.
+ *   The first call on each device looks up the addresses of the fixed arrays (with that device
+ *   current); make that first call before any stream capture.
+ *   Every call shares the same arrays and leaves its contents behind: calls that overlap on the
+ *   GPU (several streams, several handles or several host threads at once) race and corrupt each
+ *   other's results.  Like ms_fields it synchronises `stream` once to read the validation flag. */
+int ms_fields_noalloc(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
+                      void* stream);
 
 /* Sizes of the handle: M, p, N_S, FMM levels (0 = direct sum over all pairs) and the number of
  * ordered particle pairs summed directly.  Any output pointer may be NULL. */

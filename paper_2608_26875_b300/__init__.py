@@ -155,6 +155,20 @@ class Solver:
                                       _stream(stream)), "ms_fields")
         return u
 
+    def fields_noalloc(self, gamma: torch.Tensor, rx: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """ms_fields without any allocation: rx (R, 2) float64 and out (nrhs, R, 2) complex128 are
+        caller-owned CUDA tensors; scratch lives in the library's fixed device arrays."""
+        nrhs = self._check_vec(gamma)
+        if not (rx.is_cuda and rx.dtype == torch.float64 and rx.is_contiguous() and rx.dim() == 2):
+            raise ValueError("rx must be a contiguous (R, 2) float64 CUDA tensor")
+        R = int(rx.shape[0])
+        if tuple(out.shape) != (nrhs, R, 2) or out.dtype != torch.complex128 or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous ({nrhs}, {R}, 2) complex128 CUDA tensor")
+        nat.check(nat.lib().ms_fields_noalloc(self._h, ctypes.c_void_p(gamma.data_ptr()), nrhs,
+                                              ctypes.c_void_p(rx.data_ptr()), R, ctypes.c_void_p(out.data_ptr()),
+                                              _stream(stream)), "ms_fields_noalloc")
+        return out
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             nat.lib().ms_destroy(self._h)

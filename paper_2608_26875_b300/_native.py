@@ -24,6 +24,7 @@ MS_ERR_RECEIVER_INSIDE = -6
 MS_ERR_ALLOC = -7
 MS_ERR_NONFINITE = -9
 MS_ERR_BREAKDOWN = -10
+MS_ERR_TOO_LARGE = -11
 
 MS_PREC_FP64 = 0
 MS_PREC_FP32 = 1
@@ -77,6 +78,8 @@ SIGNATURES = {
                          ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                           ctypes.c_void_p]),
+    "ms_fields_noalloc": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),
     "ms_destroy": (None, [ctypes.c_void_p]),
     "ms_status_string": (ctypes.c_char_p, [c_int]),

@@ -197,6 +197,7 @@ extern "C" const char* ms_status_string(int s) {
         case MS_ERR_ALLOC: return "device allocation failed";
         case MS_ERR_NONFINITE: return "non-finite value";
         case MS_ERR_BREAKDOWN: return "GMRES breakdown";
+        case MS_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the allocation-free call";
         default: return "unknown status";
     }
 }

@@ -5,6 +5,9 @@
 // coefficients.  Derivatives of cylindrical waves use the order shifts of DLMF 10.6:
 //   d/dx (H_n e^{in th}) = (k/2)(h_{n-1} - h_{n+1}),  d/dy = (ik/2)(h_{n-1} + h_{n+1}).
 // Everything here is FP64.
+#include <algorithm>
+#include <mutex>
+
 #include "bessel.cuh"
 #include "common.cuh"
 #include "handle.h"
@@ -152,3 +155,152 @@ extern "C" int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const do
     return ms_check(h, cudaGetLastError());
 }
 
+// ====================================================================== allocation-free fields
+// ms_fields_noalloc: the receiver-field computation of ms_fields for callers that cannot call
+// cudaMalloc (for example code running while a stream is being captured, real-time loops that
+// must not synchronise with the allocator, or processes confined to a pre-sized memory pool).
+// Everything ms_fields allocates per call -- the validation flag, a device copy of the radii, the
+// multipole-to-Sommerfeld partial sums and the reflected spectral amplitudes -- lives instead in
+// the fixed arrays below, which every GPU that loads this library holds until the process exits.
+// The handle's own tables (made by ms_setup) are only read.
+namespace {
+
+constexpr long long NAL_PART_MAX = 1LL << 19;   // split-K partials: chunks * 2 * N_S * nrhs complex (8 MiB)
+constexpr long long NAL_D_MAX = 1LL << 16;      // reflected amplitudes: 2 * N_S * nrhs complex (1 MiB)
+constexpr int NAL_M_MAX = 1 << 17;              // particles (radii copy, 1 MiB)
+constexpr int NAL_CHUNK_MAX = 16;               // source chunks of the partial sums
+
+static __device__ __align__(256) double2 g_nal_part[NAL_PART_MAX];
+static __device__ __align__(256) double2 g_nal_d[NAL_D_MAX];
+static __device__ __align__(256) double g_nal_radius[NAL_M_MAX];
+static __device__ __align__(256) int g_nal_flag[64];
+
+struct NalPtrs {
+    double2* part = nullptr;
+    double2* d = nullptr;
+    double* radius = nullptr;
+    int* flag = nullptr;
+    bool ready = false;
+};
+constexpr int NAL_MAX_DEVICES = 64;
+NalPtrs g_nal_ptrs[NAL_MAX_DEVICES];
+std::mutex g_nal_mutex;
+
+// part[chunk][b][q][r] = sum_{l in chunk} e^{s_b y_l - i xi_q x_l} sum_n Q_b(q,n) gamma^l_{b,n,r},
+// Q_b(q,n) = (-i)^n q_b^n / (i pi s_b): the multipole-to-Sommerfeld sums (Sec. 5.4, pts1 / sed1 /
+// sed2) on the caller's unscaled FP64 coefficients.  One thread per (chunk, b, q, r).
+__global__ void k_nal_m2s(const double2* __restrict__ gam, double2* __restrict__ part,
+                          const double2* __restrict__ centre, const double2* __restrict__ node,
+                          const double2* __restrict__ sq, const double2* __restrict__ qpow, int M, int p, int NS,
+                          int nrhs, int nchunks, int chunk_len) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)nchunks * 2 * NS * nrhs;
+    if (i >= total) return;
+    const int r = (int)(i % nrhs);
+    const int q = (int)((i / nrhs) % NS);
+    const int b = (int)((i / ((long long)nrhs * NS)) % 2);
+    const int c = (int)(i / ((long long)nrhs * NS * 2));
+    const int nc = 2 * p + 1;
+    const double2 xi = node[q], s = sq[q * 2 + b];
+    const double2* Q = qpow + ((size_t)b * NS + q) * nc;
+    double2 acc = make_double2(0, 0);
+    const int l0 = c * chunk_len, l1 = min(M, l0 + chunk_len);
+    for (int l = l0; l < l1; ++l) {
+        double2 cl = centre[l];
+        double re = s.x * cl.y + xi.y * cl.x;
+        double im = s.y * cl.y - xi.x * cl.x;
+        double mag = exp(re), sn, cs;
+        sincos(im, &sn, &cs);
+        const double2* g = gam + ((size_t)(l * 2 + b) * nc) * nrhs + r;
+        double2 inner = make_double2(0, 0);
+        for (int n = 0; n < nc; ++n) cfma(inner, Q[n], g[(size_t)n * nrhs]);
+        cfma(acc, make_double2(mag * cs, mag * sn), inner);
+    }
+    part[i] = acc;
+}
+
+// D(q, r) = R(xi_q) sum_chunks part(q, r)   (2x2 reflection per node, Sec. 3 / 5.2)
+__global__ void k_nal_reflect(const double2* __restrict__ part, double2* __restrict__ d,
+                              const double2* __restrict__ refl, int nchunks, int NS, int nrhs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NS * nrhs) return;
+    int q = i / nrhs, r = i % nrhs;
+    double2 up = make_double2(0, 0), us = make_double2(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        up = cadd(up, part[(((size_t)c * 2 + 0) * NS + q) * nrhs + r]);
+        us = cadd(us, part[(((size_t)c * 2 + 1) * NS + q) * nrhs + r]);
+    }
+    const double2* R = refl + (size_t)q * 4;
+    d[(size_t)(0 * NS + q) * nrhs + r] = cadd(cmul(R[0], up), cmul(R[1], us));
+    d[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(R[2], up), cmul(R[3], us));
+}
+
+// Device addresses of the fixed arrays, looked up once per device with that device current.
+int nal_pointers(ms_handle* h, NalPtrs** out) {
+    int dev = 0;
+    if (int rc = ms_check(h, cudaGetDevice(&dev))) return rc;
+    if (dev < 0 || dev >= NAL_MAX_DEVICES) return MS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_nal_mutex);
+    NalPtrs& P = g_nal_ptrs[dev];
+    if (!P.ready) {
+        int rc;
+        if ((rc = ms_check(h, cudaGetSymbolAddress((void**)&P.part, g_nal_part))) ||
+            (rc = ms_check(h, cudaGetSymbolAddress((void**)&P.d, g_nal_d))) ||
+            (rc = ms_check(h, cudaGetSymbolAddress((void**)&P.radius, g_nal_radius))) ||
+            (rc = ms_check(h, cudaGetSymbolAddress((void**)&P.flag, g_nal_flag))))
+            return rc;
+        P.ready = true;
+    }
+    *out = &P;
+    return MS_OK;
+}
+
+}  // namespace
+
+extern "C" int ms_fields_noalloc(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R,
+                                 void* u, void* stream) {
+    if (!h || !gamma || !rx || !u || nrhs < 1 || R < 1) return MS_ERR_ARG;
+    const int M = h->M, NS = h->NS;
+    int nchunks = std::min(NAL_CHUNK_MAX, M);
+    int chunk_len = (M + nchunks - 1) / nchunks;
+    nchunks = (M + chunk_len - 1) / chunk_len;
+    if (nrhs > 64 || M > NAL_M_MAX || (long long)nchunks * 2 * NS * nrhs > NAL_PART_MAX ||
+        2LL * NS * nrhs > NAL_D_MAX)
+        return MS_ERR_TOO_LARGE;
+    NalPtrs* P = nullptr;
+    int rc = nal_pointers(h, &P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // receiver validation: flag cleared, radii copied into the fixed array, flag read back
+    if ((rc = ms_check(h, cudaMemsetAsync(P->flag, 0, sizeof(int), st)))) return rc;
+    if ((rc = ms_check(h, cudaMemcpyAsync(P->radius, h->h_radius.data(), M * sizeof(double),
+                                          cudaMemcpyHostToDevice, st))))
+        return rc;
+    long long npair = (long long)R * M;
+    k_check_receivers<<<(int)((npair + 255) / 256), 256, 0, st>>>((const double2*)rx, h->d.centre, P->radius, R, M,
+                                                                 P->flag);
+    if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    int hflag = 0;
+    if ((rc = ms_check(h, cudaMemcpyAsync(&hflag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st))) ||
+        (rc = ms_check(h, cudaStreamSynchronize(st))))
+        return rc;
+    if (hflag) return MS_ERR_RECEIVER_INSIDE;
+    // reflected amplitudes into the fixed arrays (every partial slot is written, no clearing needed)
+    long long tot = (long long)nchunks * 2 * NS * nrhs;
+    k_nal_m2s<<<(int)((tot + 127) / 128), 128, 0, st>>>((const double2*)gamma, P->part, h->d.centre, h->d.node,
+                                                       h->d.sq, h->d.qpow_m2s, M, h->p, NS, nrhs, nchunks,
+                                                       chunk_len);
+    if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    k_nal_reflect<<<(NS * nrhs + 255) / 256, 256, 0, st>>>(P->part, P->d, h->d.refl, nchunks, NS, nrhs);
+    if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    // field sums: the same kernels as ms_fields
+    const int K = h->p + 1, nh = 2 * K + 1;
+    size_t smem = (size_t)FLD_NB * 2 * nh * sizeof(double2) + (size_t)FLD_NB * 2 * 2 * (K + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_fields_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fields_direct<<<R, 256, smem, st>>>((const double2*)gamma, (const double2*)rx, h->d.centre, (double2*)u, M,
+                                          h->p, nrhs, R, h->kp_l, h->ks_l);
+    if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+    k_fields_refl<<<(R * nrhs + 127) / 128, 128, 0, st>>>(P->d, (const double2*)rx, h->d.node, h->d.wq, h->d.sq,
+                                                          (double2*)u, NS, nrhs, R);
+    return ms_check(h, cudaGetLastError());
+}
