@@ -107,10 +107,11 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(wl, targets: int, nrhs: int):
-    """Time the FP64 oracle on `targets` target particles of the direct translation sum and the
-    full spectral (multipole-to-Sommerfeld, reflection, Sommerfeld-to-local) part for `nrhs`
-    columns; extrapolate to one full 64-column mat-vec.  Returns (matvecs/s, cores, sample text)."""
+def oracle_sample(wl, targets: int, nrhs: int, spectral_cols: int = 8):
+    """Time the FP64 oracle on `targets` target particles of the direct translation sum (nrhs
+    columns) and on the full spectral part (multipole-to-Sommerfeld, reflection, Sommerfeld-to-local)
+    for `spectral_cols` columns; extrapolate linearly to one full 64-column mat-vec.
+    Returns (matvecs/s, cores, sample text)."""
     import synthetic as syn
     from oracle import system
     ref = system.Problem(wl)
@@ -119,15 +120,13 @@ def oracle_sample(wl, targets: int, nrhs: int):
     t0 = time.perf_counter()
     ref.translate(x, targets=idx)
     t1 = time.perf_counter()
-    ref.reflect(x, targets=idx)
+    ref.reflect(x[..., :spectral_cols], targets=idx)
     t2 = time.perf_counter()
-    per_target = (t1 - t0) / targets
-    # the direct sum scales with targets and with columns; the spectral part with columns
-    t_full = (per_target * wl.M + (t2 - t1)) * (64 / nrhs)
+    t_full = (t1 - t0) / targets * wl.M * (64 / nrhs) + (t2 - t1) * (64 / spectral_cols)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"oracle FP64 numpy/scipy: direct Graf sum for {targets} of {wl.M} targets and the full "
-              f"spectral part, {nrhs} of 64 columns, extrapolated linearly to one 64-column mat-vec "
-              f"({t1 - t0:.1f} s + {t2 - t1:.1f} s measured)")
+    sample = (f"oracle FP64 numpy/scipy: direct Graf sum for {targets} of {wl.M} targets with {nrhs} columns "
+              f"and the full spectral part with {spectral_cols} columns, extrapolated linearly to one "
+              f"64-column mat-vec ({t1 - t0:.1f} s + {t2 - t1:.1f} s measured)")
     return 1.0 / t_full, cores, sample
 
 
@@ -169,7 +168,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     wl = workload()
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    solver = P.Solver.from_workload(wl)
+    solver = P.Solver.from_workload(wl, leaf_target=args.leaf_target)
     nrhs = 64
     x = torch.as_tensor(syn.random_coeffs(1000 + rank, wl.M, wl.p, nrhs), device="cuda")
     y = torch.empty_like(x)
@@ -257,8 +256,9 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == P.MS_PREC_FP32 else "f64", "data": "synthetic",
                 "config": {"workload": wl.name, "M": wl.M, "p": wl.p, "nrhs": nrhs,
-                           "n_nodes": wl.n_panels * wl.nodes_per_panel, "omega": wl.omega,
+                           "n_nodes": solver.n_nodes, "omega": wl.omega,
                            "near_pairs": pairs, "fmm_levels": solver.fmm_levels,
+                           "leaf_target": args.leaf_target, "contour_depth": wl.depth,
                            "l2": "inputs 0.84 GB > 126 MB L2, no flush",
                            "parallelism": f"rhs-replicas x{world}"},
                 "roofline": {"bound": "alu", "kernel": "k_translate<float> near pairs (timed via ms_operator(T_NEAR))",
@@ -315,6 +315,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small case for ncu (see run_profile)")
     ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
     ap.add_argument("--M", type=int, default=2500)
+    ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -84,15 +84,21 @@ typedef struct {
 } ms_media;
 
 typedef struct {
-    int32_t n_panels;          /* Gauss-Legendre panels on the contour (default 32) */
-    int32_t nodes_per_panel;   /* nodes per panel (default 16); N_S = n_panels * nodes_per_panel */
+    int32_t n_panels;          /* uniform Gauss-Legendre panels on [-t_max, t_max] (default 32) */
+    int32_t nodes_per_panel;   /* nodes per panel (default 16); N_S = panels * nodes_per_panel, the panels
+                                  being the uniform ones split at the graded edges (see grade) */
     double  t_max;             /* contour xi(t) = t - i tanh(t)/2, |t| <= t_max (Sec. 5.1; default 20) */
     int32_t restart;           /* GMRES restart length (default 50) */
     int32_t max_iters;         /* total GMRES iteration cap per solve (default 2000) */
     int32_t check_geometry;    /* 1 = validate separation / burial (default 1) */
     int32_t use_fmm;           /* 1 = quadtree FMM for non-adjacent leaves when M is large enough
                                   (default 1); 0 = direct Graf sum over every pair */
-    int32_t leaf_target;       /* FMM: target particles per leaf box (default 40) */
+    int32_t leaf_target;       /* FMM: target particles per leaf box (default 10) */
+    double  depth;             /* contour depth d: xi(t) = t - i d tanh(t) (paper: d = 1/2, the default).
+                                  Spectral factors grow like e^{d |x_m - x_l|}: wide domains need
+                                  d ~ 3 / (horizontal extent) and panels narrow enough for e^{i t dx} */
+    int32_t grade;             /* extra panel edges at each branch point +-kp, +-ks of both layers and
+                                  at c +- d 2^j, j < grade (default 0: none) */
 } ms_options;
 
 typedef struct {

@@ -2,9 +2,12 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
-Contour (Sec. 5.1): xi(t) = t - i tanh(t)/2 on [-t_max, t_max].  The paper uses a
-trapezoid rule; we use composite Gauss-Legendre panels (reading A5) and the same nodes
-for every part of the operator.  Weights W_q = w_q xi'(t_q), xi'(t) = 1 - (i/2) sech^2 t.
+Contour (Sec. 5.1): xi(t) = t - i d tanh(t) on [-t_max, t_max], d = 1/2 in the paper.  The
+paper uses a trapezoid rule; we use composite Gauss-Legendre panels (reading A5), optionally
+graded at the branch points, and the same nodes for every part of the operator.  Weights
+W_q = w_q xi'(t_q), xi'(t) = 1 - i d sech^2 t.  The factor e^{i xi (x_m - x_l)} grows like
+e^{d |x_m - x_l|} on one half of the contour, so wide particle clouds need a shallower contour
+(reading A20).
 
 Branch (Sec. 3 remark, reading A4): s_k(xi) = sqrt(xi^2 - k^2) with Re s >= 0, taken as
 -i * sqrt(k^2 - xi^2) with the principal root, which also gives the limiting-absorption
@@ -40,19 +43,34 @@ import numpy as np
 from .media import Layered
 
 
-def contour(n_panels: int, nodes_per_panel: int, t_max: float):
-    """Nodes xi_q and weights W_q = w_q xi'(t_q) of the composite Gauss-Legendre rule."""
+def contour(n_panels: int, nodes_per_panel: int, t_max: float, depth: float = 0.5, grade: int = 0,
+            branch_points=()):
+    """Nodes xi_q and weights W_q = w_q xi'(t_q) of the composite Gauss-Legendre rule on
+    xi(t) = t - i depth tanh(t), |t| <= t_max (Sec. 5.1 has depth 1/2).
+
+    Panel edges: -t_max + k (2 t_max / n_panels), k = 0..n_panels; with grade > 0 also each
+    branch point c = +-k (k in branch_points) and c +- depth 2^j, j < grade, inside the interval;
+    sorted, dropping an edge within 1e-9 of the previous kept one."""
     g, gw = np.polynomial.legendre.leggauss(nodes_per_panel)
-    edges = np.linspace(-t_max, t_max, n_panels + 1)
+    edges = [-t_max + k * (2.0 * t_max / n_panels) for k in range(n_panels + 1)]
+    if grade > 0:
+        for kb in branch_points:
+            for c in (-kb, kb):
+                cand = [c] + [c + sg * depth * 2.0 ** j for j in range(grade) for sg in (-1.0, 1.0)]
+                edges += [v for v in cand if -t_max < v < t_max]
+    kept = []
+    for v in sorted(edges):
+        if not kept or v - kept[-1] > 1e-9:
+            kept.append(v)
     t = []
     w = []
-    for a, b in zip(edges[:-1], edges[1:]):
+    for a, b in zip(kept[:-1], kept[1:]):
         t.append(0.5 * (b - a) * g + 0.5 * (a + b))
         w.append(0.5 * (b - a) * gw)
     t = np.concatenate(t)
     w = np.concatenate(w)
-    xi = t - 0.5j * np.tanh(t)
-    dxi = 1.0 - 0.5j / np.cosh(t) ** 2
+    xi = t - 1j * depth * np.tanh(t)
+    dxi = 1.0 - 1j * depth / np.cosh(t) ** 2
     return xi, w * dxi
 
 

@@ -32,7 +32,8 @@ class Problem:
         self.radius = np.asarray(wl.radius, float)
         self.bc = np.asarray(wl.bc, int)
         self.M = self.centres.shape[0]
-        self.xi, self.W = sommerfeld.contour(wl.n_panels, wl.nodes_per_panel, wl.t_max)
+        self.xi, self.W = sommerfeld.contour(wl.n_panels, wl.nodes_per_panel, wl.t_max, wl.depth, wl.grade,
+                                             (self.L.kp_u, self.L.ks_u, self.L.kp_l, self.L.ks_l))
         self.proto_S = proto_S
         self.proto_index = np.full(self.M, -1) if proto_index is None else np.asarray(proto_index)
         self.rotation = np.asarray(wl.rotation, float)

@@ -44,7 +44,7 @@ class Solver:
     def __init__(self, centres, radius, bc, media, omega: float, p: int, proto=None, rotation=None,
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
-                 use_fmm: bool = True, leaf_target: int = 40):
+                 use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -73,6 +73,7 @@ class Solver:
         o.n_panels, o.nodes_per_panel, o.t_max = n_panels, nodes_per_panel, float(t_max)
         o.restart, o.max_iters, o.check_geometry = restart, max_iters, int(bool(check_geometry))
         o.use_fmm, o.leaf_target = int(bool(use_fmm)), int(leaf_target)
+        o.depth, o.grade = float(depth), int(grade)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")
@@ -89,7 +90,8 @@ class Solver:
     def from_workload(cls, wl, **kw):
         """Handle for a synthetic.Workload (closed-form discs unless prototypes are given)."""
         return cls(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, wl.p, rotation=wl.rotation,
-                   n_panels=wl.n_panels, nodes_per_panel=wl.nodes_per_panel, t_max=wl.t_max, **kw)
+                   n_panels=wl.n_panels, nodes_per_panel=wl.nodes_per_panel, t_max=wl.t_max,
+                   depth=wl.depth, grade=wl.grade, **kw)
 
     # ------------------------------------------------------------------ helpers
     def _check_vec(self, x: torch.Tensor, nrhs=None) -> int:

@@ -53,7 +53,7 @@ class Media(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("n_panels", c_int), ("nodes_per_panel", c_int), ("t_max", ctypes.c_double),
                 ("restart", c_int), ("max_iters", c_int), ("check_geometry", c_int),
-                ("use_fmm", c_int), ("leaf_target", c_int)]
+                ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int)]
 
 
 class Incidence(ctypes.Structure):

@@ -179,6 +179,7 @@ extern "C" void ms_destroy(ms_handle* h) {
     dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);
     dfree_t(h->d.proto); dfree_t(h->d.rot); dfree_t(h->d.sproto); dfree_t(h->d.node); dfree_t(h->d.wq);
     dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
+    dfree_t(h->d.qpm_m); dfree_t(h->d.qpm_e); dfree_t(h->d.qps_m); dfree_t(h->d.qps_e);
     ms_fmm_free(h);
     dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u);
     delete h;

@@ -112,14 +112,17 @@ __global__ void k_split_seq(const double2* __restrict__ seq, float2* __restrict_
 constexpr int TR_IB = 3;
 constexpr int TR_RB = 8;
 constexpr int TR_ICH = 42;     // dst orders per CTA (14 x TR_IB)
-constexpr int TR_JCH = 48;     // src orders per staged tile
+constexpr int TR_JCH = 41;     // src orders per staged tile
+constexpr int TR_ES = 43;      // row stride of the operator tile (bank-conflict-free for rows 3*ib)
+constexpr int TR_SEQ = TR_ICH + TR_JCH;   // sequence entries a tile needs (<= ni + nj - 1)
 constexpr int TR_THREADS = 128;
 
 template <typename T> struct SeqRef;
 template <> struct SeqRef<double> {
     const double2* s;
-    __device__ double2 entry(long long idx, int scale) const {
-        double2 v = s[idx];
+    typedef double2 M;
+    __device__ void stage(long long idx, double2* m, int* e) const { *m = s[idx]; *e = 0; }
+    __device__ static double2 make(double2 v, int e, int scale) {
         double f = pow2d(scale);
         return make_double2(v.x * f, v.y * f);
     }
@@ -127,24 +130,48 @@ template <> struct SeqRef<double> {
 template <> struct SeqRef<float> {
     const float2* m;
     const int* e;
-    __device__ float2 entry(long long idx, int scale) const {
-        float2 v = m[idx];
-        float f = pow2f(e[idx] + scale);
+    typedef float2 M;
+    __device__ void stage(long long idx, float2* mm, int* ee) const { *mm = m[idx]; *ee = e[idx]; }
+    __device__ static float2 make(float2 v, int e, int scale) {
+        float f = pow2f(e + scale);
         return make_float2(v.x * f, v.y * f);
     }
 };
 
-// CTA = (dst entity d, dst order chunk).  For each task (src entity, sequence) of d and each chunk
-// of source orders, the CTA stages the scaled operator tile and the source block in shared
-// memory; each thread accumulates a TR_IB x TR_RB register tile over all tasks and chunks.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Adjoint mode (a.adj = 1).  For a translation with vector v from s to d, the reverse one (from d
+// to s, vector -v) has h^rev_k = (-1)^k h_k, since Z_k(x) e^{ik(phi + pi)} = (-1)^k Z_k(x) e^{ik phi}.
+// So the adjoint, out_s[j] += sum_i conj(h_{n_j - n_i}) in_d[i], is the reverse-direction launch
+// (reverse list: dst s, src d) with entries (-1)^k conj(h^rev_{-k}), k = n_src - n_dst.  Run on the
+// mirrored lists (near <-> near, P2M <-> L2P, M2M <-> L2L, M2L <-> M2L) with the mirrored scale
+// signs, the forward pipeline code in adjoint mode applies T^H.
+//
+// CTA = (dst entity d, dst order chunk).  Work items are (task, source-order chunk) pairs: each
+// stages the sequence segment and the scale exponents it needs, builds the scaled operator tile
+// E[i][j] = h_{n_j - n_i} 2^{s_d a_d,i + s_s a_s,j} in shared memory, and accumulates
+// E x (source block) into a TR_IB x TR_RB register tile per thread.  The source block of the next
+// item is fetched with cp.async while the current one is multiplied (when rows are 16-byte aligned).
 template <typename T>
 __global__ void __launch_bounds__(TR_THREADS)
 k_translate(TransArgs a, SeqRef<T> seq) {
     typedef typename CT<T>::c C;
+    typedef typename SeqRef<T>::M SM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* Eb = reinterpret_cast<C*>(smem_raw);          // [TR_ICH][TR_JCH]
-    C* Xb = Eb + TR_ICH * TR_JCH;                   // [TR_JCH][nrhs]
-    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1, K = a.K, nrhs = a.nrhs;
+    const int nrhs = a.nrhs;
+    C* Eb = reinterpret_cast<C*>(smem_raw);                    // [TR_ICH][TR_ES]
+    C* Xb = Eb + TR_ICH * TR_ES;                               // [2][TR_JCH][nrhs]
+    SM* sq = reinterpret_cast<SM*>(Xb + 2 * TR_JCH * nrhs);    // [TR_SEQ]
+    int* se = reinterpret_cast<int*>(sq + TR_SEQ);             // [TR_SEQ]
+    int* sad = se + TR_SEQ;                                    // [TR_ICH]
+    int* sas = sad + TR_ICH;                                   // [TR_JCH]
+
+    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1, K = a.K;
     const int d = blockIdx.x;
     const int ic0 = blockIdx.y * TR_ICH;
     const int ni = min(TR_ICH, nd - ic0);
@@ -153,7 +180,10 @@ k_translate(TransArgs a, SeqRef<T> seq) {
     const bool act = tile < ((ni + TR_IB - 1) / TR_IB) * n_rb;
     const int ib = act ? tile / n_rb : 0, rb = act ? tile % n_rb : 0;
     const int i0 = ib * TR_IB, r0 = rb * TR_RB;
+    const bool vec = (nrhs % 2) == 0;            // 16-byte rows for cp.async and paired loads
     const int* ad = a.ad + (long long)d * a.ad_stride;
+    for (int t = threadIdx.x; t < ni; t += blockDim.x) sad[t] = ad[ic0 + t];
+
     C acc[TR_IB][TR_RB];
 #pragma unroll
     for (int u = 0; u < TR_IB; ++u)
@@ -161,45 +191,88 @@ k_translate(TransArgs a, SeqRef<T> seq) {
         for (int v = 0; v < TR_RB; ++v) acc[u][v] = mk((T)0, (T)0);
 
     const int t0 = a.dst_ptr[d], t1 = a.dst_ptr[d + 1];
-    for (int t = t0; t < t1; ++t) {
+    const int nch = (ns + TR_JCH - 1) / TR_JCH;
+    const int nitems = (t1 - t0) * nch;
+
+    // issue the copy of item it's source block into buffer buf
+    auto fetch = [&](int it, int buf) {
+        const int t = t0 + it / nch, jc = (it % nch) * TR_JCH;
+        const int nj = min(TR_JCH, ns - jc);
+        const C* src = reinterpret_cast<const C*>(a.src) + (long long)a.task_src[t] * a.src_stride + (long long)jc * nrhs;
+        C* dstb = Xb + buf * TR_JCH * nrhs;
+        if (vec) {
+            const int n16 = nj * nrhs * (int)sizeof(C) / 16;
+            for (int e = threadIdx.x; e < n16; e += blockDim.x)
+                cp_async16(reinterpret_cast<char*>(dstb) + 16 * e, reinterpret_cast<const char*>(src) + 16 * e);
+            cp_async_commit();
+        } else {
+            for (int e = threadIdx.x; e < nj * nrhs; e += blockDim.x) dstb[e] = src[e];
+        }
+    };
+    if (nitems > 0) fetch(0, 0);
+    for (int it = 0; it < nitems; ++it) {
+        const int buf = it & 1;
+        const int t = t0 + it / nch, jc = (it % nch) * TR_JCH;
+        const int nj = min(TR_JCH, ns - jc);
         const int s = a.task_src[t];
         const long long so = a.task_seq[t];
-        const C* src = reinterpret_cast<const C*>(a.src) + (long long)s * a.src_stride;
+        // sequence segment: k = (j - Ps) - (i - Pd) for i in [ic0, ic0+ni), j in [jc, jc+nj); the
+        // adjoint reads index -k of the reverse-direction sequence
+        const int klo = (jc - a.Ps) - (ic0 + ni - 1 - a.Pd), khi = (jc + nj - 1 - a.Ps) - (ic0 - a.Pd);
+        const int kmin = a.adj ? -khi : klo;
+        const int nk = ni + nj - 1;
+        for (int e = threadIdx.x; e < nk; e += blockDim.x) seq.stage(so + K + kmin + e, &sq[e], &se[e]);
         const int* as = a.as + (long long)s * a.as_stride;
-        for (int jc = 0; jc < ns; jc += TR_JCH) {
-            const int nj = min(TR_JCH, ns - jc);
-            __syncthreads();
-            for (int e = threadIdx.x; e < nj * nrhs; e += blockDim.x) {
-                int jj = e / nrhs, r = e % nrhs;
-                Xb[jj * nrhs + r] = src[(long long)(jc + jj) * nrhs + r];
+        for (int e = threadIdx.x; e < nj; e += blockDim.x) sas[e] = as[jc + e];
+        if (vec) cp_async_wait_all();
+        __syncthreads();                                   // sequence, exponents, block `buf` ready
+        if (it + 1 < nitems) fetch(it + 1, buf ^ 1);
+        for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+            int ii = e / nj, jj = e % nj;
+            int k = (jj + jc - a.Ps) - (ii + ic0 - a.Pd);
+            if (a.adj) k = -k;
+            C v = SeqRef<T>::make(sq[k - kmin], se[k - kmin], a.sd * sad[ii] + a.ss * sas[jj]);
+            if (a.adj) {
+                v = cconj(v);
+                if (k & 1) v = mk(-v.x, -v.y);
             }
-            for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
-                int ii = e / nj, jj = e % nj;
-                int i = ic0 + ii, j = jc + jj;
-                int sc = a.sd * ad[i] + a.ss * as[j];
-                // index j - i in dst / src order numbering (n = index - P)
-                int kk = (j - a.Ps) - (i - a.Pd);
-                Eb[ii * TR_JCH + jj] = seq.entry(so + K + kk, sc);
-            }
-            __syncthreads();
-            if (act) {
+            Eb[ii * TR_ES + jj] = v;
+        }
+        __syncthreads();                                   // operator tile ready
+        if (act) {
+            const C* X = Xb + buf * TR_JCH * nrhs + r0;
+            const C* E = Eb + i0 * TR_ES;
+            const int nr = min(TR_RB, nrhs - r0);
+            if (vec && nr == TR_RB) {
+#pragma unroll 2
+                for (int jj = 0; jj < nj; ++jj) {
+                    C xv[TR_RB];
+                    const C* xr = X + jj * nrhs;
+#pragma unroll
+                    for (int v = 0; v < TR_RB; ++v) xv[v] = xr[v];
+                    C ev[TR_IB];
+#pragma unroll
+                    for (int u = 0; u < TR_IB; ++u) ev[u] = E[u * TR_ES + jj];
+#pragma unroll
+                    for (int u = 0; u < TR_IB; ++u)
+#pragma unroll
+                        for (int v = 0; v < TR_RB; ++v) cfma(acc[u][v], ev[u], xv[v]);
+                }
+            } else {
                 for (int jj = 0; jj < nj; ++jj) {
                     C xv[TR_RB];
 #pragma unroll
-                    for (int v = 0; v < TR_RB; ++v) {
-                        int r = r0 + v;
-                        xv[v] = r < nrhs ? Xb[jj * nrhs + r] : mk((T)0, (T)0);
-                    }
+                    for (int v = 0; v < TR_RB; ++v) xv[v] = v < nr ? X[jj * nrhs + v] : mk((T)0, (T)0);
 #pragma unroll
                     for (int u = 0; u < TR_IB; ++u) {
-                        int ii = i0 + u;
-                        C e = ii < ni ? Eb[ii * TR_JCH + jj] : mk((T)0, (T)0);
+                        C e = (i0 + u) < ni ? E[u * TR_ES + jj] : mk((T)0, (T)0);
 #pragma unroll
                         for (int v = 0; v < TR_RB; ++v) cfma(acc[u][v], e, xv[v]);
                     }
                 }
             }
         }
+        __syncthreads();                                   // tile and block `buf` free again
     }
     if (act) {
         C* dst = reinterpret_cast<C*>(a.dst) + (long long)d * a.dst_stride;
@@ -235,15 +308,18 @@ int ms_translate_launch(ms_handle* h, const TransArgs& a, int ndst, bool fp32, c
     if (ndst == 0) return MS_OK;
     int nd = 2 * a.Pd + 1;
     dim3 grid(ndst, (nd + TR_ICH - 1) / TR_ICH);
-    int tiles = 14 * ((a.nrhs + TR_RB - 1) / TR_RB);
+    int tiles = (TR_ICH / TR_IB) * ((a.nrhs + TR_RB - 1) / TR_RB);
     int threads = std::max(32, std::min(TR_THREADS, (tiles + 31) / 32 * 32));
+    size_t tail = (size_t)TR_SEQ * sizeof(int) + (size_t)(TR_ICH + TR_JCH) * sizeof(int);
     if (fp32) {
-        size_t smem = (size_t)TR_ICH * TR_JCH * sizeof(float2) + (size_t)TR_JCH * a.nrhs * sizeof(float2);
+        size_t smem = (size_t)TR_ICH * TR_ES * sizeof(float2) + (size_t)2 * TR_JCH * a.nrhs * sizeof(float2) +
+                      (size_t)TR_SEQ * sizeof(float2) + tail;
         cudaFuncSetAttribute(k_translate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         SeqRef<float> s{h->d.seqm, h->d.seqe};
         k_translate<float><<<grid, threads, smem, st>>>(a, s);
     } else {
-        size_t smem = (size_t)TR_ICH * TR_JCH * sizeof(double2) + (size_t)TR_JCH * a.nrhs * sizeof(double2);
+        size_t smem = (size_t)TR_ICH * TR_ES * sizeof(double2) + (size_t)2 * TR_JCH * a.nrhs * sizeof(double2) +
+                      (size_t)TR_SEQ * sizeof(double2) + tail;
         cudaFuncSetAttribute(k_translate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         SeqRef<double> s{h->d.seq64};
         k_translate<double><<<grid, threads, smem, st>>>(a, s);
@@ -356,7 +432,8 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
         for (int m = 0; m < M; ++m)
             for (int t = nearL.ptr[m]; t < nearL.ptr[m + 1]; ++t) {
                 int l = nearL.src[t];
-                seq_near[b][t] = B.add(c[2 * m] - c[2 * l], c[2 * m + 1] - c[2 * l + 1], kb[b], 2 * p, 1);
+                // one order beyond 2p so that order-shifted (derivative) expansions reuse the table
+                seq_near[b][t] = B.add(c[2 * m] - c[2 * l], c[2 * m + 1] - c[2 * l + 1], kb[b], 2 * p + 1, 1);
             }
     }
     int rc;
@@ -429,7 +506,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                 double cx, cy;
                 centre(L, leaf[m], cx, cy);
                 l2p.src.push_back(leaf[m]);
-                l2p.seq.push_back(B.add(c[2 * m] - cx, c[2 * m + 1] - cy, k, p + F.P[b][L], 0));
+                l2p.seq.push_back(B.add(c[2 * m] - cx, c[2 * m + 1] - cy, k, p + 1 + F.P[b][L], 0));
             }
             l2p.ptr[M] = M;
             if ((rc = upload_list(h, l2p, F.l2p[b]))) return rc;
@@ -558,7 +635,7 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
         TransArgs a{};
         const DevList& nl = h->fmm.near[b];
         a.dst_ptr = nl.ptr; a.task_src = nl.src; a.task_seq = nl.seq;
-        a.K = 2 * p; a.Pd = p; a.Ps = p;
+        a.K = 2 * p + 1; a.Pd = p; a.Ps = p;
         a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
         a.src = (const C*)xs + (long long)b * nc * nrhs; a.src_stride = 2LL * nc * nrhs;
         a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;
@@ -624,7 +701,7 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
         {
             TransArgs a{};
             a.dst_ptr = F.l2p[b].ptr; a.task_src = F.l2p[b].src; a.task_seq = F.l2p[b].seq;
-            a.Pd = p; a.Ps = F.P[b][L]; a.K = a.Pd + a.Ps;
+            a.Pd = p; a.Ps = F.P[b][L]; a.K = p + 1 + F.P[b][L];
             a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
             a.src = lexp(L); a.src_stride = (long long)ncl(L) * nrhs;
             a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;

@@ -22,7 +22,8 @@ struct TransArgs {
     const int* dst_ptr;
     const int* task_src;
     const long long* task_seq;
-    int K, Pd, Ps;
+    int K, Pd, Ps;   // K: centre of each stored sequence (h_k at offset K + k), >= Pd + Ps
+    int adj;         // 1: apply the adjoint of the reverse-direction translation (see fmm.cu)
     void* dst;
     long long dst_stride;
     const void* src;
@@ -66,6 +67,10 @@ struct MsDeviceTables {
     double2* refl = nullptr;       // [NS][2][2] reflection matrix R(xi_q): (U_P,U_S) -> (D_P,D_S)
     double2* qpow_m2s = nullptr;   // [2][NS][nc] (-i)^n q_b^n / (i pi s_b)
     double2* qpow_s2l = nullptr;   // [2][NS][nc] i^n q_b^n W_q
+    float2* qpm_m = nullptr;       // FP32 mantissa / binary exponent copies of the two tables
+    int* qpm_e = nullptr;
+    float2* qps_m = nullptr;
+    int* qps_e = nullptr;
     // translation sequences h_k = Z_k(k|v|) e^{ik arg v}: FP64 and FP32 mantissa / exponent copies
     double2* seq64 = nullptr;
     float2* seqm = nullptr;

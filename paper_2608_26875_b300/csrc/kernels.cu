@@ -45,84 +45,133 @@ __global__ void k_from_scaled(const typename CT<T>::c* __restrict__ ys, double2*
     y[i] = make_double2(v.x * s, v.y * s);
 }
 
+// ------------------------------------------------------------------ spectral factors
+// e^{z} for the exponents of the spectral factors, with z = re + i im built in FP64 from the
+// node and the particle position.  FP64 path: FP64 exp / sincos.  FP32 path: the phase is reduced
+// mod 2 pi in FP64 (|im| reaches ~|xi| |x| ~ 10^3), then expf / sincosf in FP32.
+template <typename T> struct SpecExp;
+template <> struct SpecExp<double> {
+    __device__ static double2 eval(double re, double im) {
+        double m = exp(re), sn, cs;
+        sincos(im, &sn, &cs);
+        return make_double2(m * cs, m * sn);
+    }
+};
+template <> struct SpecExp<float> {
+    __device__ static float2 eval(double re, double im) {
+        const double twopi = 6.283185307179586476925286766559;
+        double red = im - twopi * rint(im * (1.0 / twopi));
+        float m = expf((float)re), sn, cs;
+        sincosf((float)red, &sn, &cs);
+        return make_float2(m * cs, m * sn);
+    }
+};
+// A table factor (double2, or FP32 mantissa + exponent) times 2^scale, in the precision T.
+template <typename T> struct QRef;
+template <> struct QRef<double> {
+    const double2* q;
+    __device__ double2 get(long long idx, int scale) const {
+        double2 v = q[idx];
+        double f = pow2d(scale);
+        return make_double2(v.x * f, v.y * f);
+    }
+};
+template <> struct QRef<float> {
+    const float2* m;
+    const int* e;
+    __device__ float2 get(long long idx, int scale) const {
+        float2 v = m[idx];
+        float f = pow2f(e[idx] + scale);
+        return make_float2(v.x * f, v.y * f);
+    }
+};
+
 // ------------------------------------------------------------------ multipole-to-Sommerfeld
-// part[chunk][b][q][r] = sum_{l in chunk} e^{s_b y_l - i xi_q x_l} sum_n Q_b(q,n) tau_{l,b,n} x~^l_{b,n,r}
-// with Q_b(q,n) = (-i)^n q_b^n / (i pi s_b) (pts1 / sed1 / sed2).  CTA = (b, tile of TQ nodes, chunk);
-// the generated factor F(q,l,n) is built in FP64 per source batch into shared memory.
-constexpr int M2S_TQ = 16;
-constexpr int M2S_LB = 4;
-constexpr int M2S_THREADS = 256;
+// part[chunk][b][q][r] = sum_{l in chunk} sum_n F(q,l,n) x~^l_{b,n,r},
+// F(q,l,n) = e^{s_b y_l - i xi_q x_l} * [(-i)^n q_b^n / (i pi s_b)] * tau_{l,b,n}   (pts1 / sed1 / sed2)
+// A generated-operand GEMM: CTA = (tile of M2S_QT nodes, chunk of particles, wave b), thread tile
+// M2S_QB nodes x M2S_RB columns; per particle the CTA stages the source block (cp.async when the
+// rows are 16-byte aligned) and builds F for its nodes in shared memory.
+constexpr int M2S_QT = 32;
+constexpr int M2S_QB = 4;
+constexpr int M2S_RB = 4;
+constexpr int M2S_THREADS = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(M2S_THREADS)
 k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
       const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
-      const double2* __restrict__ sq, const double2* __restrict__ qpow, int M, int p, int NS, int nrhs,
-      int chunk_len) {
+      const double2* __restrict__ sq, QRef<T> qpow, int M, int p, int NS, int nrhs, int chunk_len) {
     typedef typename CT<T>::c C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = 2 * p + 1;
-    C* F = reinterpret_cast<C*>(smem_raw);              // [TQ][LB][nc]
+    C* F = reinterpret_cast<C*>(smem_raw);            // [nc][M2S_QT + 1]
+    C* X = F + nc * (M2S_QT + 1);                     // [nc][nrhs]
+    C* Eq = X + nc * nrhs;                            // [M2S_QT]
     const int b = blockIdx.z;
-    const int q0 = blockIdx.x * M2S_TQ;
+    const int q0 = blockIdx.x * M2S_QT;
     const int chunk = blockIdx.y;
     const int l0 = chunk * chunk_len, l1 = min(M, l0 + chunk_len);
-    const int tq = threadIdx.x / 16, rl = threadIdx.x % 16;
-    const int q = q0 + tq;
-    constexpr int RMAX = 4;   // nrhs <= 64
-    C acc[RMAX];
+    const int n_rb = (nrhs + M2S_RB - 1) / M2S_RB;
+    const int tile = threadIdx.x;
+    const bool act = tile < (M2S_QT / M2S_QB) * n_rb;
+    const int qb = act ? tile / n_rb : 0, rb = act ? tile % n_rb : 0;
+    const int qi0 = qb * M2S_QB, r0 = rb * M2S_RB;
+    C acc[M2S_QB][M2S_RB];
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k) acc[k] = mk((T)0, (T)0);
+    for (int u = 0; u < M2S_QB; ++u)
+#pragma unroll
+        for (int v = 0; v < M2S_RB; ++v) acc[u][v] = mk((T)0, (T)0);
 
-    for (int lb = l0; lb < l1; lb += M2S_LB) {
-        const int nl = min(M2S_LB, l1 - lb);
+    for (int l = l0; l < l1; ++l) {
         __syncthreads();
-        for (int e = threadIdx.x; e < M2S_TQ * nl * nc; e += blockDim.x) {
-            int n = e % nc, rest = e / nc;
-            int li = rest % nl, qi = rest / nl;
-            int qq_ = q0 + qi;
-            C val = mk((T)0, (T)0);
-            if (qq_ < NS) {
-                int l = lb + li;
-                double2 cl = centre[l];
-                double2 xi = node[qq_];
-                double2 s = sq[qq_ * 2 + b];
-                // s y_l - i xi x_l
-                double re = s.x * cl.y + xi.y * cl.x;
-                double im = s.y * cl.y - xi.x * cl.x;
-                double mag = exp(re);
-                double sn, cs;
-                sincos(im, &sn, &cs);
-                double2 E = make_double2(mag * cs, mag * sn);
-                double2 f = cmul(E, qpow[((size_t)b * NS + qq_) * nc + n]);
-                double sc = pow2d(expo[(l * 2 + b) * nc + n]);
-                val = to_c<T>(make_double2(f.x * sc, f.y * sc));
+        const C* xl = xs + ((size_t)(l * 2 + b) * nc) * nrhs;
+        for (int e = threadIdx.x; e < nc * nrhs; e += blockDim.x) X[e] = xl[e];
+        const double2 cl = centre[l];
+        for (int qi = threadIdx.x; qi < M2S_QT; qi += blockDim.x) {
+            int q = q0 + qi;
+            C ev = mk((T)0, (T)0);
+            if (q < NS) {
+                double2 xi = node[q], s = sq[q * 2 + b];
+                ev = SpecExp<T>::eval(s.x * cl.y + xi.y * cl.x, s.y * cl.y - xi.x * cl.x);
             }
-            F[(qi * M2S_LB + li) * nc + n] = val;
+            Eq[qi] = ev;
         }
         __syncthreads();
-        if (q < NS) {
-            for (int li = 0; li < nl; ++li) {
-                const int l = lb + li;
-                const C* xl = xs + ((size_t)(l * 2 + b) * nc) * nrhs;
-                const C* f = F + (tq * M2S_LB + li) * nc;
+        const int* al = expo + (l * 2 + b) * nc;
+        for (int e = threadIdx.x; e < nc * M2S_QT; e += blockDim.x) {
+            int n = e / M2S_QT, qi = e % M2S_QT;
+            int q = q0 + qi;
+            C f = mk((T)0, (T)0);
+            if (q < NS) f = cmul(Eq[qi], qpow.get(((long long)b * NS + q) * nc + n, al[n]));
+            F[n * (M2S_QT + 1) + qi] = f;
+        }
+        __syncthreads();
+        if (act) {
+            const int nr = min(M2S_RB, nrhs - r0);
+            for (int n = 0; n < nc; ++n) {
+                C xv[M2S_RB], fv[M2S_QB];
 #pragma unroll
-                for (int k = 0; k < RMAX; ++k) {
-                    int r = rl + 16 * k;
-                    if (r < nrhs) {
-                        C s = acc[k];
-                        for (int n = 0; n < nc; ++n) cfma(s, f[n], xl[(size_t)n * nrhs + r]);
-                        acc[k] = s;
-                    }
-                }
+                for (int v = 0; v < M2S_RB; ++v) xv[v] = v < nr ? X[n * nrhs + r0 + v] : mk((T)0, (T)0);
+#pragma unroll
+                for (int u = 0; u < M2S_QB; ++u) fv[u] = F[n * (M2S_QT + 1) + qi0 + u];
+#pragma unroll
+                for (int u = 0; u < M2S_QB; ++u)
+#pragma unroll
+                    for (int v = 0; v < M2S_RB; ++v) cfma(acc[u][v], fv[u], xv[v]);
             }
         }
     }
-    if (q < NS) {
+    if (act) {
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k) {
-            int r = rl + 16 * k;
-            if (r < nrhs) part[(((size_t)chunk * 2 + b) * NS + q) * nrhs + r] = to_d(acc[k]);
+        for (int u = 0; u < M2S_QB; ++u) {
+            int q = q0 + qi0 + u;
+            if (q >= NS) continue;
+#pragma unroll
+            for (int v = 0; v < M2S_RB; ++v) {
+                int r = r0 + v;
+                if (r < nrhs) part[(((size_t)chunk * 2 + b) * NS + q) * nrhs + r] = to_d(acc[u][v]);
+            }
         }
     }
 }
@@ -145,69 +194,87 @@ __global__ void k_reflect(const double2* __restrict__ part, double2* __restrict_
 }
 
 // ------------------------------------------------------------------ Sommerfeld-to-local
-// a~^m_{b,n,r} (+)= tau_{m,b,n} sum_q e^{i xi_q x_m + s_b y_m} [i^n q_b^n W_q] D_b(q,r)  (ja / stm / eee1).
-// CTA = (target m, wave b); nodes in batches of QB with the generated factor in shared memory.
-constexpr int S2L_QB = 32;
-constexpr int S2L_THREADS = 256;
+// a~^m_{b,n,r} (+)= sum_q G(q,m,n) D_b(q,r),
+// G(q,m,n) = e^{i xi_q x_m + s_b y_m} * [i^n q_b^n W_q] * tau_{m,b,n}    (ja / stm / eee1)
+// CTA = (target m, wave b); thread tile S2L_NB orders x S2L_RB columns; nodes in chunks of S2L_QC
+// with the reflected amplitudes and the generated factor staged in shared memory.
+constexpr int S2L_QC = 32;
+constexpr int S2L_NB = 3;
+constexpr int S2L_RB = 8;
+constexpr int S2L_THREADS = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(S2L_THREADS)
 k_s2l(const double2* __restrict__ ud, typename CT<T>::c* __restrict__ as,
       const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
-      const double2* __restrict__ sq, const double2* __restrict__ qpow, int p, int NS, int nrhs,
-      int accumulate) {
+      const double2* __restrict__ sq, QRef<T> qpow, int p, int NS, int nrhs, int accumulate) {
     typedef typename CT<T>::c C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = 2 * p + 1;
-    C* G = reinterpret_cast<C*>(smem_raw);          // [QB][nc]
-    C* Ds = G + S2L_QB * nc;                        // [QB][nrhs]
+    C* G = reinterpret_cast<C*>(smem_raw);          // [S2L_QC][nc + 1]
+    C* Ds = G + S2L_QC * (nc + 1);                  // [S2L_QC][nrhs]
+    C* Eq = Ds + S2L_QC * nrhs;                     // [S2L_QC]
     const int m = blockIdx.x, b = blockIdx.y;
     const double2 cm = centre[m];
-    const int nout = nc * nrhs;
-    constexpr int TMAX = 16;   // ceil(61*64/256): p <= 30, nrhs <= 64
-    C acc[TMAX];
+    const int* am = expo + (m * 2 + b) * nc;
+    const int n_rb = (nrhs + S2L_RB - 1) / S2L_RB;
+    const int n_nb = (nc + S2L_NB - 1) / S2L_NB;
+    const int tile = threadIdx.x;
+    const bool act = tile < n_nb * n_rb;
+    const int nb = act ? tile / n_rb : 0, rb = act ? tile % n_rb : 0;
+    const int n0 = nb * S2L_NB, r0 = rb * S2L_RB;
+    C acc[S2L_NB][S2L_RB];
 #pragma unroll
-    for (int k = 0; k < TMAX; ++k) acc[k] = mk((T)0, (T)0);
+    for (int u = 0; u < S2L_NB; ++u)
+#pragma unroll
+        for (int v = 0; v < S2L_RB; ++v) acc[u][v] = mk((T)0, (T)0);
 
-    for (int qb = 0; qb < NS; qb += S2L_QB) {
-        const int nq = min(S2L_QB, NS - qb);
+    for (int qb = 0; qb < NS; qb += S2L_QC) {
+        const int nq = min(S2L_QC, NS - qb);
         __syncthreads();
-        for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
-            int n = e % nc, qi = e / nc;
-            int q = qb + qi;
-            double2 xi = node[q];
-            double2 s = sq[q * 2 + b];
-            // i xi x_m + s y_m
-            double re = -xi.y * cm.x + s.x * cm.y;
-            double im = xi.x * cm.x + s.y * cm.y;
-            double mag = exp(re);
-            double sn, cs;
-            sincos(im, &sn, &cs);
-            double2 g = cmul(make_double2(mag * cs, mag * sn), qpow[((size_t)b * NS + q) * nc + n]);
-            double sc = pow2d(expo[(m * 2 + b) * nc + n]);
-            G[qi * nc + n] = to_c<T>(make_double2(g.x * sc, g.y * sc));
-        }
         for (int e = threadIdx.x; e < nq * nrhs; e += blockDim.x) {
             int r = e % nrhs, qi = e / nrhs;
             Ds[qi * nrhs + r] = to_c<T>(ud[((size_t)b * NS + qb + qi) * nrhs + r]);
         }
+        for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
+            double2 xi = node[qb + qi], s = sq[(qb + qi) * 2 + b];
+            Eq[qi] = SpecExp<T>::eval(-xi.y * cm.x + s.x * cm.y, xi.x * cm.x + s.y * cm.y);
+        }
         __syncthreads();
+        for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
+            int n = e % nc, qi = e / nc;
+            G[qi * (nc + 1) + n] = cmul(Eq[qi], qpow.get(((long long)b * NS + qb + qi) * nc + n, am[n]));
+        }
+        __syncthreads();
+        if (act) {
+            const int nr = min(S2L_RB, nrhs - r0);
+            for (int qi = 0; qi < nq; ++qi) {
+                C dv[S2L_RB], gv[S2L_NB];
 #pragma unroll
-        for (int k = 0; k < TMAX; ++k) {
-            int t = threadIdx.x + k * blockDim.x;
-            if (t < nout) {
-                int n = t / nrhs, r = t % nrhs;
-                C s = acc[k];
-                for (int qi = 0; qi < nq; ++qi) cfma(s, G[qi * nc + n], Ds[qi * nrhs + r]);
-                acc[k] = s;
+                for (int v = 0; v < S2L_RB; ++v) dv[v] = v < nr ? Ds[qi * nrhs + r0 + v] : mk((T)0, (T)0);
+#pragma unroll
+                for (int u = 0; u < S2L_NB; ++u) gv[u] = (n0 + u) < nc ? G[qi * (nc + 1) + n0 + u] : mk((T)0, (T)0);
+#pragma unroll
+                for (int u = 0; u < S2L_NB; ++u)
+#pragma unroll
+                    for (int v = 0; v < S2L_RB; ++v) cfma(acc[u][v], gv[u], dv[v]);
             }
         }
     }
-    C* out = as + ((size_t)(m * 2 + b) * nc) * nrhs;
+    if (act) {
+        C* out = as + ((size_t)(m * 2 + b) * nc) * nrhs;
 #pragma unroll
-    for (int k = 0; k < TMAX; ++k) {
-        int t = threadIdx.x + k * blockDim.x;
-        if (t < nout) out[t] = accumulate ? cadd(out[t], acc[k]) : acc[k];
+        for (int u = 0; u < S2L_NB; ++u) {
+            int n = n0 + u;
+            if (n >= nc) continue;
+#pragma unroll
+            for (int v = 0; v < S2L_RB; ++v) {
+                int r = r0 + v;
+                if (r >= nrhs) continue;
+                size_t o = (size_t)n * nrhs + r;
+                out[o] = accumulate ? cadd(out[o], acc[u][v]) : acc[u][v];
+            }
+        }
     }
 }
 
@@ -320,6 +387,13 @@ int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cu
     return ms_check(h, cudaGetLastError());
 }
 
+template <typename T> QRef<T> qref_m2s(ms_handle* h);
+template <> QRef<double> qref_m2s<double>(ms_handle* h) { return QRef<double>{h->d.qpow_m2s}; }
+template <> QRef<float> qref_m2s<float>(ms_handle* h) { return QRef<float>{h->d.qpm_m, h->d.qpm_e}; }
+template <typename T> QRef<T> qref_s2l(ms_handle* h);
+template <> QRef<double> qref_s2l<double>(ms_handle* h) { return QRef<double>{h->d.qpow_s2l}; }
+template <> QRef<float> qref_s2l<float>(ms_handle* h) { return QRef<float>{h->d.qps_m, h->d.qps_e}; }
+
 static int m2s_chunks(ms_handle* h) {
     int chunks = (h->M + 63) / 64;
     if (chunks > 64) chunks = 64;
@@ -345,20 +419,25 @@ int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStre
         int chunks = m2s_chunks(h);
         int chunk_len = (M + chunks - 1) / chunks;
         chunks = (M + chunk_len - 1) / chunk_len;
-        dim3 g((NS + M2S_TQ - 1) / M2S_TQ, chunks, 2);
-        size_t smem = (size_t)M2S_TQ * M2S_LB * nc * sizeof(C);
+        dim3 g((NS + M2S_QT - 1) / M2S_QT, chunks, 2);
+        size_t smem = ((size_t)nc * (M2S_QT + 1) + (size_t)nc * nrhs + M2S_QT) * sizeof(C);
         cudaFuncSetAttribute(k_m2s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_m2s<T><<<g, M2S_THREADS, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, h->d.expo, h->d.node,
-                                               h->d.sq, h->d.qpow_m2s, M, p, NS, nrhs, chunk_len);
+        int tiles = (M2S_QT / M2S_QB) * ((nrhs + M2S_RB - 1) / M2S_RB);
+        int thr = std::max(32, std::min(M2S_THREADS, (tiles + 31) / 32 * 32));
+        QRef<T> qm = qref_m2s<T>(h);
+        k_m2s<T><<<g, thr, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, h->d.expo, h->d.node, h->d.sq, qm, M, p,
+                                       NS, nrhs, chunk_len);
         if (int rc = ms_check(h, cudaGetLastError())) return rc;
         k_reflect<<<nblk((long long)NS * nrhs, 256), 256, 0, st>>>((const double2*)h->ws_part, (double2*)h->ws_u,
                                                                    h->d.refl, chunks, NS, nrhs);
         if (int rc = ms_check(h, cudaGetLastError())) return rc;
-        size_t smem2 = (size_t)S2L_QB * nc * sizeof(C) + (size_t)S2L_QB * nrhs * sizeof(C);
+        size_t smem2 = ((size_t)S2L_QC * (nc + 1) + (size_t)S2L_QC * nrhs + S2L_QC) * sizeof(C);
         cudaFuncSetAttribute(k_s2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-        k_s2l<T><<<dim3(M, 2), S2L_THREADS, smem2, st>>>((const double2*)h->ws_u, as, h->d.centre, h->d.expo,
-                                                         h->d.node, h->d.sq, h->d.qpow_s2l, p, NS, nrhs,
-                                                         have ? 1 : 0);
+        int tiles2 = ((nc + S2L_NB - 1) / S2L_NB) * ((nrhs + S2L_RB - 1) / S2L_RB);
+        int thr2 = std::max(32, std::min(256, (tiles2 + 31) / 32 * 32));
+        QRef<T> qs = qref_s2l<T>(h);
+        k_s2l<T><<<dim3(M, 2), thr2, smem2, st>>>((const double2*)h->ws_u, as, h->d.centre, h->d.expo, h->d.node,
+                                                  h->d.sq, qs, p, NS, nrhs, have ? 1 : 0);
         if (int rc = ms_check(h, cudaGetLastError())) return rc;
         have = true;
     }

@@ -182,7 +182,37 @@ extern "C" void ms_default_options(ms_options* o) {
     o->max_iters = 2000;
     o->check_geometry = 1;
     o->use_fmm = 1;
-    o->leaf_target = 40;
+    o->leaf_target = 10;
+    o->depth = 0.5;
+    o->grade = 0;
+}
+
+// Panel edges of the Sommerfeld rule on [-t_max, t_max]: n uniform panels (edge k at
+// -t_max + k (2 t_max / n)); with grade > 0 also every branch point c in {+-kp, +-ks} of both
+// layers and c +- depth 2^j, j < grade, inside the interval.  Sorted; an edge closer than 1e-9 to
+// the previous kept edge is dropped.
+static std::vector<double> contour_edges(const ms_handle* h, const ms_options& o) {
+    std::vector<double> e;
+    for (int k = 0; k <= o.n_panels; ++k) e.push_back(-o.t_max + k * (2.0 * o.t_max / o.n_panels));
+    if (o.grade > 0) {
+        const double bp[4] = {h->kp_u, h->ks_u, h->kp_l, h->ks_l};
+        for (double kb : bp)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                double c = sg * kb;
+                std::vector<double> add = {c};
+                for (int j = 0; j < o.grade; ++j) {
+                    add.push_back(c - o.depth * std::ldexp(1.0, j));
+                    add.push_back(c + o.depth * std::ldexp(1.0, j));
+                }
+                for (double v : add)
+                    if (v > -o.t_max && v < o.t_max) e.push_back(v);
+            }
+    }
+    std::sort(e.begin(), e.end());
+    std::vector<double> out;
+    for (double v : e)
+        if (out.empty() || v - out.back() > 1e-9) out.push_back(v);
+    return out;
 }
 
 extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
@@ -198,7 +228,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     ms_default_options(&opt);
     if (o) opt = *o;
     if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || opt.restart < 1 || opt.max_iters < 1 ||
-        opt.leaf_target < 1)
+        opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30)
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {
@@ -250,7 +280,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     h->M = M;
     h->p = p;
     h->nc = nc;
-    h->NS = opt.n_panels * opt.nodes_per_panel;
+    h->NS = 0;   // set from the contour edges below
     h->omega = omega;
     h->lam_u = md->lam_u; h->mu_u = md->mu_u; h->lam_l = md->lam_l; h->mu_l = md->mu_l;
     h->kp_u = omega / sqrt(md->lam_u + 2 * md->mu_u);
@@ -261,7 +291,6 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     h->n_proto = g->n_proto;
     h->h_centres.assign(g->centres, g->centres + 2 * M);
     h->h_radius.assign(g->radius, g->radius + M);
-    const int NS = h->NS;
     int rc = MS_OK;
 
     // scale exponents a = round(log2((k R / 2)^|n| / |n|!))
@@ -318,18 +347,21 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     // contour (Sec. 5.1), per-node factors and reflection table
     std::vector<double> gx, gw;
     gauss_legendre(opt.nodes_per_panel, gx, gw);
+    const std::vector<double> edges = contour_edges(h, opt);
+    const int npan = (int)edges.size() - 1;
+    h->NS = npan * opt.nodes_per_panel;
+    const int NS = h->NS;
     std::vector<double2> node(NS), wq(NS), sq(NS * 2), qq(NS * 2), refl(NS * 4);
     std::vector<double2> qpm((size_t)2 * NS * nc), qps((size_t)2 * NS * nc);
-    double width = 2.0 * opt.t_max / opt.n_panels;
-    for (int pnl = 0; pnl < opt.n_panels; ++pnl) {
-        double a = -opt.t_max + pnl * width;
+    for (int pnl = 0; pnl < npan; ++pnl) {
+        double a = edges[pnl], width = edges[pnl + 1] - edges[pnl];
         for (int j = 0; j < opt.nodes_per_panel; ++j) {
             int q = pnl * opt.nodes_per_panel + j;
             double t = a + 0.5 * width * (gx[j] + 1.0);
             double w = 0.5 * width * gw[j];
             double th = tanh(t);
-            cd xi(t, -0.5 * th);
-            cd dxi(1.0, -0.5 * (1.0 - th * th));
+            cd xi(t, -opt.depth * th);
+            cd dxi(1.0, -opt.depth * (1.0 - th * th));
             node[q] = d2(xi);
             wq[q] = d2(w * dxi);
             cd U[2], D[2], E[2], In[2] = {0.0, 0.0};
@@ -380,6 +412,17 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         (rc = upload(h, &h->d.qpow_s2l, qps.data(), qps.size()))) {
         ms_destroy(h);
         return rc;
+    }
+    {
+        std::vector<float2> mm(qpm.size()), ms2(qps.size());
+        std::vector<int> em(qpm.size()), es(qps.size());
+        for (size_t k = 0; k < qpm.size(); ++k) split_exp(qpm[k], mm[k], em[k]);
+        for (size_t k = 0; k < qps.size(); ++k) split_exp(qps[k], ms2[k], es[k]);
+        if ((rc = upload(h, &h->d.qpm_m, mm.data(), mm.size())) || (rc = upload(h, &h->d.qpm_e, em.data(), em.size())) ||
+            (rc = upload(h, &h->d.qps_m, ms2.data(), ms2.size())) || (rc = upload(h, &h->d.qps_e, es.data(), es.size()))) {
+            ms_destroy(h);
+            return rc;
+        }
     }
     if (h->any_proto) {
         size_t nn = (size_t)g->n_proto * (2 * nc) * (2 * nc);

@@ -49,6 +49,8 @@ class Workload:
     nodes_per_panel: int = 16
     t_max: float = 20.0
     gmres_tol: float = 1e-12
+    depth: float = 0.5       # contour depth d of xi(t) = t - i d tanh(t)
+    grade: int = 0           # branch-point grading levels of the contour panels
 
     @property
     def M(self) -> int:
@@ -119,6 +121,15 @@ def receiver_line(R: int, x0: float, x1: float, y: float) -> np.ndarray:
     return np.stack([xs, np.full(R, y)], axis=1)
 
 
+def contour_for_width(width: float, t_max: float = 20.0):
+    """Sommerfeld rule for a particle cloud of horizontal extent `width`: depth 3 / width (at most
+    the paper's 1/2), uniform panels of width ~ 8 pi / width (so that e^{i t dx} is resolved for
+    every pair) and 4 grading levels at the branch points.  Returns (n_panels, depth, grade)."""
+    depth = min(0.5, 3.0 / width)
+    panel = min(1.25, 8.0 * math.pi / width)
+    return int(math.ceil(2.0 * t_max / panel)), depth, 4
+
+
 def config1(seed: int = 1002) -> Workload:
     """16 rigid discs R=0.5 in [-10,10]x[-8,-1], omega=2, p=10, one P-wave at 30 degrees."""
     rng = np.random.default_rng(seed)
@@ -141,9 +152,10 @@ def config2(seed: int = 1003, nrhs: int = 1) -> Workload:
     rot = rng.uniform(0, 2 * math.pi, M)
     irng = np.random.default_rng(2003)
     ang = np.full(nrhs, math.radians(30.0)) if nrhs == 1 else np.radians(irng.uniform(10, 170, nrhs))
+    npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
     return Workload("particles1000_p16", MEDIA_STD, 4.0, 16, c, r, bc,
                     np.zeros(M, np.int32), rot, np.zeros(nrhs, np.int32), ang,
-                    receiver_line(256, -40, 40, -0.5))
+                    receiver_line(256, -40, 40, -0.5), n_panels=npan, depth=depth, grade=grade)
 
 
 def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
@@ -161,9 +173,10 @@ def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
     irng = np.random.default_rng(2004)
     ang = np.radians(irng.uniform(10, 170, nrhs))
     kind = (np.arange(nrhs) >= nrhs // 2).astype(np.int32)
+    npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
     return Workload(f"particles{M}_p20_rhs{nrhs}", MEDIA_STD, 6.0, 20, c, r, bc,
                     np.zeros(M, np.int32), rot, kind, ang,
-                    receiver_line(256, -side / 2, side / 2, -0.5))
+                    receiver_line(256, -side / 2, side / 2, -0.5), n_panels=npan, depth=depth, grade=grade)
 
 
 def config4(seed: int = 1005, M: int = 2000, nrhs: int = 32) -> Workload:
@@ -174,15 +187,17 @@ def config4(seed: int = 1005, M: int = 2000, nrhs: int = 32) -> Workload:
     c, r = place_particles(rng, M, (-side / 2, side / 2, -side - 1.0, -1.0), 0.2, 0.5)
     irng = np.random.default_rng(2005)
     ang = np.radians(irng.uniform(10, 170, nrhs))
+    npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
     return Workload(f"discs{M}_p16_rhs{nrhs}", MEDIA_STD, 4.0, 16, c, r,
                     np.zeros(M, np.int32), np.zeros(M, np.int32), np.zeros(M),
-                    np.zeros(nrhs, np.int32), ang, receiver_line(128, -side / 2, side / 2, -0.5))
+                    np.zeros(nrhs, np.int32), ang, receiver_line(128, -side / 2, side / 2, -0.5),
+                    n_panels=npan, depth=depth, grade=grade)
 
 
 def small_case(seed: int, M: int, p: int, omega: float = 2.0, nrhs: int = 1,
                media: Media = MEDIA_STD, box=(-6.0, 6.0, -5.0, -1.0), rmin=0.3, rmax=0.6,
                mixed_bc: bool = True, n_panels: int = 32, nodes_per_panel: int = 16,
-               t_max: float = 20.0) -> Workload:
+               t_max: float = 20.0, depth: float = 0.5, grade: int = 0) -> Workload:
     """A few particles for parity tests that the oracle finishes in seconds."""
     rng = np.random.default_rng(seed)
     c, r = place_particles(rng, M, box, rmin, rmax)
@@ -192,7 +207,8 @@ def small_case(seed: int, M: int, p: int, omega: float = 2.0, nrhs: int = 1,
     kind = (np.arange(nrhs) % 2).astype(np.int32)
     return Workload(f"small{M}_p{p}", media, omega, p, c, r, bc, np.zeros(M, np.int32),
                     rng.uniform(0, 2 * math.pi, M), kind, ang,
-                    receiver_line(32, box[0], box[1], -0.5), n_panels, nodes_per_panel, t_max)
+                    receiver_line(32, box[0], box[1], -0.5), n_panels, nodes_per_panel, t_max,
+                    depth=depth, grade=grade)
 
 
 def random_coeffs(seed: int, M: int, p: int, nrhs: int) -> np.ndarray:

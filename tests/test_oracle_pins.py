@@ -298,3 +298,47 @@ def test_planted_traction_term_drop_is_caught(monkeypatch):
     monkeypatch.setattr(disc, "mode_matrix", dropped)
     with pytest.raises(AssertionError):
         test_disc_scattering_matrix_boundary_condition(1, 0.5)
+
+
+# --------------------------------------------------------------------- wide particle clouds
+def _graded_rule(width, L):
+    npan, depth, grade = syn.contour_for_width(width)
+    return sommerfeld.contour(npan, 16, 20.0, depth, grade, (L.kp_u, L.ks_u, L.kp_l, L.ks_l))
+
+
+@pytest.mark.parametrize("dx,dy", [(140.0, 2.0), (75.0, 3.5), (20.0, 2.2)])
+def test_graded_rule_reproduces_som1_at_large_separation(dx, dy):
+    """som1 (Sec. 3) on the shallow graded rule chosen for a cloud of width 143, against the closed
+    form (i/4) H_0(k r) evaluated by scipy."""
+    L = Layered(syn.MEDIA_STD, 6.0)
+    xi, W = _graded_rule(143.0, L)
+    for k in (L.kp_l, L.ks_l):
+        s = sommerfeld.branch_s(xi, k)
+        quad = (W * np.exp(-s * dy) / s * np.exp(1j * xi * dx)).sum() / (4 * np.pi)
+        ex = 0.25j * special.hankel1(0, k * math.hypot(dx, dy))
+        assert abs(quad - ex) <= 1e-9 * abs(ex)
+
+
+def test_graded_rule_reproduces_pts1_high_order_at_large_separation():
+    L = Layered(syn.MEDIA_STD, 6.0)
+    xi, W = _graded_rule(143.0, L)
+    k, xm, x, y = L.ks_l, -60.0, 70.0, 0.0
+    # high orders need a deeper source for the integrand to decay by |t| = t_max = 20
+    for n, ym in ((0, -1.4), (7, -1.4), (-13, -8.0), (20, -8.0)):
+        s = sommerfeld.branch_s(xi, k)
+        integ = ((-1.0) ** n / (1j * np.pi)) * np.exp(s * (ym - y)) / s * np.exp(1j * xi * (x - xm)) \
+            * ((s - xi) / (1j * k)) ** n
+        ex = special.hankel1(n, k * math.hypot(x - xm, y - ym)) * np.exp(1j * n * math.atan2(y - ym, x - xm))
+        assert abs((W * integ).sum() - ex) <= 1e-8 * abs(ex)
+
+
+def test_paper_contour_is_unusable_for_wide_clouds():
+    """Reading A20: with the paper's depth 1/2 and 512 nodes, e^{i xi dx} grows like e^{dx/2} on the
+    contour and its oscillation is unresolved; som1 at dx = 50 is off by orders of magnitude."""
+    L = Layered(syn.MEDIA_STD, 6.0)
+    xi, W = sommerfeld.contour(32, 16, 20.0)
+    k, dx, dy = L.ks_l, 50.0, 2.0
+    s = sommerfeld.branch_s(xi, k)
+    quad = (W * np.exp(-s * dy) / s * np.exp(1j * xi * dx)).sum() / (4 * np.pi)
+    ex = 0.25j * special.hankel1(0, k * math.hypot(dx, dy))
+    assert abs(quad - ex) > 1.0 * abs(ex)
