@@ -207,7 +207,10 @@ class Problem:
         X = np.asarray(X, float)
         Y = np.asarray(Y, float)
         nrhs = gamma.shape[3]
-        (D_P, D_S), _ = self.interface_amplitudes(gamma)
+        U_P, U_S = sommerfeld.m2s(self.xi, self.L, self.centres, gamma)
+        R = self.reflection_table()
+        D_P = R[:, 0, 0, None] * U_P + R[:, 0, 1, None] * U_S
+        D_S = R[:, 1, 0, None] * U_P + R[:, 1, 1, None] * U_S
         us = []
         gs = []
         for r in range(nrhs):
