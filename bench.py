@@ -274,6 +274,83 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_solve(args):
+    """Time to solution at relative residual 1e-8 for the 64 plane waves of the 10^4-particle
+    workload: the mixed form (FP32 operator, FP64 refinement) measured; the FP64 form measured
+    when --full-fp64 is given, else its mat-vec timed and multiplied by the mat-vecs the Krylov
+    process needed (reported as an extrapolation)."""
+    import torch
+
+    import paper_2608_26875_b300 as P
+    wl = workload()
+    s = P.Solver.from_workload(wl, leaf_target=args.leaf_target)
+    torch.cuda.synchronize()
+    g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-8, prec=P.MS_PREC_FP32)
+    torch.cuda.synchronize()
+    out = {"mode": "solve", "workload": wl.name, "tol": 1e-8, "mixed": info}
+    x = torch.empty_like(g)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.apply(g, prec=P.MS_PREC_FP64, out=x)
+    torch.cuda.synchronize()
+    ev0.record()
+    s.apply(g, prec=P.MS_PREC_FP64, out=x)
+    ev1.record()
+    torch.cuda.synchronize()
+    t64 = ev0.elapsed_time(ev1) / 1000.0
+    out["fp64_matvec_s"] = t64
+    if args.full_fp64:
+        g64, info64 = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-8, prec=P.MS_PREC_FP64)
+        out["fp64"] = info64
+        out["rel_diff_mixed_vs_fp64"] = float(torch.linalg.norm(g - g64) / torch.linalg.norm(g64))
+    else:
+        out["fp64_extrapolated_s"] = t64 * info["matvecs"]
+        out["fp64_extrapolation"] = "FP64 mat-vec time x mat-vecs of the mixed solve"
+    print(json.dumps(out), flush=True)
+
+
+def run_grad(args):
+    """Gradients per second on the inverse-scattering workload: 2000 rigid discs, p = 16, omega = 4,
+    32 plane P-waves, 128 receivers on y = -0.5.  The data are the receiver fields of the same discs
+    with centres moved by N(0, 0.05^2) (synthetic truth); one gradient is the whole evaluation at the
+    current centres: ms_setup, the forward solve, the receiver fields, and ms_grad (adjoint solve plus
+    the centre, radius and frequency derivatives).  Both precisions to relative residual 1e-10."""
+    import copy
+
+    import torch
+
+    import paper_2608_26875_b300 as P
+    import synthetic as syn
+    wl = syn.config4()
+    rx = wl.receivers
+    truth = copy.deepcopy(wl)
+    truth.centres = wl.centres + np.random.default_rng(2006).normal(0.0, 0.05, wl.centres.shape)
+    st = P.Solver.from_workload(truth)
+    gt, _ = st.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP64)
+    d = st.fields(gt, rx)
+    st.close()
+    out = {"mode": "grad", "workload": wl.name, "M": wl.M, "nrhs": wl.nrhs, "receivers": int(rx.shape[0])}
+    for name, prec in (("mixed", P.MS_PREC_FP32), ("fp64", P.MS_PREC_FP64)):
+        times = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = P.Solver.from_workload(wl)
+            g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=prec)
+            u = s.fields(g, rx)
+            w = (u - d).contiguous()
+            gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-10, prec=prec)
+            loss = 0.5 * float(torch.sum(torch.abs(w) ** 2))
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s.close()
+            if it >= args.warmup:
+                times.append(dt)
+        out[name] = {"grads_per_s": len(times) / sum(times), "s_per_grad": sum(times) / len(times),
+                     "forward": info, "adjoint": ginfo, "loss": loss,
+                     "max_abs_dL_dcentre": float(gc.abs().max()), "dL_domega": gw}
+    print(json.dumps(out), flush=True)
+
+
 def launches_per_step(solver):
     """Kernels of one ms_apply: staging in/out, near sum (2 waves), FMM (per wave: P2M, M2M per
     level, M2L per level, L2L per level, L2P), M2S, reflect, S2L, S-apply."""
@@ -313,12 +390,18 @@ def main():
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small case for ncu (see run_profile)")
+    ap.add_argument("--mode", choices=["matvec", "solve", "grad"], default="matvec")
+    ap.add_argument("--full-fp64", action="store_true", help="solve mode: run the FP64 solve too")
     ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
     ap.add_argument("--M", type=int, default=2500)
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.mode == "solve":
+        run_solve(args)
+    elif args.mode == "grad":
+        run_grad(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

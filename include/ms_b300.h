@@ -51,6 +51,8 @@ extern "C" {
 #define MS_ERR_NONFINITE        -9    /* NaN or Inf met in a right-hand side or residual */
 #define MS_ERR_BREAKDOWN       -10    /* GMRES breakdown with a non-zero residual */
 #define MS_ERR_TOO_LARGE       -11    /* request exceeds the fixed scratch of ms_fields_noalloc */
+#define MS_ERR_TIMEOUT         -12    /* a tensor-core kernel gave up waiting on its own pipeline (the
+                                         result of that call is invalid; the context stays usable) */
 
 /* ------------------------------------------------------------------ precision of an apply / solve */
 #define MS_PREC_FP64   0   /* every operator step in FP64 */
@@ -99,6 +101,9 @@ typedef struct {
                                   d ~ 3 / (horizontal extent) and panels narrow enough for e^{i t dx} */
     int32_t grade;             /* extra panel edges at each branch point +-kp, +-ks of both layers and
                                   at c +- d 2^j, j < grade (default 0: none) */
+    int32_t tensor_cores;      /* MS_PREC_FP32 spectral contractions (M2S, S2L and their adjoints):
+                                  1 = tcgen05 tensor cores, 3xTF32 split with FP32 accumulation;
+                                  0 = CUDA-core FP32 (default).  Costs 16 M N_S bytes of device tables. */
 } ms_options;
 
 typedef struct {
@@ -133,6 +138,10 @@ int ms_setup(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
  * prec: MS_PREC_FP64 or MS_PREC_FP32 (operator steps in FP32; input/output stay FP64). */
 int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream);
 
+/* y = A^H x = x - (T^H + R^H) S^H x, the conjugate transpose of ms_apply (the system of the adjoint
+ * gradient).  Same layouts, precisions and errors as ms_apply. */
+int ms_apply_adjoint(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream);
+
 /* Building block view of the same operator: y = [S] (T_sel + R_sel) x with parts a mask of
  * MS_PART_T (or its halves MS_PART_T_NEAR, MS_PART_T_FAR) | MS_PART_R | MS_PART_S.  Without
  * MS_PART_S the result is a block of local (incoming) coefficients.  Same layouts and errors as
@@ -157,6 +166,21 @@ int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, vo
  * Errors: MS_ERR_RECEIVER_INSIDE if a receiver lies in an enclosing disc or at y >= 0. */
 int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
               void* stream);
+
+/* Adjoint gradient of a real loss L of the receiver fields u = ms_fields(gamma) of the solution
+ * gamma of ms_solve for the same incidences (the inverse-scattering use, Sec. 7.5): given
+ * w = dL/d conj(u) (so that dL = Re sum conj(w) du; for L = 1/2 |u - d|^2, w = u - d), returns
+ * dL/d(centres), dL/d(radii) and dL/d(omega) through one transposed solve A^H lambda = F^H w with the
+ * adjoint kernels and the position derivatives of the translation and Sommerfeld factors.
+ *   gamma: device [M][2][nc][nrhs] (the converged solution); w: device [nrhs][R][2] complex double;
+ *   rx: device [R][2]; tol: relative residual of the transposed solve; prec: its inner precision.
+ *   g_centres: device [M][2] double or NULL; g_radii: device [M] double or NULL (0 for prototype
+ *   particles); g_omega: host double or NULL (central differences of the assembled operator at
+ *   omega +- 1e-6 omega, which builds two temporary handles).
+ *   info (may be NULL) reports the transposed solve.  Returns MS_OK, MS_NOT_CONVERGED or an error. */
+int ms_grad(ms_handle* h, const ms_incidence* inc, const void* gamma, const void* w, const double* rx, int32_t R,
+            double tol, int32_t prec, double* g_centres, double* g_radii, double* g_omega, ms_solve_info* info,
+            void* stream);
 
 /* Allocation-free variant of ms_fields (the paper has no counterpart: this is a service for
  * callers).  Some callers cannot call cudaMalloc: code that runs while a stream is being captured

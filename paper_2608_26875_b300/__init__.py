@@ -44,7 +44,8 @@ class Solver:
     def __init__(self, centres, radius, bc, media, omega: float, p: int, proto=None, rotation=None,
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
-                 use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0):
+                 use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
+                 tensor_cores: bool = False):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -74,6 +75,7 @@ class Solver:
         o.restart, o.max_iters, o.check_geometry = restart, max_iters, int(bool(check_geometry))
         o.use_fmm, o.leaf_target = int(bool(use_fmm)), int(leaf_target)
         o.depth, o.grade = float(depth), int(grade)
+        o.tensor_cores = int(bool(tensor_cores))
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")
@@ -111,6 +113,14 @@ class Solver:
         y = out if out is not None else torch.empty_like(x)
         nat.check(nat.lib().ms_apply(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                      nrhs, prec, _stream(stream)), "ms_apply")
+        return y
+
+    def apply_adjoint(self, x: torch.Tensor, prec: int = MS_PREC_FP64, out=None, stream=None) -> torch.Tensor:
+        """y = A^H x (ms_apply_adjoint)."""
+        nrhs = self._check_vec(x)
+        y = out if out is not None else torch.empty_like(x)
+        nat.check(nat.lib().ms_apply_adjoint(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                             nrhs, prec, _stream(stream)), "ms_apply_adjoint")
         return y
 
     def operator(self, x: torch.Tensor, parts: int, prec: int = MS_PREC_FP64, stream=None) -> torch.Tensor:
@@ -156,6 +166,29 @@ class Solver:
                                       ctypes.c_void_p(rx.data_ptr()), R, ctypes.c_void_p(u.data_ptr()),
                                       _stream(stream)), "ms_fields")
         return u
+
+    def grad(self, kinds, angles, gamma: torch.Tensor, w: torch.Tensor, receivers, tol: float = 1e-10,
+             prec: int = MS_PREC_FP64, want_omega: bool = True, stream=None):
+        """Adjoint gradient (ms_grad) of a real loss with dL = Re sum conj(w) du at the receivers.
+        Returns (dL/dcentres (M,2), dL/dradii (M,), dL/domega or None, info) as float64 tensors."""
+        inc, keep = self._incidence(kinds, angles)
+        nrhs = self._check_vec(gamma)
+        rx = torch.as_tensor(np.ascontiguousarray(receivers, dtype=np.float64), device=gamma.device)
+        R = int(rx.shape[0])
+        if tuple(w.shape) != (nrhs, R, 2) or w.dtype != torch.complex128 or not w.is_contiguous():
+            raise ValueError(f"w must be a contiguous ({nrhs}, {R}, 2) complex128 CUDA tensor")
+        gc = torch.empty((self.M, 2), dtype=torch.float64, device=gamma.device)
+        gr = torch.empty((self.M,), dtype=torch.float64, device=gamma.device)
+        go = ctypes.c_double(0.0)
+        info = nat.SolveInfo()
+        st = nat.check(nat.lib().ms_grad(self._h, ctypes.byref(inc), ctypes.c_void_p(gamma.data_ptr()),
+                                         ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(rx.data_ptr()), R,
+                                         float(tol), prec, ctypes.c_void_p(gc.data_ptr()),
+                                         ctypes.c_void_p(gr.data_ptr()), ctypes.byref(go) if want_omega else None,
+                                         ctypes.byref(info), _stream(stream)), "ms_grad", allow_warning=True)
+        return gc, gr, (go.value if want_omega else None), {
+            "iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
+            "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
 
     def fields_noalloc(self, gamma: torch.Tensor, rx: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         """ms_fields without any allocation: rx (R, 2) float64 and out (nrhs, R, 2) complex128 are

@@ -25,6 +25,7 @@ MS_ERR_ALLOC = -7
 MS_ERR_NONFINITE = -9
 MS_ERR_BREAKDOWN = -10
 MS_ERR_TOO_LARGE = -11
+MS_ERR_TIMEOUT = -12
 
 MS_PREC_FP64 = 0
 MS_PREC_FP32 = 1
@@ -53,7 +54,8 @@ class Media(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("n_panels", c_int), ("nodes_per_panel", c_int), ("t_max", ctypes.c_double),
                 ("restart", c_int), ("max_iters", c_int), ("check_geometry", c_int),
-                ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int)]
+                ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int),
+                ("tensor_cores", c_int)]
 
 
 class Incidence(ctypes.Structure):
@@ -71,6 +73,7 @@ SIGNATURES = {
     "ms_setup": (c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(Media), ctypes.c_double, c_int,
                          ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]),
     "ms_apply": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, ctypes.c_void_p]),
+    "ms_apply_adjoint": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, ctypes.c_void_p]),
     "ms_operator": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, c_int,
                             ctypes.c_void_p]),
     "ms_rhs": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p]),
@@ -78,6 +81,9 @@ SIGNATURES = {
                          ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                           ctypes.c_void_p]),
+    "ms_grad": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                        c_int, ctypes.c_double, c_int, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields_noalloc": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                                   ctypes.c_void_p]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),

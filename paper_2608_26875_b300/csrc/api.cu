@@ -1,5 +1,6 @@
 // C ABI entry points other than setup and solve: apply, operator parts, right-hand side,
 // sizes, teardown and status strings.
+#include <algorithm>
 #include <complex>
 #include <vector>
 
@@ -32,6 +33,7 @@ int ms_ensure_workspace(ms_handle* h, int nrhs) {
     dfree(h->ws_y);
     dfree(h->ws_part);
     dfree(h->ws_u);
+    dfree(h->ws_uf);
     h->ws_nrhs = 0;
     size_t nvec = (size_t)h->M * 2 * h->nc * nrhs * sizeof(double2);
     size_t npart = (size_t)64 * 2 * h->NS * nrhs * sizeof(double2);
@@ -39,7 +41,8 @@ int ms_ensure_workspace(ms_handle* h, int nrhs) {
     cudaError_t e;
     if ((e = cudaMalloc(&h->ws_x, nvec)) != cudaSuccess || (e = cudaMalloc(&h->ws_a, nvec)) != cudaSuccess ||
         (e = cudaMalloc(&h->ws_y, nvec)) != cudaSuccess || (e = cudaMalloc(&h->ws_part, npart)) != cudaSuccess ||
-        (e = cudaMalloc(&h->ws_u, nu)) != cudaSuccess) {
+        (e = cudaMalloc(&h->ws_u, nu)) != cudaSuccess ||
+        (e = cudaMalloc(&h->ws_uf, (size_t)2 * std::max(h->NSp, h->NS) * nrhs * sizeof(float2))) != cudaSuccess) {
         h->last_cuda = (int)e;
         return MS_ERR_ALLOC;
     }
@@ -66,7 +69,9 @@ static int apply_common(ms_handle* h, const void* x, void* y, int nrhs, int prec
     if (rc) return rc;
     // without S the result is a local (incoming) block, scaled the other way
     bool local = !(parts & MS_PART_S) && (parts & (MS_PART_T | MS_PART_R | MS_PART_T_NEAR | MS_PART_T_FAR));
-    return ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, local);
+    if ((rc = ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, local))) return rc;
+    if (prec == MS_PREC_FP32 && h->opt.tensor_cores && (parts & MS_PART_R)) return ms_spectral_tc_status(h, st);
+    return MS_OK;
 }
 
 extern "C" int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
@@ -84,10 +89,12 @@ extern "C" int ms_operator(ms_handle* h, const void* x, void* y, int32_t nrhs, i
 }
 
 // ------------------------------------------------------------------ plane-wave right-hand side
-// a~0[m,b,n,r] = 2^{a_{m,b,n}} D_b(r) e^{i xi_r x_m + s_{b,r} y_m} i^n q_{b,r}^n  (Jacobi-Anger about x_m)
+// a~0[m,b,n,r] (+)= 2^{a_{m,b,n}} D_b(r) e^{i xi_r x_m + s_{b,r} y_m} i^n q_{b,r}^n  (Jacobi-Anger about
+// x_m); expo = zeros gives the unscaled a0.
 __global__ void k_incident(double2* __restrict__ as, const double2* __restrict__ centre, const int* __restrict__ expo,
                            const double* __restrict__ xi, const double2* __restrict__ amp,
-                           const double2* __restrict__ s, const double2* __restrict__ q, int M, int p, int nrhs) {
+                           const double2* __restrict__ s, const double2* __restrict__ q, int M, int p, int nrhs,
+                           int accumulate) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int nc = 2 * p + 1;
     long long total = (long long)M * 2 * nc * nrhs;
@@ -113,7 +120,15 @@ __global__ void k_incident(double2* __restrict__ as, const double2* __restrict__
     for (int k = 0; k < an; ++k) f = cmul(f, iq);
     double sc = pow2d(expo[row]);
     v = cmul(v, f);
-    as[i] = make_double2(v.x * sc, v.y * sc);
+    v = make_double2(v.x * sc, v.y * sc);
+    as[i] = accumulate ? cadd(as[i], v) : v;
+}
+
+void ms_incident_launch(ms_handle* h, const double* xi, const double2* amp, const double2* s, const double2* q,
+                        double2* out, const int* expo, int nrhs, int accumulate, cudaStream_t st) {
+    long long total = (long long)h->M * 2 * h->nc * nrhs;
+    k_incident<<<(int)((total + 255) / 256), 256, 0, st>>>(out, h->d.centre, expo, xi, amp, s, q, h->M, h->p, nrhs,
+                                                          accumulate);
 }
 
 extern "C" int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stream) {
@@ -151,9 +166,7 @@ extern "C" int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stre
     cudaMemcpyAsync(d_amp, amp.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_s, s.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_q, q.data(), nrhs * 2 * sizeof(double2), cudaMemcpyHostToDevice, st);
-    long long total = (long long)h->M * 2 * h->nc * nrhs;
-    k_incident<<<(int)((total + 255) / 256), 256, 0, st>>>((double2*)h->ws_a, h->d.centre, h->d.expo, d_xi, d_amp, d_s,
-                                                          d_q, h->M, h->p, nrhs);
+    ms_incident_launch(h, d_xi, d_amp, d_s, d_q, (double2*)h->ws_a, h->d.expo, nrhs, 0, st);
     rc = ms_check(h, cudaGetLastError());
     // b~ = S~ a~0 (identity off, S on, no operator part: the workspace a~ is used as is)
     if (!rc) rc = ms_sapply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, false, true, st);
@@ -180,8 +193,10 @@ extern "C" void ms_destroy(ms_handle* h) {
     dfree_t(h->d.proto); dfree_t(h->d.rot); dfree_t(h->d.sproto); dfree_t(h->d.node); dfree_t(h->d.wq);
     dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
     dfree_t(h->d.qpm_m); dfree_t(h->d.qpm_e); dfree_t(h->d.qps_m); dfree_t(h->d.qps_e);
+    dfree_t(h->d.zexp); dfree_t(h->d.dsdr);
+    ms_spectral_tc_free(h);
     ms_fmm_free(h);
-    dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u);
+    dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u); dfree(h->ws_uf);
     delete h;
 }
 
@@ -199,6 +214,7 @@ extern "C" const char* ms_status_string(int s) {
         case MS_ERR_NONFINITE: return "non-finite value";
         case MS_ERR_BREAKDOWN: return "GMRES breakdown";
         case MS_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the allocation-free call";
+        case MS_ERR_TIMEOUT: return "a tensor-core kernel gave up waiting on its pipeline";
         default: return "unknown status";
     }
 }

@@ -114,7 +114,7 @@ constexpr int TR_RB = 8;
 constexpr int TR_ICH = 42;     // dst orders per CTA (14 x TR_IB)
 constexpr int TR_JCH = 41;     // src orders per staged tile
 constexpr int TR_ES = 43;      // row stride of the operator tile (bank-conflict-free for rows 3*ib)
-constexpr int TR_SEQ = TR_ICH + TR_JCH;   // sequence entries a tile needs (<= ni + nj - 1)
+constexpr int TR_SEQ = TR_ICH + TR_JCH + 2;   // sequence entries a tile needs (<= ni + nj + 1)
 constexpr int TR_THREADS = 128;
 
 template <typename T> struct SeqRef;
@@ -219,8 +219,8 @@ k_translate(TransArgs a, SeqRef<T> seq) {
         // sequence segment: k = (j - Ps) - (i - Pd) for i in [ic0, ic0+ni), j in [jc, jc+nj); the
         // adjoint reads index -k of the reverse-direction sequence
         const int klo = (jc - a.Ps) - (ic0 + ni - 1 - a.Pd), khi = (jc + nj - 1 - a.Ps) - (ic0 - a.Pd);
-        const int kmin = a.adj ? -khi : klo;
-        const int nk = ni + nj - 1;
+        const int kmin = (a.adj ? -khi : klo) - a.deriv;      // one more entry each side for derivatives
+        const int nk = ni + nj - 1 + 2 * a.deriv;
         for (int e = threadIdx.x; e < nk; e += blockDim.x) seq.stage(so + K + kmin + e, &sq[e], &se[e]);
         const int* as = a.as + (long long)s * a.as_stride;
         for (int e = threadIdx.x; e < nj; e += blockDim.x) sas[e] = as[jc + e];
@@ -231,7 +231,16 @@ k_translate(TransArgs a, SeqRef<T> seq) {
             int ii = e / nj, jj = e % nj;
             int k = (jj + jc - a.Ps) - (ii + ic0 - a.Pd);
             if (a.adj) k = -k;
-            C v = SeqRef<T>::make(sq[k - kmin], se[k - kmin], a.sd * sad[ii] + a.ss * sas[jj]);
+            const int sc = a.sd * sad[ii] + a.ss * sas[jj];
+            C v;
+            if (a.deriv) {
+                // d/dv of h_k = Z_k(kap|v|) e^{ik arg v}: c1 h_{k-1} + c2 h_{k+1} (DLMF 10.6)
+                C lo = SeqRef<T>::make(sq[k - 1 - kmin], se[k - 1 - kmin], sc);
+                C hi = SeqRef<T>::make(sq[k + 1 - kmin], se[k + 1 - kmin], sc);
+                v = cadd(cmul(to_c<T>(a.dc1), lo), cmul(to_c<T>(a.dc2), hi));
+            } else {
+                v = SeqRef<T>::make(sq[k - kmin], se[k - kmin], sc);
+            }
             if (a.adj) {
                 v = cconj(v);
                 if (k & 1) v = mk(-v.x, -v.y);
@@ -620,15 +629,27 @@ __global__ void k_zero_c(double2* a, long long n) {
 }
 
 template <typename T>
-int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool far, cudaStream_t st) {
+int ms_translate_gen(ms_handle* h, const void* xs, void* dst_, int nrhs, bool near, bool far, int adj, int deriv_axis,
+                     bool unscaled, cudaStream_t st) {
     typedef typename CT<T>::c C;
     const bool f32 = sizeof(T) == 4;
     const int M = h->M, p = h->p, nc = h->nc;
+    C* dst = (C*)dst_;
+    const int* pexp = unscaled ? h->d.zexp : h->d.expo;      // particle exponents (zeros: unscaled)
+    const long long pstride = unscaled ? 0 : 2 * nc;
+    const double kb[2] = {h->kp_l, h->ks_l};
     int rc;
+    auto set_deriv = [&](TransArgs& a, int b) {
+        if (!deriv_axis) return;
+        a.deriv = 1;
+        double k = kb[b];
+        if (deriv_axis == 1) { a.dc1 = make_double2(0.5 * k, 0.0); a.dc2 = make_double2(-0.5 * k, 0.0); }
+        else { a.dc1 = make_double2(0.0, 0.5 * k); a.dc2 = make_double2(0.0, 0.5 * k); }
+    };
     if (!near) {
-        // far field only: start from zero (sizeof(C) bytes per coefficient)
+        // far field only: start from zero
         long long n = (long long)M * 2 * nc * nrhs * (long long)sizeof(C) / (long long)sizeof(double2);
-        k_zero_c<<<(int)((n + 255) / 256), 256, 0, st>>>((double2*)h->ws_a, n);
+        k_zero_c<<<(int)((n + 255) / 256), 256, 0, st>>>((double2*)dst, n);
         if ((rc = ms_check(h, cudaGetLastError()))) return rc;
     }
     for (int b = 0; b < 2 && near; ++b) {
@@ -636,11 +657,12 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
         const DevList& nl = h->fmm.near[b];
         a.dst_ptr = nl.ptr; a.task_src = nl.src; a.task_seq = nl.seq;
         a.K = 2 * p + 1; a.Pd = p; a.Ps = p;
-        a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
+        a.dst = dst + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
         a.src = (const C*)xs + (long long)b * nc * nrhs; a.src_stride = 2LL * nc * nrhs;
-        a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;
-        a.as = h->d.expo + b * nc; a.as_stride = 2 * nc; a.ss = 1;
-        a.nrhs = nrhs; a.accumulate = 0;
+        a.ad = pexp + (unscaled ? 0 : b * nc); a.ad_stride = pstride; a.sd = 1;
+        a.as = pexp + (unscaled ? 0 : b * nc); a.as_stride = pstride; a.ss = 1;
+        a.nrhs = nrhs; a.accumulate = 0; a.adj = adj;
+        set_deriv(a, b);
         if ((rc = ms_translate_launch(h, a, M, f32, st))) return rc;
     }
     const int L = h->fmm_levels;
@@ -650,6 +672,7 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
         auto mexp = [&](int lev) { return (C*)F.mexp[b][lev]; };
         auto lexp = [&](int lev) { return (C*)F.lexp[b][lev]; };
         auto ncl = [&](int lev) { return 2 * F.P[b][lev] + 1; };
+        auto bexp = [&](int lev) { return unscaled ? (const int*)h->d.zexp : (const int*)F.expo[b][lev]; };
         // P2M
         {
             TransArgs a{};
@@ -657,9 +680,9 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
             a.Pd = F.P[b][L]; a.Ps = p; a.K = a.Pd + a.Ps;
             a.dst = mexp(L); a.dst_stride = (long long)ncl(L) * nrhs;
             a.src = (const C*)xs + (long long)b * nc * nrhs; a.src_stride = 2LL * nc * nrhs;
-            a.ad = F.expo[b][L]; a.ad_stride = 0; a.sd = -1;
-            a.as = h->d.expo + b * nc; a.as_stride = 2 * nc; a.ss = 1;
-            a.nrhs = nrhs; a.accumulate = 0;
+            a.ad = bexp(L); a.ad_stride = 0; a.sd = -1;
+            a.as = pexp + (unscaled ? 0 : b * nc); a.as_stride = pstride; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0; a.adj = adj;
             if ((rc = ms_translate_launch(h, a, F.p2m[b].ndst, f32, st))) return rc;
         }
         // M2M upward
@@ -669,9 +692,9 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
             a.Pd = F.P[b][lev]; a.Ps = F.P[b][lev + 1]; a.K = a.Pd + a.Ps;
             a.dst = mexp(lev); a.dst_stride = (long long)ncl(lev) * nrhs;
             a.src = mexp(lev + 1); a.src_stride = (long long)ncl(lev + 1) * nrhs;
-            a.ad = F.expo[b][lev]; a.ad_stride = 0; a.sd = -1;
-            a.as = F.expo[b][lev + 1]; a.as_stride = 0; a.ss = 1;
-            a.nrhs = nrhs; a.accumulate = 0;
+            a.ad = bexp(lev); a.ad_stride = 0; a.sd = -1;
+            a.as = bexp(lev + 1); a.as_stride = 0; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0; a.adj = adj;
             if ((rc = ms_translate_launch(h, a, F.m2m[b][lev].ndst, f32, st))) return rc;
         }
         // M2L and L2L downward
@@ -681,9 +704,9 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
             a.Pd = F.P[b][lev]; a.Ps = F.P[b][lev]; a.K = 2 * a.Pd;
             a.dst = lexp(lev); a.dst_stride = (long long)ncl(lev) * nrhs;
             a.src = mexp(lev); a.src_stride = (long long)ncl(lev) * nrhs;
-            a.ad = F.expo[b][lev]; a.ad_stride = 0; a.sd = 1;
-            a.as = F.expo[b][lev]; a.as_stride = 0; a.ss = 1;
-            a.nrhs = nrhs; a.accumulate = 0;
+            a.ad = bexp(lev); a.ad_stride = 0; a.sd = 1;
+            a.as = bexp(lev); a.as_stride = 0; a.ss = 1;
+            a.nrhs = nrhs; a.accumulate = 0; a.adj = adj;
             if ((rc = ms_translate_launch(h, a, F.m2l[b][lev].ndst, f32, st))) return rc;
             if (lev > 2) {
                 TransArgs c{};
@@ -691,28 +714,36 @@ int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool 
                 c.Pd = F.P[b][lev]; c.Ps = F.P[b][lev - 1]; c.K = c.Pd + c.Ps;
                 c.dst = lexp(lev); c.dst_stride = (long long)ncl(lev) * nrhs;
                 c.src = lexp(lev - 1); c.src_stride = (long long)ncl(lev - 1) * nrhs;
-                c.ad = F.expo[b][lev]; c.ad_stride = 0; c.sd = 1;
-                c.as = F.expo[b][lev - 1]; c.as_stride = 0; c.ss = -1;
-                c.nrhs = nrhs; c.accumulate = 1;
+                c.ad = bexp(lev); c.ad_stride = 0; c.sd = 1;
+                c.as = bexp(lev - 1); c.as_stride = 0; c.ss = -1;
+                c.nrhs = nrhs; c.accumulate = 1; c.adj = adj;
                 if ((rc = ms_translate_launch(h, c, F.l2l[b][lev].ndst, f32, st))) return rc;
             }
         }
-        // L2P
+        // L2P (in adjoint mode: the adjoint of P2M); the particle-position derivative acts here
         {
             TransArgs a{};
             a.dst_ptr = F.l2p[b].ptr; a.task_src = F.l2p[b].src; a.task_seq = F.l2p[b].seq;
             a.Pd = p; a.Ps = F.P[b][L]; a.K = p + 1 + F.P[b][L];
-            a.dst = (C*)h->ws_a + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
+            a.dst = dst + (long long)b * nc * nrhs; a.dst_stride = 2LL * nc * nrhs;
             a.src = lexp(L); a.src_stride = (long long)ncl(L) * nrhs;
-            a.ad = h->d.expo + b * nc; a.ad_stride = 2 * nc; a.sd = 1;
-            a.as = F.expo[b][L]; a.as_stride = 0; a.ss = -1;
-            a.nrhs = nrhs; a.accumulate = 1;
+            a.ad = pexp + (unscaled ? 0 : b * nc); a.ad_stride = pstride; a.sd = 1;
+            a.as = bexp(L); a.as_stride = 0; a.ss = -1;
+            a.nrhs = nrhs; a.accumulate = 1; a.adj = adj;
+            set_deriv(a, b);
             if ((rc = ms_translate_launch(h, a, M, f32, st))) return rc;
         }
     }
     return MS_OK;
 }
 
+template <typename T>
+int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool far, cudaStream_t st) {
+    return ms_translate_gen<T>(h, xs, h->ws_a, nrhs, near, far, 0, 0, false, st);
+}
+
+template int ms_translate_gen<double>(ms_handle*, const void*, void*, int, bool, bool, int, int, bool, cudaStream_t);
+template int ms_translate_gen<float>(ms_handle*, const void*, void*, int, bool, bool, int, int, bool, cudaStream_t);
 template int ms_translate_scaled<double>(ms_handle*, const void*, int, bool, bool, cudaStream_t);
 template int ms_translate_scaled<float>(ms_handle*, const void*, int, bool, bool, cudaStream_t);
 

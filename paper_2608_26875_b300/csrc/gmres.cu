@@ -4,9 +4,7 @@
 // Gram-Schmidt applied twice (CGS2) with FP64 accumulation of every inner product, whatever the
 // vector precision.  The small Hessenberg / Givens work runs on the host in FP64.
 //
-// Both precisions use iterative refinement: the outer loop keeps x and r = b - A x in FP64 in
-// the ABI basis; each step solves the diagonally scaled system for the correction with
-// restarted GMRES in FP64 (MS_PREC_FP64, inner tolerance 1e-7) or FP32 (MS_PREC_FP32, 1e-5).
+// Both precisions use iterative refinement (ms_refine_solve), for A and for A^H.
 #include <math.h>
 
 #include <chrono>
@@ -105,19 +103,20 @@ __global__ void k_sub(const double2* a, const double2* b, double2* y, long long 
     if (e < n) y[e] = csub(a[e], b[e]);
 }
 
-// scaled FP32 copy of an unscaled FP64 vector, and back-accumulation x += 2^a d~
+// scaled FP32 copy of an unscaled FP64 vector (r 2^{-sign a}), and back-accumulation
+// x += 2^{sign a} d~ (sign = +1 for outgoing-type unknowns, -1 for the local-type adjoint ones)
 __global__ void k_scale_down_f(const double2* __restrict__ r, float2* __restrict__ rs, const int* __restrict__ expo,
-                               long long n, int nrhs) {
+                               long long n, int nrhs, int sign) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= n) return;
-    double s = pow2d(-expo[e / nrhs]);
+    double s = pow2d(-sign * expo[e / nrhs]);
     rs[e] = make_float2((float)(r[e].x * s), (float)(r[e].y * s));
 }
 __global__ void k_add_up_f(double2* __restrict__ x, const float2* __restrict__ ds, const int* __restrict__ expo,
-                           long long n, int nrhs) {
+                           long long n, int nrhs, int sign) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= n) return;
-    double s = pow2d(expo[e / nrhs]);
+    double s = pow2d(sign * expo[e / nrhs]);
     x[e].x += (double)ds[e].x * s;
     x[e].y += (double)ds[e].y * s;
 }
@@ -307,44 +306,51 @@ int gmres(Krylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x,
 
 }  // namespace
 
-extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
-                        ms_solve_info* info, void* stream) {
-    if (!h || !inc || !gamma || !(tol > 0)) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
-    const int nrhs = inc->nrhs;
-    if (nrhs < 1) return MS_ERR_ARG;
-    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+// Solve A x = b (adjoint = false) or A^H x = b (adjoint = true) for every column to relative residual
+// tol by iterative refinement.  The outer loop keeps x and r = b - op x in FP64 in the ABI basis; each
+// step solves the diagonally scaled system (D^-1 A D, or its adjoint D A^H D^-1 for the local-type
+// adjoint unknowns) for the correction with restarted GMRES in FP64 (inner tolerance 1e-7) or FP32
+// (1e-5).  x is overwritten (zero initial guess).
+int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
+                    ms_solve_info* info, cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = (cudaStream_t)stream;
     int rc = ms_ensure_workspace(h, nrhs);
     if (rc) return rc;
     const long long N = (long long)h->M * 2 * h->nc;
     const long long tot = N * nrhs;
-    double2 *b = nullptr, *x = (double2*)gamma;
-    if ((rc = ms_check(h, cudaMalloc(&b, tot * sizeof(double2))))) return rc;
-    if ((rc = ms_rhs(h, inc, b, stream))) { cudaFree(b); return rc; }
-    if ((rc = ms_check(h, cudaMemsetAsync(x, 0, tot * sizeof(double2), st)))) { cudaFree(b); return rc; }
-
+    const bool local = adjoint;                 // adjoint unknowns scale like local coefficients
+    const int sgn = local ? -1 : 1;
+    if ((rc = ms_check(h, cudaMemsetAsync(x, 0, tot * sizeof(double2), st)))) return rc;
     int iters = 0, matvecs = 0, refinements = 0;
     std::vector<double> relres;
     auto op64 = [&](const double2* in, double2* out) -> int {
         int r2;
-        if ((r2 = ms_to_scaled(h, in, h->ws_x, nrhs, MS_PREC_FP64, st))) return r2;
-        if ((r2 = ms_apply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st)))
-            return r2;
-        return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st);
+        if (!adjoint) {
+            if ((r2 = ms_to_scaled(h, in, h->ws_x, nrhs, MS_PREC_FP64, st))) return r2;
+            if ((r2 = ms_apply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true,
+                                              st)))
+                return r2;
+            return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st);
+        }
+        if ((r2 = ms_to_scaled(h, in, h->ws_y, nrhs, MS_PREC_FP64, st, true))) return r2;
+        if ((r2 = ms_apply_adjoint_scaled<double>(h, h->ws_y, h->ws_y, nrhs, st))) return r2;
+        return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st, true);
     };
-    // Iterative refinement.  The outer loop keeps x and r = b - A x in FP64 in the ABI basis, so
-    // the tolerance means what the caller reads.  Each step solves the diagonally scaled system
-    // D^-1 A D d~ = D^-1 r (D = diag(2^a), condition numbers many orders below A's) by GMRES in
-    // the inner precision, then x += D d~.
+    auto op32 = [&](const float2* in, float2* out) -> int {
+        if (adjoint) return ms_apply_adjoint_scaled<float>(h, in, out, nrhs, st);
+        return ms_apply_scaled<float>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+    };
+    auto op64s = [&](const double2* in, double2* out) -> int {
+        if (adjoint) return ms_apply_adjoint_scaled<double>(h, in, out, nrhs, st);
+        return ms_apply_scaled<double>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+    };
     Krylov<double> K64{h, st, N, nrhs, 1};
     double2* r = nullptr;
     void *rs = nullptr, *ds = nullptr;
     const size_t esz = prec == MS_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     if ((rc = K64.init()) || (rc = ms_check(h, cudaMalloc(&r, tot * sizeof(double2)))) ||
         (rc = ms_check(h, cudaMalloc(&rs, tot * esz))) || (rc = ms_check(h, cudaMalloc(&ds, tot * esz)))) {
-        cudaFree(b); cudaFree(r); cudaFree(rs); cudaFree(ds);
+        cudaFree(r); cudaFree(rs); cudaFree(ds);
         return rc ? rc : MS_ERR_ALLOC;
     }
     Krylov<double>* K64i = nullptr;
@@ -356,12 +362,6 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
         K32 = new Krylov<float>{h, st, N, nrhs, h->opt.restart};
         rc = K32->init();
     }
-    auto op32 = [&](const float2* in, float2* out) -> int {
-        return ms_apply_scaled<float>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
-    };
-    auto op64s = [&](const double2* in, double2* out) -> int {
-        return ms_apply_scaled<double>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
-    };
     std::vector<double> bn, rn;
     if (!rc) rc = K64.norms(b, bn);
     const double inner_tol = prec == MS_PREC_FP64 ? 1e-7 : 1e-5;
@@ -375,7 +375,7 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
         bool all = true;
         relres.assign(nrhs, 0.0);
         for (int c = 0; c < nrhs; ++c) {
-            if (!std::isfinite(rn[c])) { rc = MS_ERR_NONFINITE; break; }
+            if (!std::isfinite(rn[c]) || !std::isfinite(bn[c])) { rc = MS_ERR_NONFINITE; break; }
             relres[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
             all = all && relres[c] <= tol;
         }
@@ -383,21 +383,22 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
         int it = 0;
         std::vector<double> inner_res;
         if (prec == MS_PREC_FP64) {
-            if ((rc = ms_to_scaled(h, r, rs, nrhs, MS_PREC_FP64, st))) break;
+            if ((rc = ms_to_scaled(h, r, rs, nrhs, MS_PREC_FP64, st, local))) break;
             if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
             if ((rc = gmres<double>(*K64i, op64s, (const double2*)rs, (double2*)ds, inner_tol, left, it, matvecs,
                                     inner_res)))
                 break;
-            if ((rc = ms_from_scaled(h, ds, K64.w, nrhs, MS_PREC_FP64, st))) break;
+            if ((rc = ms_from_scaled(h, ds, K64.w, nrhs, MS_PREC_FP64, st, local))) break;
             std::vector<cd> one(nrhs, cd(1.0, 0.0));
-            if ((rc = K64.update(K64.w, 1, x, one, -1.0))) break;       // x += D d~
+            if ((rc = K64.update(K64.w, 1, x, one, -1.0))) break;       // x += D d~ (or D^-1 d~)
         } else {
-            k_scale_down_f<<<nb(tot, 256), 256, 0, st>>>(r, (float2*)rs, h->d.expo, tot, nrhs);
+            k_scale_down_f<<<nb(tot, 256), 256, 0, st>>>(r, (float2*)rs, h->d.expo, tot, nrhs, sgn);
             if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
             if ((rc = gmres<float>(*K32, op32, (const float2*)rs, (float2*)ds, inner_tol, left, it, matvecs,
                                    inner_res)))
                 break;
-            k_add_up_f<<<nb(tot, 256), 256, 0, st>>>(x, (const float2*)ds, h->d.expo, tot, nrhs);
+            if (h->opt.tensor_cores && (rc = ms_spectral_tc_status(h, st))) break;
+            k_add_up_f<<<nb(tot, 256), 256, 0, st>>>(x, (const float2*)ds, h->d.expo, tot, nrhs, sgn);
         }
         iters += it;
         left -= it;
@@ -407,7 +408,6 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
     delete K32;
     cudaFree(r); cudaFree(rs); cudaFree(ds);
     cudaStreamSynchronize(st);
-    cudaFree(b);
     double worst = 0;
     for (double v : relres) worst = std::max(worst, v);
     if (info) {
@@ -419,4 +419,44 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
     }
     if (rc) return rc;
     return worst <= tol ? MS_OK : MS_NOT_CONVERGED;
+}
+
+extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
+                        ms_solve_info* info, void* stream) {
+    if (!h || !inc || !gamma || !(tol > 0)) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    const int nrhs = inc->nrhs;
+    if (nrhs < 1) return MS_ERR_ARG;
+    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ms_ensure_workspace(h, nrhs);
+    if (rc) return rc;
+    const long long tot = (long long)h->M * 2 * h->nc * nrhs;
+    double2* b = nullptr;
+    if ((rc = ms_check(h, cudaMalloc(&b, tot * sizeof(double2))))) return rc;
+    if ((rc = ms_rhs(h, inc, b, stream))) { cudaFree(b); return rc; }
+    rc = ms_refine_solve(h, b, (double2*)gamma, nrhs, tol, prec, false, info, st);
+    cudaFree(b);
+    if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+// y = A^H x in the ABI basis (the transposed system of the gradient), through the adjoint kernels.
+extern "C" int ms_apply_adjoint(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
+    if (!h || !x || !y || nrhs < 1) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+    int rc = ms_ensure_workspace(h, nrhs);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ms_to_scaled(h, x, h->ws_y, nrhs, prec, st, true))) return rc;
+    if (prec == MS_PREC_FP64)
+        rc = ms_apply_adjoint_scaled<double>(h, h->ws_y, h->ws_y, nrhs, st);
+    else
+        rc = ms_apply_adjoint_scaled<float>(h, h->ws_y, h->ws_y, nrhs, st);
+    if (rc) return rc;
+    if ((rc = ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, true))) return rc;
+    if (prec == MS_PREC_FP32 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
+    return MS_OK;
 }

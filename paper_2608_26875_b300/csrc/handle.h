@@ -24,6 +24,8 @@ struct TransArgs {
     const long long* task_seq;
     int K, Pd, Ps;   // K: centre of each stored sequence (h_k at offset K + k), >= Pd + Ps
     int adj;         // 1: apply the adjoint of the reverse-direction translation (see fmm.cu)
+    int deriv;       // 1: entries c1 h_{k-1} + c2 h_{k+1} (derivative in the translation vector)
+    double2 dc1, dc2;
     void* dst;
     long long dst_stride;
     const void* src;
@@ -75,10 +77,22 @@ struct MsDeviceTables {
     double2* seq64 = nullptr;
     float2* seqm = nullptr;
     int* seqe = nullptr;
+    int* zexp = nullptr;           // zeros: exponent table of the unscaled (gradient) path
+    double2* dsdr = nullptr;       // [M][nc][2][2] derivative of the disc scattering matrix in R_m
+    // tensor-core spectral path (FP32): exponential factors per (wave, particle, node), rows padded
+    // to NSp nodes with zeros, and node-contiguous copies of the FP32 power tables
+    float2* es2l = nullptr;        // [2][M][NSp] e^{i xi_q x_m + s_b y_m}
+    float2* em2s = nullptr;        // [2][M][NSp] e^{s_b y_m - i xi_q x_m}
+    float2* qpmT_m = nullptr;      // [2][nc][NSp] mantissa / exponent of (-i)^n q^n / (i pi s)
+    int* qpmT_e = nullptr;
+    float2* qpsT_m = nullptr;      // [2][nc][NSp] mantissa / exponent of i^n q^n W_q
+    int* qpsT_e = nullptr;
+    int* tc_err = nullptr;         // set by a tensor-core kernel whose pipeline wait gave up
 };
 
 struct ms_handle {
     int M = 0, p = 0, nc = 0, NS = 0;
+    int NSp = 0;                   // NS rounded up to the tensor-core K chunk (16 nodes)
     double omega = 0;
     double lam_u = 0, mu_u = 0, lam_l = 0, mu_l = 0;
     double kp_u = 0, ks_u = 0, kp_l = 0, ks_l = 0;
@@ -86,7 +100,9 @@ struct ms_handle {
     bool any_proto = false;
     ms_options opt{};
     MsDeviceTables d;
-    std::vector<double> h_centres, h_radius;
+    std::vector<double> h_centres, h_radius, h_rot, h_protoS;
+    std::vector<int> h_bc, h_proto;
+    ms_media media{};
     std::vector<int> h_expo;       // host copy of the exponents
     int nnz_near = 0;
     int fmm_levels = 0;            // 0: direct sum over all pairs
@@ -99,6 +115,7 @@ struct ms_handle {
     void* ws_y = nullptr;          // scaled output [M][2][nc][nrhs]
     void* ws_part = nullptr;       // M2S split-K partials [chunks][2][NS][nrhs] (double2)
     void* ws_u = nullptr;          // [2][NS][nrhs] double2 upgoing amplitudes, then reflected D
+    void* ws_uf = nullptr;         // [2][NSp][nrhs] float2 copy of the reflected amplitudes (tensor cores)
     int last_cuda = 0;
 };
 
@@ -109,15 +126,35 @@ template <typename T>
 int ms_apply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, int parts, bool identity,
                     cudaStream_t st);
 template <typename T>
-int ms_local_scaled(ms_handle* h, const void* xs, int nrhs, int parts, cudaStream_t st);
+int ms_local_scaled(ms_handle* h, const void* xs, int nrhs, int parts, cudaStream_t st, int adj = 0);
 template <typename T>
 int ms_sapply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, bool identity, bool apply_s,
-                     cudaStream_t st);
+                     cudaStream_t st, int adj = 0, const void* in = nullptr);
+template <typename T>
+int ms_apply_adjoint_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, cudaStream_t st);
+template <typename T>
+int ms_m2s_launch(ms_handle* h, const void* xs, int nrhs, const int* expo, int adj, int* nchunks, cudaStream_t st);
+int ms_reflect_launch(ms_handle* h, const double2* part, int nchunks, double2* out, int nrhs, int adj,
+                      cudaStream_t st);
+template <typename T>
+int ms_s2l_launch(ms_handle* h, const double2* ud, void* out, int nrhs, const int* expo, int adj, int accumulate,
+                  cudaStream_t st);
 int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target);
 template <typename T>
 int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool far, cudaStream_t st);
+template <typename T>
+int ms_translate_gen(ms_handle* h, const void* xs, void* dst, int nrhs, bool near, bool far, int adj, int deriv_axis,
+                     bool unscaled, cudaStream_t st);
 int ms_fmm_workspace(ms_handle* h, int nrhs);
 void ms_fmm_free(ms_handle* h);
-int ms_to_scaled(ms_handle* h, const void* x, void* xs, int nrhs, int prec, cudaStream_t st);
+int ms_to_scaled(ms_handle* h, const void* x, void* xs, int nrhs, int prec, cudaStream_t st, bool local = false);
+int ms_spectral_tc_setup(ms_handle* h);
+void ms_spectral_tc_free(ms_handle* h);
+int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nchunks, cudaStream_t st);
+int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int adj, int accumulate,
+                     cudaStream_t st);
+int ms_spectral_tc_status(ms_handle* h, cudaStream_t st);
+int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
+                    ms_solve_info* info, cudaStream_t st);
 int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st,
                    bool local = false);

@@ -22,13 +22,14 @@
 namespace {
 
 // ------------------------------------------------------------------ precision staging
+// outgoing-type blocks: x~ = x 2^-a (sign = +1); local-type blocks: a~ = a 2^a (sign = -1)
 template <typename T>
 __global__ void k_to_scaled(const double2* __restrict__ x, typename CT<T>::c* __restrict__ xs,
-                            const int* __restrict__ expo, long long total, int nrhs) {
+                            const int* __restrict__ expo, long long total, int nrhs, int sign) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= total) return;
     int row = (int)(i / nrhs);
-    double s = pow2d(-expo[row]);
+    double s = pow2d(-sign * expo[row]);
     double2 v = x[i];
     xs[i] = to_c<T>(make_double2(v.x * s, v.y * s));
 }
@@ -97,7 +98,10 @@ constexpr int M2S_QB = 4;
 constexpr int M2S_RB = 4;
 constexpr int M2S_THREADS = 128;
 
-template <typename T>
+// ADJ = 1 computes the adjoint of the Sommerfeld-to-local map instead (C^H): factor
+// conj(e^{i xi x + s y} [i^n q^n W_q]) tau = e^{-i conj(xi) x + conj(s) y} conj(.) tau, read from the
+// S2L table and conjugated.
+template <typename T, int ADJ>
 __global__ void __launch_bounds__(M2S_THREADS)
 k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
       const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
@@ -133,7 +137,8 @@ k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
             C ev = mk((T)0, (T)0);
             if (q < NS) {
                 double2 xi = node[q], s = sq[q * 2 + b];
-                ev = SpecExp<T>::eval(s.x * cl.y + xi.y * cl.x, s.y * cl.y - xi.x * cl.x);
+                ev = ADJ ? SpecExp<T>::eval(s.x * cl.y - xi.y * cl.x, -s.y * cl.y - xi.x * cl.x)
+                         : SpecExp<T>::eval(s.x * cl.y + xi.y * cl.x, s.y * cl.y - xi.x * cl.x);
             }
             Eq[qi] = ev;
         }
@@ -143,7 +148,10 @@ k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
             int n = e / M2S_QT, qi = e % M2S_QT;
             int q = q0 + qi;
             C f = mk((T)0, (T)0);
-            if (q < NS) f = cmul(Eq[qi], qpow.get(((long long)b * NS + q) * nc + n, al[n]));
+            if (q < NS) {
+                C qv = qpow.get(((long long)b * NS + q) * nc + n, al[n]);
+                f = cmul(Eq[qi], ADJ ? cconj(qv) : qv);
+            }
             F[n * (M2S_QT + 1) + qi] = f;
         }
         __syncthreads();
@@ -178,8 +186,9 @@ k_m2s(const typename CT<T>::c* __restrict__ xs, double2* __restrict__ part,
 
 // ------------------------------------------------------------------ reduce chunks + reflect
 // U_b(q,r) = sum_chunks part; D(q,r) = R(xi_q) U(q,r).  Output ud[b][q][r] holds D.
+// adj = 1: D = R(xi_q)^H U (conjugate transpose, for the adjoint operator).
 __global__ void k_reflect(const double2* __restrict__ part, double2* __restrict__ ud,
-                          const double2* __restrict__ refl, int nchunks, int NS, int nrhs) {
+                          const double2* __restrict__ refl, int nchunks, int NS, int nrhs, int adj) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NS * nrhs) return;
     int q = i / nrhs, r = i % nrhs;
@@ -189,8 +198,13 @@ __global__ void k_reflect(const double2* __restrict__ part, double2* __restrict_
         us = cadd(us, part[(((size_t)c * 2 + 1) * NS + q) * nrhs + r]);
     }
     const double2* R = refl + (size_t)q * 4;
-    ud[(size_t)(0 * NS + q) * nrhs + r] = cadd(cmul(R[0], up), cmul(R[1], us));
-    ud[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(R[2], up), cmul(R[3], us));
+    if (adj) {
+        ud[(size_t)(0 * NS + q) * nrhs + r] = cadd(cmul(cconj(R[0]), up), cmul(cconj(R[2]), us));
+        ud[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(cconj(R[1]), up), cmul(cconj(R[3]), us));
+    } else {
+        ud[(size_t)(0 * NS + q) * nrhs + r] = cadd(cmul(R[0], up), cmul(R[1], us));
+        ud[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(R[2], up), cmul(R[3], us));
+    }
 }
 
 // ------------------------------------------------------------------ Sommerfeld-to-local
@@ -203,7 +217,9 @@ constexpr int S2L_NB = 3;
 constexpr int S2L_RB = 8;
 constexpr int S2L_THREADS = 128;
 
-template <typename T>
+// ADJ = 1 computes the adjoint of the multipole-to-Sommerfeld map instead (B^H): factor
+// conj(e^{-i xi x + s y} [(-i)^n q^n / (i pi s)]) tau = e^{i conj(xi) x + conj(s) y} conj(.) tau.
+template <typename T, int ADJ>
 __global__ void __launch_bounds__(S2L_THREADS)
 k_s2l(const double2* __restrict__ ud, typename CT<T>::c* __restrict__ as,
       const double2* __restrict__ centre, const int* __restrict__ expo, const double2* __restrict__ node,
@@ -238,12 +254,14 @@ k_s2l(const double2* __restrict__ ud, typename CT<T>::c* __restrict__ as,
         }
         for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
             double2 xi = node[qb + qi], s = sq[(qb + qi) * 2 + b];
-            Eq[qi] = SpecExp<T>::eval(-xi.y * cm.x + s.x * cm.y, xi.x * cm.x + s.y * cm.y);
+            Eq[qi] = ADJ ? SpecExp<T>::eval(xi.y * cm.x + s.x * cm.y, xi.x * cm.x - s.y * cm.y)
+                         : SpecExp<T>::eval(-xi.y * cm.x + s.x * cm.y, xi.x * cm.x + s.y * cm.y);
         }
         __syncthreads();
         for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
             int n = e % nc, qi = e / nc;
-            G[qi * (nc + 1) + n] = cmul(Eq[qi], qpow.get(((long long)b * NS + qb + qi) * nc + n, am[n]));
+            C qv = qpow.get(((long long)b * NS + qb + qi) * nc + n, am[n]);
+            G[qi * (nc + 1) + n] = cmul(Eq[qi], ADJ ? cconj(qv) : qv);
         }
         __syncthreads();
         if (act) {
@@ -285,7 +303,7 @@ template <typename T>
 __global__ void k_sapply_disc(const typename CT<T>::c* __restrict__ xs, const typename CT<T>::c* __restrict__ as,
                               typename CT<T>::c* __restrict__ ys, const typename CT<T>::c* __restrict__ sd,
                               const int* __restrict__ proto, int M, int nc, int nrhs, int identity,
-                              int apply_s) {
+                              int apply_s, int adj) {
     typedef typename CT<T>::c C;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long total = (long long)M * nc * nrhs;
@@ -300,8 +318,13 @@ __global__ void k_sapply_disc(const typename CT<T>::c* __restrict__ xs, const ty
     C yp, y2;
     if (apply_s) {
         const C* S = sd + ((size_t)m * nc + n) * 4;
-        yp = cadd(cmul(S[0], ap), cmul(S[1], a2));
-        y2 = cadd(cmul(S[2], ap), cmul(S[3], a2));
+        if (adj) {   // S~^H per mode
+            yp = cadd(cmul(cconj(S[0]), ap), cmul(cconj(S[2]), a2));
+            y2 = cadd(cmul(cconj(S[1]), ap), cmul(cconj(S[3]), a2));
+        } else {
+            yp = cadd(cmul(S[0], ap), cmul(S[1], a2));
+            y2 = cadd(cmul(S[2], ap), cmul(S[3], a2));
+        }
     } else {
         yp = ap;
         y2 = a2;
@@ -321,7 +344,8 @@ template <typename T>
 __global__ void k_sapply_proto(const typename CT<T>::c* __restrict__ xs, const typename CT<T>::c* __restrict__ as,
                                typename CT<T>::c* __restrict__ ys, const double2* __restrict__ sproto,
                                const int* __restrict__ proto, const double* __restrict__ rot,
-                               const int* __restrict__ expo, int p, int nrhs, int identity, int apply_s) {
+                               const int* __restrict__ expo, int p, int nrhs, int identity, int apply_s,
+                               int adj) {
     typedef typename CT<T>::c C;
     const int m = blockIdx.x;
     const int pi = proto[m];
@@ -334,16 +358,18 @@ __global__ void k_sapply_proto(const typename CT<T>::c* __restrict__ xs, const t
         int row = t / nrhs, r = t % nrhs;
         C y;
         if (apply_s) {
-            int ni = row % nc - p;
-            int ai = expo[m * N2 + row];
             C s = mk((T)0, (T)0);
             for (int col = 0; col < N2; ++col) {
-                int nj = col % nc - p;
+                // entry (row, col) of S~, or of S~^H = conj(S~(col, row)) in adjoint mode
+                int rr = adj ? col : row, cc = adj ? row : col;
+                int ni2 = rr % nc - p, nj = cc % nc - p;
                 double sn, cs;
-                sincos(-(double)(ni - nj) * phi, &sn, &cs);
-                double2 v = cmul(S[(size_t)row * N2 + col], make_double2(cs, sn));
-                double sc = pow2d(-ai - expo[m * N2 + col]);
-                cfma(s, to_c<T>(make_double2(v.x * sc, v.y * sc)), a[(size_t)col * nrhs + r]);
+                sincos(-(double)(ni2 - nj) * phi, &sn, &cs);
+                double2 v = cmul(S[(size_t)rr * N2 + cc], make_double2(cs, sn));
+                double sc = pow2d(-expo[m * N2 + rr] - expo[m * N2 + cc]);
+                v = make_double2(v.x * sc, v.y * sc);
+                if (adj) v = cconj(v);
+                cfma(s, to_c<T>(v), a[(size_t)col * nrhs + r]);
             }
             y = s;
         } else {
@@ -366,12 +392,15 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ host launchers
 
-int ms_to_scaled(ms_handle* h, const void* x, void* xs, int nrhs, int prec, cudaStream_t st) {
+int ms_to_scaled(ms_handle* h, const void* x, void* xs, int nrhs, int prec, cudaStream_t st, bool local) {
     long long total = (long long)h->M * 2 * h->nc * nrhs;
+    int sign = local ? -1 : 1;
     if (prec == MS_PREC_FP64)
-        k_to_scaled<double><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (double2*)xs, h->d.expo, total, nrhs);
+        k_to_scaled<double><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (double2*)xs, h->d.expo, total, nrhs,
+                                                             sign);
     else
-        k_to_scaled<float><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (float2*)xs, h->d.expo, total, nrhs);
+        k_to_scaled<float><<<nblk(total, 256), 256, 0, st>>>((const double2*)x, (float2*)xs, h->d.expo, total, nrhs,
+                                                            sign);
     return ms_check(h, cudaGetLastError());
 }
 
@@ -400,45 +429,94 @@ static int m2s_chunks(ms_handle* h) {
     return chunks;
 }
 
-// a~ (workspace) = (T~ + R~) xs for the parts selected (scaled basis); zero if none.
+// ------------------------------------------------------------------ spectral part, host side
+// M2S (or, adj = 1, its Sommerfeld-to-local adjoint C^H) into the chunk partials of the workspace;
+// returns the number of chunks.  expo: the scale exponents (zeros for the unscaled FP64 path).
 template <typename T>
-int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStream_t st) {
+int ms_m2s_launch(ms_handle* h, const void* xs_, int nrhs, const int* expo, int adj, int* nchunks,
+                  cudaStream_t st) {
     typedef typename CT<T>::c C;
-    const C* xs = (const C*)xs_;
-    C* as = (C*)h->ws_a;
     const int M = h->M, p = h->p, nc = h->nc, NS = h->NS;
+    int chunks = m2s_chunks(h);
+    int chunk_len = (M + chunks - 1) / chunks;
+    chunks = (M + chunk_len - 1) / chunk_len;
+    *nchunks = chunks;
+    dim3 g((NS + M2S_QT - 1) / M2S_QT, chunks, 2);
+    size_t smem = ((size_t)nc * (M2S_QT + 1) + (size_t)nc * nrhs + M2S_QT) * sizeof(C);
+    int tiles = (M2S_QT / M2S_QB) * ((nrhs + M2S_RB - 1) / M2S_RB);
+    int thr = std::max(32, std::min(M2S_THREADS, (tiles + 31) / 32 * 32));
+    const C* xs = (const C*)xs_;
+    if (!adj) {
+        cudaFuncSetAttribute(k_m2s<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2s<T, 0><<<g, thr, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, expo, h->d.node, h->d.sq,
+                                          qref_m2s<T>(h), M, p, NS, nrhs, chunk_len);
+    } else {
+        cudaFuncSetAttribute(k_m2s<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2s<T, 1><<<g, thr, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, expo, h->d.node, h->d.sq,
+                                          qref_s2l<T>(h), M, p, NS, nrhs, chunk_len);
+    }
+    return ms_check(h, cudaGetLastError());
+}
+
+int ms_reflect_launch(ms_handle* h, const double2* part, int nchunks, double2* out, int nrhs, int adj,
+                      cudaStream_t st) {
+    k_reflect<<<nblk((long long)h->NS * nrhs, 256), 256, 0, st>>>(part, out, h->d.refl, nchunks, h->NS, nrhs, adj);
+    return ms_check(h, cudaGetLastError());
+}
+
+// S2L of the amplitudes ud[2][N_S][nrhs] (or, adj = 1, the multipole-to-Sommerfeld adjoint B^H) into
+// the particle block out (written, or added when accumulate).
+template <typename T>
+int ms_s2l_launch(ms_handle* h, const double2* ud, void* out, int nrhs, const int* expo, int adj, int accumulate,
+                  cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const int M = h->M, p = h->p, nc = h->nc, NS = h->NS;
+    size_t smem2 = ((size_t)S2L_QC * (nc + 1) + (size_t)S2L_QC * nrhs + S2L_QC) * sizeof(C);
+    int tiles2 = ((nc + S2L_NB - 1) / S2L_NB) * ((nrhs + S2L_RB - 1) / S2L_RB);
+    int thr2 = std::max(32, std::min(256, (tiles2 + 31) / 32 * 32));
+    if (!adj) {
+        cudaFuncSetAttribute(k_s2l<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        k_s2l<T, 0><<<dim3(M, 2), thr2, smem2, st>>>(ud, (C*)out, h->d.centre, expo, h->d.node, h->d.sq,
+                                                     qref_s2l<T>(h), p, NS, nrhs, accumulate);
+    } else {
+        cudaFuncSetAttribute(k_s2l<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        k_s2l<T, 1><<<dim3(M, 2), thr2, smem2, st>>>(ud, (C*)out, h->d.centre, expo, h->d.node, h->d.sq,
+                                                     qref_m2s<T>(h), p, NS, nrhs, accumulate);
+    }
+    return ms_check(h, cudaGetLastError());
+}
+
+// a~ (workspace) = (T~ + R~) xs for the parts selected (scaled basis); zero if none.  With adj = 1
+// the adjoints T~^H and R~^H = D B^H R^H C^H D instead.
+template <typename T>
+int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStream_t st, int adj) {
+    typedef typename CT<T>::c C;
+    C* as = (C*)h->ws_a;
+    const int M = h->M, nc = h->nc;
     long long nall = (long long)M * 2 * nc * nrhs;
     bool have = false;
     if (parts & (MS_PART_T | MS_PART_T_NEAR | MS_PART_T_FAR)) {
         bool near = (parts & (MS_PART_T | MS_PART_T_NEAR)) != 0;
         bool far = (parts & (MS_PART_T | MS_PART_T_FAR)) != 0;
-        if (int rc = ms_translate_scaled<T>(h, xs_, nrhs, near, far, st)) return rc;
+        if (int rc = ms_translate_gen<T>(h, xs_, h->ws_a, nrhs, near, far, adj, 0, false, st)) return rc;
         have = true;
     }
     if (parts & MS_PART_R) {
-        int chunks = m2s_chunks(h);
-        int chunk_len = (M + chunks - 1) / chunks;
-        chunks = (M + chunk_len - 1) / chunk_len;
-        dim3 g((NS + M2S_QT - 1) / M2S_QT, chunks, 2);
-        size_t smem = ((size_t)nc * (M2S_QT + 1) + (size_t)nc * nrhs + M2S_QT) * sizeof(C);
-        cudaFuncSetAttribute(k_m2s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int tiles = (M2S_QT / M2S_QB) * ((nrhs + M2S_RB - 1) / M2S_RB);
-        int thr = std::max(32, std::min(M2S_THREADS, (tiles + 31) / 32 * 32));
-        QRef<T> qm = qref_m2s<T>(h);
-        k_m2s<T><<<g, thr, smem, st>>>(xs, (double2*)h->ws_part, h->d.centre, h->d.expo, h->d.node, h->d.sq, qm, M, p,
-                                       NS, nrhs, chunk_len);
-        if (int rc = ms_check(h, cudaGetLastError())) return rc;
-        k_reflect<<<nblk((long long)NS * nrhs, 256), 256, 0, st>>>((const double2*)h->ws_part, (double2*)h->ws_u,
-                                                                   h->d.refl, chunks, NS, nrhs);
-        if (int rc = ms_check(h, cudaGetLastError())) return rc;
-        size_t smem2 = ((size_t)S2L_QC * (nc + 1) + (size_t)S2L_QC * nrhs + S2L_QC) * sizeof(C);
-        cudaFuncSetAttribute(k_s2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-        int tiles2 = ((nc + S2L_NB - 1) / S2L_NB) * ((nrhs + S2L_RB - 1) / S2L_RB);
-        int thr2 = std::max(32, std::min(256, (tiles2 + 31) / 32 * 32));
-        QRef<T> qs = qref_s2l<T>(h);
-        k_s2l<T><<<dim3(M, 2), thr2, smem2, st>>>((const double2*)h->ws_u, as, h->d.centre, h->d.expo, h->d.node,
-                                                  h->d.sq, qs, p, NS, nrhs, have ? 1 : 0);
-        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+        int chunks = 0;
+        const bool tcore = sizeof(T) == 4 && h->opt.tensor_cores;
+        if (tcore) {
+            if (int rc = ms_m2s_tc_launch(h, (const float2*)xs_, nrhs, adj, &chunks, st)) return rc;
+        } else if (int rc = ms_m2s_launch<T>(h, xs_, nrhs, h->d.expo, adj, &chunks, st)) {
+            return rc;
+        }
+        if (int rc = ms_reflect_launch(h, (const double2*)h->ws_part, chunks, (double2*)h->ws_u, nrhs, adj, st))
+            return rc;
+        if (tcore) {
+            if (int rc = ms_s2l_tc_launch(h, (const double2*)h->ws_u, (float2*)as, nrhs, adj, have ? 1 : 0, st))
+                return rc;
+        } else if (int rc = ms_s2l_launch<T>(h, (const double2*)h->ws_u, as, nrhs, h->d.expo, adj, have ? 1 : 0, st)) {
+            return rc;
+        }
         have = true;
     }
     if (!have) {
@@ -448,23 +526,23 @@ int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStre
     return MS_OK;
 }
 
-// ys = [xs -] [S~] a~ with a~ the workspace (scaled basis).
+// ys = [xs -] [S~ or S~^H] in, with `in` the workspace a~ unless given.
 template <typename T>
 int ms_sapply_scaled(ms_handle* h, const void* xs_, void* ys_, int nrhs, bool identity, bool apply_s,
-                     cudaStream_t st) {
+                     cudaStream_t st, int adj, const void* in) {
     typedef typename CT<T>::c C;
     const C* xs = (const C*)xs_;
     C* ys = (C*)ys_;
-    const C* as = (const C*)h->ws_a;
+    const C* as = (const C*)(in ? in : h->ws_a);
     const int M = h->M, p = h->p, nc = h->nc;
     const C* sd = (const C*)(sizeof(T) == 8 ? (const void*)h->d.sdisc : (const void*)h->d.sdisc_f);
     long long nd = (long long)M * nc * nrhs;
     k_sapply_disc<T><<<nblk(nd, 256), 256, 0, st>>>(xs, as, ys, sd, h->d.proto, M, nc, nrhs, identity ? 1 : 0,
-                                                    apply_s ? 1 : 0);
+                                                    apply_s ? 1 : 0, adj);
     if (int rc = ms_check(h, cudaGetLastError())) return rc;
     if (h->any_proto) {
         k_sapply_proto<T><<<M, 256, 0, st>>>(xs, as, ys, h->d.sproto, h->d.proto, h->d.rot, h->d.expo, p, nrhs,
-                                             identity ? 1 : 0, apply_s ? 1 : 0);
+                                             identity ? 1 : 0, apply_s ? 1 : 0, adj);
         if (int rc = ms_check(h, cudaGetLastError())) return rc;
     }
     return MS_OK;
@@ -473,14 +551,37 @@ int ms_sapply_scaled(ms_handle* h, const void* xs_, void* ys_, int nrhs, bool id
 // ys = [xs -] [S~] (T~ + R~) xs for the parts selected (all in the scaled basis).
 template <typename T>
 int ms_apply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, int parts, bool identity, cudaStream_t st) {
-    int rc = ms_local_scaled<T>(h, xs, nrhs, parts, st);
+    int rc = ms_local_scaled<T>(h, xs, nrhs, parts, st, 0);
     if (rc) return rc;
-    return ms_sapply_scaled<T>(h, xs, ys, nrhs, identity, (parts & MS_PART_S) != 0, st);
+    return ms_sapply_scaled<T>(h, xs, ys, nrhs, identity, (parts & MS_PART_S) != 0, st, 0, nullptr);
 }
 
-template int ms_local_scaled<double>(ms_handle*, const void*, int, int, cudaStream_t);
-template int ms_local_scaled<float>(ms_handle*, const void*, int, int, cudaStream_t);
-template int ms_sapply_scaled<double>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t);
-template int ms_sapply_scaled<float>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t);
+template <typename T>
+__global__ void k_csub(const typename CT<T>::c* a, const typename CT<T>::c* b, typename CT<T>::c* y, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = csub(a[i], b[i]);
+}
+
+// Adjoint operator in the scaled basis: ys = y - (T~^H + R~^H) S~^H y, y = xs.  Uses ws_x as scratch,
+// so xs and ys must not be ws_x.
+template <typename T>
+int ms_apply_adjoint_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    int rc;
+    if ((rc = ms_sapply_scaled<T>(h, nullptr, h->ws_x, nrhs, false, true, st, 1, xs))) return rc;
+    if ((rc = ms_local_scaled<T>(h, h->ws_x, nrhs, MS_PART_T | MS_PART_R, st, 1))) return rc;
+    long long n = (long long)h->M * 2 * h->nc * nrhs;
+    k_csub<T><<<nblk(n, 256), 256, 0, st>>>((const C*)xs, (const C*)h->ws_a, (C*)ys, n);
+    return ms_check(h, cudaGetLastError());
+}
+
+template int ms_local_scaled<double>(ms_handle*, const void*, int, int, cudaStream_t, int);
+template int ms_local_scaled<float>(ms_handle*, const void*, int, int, cudaStream_t, int);
+template int ms_sapply_scaled<double>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t, int, const void*);
+template int ms_sapply_scaled<float>(ms_handle*, const void*, void*, int, bool, bool, cudaStream_t, int, const void*);
 template int ms_apply_scaled<double>(ms_handle*, const void*, void*, int, int, bool, cudaStream_t);
 template int ms_apply_scaled<float>(ms_handle*, const void*, void*, int, int, bool, cudaStream_t);
+template int ms_apply_adjoint_scaled<double>(ms_handle*, const void*, void*, int, cudaStream_t);
+template int ms_apply_adjoint_scaled<float>(ms_handle*, const void*, void*, int, cudaStream_t);
+template int ms_m2s_launch<double>(ms_handle*, const void*, int, const int*, int, int*, cudaStream_t);
+template int ms_s2l_launch<double>(ms_handle*, const double2*, void*, int, const int*, int, int, cudaStream_t);

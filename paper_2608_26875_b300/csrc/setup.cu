@@ -163,6 +163,35 @@ static void disc_mode(int kind, int n, double kp, double ks, double R, int bc, d
     M[3] = mu * (g2 - g1 / R + nn * nn * g / (R * R));         // t_theta from S
 }
 
+// d/dR of disc_mode: derivatives of Z_n(kR) up to third order (DLMF 10.6.1 applied repeatedly).
+static void disc_mode_dR(int kind, int n, double kp, double ks, double R, int bc, double lam, double mu, cd M[4]) {
+    cd I(0, 1);
+    auto zd = [&](double k, cd* z) {   // z[0..3] = Z, dZ/dR, d2Z/dR2, d3Z/dR3 of Z_n(kR)
+        cd a = zfun(kind, n - 3, k * R), b = zfun(kind, n - 2, k * R), c = zfun(kind, n - 1, k * R),
+           d = zfun(kind, n, k * R), e = zfun(kind, n + 1, k * R), f = zfun(kind, n + 2, k * R),
+           g = zfun(kind, n + 3, k * R);
+        z[0] = d;
+        z[1] = 0.5 * k * (c - e);
+        z[2] = 0.25 * k * k * (b - 2.0 * d + f);
+        z[3] = 0.125 * k * k * k * (a - 3.0 * c + 3.0 * e - g);
+    };
+    cd f[4], g[4];
+    zd(kp, f);
+    zd(ks, g);
+    double nn = (double)n, R2 = R * R, R3 = R2 * R;
+    if (bc == 0) {
+        M[0] = f[2];
+        M[1] = I * nn / R2 * g[0] - I * nn / R * g[1];
+        M[2] = -I * nn / R2 * f[0] + I * nn / R * f[1];
+        M[3] = g[2];
+        return;
+    }
+    M[0] = -lam * kp * kp * f[1] + 2.0 * mu * f[3];
+    M[1] = -2.0 * mu * I * nn * (g[2] / R - 2.0 * g[1] / R2 + 2.0 * g[0] / R3);
+    M[2] = 2.0 * mu * I * nn * (f[2] / R - 2.0 * f[1] / R2 + 2.0 * f[0] / R3);
+    M[3] = mu * (g[3] - g[2] / R + g[1] / R2 + nn * nn * g[1] / R2 - 2.0 * nn * nn * g[0] / R3);
+}
+
 // ------------------------------------------------------------------ device upload helper
 template <typename X>
 static int upload(ms_handle* h, X** dst, const X* src, size_t n) {
@@ -185,6 +214,7 @@ extern "C" void ms_default_options(ms_options* o) {
     o->leaf_target = 10;
     o->depth = 0.5;
     o->grade = 0;
+    o->tensor_cores = 0;
 }
 
 // Panel edges of the Sommerfeld rule on [-t_max, t_max]: n uniform panels (edge k at
@@ -228,7 +258,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     ms_default_options(&opt);
     if (o) opt = *o;
     if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || opt.restart < 1 || opt.max_iters < 1 ||
-        opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30)
+        opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30 ||
+        (opt.tensor_cores != 0 && opt.tensor_cores != 1))
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {
@@ -291,6 +322,11 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     h->n_proto = g->n_proto;
     h->h_centres.assign(g->centres, g->centres + 2 * M);
     h->h_radius.assign(g->radius, g->radius + M);
+    h->h_bc.assign(g->bc, g->bc + M);
+    if (g->proto) h->h_proto.assign(g->proto, g->proto + M);
+    if (g->rotation) h->h_rot.assign(g->rotation, g->rotation + M);
+    if (g->n_proto > 0) h->h_protoS.assign(g->proto_S, g->proto_S + (size_t)g->n_proto * 2 * (2 * nc) * (2 * nc));
+    h->media = *md;
     int rc = MS_OK;
 
     // scale exponents a = round(log2((k R / 2)^|n| / |n|!))
@@ -311,6 +347,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
 
     // scattering matrices: discs closed form, scaled S~ = D^-1 S D^-1
     std::vector<double2> sdisc((size_t)M * nc * 4);
+    std::vector<double2> dsdr((size_t)M * nc * 4);   // unscaled dS/dR (zero for prototypes)
     std::vector<float2> sdisc_f((size_t)M * nc * 4);
     std::vector<int> proto(M, -1);
     std::vector<double> rot(M, 0.0);
@@ -329,9 +366,20 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
                 cd MH[4], MJ[4];
                 disc_mode(1, n, h->kp_l, h->ks_l, g->radius[m], g->bc[m], h->lam_l, h->mu_l, MH);
                 disc_mode(0, n, h->kp_l, h->ks_l, g->radius[m], g->bc[m], h->lam_l, h->mu_l, MJ);
+                cd MHc[4] = {MH[0], MH[1], MH[2], MH[3]};
                 cd B[4] = {-MJ[0], -MJ[1], -MJ[2], -MJ[3]};
                 if (!solve_small(2, MH, B, 2)) { ms_destroy(h); return MS_ERR_ARG; }
                 for (int k = 0; k < 4; ++k) S[k] = B[k];
+                // dS = -M_H^{-1} (dM_J + dM_H S)
+                cd dMH[4], dMJ[4];
+                disc_mode_dR(1, n, h->kp_l, h->ks_l, g->radius[m], g->bc[m], h->lam_l, h->mu_l, dMH);
+                disc_mode_dR(0, n, h->kp_l, h->ks_l, g->radius[m], g->bc[m], h->lam_l, h->mu_l, dMJ);
+                cd rhs[4];
+                for (int r = 0; r < 2; ++r)
+                    for (int c = 0; c < 2; ++c)
+                        rhs[r * 2 + c] = -(dMJ[r * 2 + c] + dMH[r * 2 + 0] * S[0 * 2 + c] + dMH[r * 2 + 1] * S[1 * 2 + c]);
+                if (!solve_small(2, MHc, rhs, 2)) { ms_destroy(h); return MS_ERR_ARG; }
+                for (int k = 0; k < 4; ++k) dsdr[((size_t)m * nc + i) * 4 + k] = d2(rhs[k]);
             }
             int ap = expo[((size_t)m * 2 + 0) * nc + i], as = expo[((size_t)m * 2 + 1) * nc + i];
             int ea[2] = {ap, as};
@@ -401,6 +449,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         (rc = upload(h, &h->d.expo, expo.data(), expo.size())) ||
         (rc = upload(h, &h->d.sdisc, sdisc.data(), sdisc.size())) ||
         (rc = upload(h, &h->d.sdisc_f, sdisc_f.data(), sdisc_f.size())) ||
+        (rc = upload(h, &h->d.dsdr, dsdr.data(), dsdr.size())) ||
         (rc = upload(h, &h->d.proto, proto.data(), proto.size())) ||
         (rc = upload(h, &h->d.rot, rot.data(), rot.size())) ||
         (rc = upload(h, &h->d.node, node.data(), node.size())) ||
@@ -424,6 +473,10 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
             return rc;
         }
     }
+    {
+        std::vector<int> z(std::max((size_t)M * 2 * nc, (size_t)4096), 0);
+        if ((rc = upload(h, &h->d.zexp, z.data(), z.size()))) { ms_destroy(h); return rc; }
+    }
     if (h->any_proto) {
         size_t nn = (size_t)g->n_proto * (2 * nc) * (2 * nc);
         std::vector<double2> sp(nn);
@@ -431,6 +484,10 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         if ((rc = upload(h, &h->d.sproto, sp.data(), nn))) { ms_destroy(h); return rc; }
     }
     if ((rc = ms_build_translations(h, opt.use_fmm, opt.leaf_target))) {
+        ms_destroy(h);
+        return rc;
+    }
+    if (opt.tensor_cores && (rc = ms_spectral_tc_setup(h))) {
         ms_destroy(h);
         return rc;
     }

@@ -1,0 +1,474 @@
+// Spectral part of the FP32 operator on the fifth-generation tensor cores (tcgen05, kind::tf32),
+// with FP32-level accuracy from the 3xTF32 split (a b ~ ah bh + ah bl + al bh, FP32 accumulation
+// in tensor memory).
+//
+// Both spectral maps are dense complex contractions across the block of right-hand sides:
+//   S2L (Sec. 5.3):  a~_b[(m,n), r] (+)= sum_q G_b(q, m, n) D_b(q, r)
+//   M2S (Sec. 5.4):  U_b[q, r]       =  sum_(l,n) F_b(q, l, n) x~_b[(l,n), r]
+// with generated operator entries  G = E_s2l(q, m) Qs(q, n) 2^{a(m,b,n)},  F = E_m2s(q, l) Qm(q, n) 2^{a(l,b,n)},
+//   E_s2l(q, m) = e^{i xi_q x_m + s_b y_m},  E_m2s(q, l) = e^{s_b y_l - i xi_q x_l},
+//   Qs(q, n) = i^n q_b^n W_q,  Qm(q, n) = (-i)^n q_b^n / (i pi s_b)          (ja/stm/eee1, pts1/sed1/sed2).
+// The adjoints (B^H for S2L-shaped, C^H for M2S-shaped launches) take the other map's tables, conjugated.
+//
+// Complex products as real MMAs.  With k = 2 kappa + t running over the contracted complex index kappa:
+//   A[r][2k]   = Re Y(kappa, r),  A[r][2k+1]   = -Im Y(kappa, r),   r < 64
+//   A[64+r][2k] = Im Y(kappa, r), A[64+r][2k+1] = Re Y(kappa, r)
+//   B[j][2k]   = Re Z(j, kappa),  B[j][2k+1]   = Im Z(j, kappa)
+// gives C = A B^T with C[r][j] = Re sum Z Y and C[64+r][j] = Im sum Z Y.  A (the data: amplitudes or
+// coefficients, M = 128) and B (the generated operator, N = 256 rows) are written into shared memory
+// by the CTA's threads, K-chunk by K-chunk, in a two-stage pipeline; one thread issues the MMAs and
+// commits them to the stage's mbarrier.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int KC = 32;                         // real K per chunk (16 complex)
+constexpr int KCC = KC / 2;
+constexpr int NT = 256;                        // MMA N: generated-operator rows per tile
+constexpr int MA = 128;                        // MMA M: 2 x 64 right-hand-side columns
+constexpr int THREADS = 256;
+constexpr int NSTAGE = 2;
+constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
+constexpr uint32_t B_TILE = NT * KC * 4;       // 32 KB
+constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;
+constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;
+constexpr uint32_t IDESC = tc::idesc_tf32(MA, NT);
+constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
+constexpr uint32_t TMEM_COLS = 256;
+static_assert(SMEM <= 227 * 1024, "shared memory");
+
+struct Stage {
+    float *ah, *al, *bh, *bl;
+};
+__device__ __forceinline__ Stage stage_ptrs(unsigned char* base, int s) {
+    float* p = reinterpret_cast<float*>(base + (size_t)s * STAGE);
+    return {p, p + MA * KC, p + 2 * MA * KC, p + 2 * MA * KC + NT * KC};
+}
+
+__device__ __forceinline__ void put4(float* hi, float* lo, int off, float a, float b, float c, float d) {
+    float4 h, l;
+    tc::split(a, h.x, l.x);
+    tc::split(b, h.y, l.y);
+    tc::split(c, h.z, l.z);
+    tc::split(d, h.w, l.w);
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+// A rows from two consecutive complex values y0, y1 of column r (row rp = r or 64 + r)
+__device__ __forceinline__ void put_a(const Stage& st, int rp, int kk, float2 y0, float2 y1) {
+    const int off = tc::kmajor_off(rp, 4 * kk, KC);
+    if (rp < 64)
+        put4(st.ah, st.al, off, y0.x, -y0.y, y1.x, -y1.y);
+    else
+        put4(st.ah, st.al, off, y0.y, y0.x, y1.y, y1.x);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 gen_entry(float2 e, float2 qm, int ex, int conj) {
+    float2 v = cmulf(e, qm);
+    float f = pow2f(ex);
+    return make_float2(v.x * f, conj ? -v.y * f : v.y * f);
+}
+
+// The shared pipeline.  P provides load_a(Stage, chunk), gen_b(Stage, chunk), epilogue(tmem, ok).
+template <class P>
+__device__ __forceinline__ void run_pipeline(P& pol, int nchunks, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NSTAGE);
+    int* fail = reinterpret_cast<int*>(tslot + 1);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) tc::mbar_init(&bar[s], 1);
+        tc::mbar_fence_init();
+        *fail = 0;
+    }
+    if (tid < 32) tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    int issued = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % NSTAGE;
+        if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
+        const Stage st = stage_ptrs(smem, s);
+        pol.load_a(st, c);
+        pol.gen_b(st, c);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (*fail) break;
+        if (tid == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t a0 = tc::smem_u32(pass == 2 ? st.al : st.ah);
+                const uint32_t b0 = tc::smem_u32(pass == 1 ? st.bl : st.bh);
+#pragma unroll
+                for (int ks = 0; ks < KC / 8; ++ks) {
+                    tc::mma_tf32(tmem, tc::smem_desc(a0 + ks * 256, LBO, SBO), tc::smem_desc(b0 + ks * 256, LBO, SBO),
+                                 IDESC, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(&bar[s]);
+        }
+        issued = c + 1;
+    }
+    // the last commit covers every MMA issued before it
+    bool ok = !*fail && issued == nchunks;
+    if (issued > 0) {
+        const int c = issued - 1;
+        if (!tc::mbar_wait(&bar[c % NSTAGE], (c / NSTAGE) & 1)) ok = false;
+    }
+    tc::fence_after();
+    if (!ok && tid == 0) atomicExch(err, 1);
+    pol.epilogue(tmem, ok && nchunks > 0);
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) tc::tmem_free(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ S2L-shaped launch
+// out_b[(m,n), r] (+)= sum_q Z(q, m, n) D_b(q, r);  tile = 256 consecutive rows j = m nc + n.
+struct S2LPolicy {
+    const float2* D;       // [NSp][nrhs] this wave (zero beyond NS)
+    const float2* E;       // [M][NSp] this wave
+    const float2* Qm;      // [nc][NSp] this wave
+    const int* Qe;
+    const int* expo;       // [M][2][nc]
+    float2* out;           // [M][2][nc][nrhs]
+    int M, nc, NSp, nrhs, b, j0, accumulate, conj;
+    int j, m, n, a;
+    bool valid;
+
+    __device__ void init() {
+        j = j0 + threadIdx.x;
+        valid = j < M * nc;
+        m = valid ? j / nc : 0;
+        n = valid ? j - m * nc : 0;
+        a = valid ? expo[((size_t)m * 2 + b) * nc + n] : 0;
+    }
+    __device__ void load_a(const Stage& st, int c) {
+        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
+        const bool ok = r < nrhs;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int kk = h * 4 + u;
+            const int q = c * KCC + 2 * kk;
+            float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+            if (ok) {
+                y0 = D[(size_t)q * nrhs + r];
+                y1 = D[(size_t)(q + 1) * nrhs + r];
+            }
+            put_a(st, rp, kk, y0, y1);
+        }
+    }
+    __device__ void gen_b(const Stage& st, int c) {
+        const int t = threadIdx.x;
+        const int q0 = c * KCC;
+#pragma unroll
+        for (int kk = 0; kk < KC / 4; ++kk) {
+            float2 g0 = make_float2(0.f, 0.f), g1 = g0;
+            if (valid) {
+                const int q = q0 + 2 * kk;
+                const float4 e = *reinterpret_cast<const float4*>(E + (size_t)m * NSp + q);
+                const float4 qm = *reinterpret_cast<const float4*>(Qm + (size_t)n * NSp + q);
+                const int2 qe = *reinterpret_cast<const int2*>(Qe + (size_t)n * NSp + q);
+                g0 = gen_entry(make_float2(e.x, e.y), make_float2(qm.x, qm.y), qe.x + a, conj);
+                g1 = gen_entry(make_float2(e.z, e.w), make_float2(qm.z, qm.w), qe.y + a, conj);
+            }
+            put4(st.bh, st.bl, tc::kmajor_off(t, 4 * kk, KC), g0.x, g0.y, g1.x, g1.y);
+        }
+    }
+    __device__ void epilogue(uint32_t tmem, bool ok) {
+        if (!ok) return;
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int quarter = w & 3, half = w >> 2;
+        const int rp = 32 * quarter + lane, r = rp & 63, comp = rp >> 6;
+#pragma unroll 1
+        for (int cb = 0; cb < 8; ++cb) {
+            const int col0 = 128 * half + 16 * cb;
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
+            if (r >= nrhs) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int jj = j0 + col0 + i;
+                if (jj >= M * nc) break;
+                const int m2 = jj / nc, n2 = jj - m2 * nc;
+                float* dst = reinterpret_cast<float*>(out + (((size_t)m2 * 2 + b) * nc + n2) * nrhs + r) + comp;
+                *dst = accumulate ? *dst + v[i] : v[i];
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float2* __restrict__ Qm,
+         const int* __restrict__ Qe, const int* __restrict__ expo, float2* __restrict__ out, int M, int nc, int NSp,
+         int nrhs, int accumulate, int conj, int* err) {
+    const int b = blockIdx.y;
+    S2LPolicy pol{D + (size_t)b * NSp * nrhs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp,
+                  Qe + (size_t)b * nc * NSp, expo, out, M, nc, NSp, nrhs, b, (int)blockIdx.x * NT, accumulate, conj};
+    pol.init();
+    run_pipeline(pol, NSp / KCC, err);
+}
+
+// ------------------------------------------------------------------ M2S-shaped launch
+// part[split][b][q][r] = sum_{(l,n) in split's rows} Z(q, l, n) x~_b[(l,n), r];  tile = 256 nodes.
+struct M2SPolicy {
+    const float2* xs;      // [M][2][nc][nrhs]
+    const float2* E;       // [M][NSp] this wave
+    const float2* Qm;      // [NS][nc] this wave
+    const int* Qe;
+    const int* expo;
+    double2* part;         // [nsplit][2][NS][nrhs]
+    int M, nc, NS, NSp, nrhs, b, q0, i0, i1, split, conj;
+    int q;
+    bool valid;
+
+    __device__ void init() {
+        q = q0 + threadIdx.x;
+        valid = q < NS;
+    }
+    __device__ void load_a(const Stage& st, int c) {
+        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
+        const bool ok = r < nrhs;
+        const int base = i0 + c * KCC + h * 8;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int kk = h * 4 + u;
+            float2 y[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int i = base + 2 * u + v;
+                y[v] = make_float2(0.f, 0.f);
+                if (ok && i < i1) {
+                    const int l = i / nc, n = i - l * nc;
+                    y[v] = xs[(((size_t)l * 2 + b) * nc + n) * nrhs + r];
+                }
+            }
+            put_a(st, rp, kk, y[0], y[1]);
+        }
+    }
+    __device__ void gen_b(const Stage& st, int c) {
+        const int t = threadIdx.x;
+        const int ib = i0 + c * KCC;
+        int l = ib / nc, n = ib - l * nc;
+        float2 e = make_float2(0.f, 0.f);
+        if (valid && ib < i1) e = E[(size_t)l * NSp + q];
+#pragma unroll
+        for (int kk = 0; kk < KC / 4; ++kk) {
+            float2 g[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int i = ib + 2 * kk + v;
+                g[v] = make_float2(0.f, 0.f);
+                if (valid && i < i1) {
+                    const float2 qm = Qm[(size_t)q * nc + n];
+                    const int ex = Qe[(size_t)q * nc + n] + expo[((size_t)l * 2 + b) * nc + n];
+                    g[v] = gen_entry(e, qm, ex, conj);
+                }
+                if (++n == nc) {
+                    n = 0;
+                    ++l;
+                    if (valid && i + 1 < i1) e = E[(size_t)l * NSp + q];
+                }
+            }
+            put4(st.bh, st.bl, tc::kmajor_off(t, 4 * kk, KC), g[0].x, g[0].y, g[1].x, g[1].y);
+        }
+    }
+    __device__ void epilogue(uint32_t tmem, bool ok) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int quarter = w & 3, half = w >> 2;
+        const int rp = 32 * quarter + lane, r = rp & 63, comp = rp >> 6;
+#pragma unroll 1
+        for (int cb = 0; cb < 8; ++cb) {
+            const int col0 = 128 * half + 16 * cb;
+            float v[16];
+            if (ok) {
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
+            if (r >= nrhs) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int qq = q0 + col0 + i;
+                if (qq >= NS) break;
+                double* dst = reinterpret_cast<double*>(part + (((size_t)split * 2 + b) * NS + qq) * nrhs + r) + comp;
+                *dst = (double)v[i];
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const float2* __restrict__ Qm,
+         const int* __restrict__ Qe, const int* __restrict__ expo, double2* __restrict__ part, int M, int nc, int NS,
+         int NSp, int nrhs, int rows_per_split, int conj, int* err) {
+    const int b = blockIdx.z, split = blockIdx.y;
+    const int i0 = split * rows_per_split, i1 = min(M * nc, i0 + rows_per_split);
+    M2SPolicy pol{xs, E + (size_t)b * M * NSp, Qm + (size_t)b * NS * nc, Qe + (size_t)b * NS * nc, expo, part,
+                  M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
+    pol.init();
+    const int nchunks = i1 > i0 ? (i1 - i0 + KCC - 1) / KCC : 0;
+    run_pipeline(pol, nchunks, err);
+}
+
+// ------------------------------------------------------------------ setup-time tables
+// E_s2l[b][m][q] = e^{i xi_q x_m + s_b y_m},  E_m2s[b][m][q] = e^{s_b y_m - i xi_q x_m}  (FP64, rounded)
+__global__ void k_etab(const double2* __restrict__ centre, const double2* __restrict__ node,
+                       const double2* __restrict__ sq, float2* __restrict__ es2l, float2* __restrict__ em2s, int M,
+                       int NS, int NSp) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= 2LL * M * NSp) return;
+    const int q = (int)(i % NSp);
+    const long long bm = i / NSp;
+    const int m = (int)(bm % M), b = (int)(bm / M);
+    if (q >= NS) {
+        es2l[i] = make_float2(0.f, 0.f);
+        em2s[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const double2 c = centre[m], xi = node[q], s = sq[q * 2 + b];
+    double re = -xi.y * c.x + s.x * c.y, im = xi.x * c.x + s.y * c.y;
+    double mg = exp(re), sn, cs;
+    sincos(im, &sn, &cs);
+    es2l[i] = make_float2((float)(mg * cs), (float)(mg * sn));
+    re = s.x * c.y + xi.y * c.x;
+    im = s.y * c.y - xi.x * c.x;
+    mg = exp(re);
+    sincos(im, &sn, &cs);
+    em2s[i] = make_float2((float)(mg * cs), (float)(mg * sn));
+}
+
+// amplitudes [2][NS][nrhs] FP64 -> [2][NSp][nrhs] FP32, zero beyond NS
+__global__ void k_amp_f(const double2* __restrict__ ud, float2* __restrict__ uf, int NS, int NSp, int nrhs) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= 2LL * NSp * nrhs) return;
+    const int r = (int)(i % nrhs);
+    const long long bq = i / nrhs;
+    const int q = (int)(bq % NSp), b = (int)(bq / NSp);
+    uf[i] = q < NS ? make_float2((float)ud[((size_t)b * NS + q) * nrhs + r].x,
+                                 (float)ud[((size_t)b * NS + q) * nrhs + r].y)
+                   : make_float2(0.f, 0.f);
+}
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+int ms_spectral_tc_setup(ms_handle* h) {
+    const int M = h->M, NS = h->NS, nc = h->nc;
+    const int NSp = (NS + KCC - 1) / KCC * KCC;
+    h->NSp = NSp;
+    MsDeviceTables& d = h->d;
+    size_t ne = (size_t)2 * M * NSp;
+    if (cudaMalloc(&d.es2l, ne * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&d.em2s, ne * sizeof(float2)) != cudaSuccess)
+        return MS_ERR_ALLOC;
+    k_etab<<<nblk((long long)ne, 256), 256>>>(d.centre, d.node, d.sq, d.es2l, d.em2s, M, NS, NSp);
+    if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    // node-contiguous copies [b][n][NSp] of the FP32 power tables
+    std::vector<float2> hm((size_t)2 * NS * nc), hs((size_t)2 * NS * nc);
+    std::vector<int> em((size_t)2 * NS * nc), es((size_t)2 * NS * nc);
+    cudaMemcpy(hm.data(), d.qpm_m, hm.size() * sizeof(float2), cudaMemcpyDeviceToHost);
+    cudaMemcpy(hs.data(), d.qps_m, hs.size() * sizeof(float2), cudaMemcpyDeviceToHost);
+    cudaMemcpy(em.data(), d.qpm_e, em.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (int rc = ms_check(h, cudaMemcpy(es.data(), d.qps_e, es.size() * sizeof(int), cudaMemcpyDeviceToHost)))
+        return rc;
+    size_t nt = (size_t)2 * nc * NSp;
+    std::vector<float2> tm(nt, make_float2(0.f, 0.f)), ts(nt, make_float2(0.f, 0.f));
+    std::vector<int> tme(nt, 0), tse(nt, 0);
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < NS; ++q)
+            for (int n = 0; n < nc; ++n) {
+                size_t src = ((size_t)b * NS + q) * nc + n, dst = ((size_t)b * nc + n) * NSp + q;
+                tm[dst] = hm[src];
+                ts[dst] = hs[src];
+                tme[dst] = em[src];
+                tse[dst] = es[src];
+            }
+    if (cudaMalloc(&d.qpmT_m, nt * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&d.qpsT_m, nt * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&d.qpmT_e, nt * sizeof(int)) != cudaSuccess || cudaMalloc(&d.qpsT_e, nt * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d.tc_err, sizeof(int)) != cudaSuccess)
+        return MS_ERR_ALLOC;
+    cudaMemcpy(d.qpmT_m, tm.data(), nt * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.qpsT_m, ts.data(), nt * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.qpmT_e, tme.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.qpsT_e, tse.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemset(d.tc_err, 0, sizeof(int));
+    cudaFuncSetAttribute(k_s2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaFuncSetAttribute(k_m2s_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    return ms_check(h, cudaDeviceSynchronize());
+}
+
+void ms_spectral_tc_free(ms_handle* h) {
+    MsDeviceTables& d = h->d;
+    cudaFree(d.es2l);
+    cudaFree(d.em2s);
+    cudaFree(d.qpmT_m);
+    cudaFree(d.qpsT_m);
+    cudaFree(d.qpmT_e);
+    cudaFree(d.qpsT_e);
+    cudaFree(d.tc_err);
+    d.es2l = d.em2s = d.qpmT_m = d.qpsT_m = nullptr;
+    d.qpmT_e = d.qpsT_e = d.tc_err = nullptr;
+}
+
+// M2S (adj = 0) or C^H (adj = 1) of the FP32 scaled block into the chunk partials; *nchunks = splits.
+int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nchunks, cudaStream_t st) {
+    const int M = h->M, nc = h->nc, NS = h->NS, NSp = h->NSp;
+    const int rows = M * nc;
+    const int ntile = (NS + NT - 1) / NT;
+    int nsplit = std::max(1, std::min(64, (rows + 2047) / 2048));
+    int per = (rows + nsplit - 1) / nsplit;
+    per = (per + KCC - 1) / KCC * KCC;
+    nsplit = (rows + per - 1) / per;
+    *nchunks = nsplit;
+    const MsDeviceTables& d = h->d;
+    k_m2s_tc<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qps_m : d.qpm_m,
+                                                             adj ? d.qps_e : d.qpm_e, d.expo, (double2*)h->ws_part, M,
+                                                             nc, NS, NSp, nrhs, per, adj, d.tc_err);
+    return ms_check(h, cudaGetLastError());
+}
+
+// S2L (adj = 0) or B^H (adj = 1) of the amplitudes ud[2][NS][nrhs] into the FP32 block out.
+int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int adj, int accumulate,
+                     cudaStream_t st) {
+    const int M = h->M, nc = h->nc, NS = h->NS, NSp = h->NSp;
+    const MsDeviceTables& d = h->d;
+    float2* uf = (float2*)h->ws_uf;
+    k_amp_f<<<nblk(2LL * NSp * nrhs, 256), 256, 0, st>>>(ud, uf, NS, NSp, nrhs);
+    if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    const int ntile = (M * nc + NT - 1) / NT;
+    k_s2l_tc<<<dim3(ntile, 2), THREADS, SMEM, st>>>(uf, adj ? d.em2s : d.es2l, adj ? d.qpmT_m : d.qpsT_m,
+                                                     adj ? d.qpmT_e : d.qpsT_e, d.expo, out, M, nc, NSp, nrhs,
+                                                     accumulate, adj, d.tc_err);
+    return ms_check(h, cudaGetLastError());
+}
+
+// Reads and clears the tensor-core kernels' timeout flag (MS_ERR_TIMEOUT if a wait gave up).
+int ms_spectral_tc_status(ms_handle* h, cudaStream_t st) {
+    int v = 0;
+    if (int rc = ms_check(h, cudaMemcpyAsync(&v, h->d.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st))) return rc;
+    if (int rc = ms_check(h, cudaStreamSynchronize(st))) return rc;
+    if (v) {
+        cudaMemsetAsync(h->d.tc_err, 0, sizeof(int), st);
+        return MS_ERR_TIMEOUT;
+    }
+    return MS_OK;
+}

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every declared entry point, the
 Python binding declares exactly the header's functions, and host-side validation answers with
 the documented status codes before any device work."""
+import ctypes
 import glob
 import os
 import re
@@ -58,6 +59,12 @@ def test_default_options(lib):
     import paper_2608_26875_b300 as P
     o = P.default_options()
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
+    assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 0)
+    assert ctypes.sizeof(o) == 56      # the C struct: 8 int32, 2 doubles, padding
+
+
+def test_timeout_status_string(lib):
+    assert b"tensor-core" in lib.ms_status_string(-12)
 
 
 @pytest.mark.parametrize("case", ["overlap", "not_buried", "bad_bc", "bad_p", "bad_omega", "bad_radius"])
