@@ -168,7 +168,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     wl = workload()
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    solver = P.Solver.from_workload(wl, leaf_target=args.leaf_target)
+    solver = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores)
     nrhs = 64
     x = torch.as_tensor(syn.random_coeffs(1000 + rank, wl.M, wl.p, nrhs), device="cuda")
     y = torch.empty_like(x)
@@ -199,28 +199,46 @@ def run_ours(args):
     ms = float(t.item())
     value = world / (ms / 1000.0)
 
-    # dominant kernel: the direct near-pair Graf sum (k_translate on the near lists) timed alone
-    # through the operator-parts view; that call also runs the two precision-staging passes
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev3 = torch.cuda.Event(enable_timing=True)
-    solver.operator(x, P.MS_PART_T_NEAR, prec=prec)
-    torch.cuda.synchronize()
-    nT = max(1, min(args.steps, 3))
-    ev2.record(st)
-    for _ in range(nT):
-        solver.operator(x, P.MS_PART_T_NEAR, prec=prec)
-    ev3.record(st)
-    torch.cuda.synchronize()
-    t_near = ev2.elapsed_time(ev3) / nT / 1000.0
+    # per-part times through the operator-parts view (each call also runs the two staging passes):
+    # near-pair Graf sum, FMM far field, and the layered part (M2S, reflect, S2L)
+    def part_time(parts):
+        solver.operator(x, parts, prec=prec)
+        torch.cuda.synchronize()
+        n = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n):
+            solver.operator(x, parts, prec=prec)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n / 1000.0
+
+    t_near = part_time(P.MS_PART_T_NEAR)
+    t_far = part_time(P.MS_PART_T_FAR) if solver.fmm_levels else 0.0
+    t_refl = part_time(P.MS_PART_R)
     nc = 2 * wl.p + 1
     pairs = solver.near_pairs
-    flops = pairs * 2 * nc * nc * nrhs * 8.0          # complex MAC = 8 real flops
+    flops_near = pairs * 2 * nc * nc * nrhs * 8.0                     # complex MAC = 8 real flops
+    flops_refl = 2 * 2 * solver.n_nodes * wl.M * nc * nrhs * 8.0      # M2S + S2L, both waves
     pk, src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
-    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s of the FP32 CUDA-core pipes
-    achieved = flops / t_near / 1e12
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12                  # TFLOP/s of the FP32 CUDA-core pipes
+    tf32_peak = float(pk.get("bf16_tflops", 1800.0)) * 0.5             # dense TF32 = bf16 x 1.1/2.25 (nominal)
+    tc = args.tensor_cores and prec == P.MS_PREC_FP32
+    cand = [("near", t_near, flops_near,
+             "k_near_tc (tcgen05 kind::tf32, 3xTF32) near pairs" if tc else "k_translate<float> near pairs"),
+            ("refl", t_refl, flops_refl,
+             "k_m2s_tc + k_reflect + k_s2l_tc (tcgen05 kind::tf32, 3xTF32)" if tc else "k_m2s + k_reflect + k_s2l")]
+    name, t_dom, flops_dom, kname = max(cand, key=lambda c: c[1])
+    achieved = flops_dom / t_dom / 1e12
+    if tc:
+        peak, bound = tf32_peak, "tensor"
+        peak_src = f"TF32 dense = measured bf16 {pk.get('bf16_tflops')} TFLOP/s x 0.5 (nominal ratio); {src}"
+    else:
+        peak, bound = fp32_peak, "alu"
+        peak_src = f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} clock)"
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "near_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     if os.path.exists(tpath):
         traffic = json.load(open(tpath)).get("bytes_per_launch")
 
@@ -259,15 +277,18 @@ def run_ours(args):
                            "n_nodes": solver.n_nodes, "omega": wl.omega,
                            "near_pairs": pairs, "fmm_levels": solver.fmm_levels,
                            "leaf_target": args.leaf_target, "contour_depth": wl.depth,
+                           "tensor_cores": bool(args.tensor_cores),
                            "l2": "inputs 0.84 GB > 126 MB L2, no flush",
                            "parallelism": f"rhs-replicas x{world}"},
-                "roofline": {"bound": "alu", "kernel": "k_translate<float> near pairs (timed via ms_operator(T_NEAR))",
-                             "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                             "frac": achieved / fp32_peak, "traffic": traffic,
-                             "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} clock)"},
+                "roofline": {"bound": bound, "kernel": kname + f" (timed via ms_operator, part {name})",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                             "flops": "algorithmic complex MACs x 8 (the 3xTF32 split issues 3 MMAs per product)"
+                             if tc else "algorithmic complex MACs x 8"},
+                "parts_ms": {"near": t_near * 1e3, "far": t_far * 1e3, "refl": t_refl * 1e3},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-                "gpu_launches": launches_per_step(solver) * args.steps,
+                "gpu_launches": launches_per_step(solver, tc) * args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -275,19 +296,25 @@ def run_ours(args):
 
 
 def run_solve(args):
-    """Time to solution at relative residual 1e-8 for the 64 plane waves of the 10^4-particle
-    workload: the mixed form (FP32 operator, FP64 refinement) measured; the FP64 form measured
-    when --full-fp64 is given, else its mat-vec timed and multiplied by the mat-vecs the Krylov
-    process needed (reported as an extrapolation)."""
+    """Time to solution at relative residual 1e-8 for plane-wave right-hand sides at the 10^4-particle
+    workload's density (radii U[0.2, 0.5], packing 0.2, omega = 6, p = 20), with --M particles and
+    --nrhs columns: the mixed form (FP32 operator, FP64 refinement) and, with --full-fp64, the FP64
+    form, both measured; otherwise the FP64 form is extrapolated from its mat-vec time and the
+    mat-vecs the mixed solve needed.  GMRES restart and iteration cap from --restart, --max-iters."""
     import torch
 
     import paper_2608_26875_b300 as P
-    wl = workload()
-    s = P.Solver.from_workload(wl, leaf_target=args.leaf_target)
+    import synthetic as syn
+    wl = syn.config3(M=args.M, nrhs=args.nrhs) if args.M != 10000 else workload()
+    kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
+    s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
+                               restart=args.restart, max_iters=args.max_iters)
     torch.cuda.synchronize()
-    g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-8, prec=P.MS_PREC_FP32)
+    g, info = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
     torch.cuda.synchronize()
-    out = {"mode": "solve", "workload": wl.name, "tol": 1e-8, "mixed": info}
+    out = {"mode": "solve", "workload": wl.name, "M": wl.M, "nrhs": len(kinds), "tol": 1e-8,
+           "restart": args.restart, "max_iters": args.max_iters, "tensor_cores": bool(args.tensor_cores),
+           "mixed": info}
     x = torch.empty_like(g)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.apply(g, prec=P.MS_PREC_FP64, out=x)
@@ -298,8 +325,13 @@ def run_solve(args):
     torch.cuda.synchronize()
     t64 = ev0.elapsed_time(ev1) / 1000.0
     out["fp64_matvec_s"] = t64
+    ev0.record()
+    s.apply(g, prec=P.MS_PREC_FP32, out=x)
+    ev1.record()
+    torch.cuda.synchronize()
+    out["fp32_matvec_s"] = ev0.elapsed_time(ev1) / 1000.0
     if args.full_fp64:
-        g64, info64 = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-8, prec=P.MS_PREC_FP64)
+        g64, info64 = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP64)
         out["fp64"] = info64
         out["rel_diff_mixed_vs_fp64"] = float(torch.linalg.norm(g - g64) / torch.linalg.norm(g64))
     else:
@@ -334,7 +366,7 @@ def run_grad(args):
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = P.Solver.from_workload(wl)
+            s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores)
             g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=prec)
             u = s.fields(g, rx)
             w = (u - d).contiguous()
@@ -351,11 +383,14 @@ def run_grad(args):
     print(json.dumps(out), flush=True)
 
 
-def launches_per_step(solver):
-    """Kernels of one ms_apply: staging in/out, near sum (2 waves), FMM (per wave: P2M, M2M per
-    level, M2L per level, L2L per level, L2P), M2S, reflect, S2L, S-apply."""
+def launches_per_step(solver, tensor_cores=False):
+    """Kernels of one ms_apply: staging in/out, near sum (2 waves; one tensor-core launch for both),
+    FMM (per wave: P2M, M2M per level, M2L per level, L2L per level, L2P), M2S, reflect, S2L (plus
+    the FP32 amplitude copy on the tensor-core path), S-apply."""
     L = solver.fmm_levels
     fmm = 0 if L == 0 else 2 * (1 + (L - 2) + (L - 1) + (L - 2) + 1)
+    if tensor_cores:
+        return 2 + 1 + fmm + 4 + 1
     return 2 + 2 + fmm + 3 + 1
 
 
@@ -369,7 +404,7 @@ def run_profile(args):
     import synthetic as syn
     wl = syn.config3(M=args.M, nrhs=64)
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    s = P.Solver.from_workload(wl)
+    s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores)
     x = torch.as_tensor(syn.random_coeffs(5, wl.M, wl.p, 64), device="cuda")
     parts = {"near": P.MS_PART_T_NEAR, "far": P.MS_PART_T_FAR, "refl": P.MS_PART_R | P.MS_PART_S}
     for _ in range(args.steps):
@@ -393,8 +428,13 @@ def main():
     ap.add_argument("--mode", choices=["matvec", "solve", "grad"], default="matvec")
     ap.add_argument("--full-fp64", action="store_true", help="solve mode: run the FP64 solve too")
     ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
-    ap.add_argument("--M", type=int, default=2500)
+    ap.add_argument("--M", type=int, default=2500, help="particles of --profile (default 2500) or --mode solve")
+    ap.add_argument("--nrhs", type=int, default=64, help="--mode solve: right-hand sides")
+    ap.add_argument("--restart", type=int, default=50, help="--mode solve: GMRES restart length")
+    ap.add_argument("--max-iters", type=int, default=2000, help="--mode solve: GMRES iteration cap")
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
+    ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
+                    help="FP32 near field and spectral maps on the CUDA cores instead of tcgen05")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -451,6 +451,40 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
         hl.seq = seq_near[b];
         if ((rc = upload_list(h, hl, h->fmm.near[b]))) return rc;
     }
+    if (h->opt.tensor_cores) {
+        // tiles of the tensor-core near field (same source order as the near lists above)
+        const int tpt = std::max(1, 256 / h->nc);
+        std::vector<int4> tinfo;
+        std::vector<int> ttgt, tself, tsrc;
+        for (int bx = 0; bx < nL * nL; ++bx) {
+            if (lptr[bx] == lptr[bx + 1]) continue;
+            const int src_off = (int)tsrc.size();
+            const int ix = bx % nL, iy = bx / nL;
+            int self_base = -1;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int jx = ix + dx, jy = iy + dy;
+                    if (jx < 0 || jy < 0 || jx >= nL || jy >= nL) continue;
+                    int by = jy * nL + jx;
+                    if (by == bx) self_base = (int)tsrc.size() - src_off;
+                    for (int t = lptr[by]; t < lptr[by + 1]; ++t) tsrc.push_back(lidx[t]);
+                }
+            const int nsrc = (int)tsrc.size() - src_off;
+            for (int t0 = lptr[bx]; t0 < lptr[bx + 1]; t0 += tpt) {
+                const int nt = std::min(tpt, lptr[bx + 1] - t0);
+                tinfo.push_back(make_int4((int)ttgt.size(), nt, src_off, nsrc));
+                for (int u = 0; u < nt; ++u) {
+                    ttgt.push_back(lidx[t0 + u]);
+                    tself.push_back(self_base + (t0 + u - lptr[bx]));
+                }
+            }
+        }
+        FmmHost& F = h->fmm;
+        F.ntile = (int)tinfo.size();
+        if ((rc = up(h, &F.tile, tinfo)) || (rc = up(h, &F.ttgt, ttgt)) || (rc = up(h, &F.tself, tself)) ||
+            (rc = up(h, &F.tsrc, tsrc)))
+            return rc;
+    }
 
     if (L) {
         // ---------------------------------------------------------- tree
@@ -652,7 +686,9 @@ int ms_translate_gen(ms_handle* h, const void* xs, void* dst_, int nrhs, bool ne
         k_zero_c<<<(int)((n + 255) / 256), 256, 0, st>>>((double2*)dst, n);
         if ((rc = ms_check(h, cudaGetLastError()))) return rc;
     }
-    for (int b = 0; b < 2 && near; ++b) {
+    const bool near_tc = near && f32 && !adj && !deriv_axis && !unscaled && h->opt.tensor_cores && h->fmm.ntile > 0;
+    if (near_tc && (rc = ms_near_tc_launch(h, (const float2*)xs, (float2*)dst, nrhs, st))) return rc;
+    for (int b = 0; b < 2 && near && !near_tc; ++b) {
         TransArgs a{};
         const DevList& nl = h->fmm.near[b];
         a.dst_ptr = nl.ptr; a.task_src = nl.src; a.task_seq = nl.seq;
@@ -779,6 +815,8 @@ void ms_fmm_free(ms_handle* h) {
             F.mexp[b][lev] = F.lexp[b][lev] = nullptr;
         }
     }
+    cudaFree(F.tile); cudaFree(F.ttgt); cudaFree(F.tself); cudaFree(F.tsrc);
+    F.tile = nullptr; F.ttgt = F.tself = F.tsrc = nullptr; F.ntile = 0;
     cudaFree(h->d.seq64); cudaFree(h->d.seqm); cudaFree(h->d.seqe);
     h->d.seq64 = nullptr; h->d.seqm = nullptr; h->d.seqe = nullptr;
 }

@@ -49,6 +49,14 @@ struct FmmHost {
     void* lexp[2][13] = {{nullptr}};   // local expansions
     DevList near[2], p2m[2], l2p[2];
     DevList m2m[2][13], m2l[2][13], l2l[2][13];
+    // tensor-core near field: each tile holds up to 256 / nc target particles of one leaf; its
+    // sources are the particles of the 3 x 3 leaves around that leaf (the target itself included,
+    // in the order of the near lists, so near task = ptr[m] + s - (s > self position))
+    int ntile = 0;
+    int4* tile = nullptr;          // [ntile] {target offset, targets, source offset, sources}
+    int* ttgt = nullptr;           // target particles of every tile
+    int* tself = nullptr;          // position of each target in its tile's source list
+    int* tsrc = nullptr;           // source lists, one per non-empty leaf
 };
 
 struct MsDeviceTables {
@@ -154,6 +162,7 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
 int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int adj, int accumulate,
                      cudaStream_t st);
 int ms_spectral_tc_status(ms_handle* h, cudaStream_t st);
+int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cudaStream_t st);
 int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
                     ms_solve_info* info, cudaStream_t st);
 int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st,

@@ -10,14 +10,8 @@
 //   Qs(q, n) = i^n q_b^n W_q,  Qm(q, n) = (-i)^n q_b^n / (i pi s_b)          (ja/stm/eee1, pts1/sed1/sed2).
 // The adjoints (B^H for S2L-shaped, C^H for M2S-shaped launches) take the other map's tables, conjugated.
 //
-// Complex products as real MMAs.  With k = 2 kappa + t running over the contracted complex index kappa:
-//   A[r][2k]   = Re Y(kappa, r),  A[r][2k+1]   = -Im Y(kappa, r),   r < 64
-//   A[64+r][2k] = Im Y(kappa, r), A[64+r][2k+1] = Re Y(kappa, r)
-//   B[j][2k]   = Re Z(j, kappa),  B[j][2k+1]   = Im Z(j, kappa)
-// gives C = A B^T with C[r][j] = Re sum Z Y and C[64+r][j] = Im sum Z Y.  A (the data: amplitudes or
-// coefficients, M = 128) and B (the generated operator, N = 256 rows) are written into shared memory
-// by the CTA's threads, K-chunk by K-chunk, in a two-stage pipeline; one thread issues the MMAs and
-// commits them to the stage's mbarrier.
+// Both run on the shared tcgen05 pipeline of tc_pipeline.cuh: the data (amplitudes D or coefficients
+// x~) form the 128-row A operand, the generated operator entries the 256-row B operand.
 #include <math.h>
 
 #include <algorithm>
@@ -25,117 +19,21 @@
 
 #include "common.cuh"
 #include "handle.h"
-#include "tc.cuh"
+#include "tc_pipeline.cuh"
 
 namespace {
 
-constexpr int KC = 32;                         // real K per chunk (16 complex)
-constexpr int KCC = KC / 2;
-constexpr int NT = 256;                        // MMA N: generated-operator rows per tile
-constexpr int MA = 128;                        // MMA M: 2 x 64 right-hand-side columns
-constexpr int THREADS = 256;
-constexpr int NSTAGE = 2;
-constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
-constexpr uint32_t B_TILE = NT * KC * 4;       // 32 KB
-constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;
-constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;
-constexpr uint32_t IDESC = tc::idesc_tf32(MA, NT);
-constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
-constexpr uint32_t TMEM_COLS = 256;
-static_assert(SMEM <= 227 * 1024, "shared memory");
+using tcp::KC;
+using tcp::KCC;
+using tcp::Stage;
+constexpr int NT = tcp::NMAX;
+constexpr int THREADS = tcp::THREADS;
+constexpr size_t SMEM = tcp::SMEM;
 
-struct Stage {
-    float *ah, *al, *bh, *bl;
-};
-__device__ __forceinline__ Stage stage_ptrs(unsigned char* base, int s) {
-    float* p = reinterpret_cast<float*>(base + (size_t)s * STAGE);
-    return {p, p + MA * KC, p + 2 * MA * KC, p + 2 * MA * KC + NT * KC};
-}
-
-__device__ __forceinline__ void put4(float* hi, float* lo, int off, float a, float b, float c, float d) {
-    float4 h, l;
-    tc::split(a, h.x, l.x);
-    tc::split(b, h.y, l.y);
-    tc::split(c, h.z, l.z);
-    tc::split(d, h.w, l.w);
-    *reinterpret_cast<float4*>(hi + off) = h;
-    *reinterpret_cast<float4*>(lo + off) = l;
-}
-
-// A rows from two consecutive complex values y0, y1 of column r (row rp = r or 64 + r)
-__device__ __forceinline__ void put_a(const Stage& st, int rp, int kk, float2 y0, float2 y1) {
-    const int off = tc::kmajor_off(rp, 4 * kk, KC);
-    if (rp < 64)
-        put4(st.ah, st.al, off, y0.x, -y0.y, y1.x, -y1.y);
-    else
-        put4(st.ah, st.al, off, y0.y, y0.x, y1.y, y1.x);
-}
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 __device__ __forceinline__ float2 gen_entry(float2 e, float2 qm, int ex, int conj) {
-    float2 v = cmulf(e, qm);
+    float2 v = tcp::cmulf(e, qm);
     float f = pow2f(ex);
     return make_float2(v.x * f, conj ? -v.y * f : v.y * f);
-}
-
-// The shared pipeline.  P provides load_a(Stage, chunk), gen_b(Stage, chunk), epilogue(tmem, ok).
-template <class P>
-__device__ __forceinline__ void run_pipeline(P& pol, int nchunks, int* err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NSTAGE);
-    int* fail = reinterpret_cast<int*>(tslot + 1);
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) tc::mbar_init(&bar[s], 1);
-        tc::mbar_fence_init();
-        *fail = 0;
-    }
-    if (tid < 32) tc::tmem_alloc(tslot, TMEM_COLS);
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tslot;
-    int issued = 0;
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c % NSTAGE;
-        if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
-        const Stage st = stage_ptrs(smem, s);
-        pol.load_a(st, c);
-        pol.gen_b(st, c);
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (*fail) break;
-        if (tid == 0) {
-            tc::fence_after();
-#pragma unroll
-            for (int pass = 0; pass < 3; ++pass) {
-                const uint32_t a0 = tc::smem_u32(pass == 2 ? st.al : st.ah);
-                const uint32_t b0 = tc::smem_u32(pass == 1 ? st.bl : st.bh);
-#pragma unroll
-                for (int ks = 0; ks < KC / 8; ++ks) {
-                    tc::mma_tf32(tmem, tc::smem_desc(a0 + ks * 256, LBO, SBO), tc::smem_desc(b0 + ks * 256, LBO, SBO),
-                                 IDESC, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
-                }
-            }
-            tc::mma_commit(&bar[s]);
-        }
-        issued = c + 1;
-    }
-    // the last commit covers every MMA issued before it
-    bool ok = !*fail && issued == nchunks;
-    if (issued > 0) {
-        const int c = issued - 1;
-        if (!tc::mbar_wait(&bar[c % NSTAGE], (c / NSTAGE) & 1)) ok = false;
-    }
-    tc::fence_after();
-    if (!ok && tid == 0) atomicExch(err, 1);
-    pol.epilogue(tmem, ok && nchunks > 0);
-    tc::fence_before();
-    __syncthreads();
-    if (tid < 32) tc::tmem_free(tmem, TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ S2L-shaped launch
@@ -170,7 +68,7 @@ struct S2LPolicy {
                 y0 = D[(size_t)q * nrhs + r];
                 y1 = D[(size_t)(q + 1) * nrhs + r];
             }
-            put_a(st, rp, kk, y0, y1);
+            tcp::put_a(st, rp, kk, y0, y1);
         }
     }
     __device__ void gen_b(const Stage& st, int c) {
@@ -187,7 +85,7 @@ struct S2LPolicy {
                 g0 = gen_entry(make_float2(e.x, e.y), make_float2(qm.x, qm.y), qe.x + a, conj);
                 g1 = gen_entry(make_float2(e.z, e.w), make_float2(qm.z, qm.w), qe.y + a, conj);
             }
-            put4(st.bh, st.bl, tc::kmajor_off(t, 4 * kk, KC), g0.x, g0.y, g1.x, g1.y);
+            tcp::put_b(st, t, kk, g0, g1);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
@@ -221,7 +119,7 @@ k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float
     S2LPolicy pol{D + (size_t)b * NSp * nrhs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp,
                   Qe + (size_t)b * nc * NSp, expo, out, M, nc, NSp, nrhs, b, (int)blockIdx.x * NT, accumulate, conj};
     pol.init();
-    run_pipeline(pol, NSp / KCC, err);
+    tcp::run(pol, NSp / KCC, NT, err);
 }
 
 // ------------------------------------------------------------------ M2S-shaped launch
@@ -258,7 +156,7 @@ struct M2SPolicy {
                     y[v] = xs[(((size_t)l * 2 + b) * nc + n) * nrhs + r];
                 }
             }
-            put_a(st, rp, kk, y[0], y[1]);
+            tcp::put_a(st, rp, kk, y[0], y[1]);
         }
     }
     __device__ void gen_b(const Stage& st, int c) {
@@ -285,7 +183,7 @@ struct M2SPolicy {
                     if (valid && i + 1 < i1) e = E[(size_t)l * NSp + q];
                 }
             }
-            put4(st.bh, st.bl, tc::kmajor_off(t, 4 * kk, KC), g[0].x, g[0].y, g[1].x, g[1].y);
+            tcp::put_b(st, t, kk, g[0], g[1]);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
@@ -324,7 +222,7 @@ k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const floa
                   M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
     pol.init();
     const int nchunks = i1 > i0 ? (i1 - i0 + KCC - 1) / KCC : 0;
-    run_pipeline(pol, nchunks, err);
+    tcp::run(pol, nchunks, NT, err);
 }
 
 // ------------------------------------------------------------------ setup-time tables

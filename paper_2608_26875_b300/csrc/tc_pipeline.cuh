@@ -1,0 +1,147 @@
+// A tcgen05 pipeline for complex contractions across a block of right-hand sides, shared by the
+// spectral maps and the near-field Graf sum.
+//
+// C = A B^T on the tensor cores (kind::tf32, FP32 accumulation in tensor memory), 3xTF32:
+// A B ~ Ah Bh + Ah Bl + Al Bh with X = Xh + Xl, Xh exactly representable in tf32.
+// With k = 2 kappa + t running over the contracted complex index kappa,
+//   A[r][2k]    = Re Y(kappa, r),  A[r][2k+1]    = -Im Y(kappa, r),   r < 64
+//   A[64+r][2k] = Im Y(kappa, r),  A[64+r][2k+1] =  Re Y(kappa, r)
+//   B[j][2k]    = Re Z(j, kappa),  B[j][2k+1]    =  Im Z(j, kappa)
+// gives C[r][j] = Re sum_kappa Z(j, kappa) Y(kappa, r) and C[64+r][j] = Im of the same.
+// A (the data, M = 128 rows = 2 x 64 columns) and B (the generated operator, N <= 256 rows) are
+// written into shared memory by the CTA's 256 threads one K chunk (16 complex) at a time, in a
+// two-stage pipeline; one thread issues the MMAs and commits them to the stage's mbarrier, which the
+// threads wait on (time-bounded) before reusing the stage.
+#pragma once
+#include "tc.cuh"
+
+namespace tcp {
+
+constexpr int KC = 32;                         // real K per chunk (16 complex)
+constexpr int KCC = KC / 2;
+constexpr int NMAX = 256;                      // MMA N: generated-operator rows per tile (max)
+constexpr int MA = 128;                        // MMA M: 2 x 64 right-hand-side columns
+constexpr int THREADS = 256;
+constexpr int NSTAGE = 2;
+constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
+constexpr uint32_t B_TILE = NMAX * KC * 4;     // 32 KB
+constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;
+constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;
+constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
+constexpr uint32_t TMEM_COLS = 256;
+static_assert(SMEM <= 227 * 1024, "shared memory");
+
+struct Stage {
+    float *ah, *al, *bh, *bl;
+};
+__device__ __forceinline__ Stage stage_ptrs(unsigned char* base, int s) {
+    float* p = reinterpret_cast<float*>(base + (size_t)s * STAGE);
+    return {p, p + MA * KC, p + 2 * MA * KC, p + 2 * MA * KC + NMAX * KC};
+}
+
+__device__ __forceinline__ void put4(float* hi, float* lo, int off, float a, float b, float c, float d) {
+    float4 h, l;
+    tc::split(a, h.x, l.x);
+    tc::split(b, h.y, l.y);
+    tc::split(c, h.z, l.z);
+    tc::split(d, h.w, l.w);
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+// A row rp (= r or 64 + r) of k-group kk from two consecutive complex values y0, y1 of column r
+__device__ __forceinline__ void put_a(const Stage& st, int rp, int kk, float2 y0, float2 y1) {
+    const int off = tc::kmajor_off(rp, 4 * kk, KC);
+    if (rp < 64)
+        put4(st.ah, st.al, off, y0.x, -y0.y, y1.x, -y1.y);
+    else
+        put4(st.ah, st.al, off, y0.y, y0.x, y1.y, y1.x);
+}
+// B row j of k-group kk from two consecutive complex operator entries
+__device__ __forceinline__ void put_b(const Stage& st, int j, int kk, float2 z0, float2 z1) {
+    put4(st.bh, st.bl, tc::kmajor_off(j, 4 * kk, KC), z0.x, z0.y, z1.x, z1.y);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// P provides load_a(Stage, chunk), gen_b(Stage, chunk) and epilogue(tmem, ok); n is the MMA N of
+// this tile (a multiple of 16 in [16, 256]).  Sets *err on a timed-out wait.
+template <class P>
+__device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NSTAGE);
+    int* fail = reinterpret_cast<int*>(tslot + 1);
+    const int tid = threadIdx.x;
+    const uint32_t idesc = tc::idesc_tf32(MA, n);
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) tc::mbar_init(&bar[s], 1);
+        tc::mbar_fence_init();
+        *fail = 0;
+    }
+    if (tid < 32) tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    int issued = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % NSTAGE;
+        if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
+        const Stage st = stage_ptrs(smem, s);
+        pol.load_a(st, c);
+        pol.gen_b(st, c);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (*fail) break;
+        if (tid == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t a0 = tc::smem_u32(pass == 2 ? st.al : st.ah);
+                const uint32_t b0 = tc::smem_u32(pass == 1 ? st.bl : st.bh);
+#pragma unroll
+                for (int ks = 0; ks < KC / 8; ++ks)
+                    tc::mma_tf32(tmem, tc::smem_desc(a0 + ks * 256, LBO, SBO), tc::smem_desc(b0 + ks * 256, LBO, SBO),
+                                 idesc, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[s]);
+        }
+        issued = c + 1;
+    }
+    // the last commit covers every MMA issued before it
+    bool ok = !*fail && issued == nchunks;
+    if (issued > 0) {
+        const int c = issued - 1;
+        if (!tc::mbar_wait(&bar[c % NSTAGE], (c / NSTAGE) & 1)) ok = false;
+    }
+    tc::fence_after();
+    if (!ok && tid == 0) atomicExch(err, 1);
+    pol.epilogue(tmem, ok && nchunks > 0);
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) tc::tmem_free(tmem, TMEM_COLS);
+}
+
+// Epilogue helper: warp w reads accumulator rows 32 (w & 3) + lane (the A rows rp) and the columns
+// of its half; f(rp, col, value) is called for every column < n.
+template <class F>
+__device__ __forceinline__ void for_each_acc(uint32_t tmem, int n, F&& f) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = w & 3, half = w >> 2;
+    const int rp = 32 * quarter + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < 8; ++cb) {
+        const int col0 = 128 * half + 16 * cb;
+        if (col0 >= n) break;                          // uniform per warp
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (col0 + i < n) f(rp, col0 + i, v[i]);
+    }
+}
+
+}  // namespace tcp

@@ -68,39 +68,45 @@ def test_gradient_matches_oracle_adjoint():
 
 def _gpu_loss(wl, rx, d, **kw):
     s = P.Solver.from_workload(wl, **kw)
-    g, _ = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-13, prec=P.MS_PREC_FP64)
+    g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-13, prec=P.MS_PREC_FP64)
+    assert info["status"] == 0, info          # central differences need converged solves
     u = s.fields(g, rx).cpu().numpy()
     return 0.5 * float(np.sum(np.abs(u - d) ** 2))
 
 
-def _fd_case(M, seed=7):
-    wl = syn.config4(M=M, nrhs=2)            # rigid discs at the inverse-problem density
-    rx = wl.receivers[::8]
+def _fd_case(M, side, seed=7):
+    """Rigid discs R ~ U[0.2, 0.5] spread thinly enough that GMRES reaches 1e-13 quickly."""
+    npan, depth, grade = syn.contour_for_width(side)
+    wl = syn.small_case(400 + M, M, 10, omega=2.0, nrhs=2, box=(-side / 2, side / 2, -side, -1.0),
+                        rmin=0.2, rmax=0.5, mixed_bc=False, n_panels=npan, depth=depth, grade=grade)
+    rx = wl.receivers[::2]
     rng = np.random.default_rng(seed)
     d = 0.05 * (rng.standard_normal((2, rx.shape[0], 2)) + 1j * rng.standard_normal((2, rx.shape[0], 2)))
     return wl, rx, d
 
 
-def _grad(wl, rx, d, **kw):
+def _grad(wl, rx, d, tol=1e-13, **kw):
     s = P.Solver.from_workload(wl, **kw)
-    g, _ = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-13, prec=P.MS_PREC_FP64)
+    g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=tol, prec=P.MS_PREC_FP64)
+    assert info["status"] == 0, info
     u = s.fields(g, rx)
-    gc, gr, gw, info = s.grad(wl.inc_kind, wl.inc_angle, g, (u - dev(d)).contiguous(), rx, tol=1e-13)
+    gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, (u - dev(d)).contiguous(), rx, tol=tol)
+    assert ginfo["status"] == 0, ginfo
     return gc.cpu().numpy(), gr.cpu().numpy(), gw, s
 
 
 def test_gradient_matches_gpu_central_differences():
     """Direct Graf sum (no tree): adjoint gradient vs central differences of the GPU FP64 loss."""
-    wl, rx, d = _fd_case(60)
+    wl, rx, d = _fd_case(40, 40.0)
     gc, gr, gw, _ = _grad(wl, rx, d, use_fmm=False)
     h = 1e-6
-    for m, axis in ((0, 0), (7, 1), (31, 0), (59, 1)):
+    for m, axis in ((0, 0), (7, 1), (21, 0), (39, 1)):
         wp, wm = copy.deepcopy(wl), copy.deepcopy(wl)
         wp.centres = wl.centres.copy(); wp.centres[m, axis] += h
         wm.centres = wl.centres.copy(); wm.centres[m, axis] -= h
         fd = (_gpu_loss(wp, rx, d, use_fmm=False) - _gpu_loss(wm, rx, d, use_fmm=False)) / (2 * h)
         assert abs(gc[m, axis] - fd) <= 1e-6 * np.abs(gc).max(), (m, axis, gc[m, axis], fd)
-    for m in (3, 50):
+    for m in (3, 30):
         wp, wm = copy.deepcopy(wl), copy.deepcopy(wl)
         wp.radius = wl.radius.copy(); wp.radius[m] += h
         wm.radius = wl.radius.copy(); wm.radius[m] -= h
@@ -111,10 +117,10 @@ def test_gradient_matches_gpu_central_differences():
 def test_gradient_with_fmm_matches_direct_sum():
     """The FMM's position derivatives (L2P for targets, the adjoint P2M for sources) against the
     gradient of the direct Graf sum on the same geometry."""
-    wl, rx, d = _fd_case(400)
-    gcf, grf, gwf, s = _grad(wl, rx, d, leaf_target=8)
+    wl, rx, d = _fd_case(300, 110.0)
+    gcf, grf, gwf, s = _grad(wl, rx, d, tol=1e-11, leaf_target=8)
     assert s.fmm_levels >= 3
-    gcd, grd, gwd, _ = _grad(wl, rx, d, use_fmm=False)
+    gcd, grd, gwd, _ = _grad(wl, rx, d, tol=1e-11, use_fmm=False)
     assert np.abs(gcf - gcd).max() <= 1e-8 * np.abs(gcd).max()
     assert np.abs(grf - grd).max() <= 1e-8 * np.abs(grd).max()
     assert abs(gwf - gwd) <= 1e-6 * abs(gwd)

@@ -2,7 +2,8 @@
 FP32 accumulation) against the FP64 oracle, the CUDA-core FP32 kernels and the FP64 GPU path.
 
 The bar is the FP32 operator's: 2e-5 of the largest entry in the scaled norm (|y| / tau, tau the
-order scale (k R / 2)^|n| / |n|!).  The cases cover one particle, quadrature rules whose node count
+order scale (k R / 2)^|n| / |n|!), or 1.5 times the CUDA-core FP32 kernels' own error where the
+contour's growth on a wide cloud amplifies both (capped at 1e-4).  The cases cover one particle, quadrature rules whose node count
 is not a multiple of the 16-node K chunk, output row counts that leave a ragged last 256-row tile,
 several multipole-to-Sommerfeld K splits, 1 to 64 right-hand sides, and the adjoint maps.
 """
@@ -44,24 +45,33 @@ def dev(a):
 
 
 CASES = [
-    # (seed, M, p, nrhs, omega, n_panels, nodes_per_panel)
-    (51, 1, 3, 1, 2.0, 32, 16),      # one particle: the reflected self term only
-    (52, 7, 6, 3, 2.5, 5, 7),        # N_S = 35 nodes: ragged last K chunk of S2L, ragged node tile of M2S
-    (53, 20, 10, 64, 3.0, 32, 16),   # full 64-column block; 420 rows: ragged 256-row S2L tile
-    (54, 150, 8, 17, 3.0, 20, 16),   # 2550 rows: two M2S K splits; 17 columns
+    # (seed, M, p, nrhs, omega, n_panels, nodes_per_panel, box)
+    (51, 1, 3, 1, 2.0, 32, 16, (-8.0, 8.0, -6.0, -1.0)),      # one particle: the reflected self term only
+    (52, 7, 6, 3, 2.5, 5, 7, (-8.0, 8.0, -6.0, -1.0)),        # N_S = 35: ragged last K chunk / node tile
+    (53, 20, 10, 64, 3.0, 32, 16, (-8.0, 8.0, -6.0, -1.0)),   # 64 columns; 420 rows: ragged 256-row tile
+    (54, 150, 8, 17, 3.0, 0, 16, (-12.0, 12.0, -14.0, -1.0)),   # 2550 rows: two M2S K splits; 17 columns
 ]
 
 
-@pytest.mark.parametrize("seed,M,p,nrhs,omega,npan,npp", CASES)
-def test_reflected_part_fp32_tensor_cores_matches_oracle(seed, M, p, nrhs, omega, npan, npp):
-    wl = syn.small_case(seed, M, p, omega=omega, nrhs=nrhs, n_panels=npan, nodes_per_panel=npp,
-                        box=(-8.0, 8.0, -6.0, -1.0))
+@pytest.mark.parametrize("seed,M,p,nrhs,omega,npan,npp,box", CASES)
+def test_reflected_part_fp32_tensor_cores_matches_oracle(seed, M, p, nrhs, omega, npan, npp, box):
+    depth, grade = 0.5, 0
+    if npan == 0:        # a 24-wide cloud: the contour adapted to the width (growth e^{d W} <= e^3)
+        npan, depth, grade = syn.contour_for_width(box[1] - box[0])
+    wl = syn.small_case(seed, M, p, omega=omega, nrhs=nrhs, n_panels=npan, nodes_per_panel=npp, box=box,
+                        depth=depth, grade=grade)
     ref = system.Problem(wl)
     x = syn.random_coeffs(seed + 3, M, p, nrhs)
     want = ref.apply_S(ref.reflect(x))
     s = P.Solver.from_workload(wl, tensor_cores=True)
     got = s.operator(dev(x), P.MS_PART_R | P.MS_PART_S, prec=P.MS_PREC_FP32).cpu().numpy()
-    assert scaled_err(got, want, wl) <= 2e-5
+    e_tc = scaled_err(got, want, wl)
+    # the CUDA-core FP32 kernels on the same inputs: the tensor-core path must be as accurate.  On a
+    # wide cloud the contour's growth e^{d W} (<= e^3 on the adapted rule) scales both errors.
+    cc = P.Solver.from_workload(wl, tensor_cores=False)
+    e_cc = scaled_err(cc.operator(dev(x), P.MS_PART_R | P.MS_PART_S, prec=P.MS_PREC_FP32).cpu().numpy(), want, wl)
+    assert e_tc <= max(2e-5, 1.5 * e_cc), (e_tc, e_cc)
+    assert e_tc <= 1e-4
 
 
 def test_tensor_cores_and_cuda_cores_agree_with_fp64():
@@ -83,7 +93,8 @@ def test_tensor_cores_and_cuda_cores_agree_with_fp64():
 
 @pytest.mark.parametrize("M,nrhs", [(9, 5), (400, 64)])
 def test_adjoint_fp32_tensor_cores_dot_product(M, nrhs):
-    wl = syn.small_case(71, M, 7, omega=2.5, nrhs=nrhs, box=(-10.0, 10.0, -9.0, -1.0), rmin=0.2, rmax=0.35)
+    side = 20.0 if M < 100 else 40.0
+    wl = syn.small_case(71, M, 7, omega=2.5, nrhs=nrhs, box=(-side / 2, side / 2, -side, -1.0), rmin=0.2, rmax=0.35)
     s = P.Solver.from_workload(wl, tensor_cores=True)
     x = dev(syn.random_coeffs(72, wl.M, wl.p, nrhs))
     y = dev(syn.random_coeffs(73, wl.M, wl.p, nrhs))
@@ -106,3 +117,32 @@ def test_mixed_solve_with_tensor_cores_reaches_fp64_accuracy():
     g64, _ = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-12, prec=P.MS_PREC_FP64)
     assert info["status"] == 0
     assert float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)) <= 1e-8
+
+
+# --------------------------------------------------------------------- near-field Graf sum
+@pytest.mark.parametrize("seed,M,p,nrhs", [(91, 1, 4, 2), (92, 9, 6, 3), (93, 16, 10, 64)])
+def test_translation_fp32_tensor_cores_matches_oracle(seed, M, p, nrhs):
+    """All pairs direct (one leaf): the translation sum S T x against the oracle's Graf sum."""
+    wl = syn.small_case(seed, M, p, omega=2.5, nrhs=nrhs)
+    ref = system.Problem(wl)
+    x = syn.random_coeffs(seed + 5, M, p, nrhs)
+    want = ref.apply_S(ref.translate(x))
+    s = P.Solver.from_workload(wl, tensor_cores=True)
+    got = s.operator(dev(x), P.MS_PART_T | P.MS_PART_S, prec=P.MS_PREC_FP32).cpu().numpy()
+    if M == 1:
+        assert not np.any(got)
+        return
+    assert scaled_err(got, want, wl) <= 2e-5
+
+
+@pytest.mark.parametrize("M,nrhs,leaf", [(600, 64, 10), (2500, 7, 10), (1200, 32, 6)])
+def test_near_field_fp32_tensor_cores_matches_fp64(M, nrhs, leaf):
+    """Quadtree near lists (3 x 3 leaves): tensor-core tiles against the FP64 near sum."""
+    wl = syn.config3(M=M, nrhs=nrhs)
+    x = dev(syn.random_coeffs(94, wl.M, wl.p, nrhs))
+    s = P.Solver.from_workload(wl, tensor_cores=True, leaf_target=leaf)
+    assert s.fmm_levels >= 2
+    parts = P.MS_PART_T_NEAR | P.MS_PART_S
+    want = s.operator(x, parts, prec=P.MS_PREC_FP64).cpu().numpy()
+    got = s.operator(x, parts, prec=P.MS_PREC_FP32).cpu().numpy()
+    assert scaled_err(got, want, wl) <= 2e-5
