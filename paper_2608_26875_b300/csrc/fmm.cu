@@ -479,10 +479,10 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                 }
             }
         }
-        FmmHost& F = h->fmm;
-        F.ntile = (int)tinfo.size();
-        if ((rc = up(h, &F.tile, tinfo)) || (rc = up(h, &F.ttgt, ttgt)) || (rc = up(h, &F.tself, tself)) ||
-            (rc = up(h, &F.tsrc, tsrc)))
+        TcTiles& T = h->fmm.near_tc;
+        T.n = (int)tinfo.size();
+        if ((rc = up(h, &T.tile, tinfo)) || (rc = up(h, &T.tgt, ttgt)) || (rc = up(h, &T.self, tself)) ||
+            (rc = up(h, &T.src, tsrc)))
             return rc;
     }
 
@@ -586,6 +586,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                 }
                 m2l.ptr[n * n] = (int)m2l.src.size();
                 if ((rc = upload_list(h, m2l, F.m2l[b][lev]))) return rc;
+                if (h->opt.tensor_cores && (rc = ms_m2l_tc_tiles(h, b, lev, m2l.ptr))) return rc;
                 if (lev < L) {
                     // M2M: parent (lev) <- children (lev+1); v = c_parent - c_child = (+-w/4, +-w/4)
                     int nc2 = 2 * n;
@@ -686,7 +687,8 @@ int ms_translate_gen(ms_handle* h, const void* xs, void* dst_, int nrhs, bool ne
         k_zero_c<<<(int)((n + 255) / 256), 256, 0, st>>>((double2*)dst, n);
         if ((rc = ms_check(h, cudaGetLastError()))) return rc;
     }
-    const bool near_tc = near && f32 && !adj && !deriv_axis && !unscaled && h->opt.tensor_cores && h->fmm.ntile > 0;
+    const bool tcore = f32 && !adj && !deriv_axis && !unscaled && h->opt.tensor_cores;
+    const bool near_tc = near && tcore && h->fmm.near_tc.n > 0;
     if (near_tc && (rc = ms_near_tc_launch(h, (const float2*)xs, (float2*)dst, nrhs, st))) return rc;
     for (int b = 0; b < 2 && near && !near_tc; ++b) {
         TransArgs a{};
@@ -743,7 +745,11 @@ int ms_translate_gen(ms_handle* h, const void* xs, void* dst_, int nrhs, bool ne
             a.ad = bexp(lev); a.ad_stride = 0; a.sd = 1;
             a.as = bexp(lev); a.as_stride = 0; a.ss = 1;
             a.nrhs = nrhs; a.accumulate = 0; a.adj = adj;
-            if ((rc = ms_translate_launch(h, a, F.m2l[b][lev].ndst, f32, st))) return rc;
+            if (tcore) {
+                if ((rc = ms_m2l_tc_launch(h, b, lev, (const float2*)mexp(lev), (float2*)lexp(lev), nrhs, st))) return rc;
+            } else if ((rc = ms_translate_launch(h, a, F.m2l[b][lev].ndst, f32, st))) {
+                return rc;
+            }
             if (lev > 2) {
                 TransArgs c{};
                 c.dst_ptr = F.l2l[b][lev].ptr; c.task_src = F.l2l[b][lev].src; c.task_seq = F.l2l[b][lev].seq;
@@ -815,8 +821,9 @@ void ms_fmm_free(ms_handle* h) {
             F.mexp[b][lev] = F.lexp[b][lev] = nullptr;
         }
     }
-    cudaFree(F.tile); cudaFree(F.ttgt); cudaFree(F.tself); cudaFree(F.tsrc);
-    F.tile = nullptr; F.ttgt = F.tself = F.tsrc = nullptr; F.ntile = 0;
+    ms_tc_tiles_free(F.near_tc);
+    for (int b = 0; b < 2; ++b)
+        for (int lev = 0; lev <= 12; ++lev) ms_tc_tiles_free(F.m2l_tc[b][lev]);
     cudaFree(h->d.seq64); cudaFree(h->d.seqm); cudaFree(h->d.seqe);
     h->d.seq64 = nullptr; h->d.seqm = nullptr; h->d.seqe = nullptr;
 }

@@ -40,6 +40,16 @@ struct TransArgs {
     int accumulate;
 };
 
+// Tiles of a tensor-core translation launch.
+struct TcTiles {
+    int n = 0;
+    int4* tile = nullptr;          // [n] {target offset, targets, source offset, sources}
+    int* tgt = nullptr;            // target entities of every tile
+    int* self = nullptr;           // position of each target in its source list (-1: none)
+    int* src = nullptr;            // source entities (near: one list per leaf)
+    int* row = nullptr;            // per tile: first output order (M2L), or NULL
+};
+
 struct FmmHost {
     int nbox[13] = {0};
     double w[13] = {0};
@@ -49,14 +59,11 @@ struct FmmHost {
     void* lexp[2][13] = {{nullptr}};   // local expansions
     DevList near[2], p2m[2], l2p[2];
     DevList m2m[2][13], m2l[2][13], l2l[2][13];
-    // tensor-core near field: each tile holds up to 256 / nc target particles of one leaf; its
-    // sources are the particles of the 3 x 3 leaves around that leaf (the target itself included,
-    // in the order of the near lists, so near task = ptr[m] + s - (s > self position))
-    int ntile = 0;
-    int4* tile = nullptr;          // [ntile] {target offset, targets, source offset, sources}
-    int* ttgt = nullptr;           // target particles of every tile
-    int* tself = nullptr;          // position of each target in its tile's source list
-    int* tsrc = nullptr;           // source lists, one per non-empty leaf
+    // tensor-core tiles of the near lists (up to 256 / nc target particles of one leaf against the
+    // particles of the 3 x 3 leaves around it, the target included, in near-list order: near task =
+    // ptr[m] + s - (s > self position)) and of the M2L lists (256-row ranges of one box)
+    TcTiles near_tc;
+    TcTiles m2l_tc[2][13];
 };
 
 struct MsDeviceTables {
@@ -163,6 +170,9 @@ int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int
                      cudaStream_t st);
 int ms_spectral_tc_status(ms_handle* h, cudaStream_t st);
 int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cudaStream_t st);
+int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* lexp, int nrhs, cudaStream_t st);
+int ms_m2l_tc_tiles(ms_handle* h, int b, int lev, const std::vector<int>& ptr);
+void ms_tc_tiles_free(TcTiles& T);
 int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
                     ms_solve_info* info, cudaStream_t st);
 int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st,

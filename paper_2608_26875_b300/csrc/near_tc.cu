@@ -1,14 +1,16 @@
-// Near-field Graf sum of the FP32 operator on the tensor cores (row a2, Sec. 4.2):
-//   a~^m_{b,i,r} = sum_{l in N(m), l != m} sum_j h^{ml}_{j-i} 2^{a(m,b,i) + a(l,b,j)} x~^l_{b,j,r},
-// h^{ml}_k = H_k(kappa_b |x_m - x_l|) e^{ik arg(x_m - x_l)} (DLMF 10.23.7), read from the per-pair
-// sequences built at setup (FP32 mantissa and binary exponent).
+// Toeplitz translation lists of the FP32 operator on the tensor cores: the near-field Graf sum
+// (row a2, Sec. 4.2) and the FMM's multipole-to-local stage (row a3).  Both have the form
+//   out^d_{i,r} = sum_{e in list(d)} sum_j h^{de}_{(j - Ps) - (i - Pd)} 2^{a_d(i) + a_e(j)} in^e_{j,r},
+// with h^{de}_k = Z_k(kappa |v|) e^{ik arg v}, v = c_d - c_e (DLMF 10.23.7), read from the per-task
+// sequences built at setup (FP32 mantissa and binary exponent, entries k in [-K, K]).
 //
-// Targets of one leaf share their sources (the particles of the 3 x 3 leaves around it), so a tile of
-// up to 256 / nc targets of a leaf is one dense contraction: output rows (m, i), contracted index
-// (s, j) over the leaf's source list, with the self block set to zero.  The coefficients form the
-// 128-row A operand, the Toeplitz blocks h_{j-i} of every (target, source) pair the B operand; see
-// tc_pipeline.cuh.
+// A tile is up to 256 output rows: several targets sharing one source list (the particles of one
+// leaf against the 3 x 3 leaves around it; the self block is zero), or a row range of one box (M2L:
+// 2P + 1 rows against its interaction list).  Each tile is one dense contraction over (source,
+// order): the input expansions form the 128-row A operand and the Toeplitz blocks the B operand
+// (tc_pipeline.cuh).  Task of target d and source slot s: tptr[d] + s - (s > self(d)).
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "handle.h"
@@ -19,117 +21,203 @@ namespace {
 using tcp::KCC;
 using tcp::Stage;
 
-struct NearPolicy {
-    const float2* xs;          // [M][2][nc][nrhs] scaled coefficients
-    const float2* seqm;        // sequence mantissas
-    const int* seqe;           // sequence exponents
-    const long long* tseq;     // [near tasks] sequence offset of each (target, source) task
-    const int* nptr;           // [M + 1] near tasks of each target
-    const int* tgt;            // this tile's targets
-    const int* self;           // their positions in the source list
-    const int* src;            // this tile's source list
-    const int* expo;           // [M][2][nc]
-    float2* out;               // [M][2][nc][nrhs]
-    int nc, nrhs, b, ntgt, nsrc, K;
-    int i, a_mi, ptr_m, self_m;
+struct ListArgs {
+    const float2* in;            // source entity e, order j: in + e * in_stride + j * nrhs
+    long long in_stride;
+    float2* out;                 // target entity d, order i: out + d * out_stride + i * nrhs
+    long long out_stride;
+    const float2* seqm;
+    const int* seqe;
+    const long long* tseq;       // per task: sequence offset
+    const int* tptr;             // per target entity: first task
+    const int* ad;               // target exponents ad[d * ad_stride + i]
+    long long ad_stride;
+    const int* as;               // source exponents as[e * as_stride + j]
+    long long as_stride;
+    const int4* tiles;           // {target offset, targets, source offset, sources}
+    const int* ttgt;             // target entities of the tiles
+    const int* tself;            // position of each target in its source list (-1: none)
+    const int* tsrc;             // source entities, indexed by the tile's source offset
+    const int* trow;             // per tile: first output order (NULL: 0)
+    int Pd, Ps, K, nrhs;
+};
+
+struct ListPolicy {
+    const ListArgs& a;
+    const int* tgt;
+    const int* self;
+    const int* src;
+    int ntgt, nsrc, nrow, i0, nd, ns;
+    int i, ad_i, ptr_t, self_t;
     bool valid;
 
     __device__ void init() {
         const int row = threadIdx.x;
-        const int tt = row / nc;
-        i = row - tt * nc;
-        valid = tt < ntgt;
-        a_mi = ptr_m = 0;
-        self_m = -1;
+        const int tt = row / nrow;
+        i = i0 + (row - tt * nrow);
+        valid = tt < ntgt && i < nd;
+        ad_i = ptr_t = 0;
+        self_t = -1;
         if (valid) {
-            const int m = tgt[tt];
-            a_mi = expo[((size_t)m * 2 + b) * nc + i];
-            ptr_m = nptr[m];
-            self_m = self[tt];
+            const int d = tgt[tt];
+            ad_i = a.ad[(long long)d * a.ad_stride + i];
+            ptr_t = a.tptr[d];
+            self_t = self[tt];
         }
     }
     __device__ void load_a(const Stage& st, int c) {
         const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
-        const bool ok = r < nrhs;
+        const bool ok = r < a.nrhs;
         const int f0 = c * KCC + h * 8;
-        int s = f0 / nc, j = f0 - s * nc;
+        int s = f0 / ns, j = f0 - s * ns;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 y[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 y[v] = make_float2(0.f, 0.f);
-                if (ok && s < nsrc) y[v] = xs[(((size_t)src[s] * 2 + b) * nc + j) * nrhs + r];
-                if (++j == nc) { j = 0; ++s; }
+                if (ok && s < nsrc) y[v] = a.in[(long long)src[s] * a.in_stride + (long long)j * a.nrhs + r];
+                if (++j == ns) { j = 0; ++s; }
             }
             tcp::put_a(st, rp, h * 4 + u, y[0], y[1]);
         }
     }
     __device__ void gen_b(const Stage& st, int c) {
         const int f0 = c * KCC;
-        int s = f0 / nc, j = f0 - s * nc;
-        int cs = -1, l = 0;
+        int s = f0 / ns, j = f0 - s * ns;
+        int cs = -1, e = 0;
         long long off = 0;
+        const int kbase = a.K - a.Ps - (i - a.Pd);       // sequence index = off + kbase + j
 #pragma unroll
         for (int kk = 0; kk < tcp::KC / 4; ++kk) {
             float2 z[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 z[v] = make_float2(0.f, 0.f);
-                if (valid && s < nsrc && s != self_m) {
+                if (valid && s < nsrc && s != self_t) {
                     if (s != cs) {
                         cs = s;
-                        l = src[s];
-                        off = tseq[ptr_m + s - (s > self_m ? 1 : 0)];
+                        e = src[s];
+                        off = a.tseq[ptr_t + s - (s > self_t ? 1 : 0)];
                     }
-                    const long long idx = off + K + (j - i);
-                    const float2 mv = seqm[idx];
-                    const float f = pow2f(seqe[idx] + a_mi + expo[((size_t)l * 2 + b) * nc + j]);
+                    const long long idx = off + kbase + j;
+                    const float2 mv = a.seqm[idx];
+                    const float f = pow2f(a.seqe[idx] + ad_i + a.as[(long long)e * a.as_stride + j]);
                     z[v] = make_float2(mv.x * f, mv.y * f);
                 }
-                if (++j == nc) { j = 0; ++s; }
+                if (++j == ns) { j = 0; ++s; }
             }
             tcp::put_b(st, threadIdx.x, kk, z[0], z[1]);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
+        const int n = ((ntgt * nrow + 15) / 16) * 16;
         if (!ok) return;
-        const int n = ((ntgt * nc + 15) / 16) * 16;
         tcp::for_each_acc(tmem, n, [&](int rp, int col, float v) {
             const int r = rp & 63, comp = rp >> 6;
-            if (r >= nrhs) return;
-            const int tt = col / nc;
-            if (tt >= ntgt) return;
-            const int i2 = col - tt * nc, m2 = tgt[tt];
-            reinterpret_cast<float*>(out + (((size_t)m2 * 2 + b) * nc + i2) * nrhs + r)[comp] = v;
+            if (r >= a.nrhs) return;
+            const int tt = col / nrow;
+            const int i2 = i0 + (col - tt * nrow);
+            if (tt >= ntgt || i2 >= nd) return;
+            reinterpret_cast<float*>(a.out + (long long)tgt[tt] * a.out_stride + (long long)i2 * a.nrhs + r)[comp] = v;
         });
     }
 };
 
-__global__ void __launch_bounds__(tcp::THREADS, 1)
-k_near_tc(const float2* __restrict__ xs, const float2* __restrict__ seqm, const int* __restrict__ seqe,
-          const long long* __restrict__ tseq0, const long long* __restrict__ tseq1, const int* __restrict__ nptr,
-          const int4* __restrict__ tiles, const int* __restrict__ ttgt, const int* __restrict__ tself,
-          const int* __restrict__ tsrc, const int* __restrict__ expo, float2* __restrict__ out, int nc, int nrhs,
-          int K, int* err) {
-    const int b = blockIdx.y;
-    const int4 t = tiles[blockIdx.x];
-    NearPolicy pol{xs, seqm, seqe, b ? tseq1 : tseq0, nptr, ttgt + t.x, tself + t.x, tsrc + t.z, expo, out,
-                   nc, nrhs, b, t.y, t.w, K};
+__global__ void __launch_bounds__(tcp::THREADS, 1) k_list_tc(ListArgs a, int* err) {
+    const int4 t = a.tiles[blockIdx.x];
+    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1;
+    const int i0 = a.trow ? a.trow[blockIdx.x] : 0;
+    const int nrow = t.y == 1 ? min(tcp::NMAX, nd - i0) : nd;
+    ListPolicy pol{a, a.ttgt + t.x, a.tself + t.x, a.tsrc + t.z, t.y, t.w, nrow, i0, nd, ns};
     pol.init();
-    const int n = ((t.y * nc + 15) / 16) * 16;
-    const int nchunks = (t.w * nc + KCC - 1) / KCC;
+    const int n = ((t.y * nrow + 15) / 16) * 16;
+    const int nchunks = (t.w * ns + KCC - 1) / KCC;
     tcp::run(pol, nchunks, n, err);
+}
+
+inline int upv(ms_handle* h, void** dst, const void* src, size_t bytes) {
+    *dst = nullptr;
+    if (!bytes) return MS_OK;
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return MS_ERR_ALLOC;
+    return ms_check(h, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
 }
 
 }  // namespace
 
+// Tiles of the FMM multipole-to-local stage for (wave b, level lev): one tile per 256-row range of
+// every box that has an interaction list; its sources are the box's M2L tasks.  Boxes without a list
+// keep zero local expansions (the launch clears the level first).
+int ms_m2l_tc_tiles(ms_handle* h, int b, int lev, const std::vector<int>& ptr) {
+    FmmHost& F = h->fmm;
+    const int nd = 2 * F.P[b][lev] + 1;
+    std::vector<int4> tiles;
+    std::vector<int> tgt, self, row;
+    for (int d = 0; d + 1 < (int)ptr.size(); ++d) {
+        if (ptr[d + 1] == ptr[d]) continue;
+        for (int i0 = 0; i0 < nd; i0 += tcp::NMAX) {
+            tiles.push_back(make_int4((int)tgt.size(), 1, ptr[d], ptr[d + 1] - ptr[d]));
+            tgt.push_back(d);
+            self.push_back(-1);
+            row.push_back(i0);
+        }
+    }
+    TcTiles& T = F.m2l_tc[b][lev];
+    T.n = (int)tiles.size();
+    int rc;
+    if ((rc = upv(h, (void**)&T.tile, tiles.data(), tiles.size() * sizeof(int4))) ||
+        (rc = upv(h, (void**)&T.tgt, tgt.data(), tgt.size() * sizeof(int))) ||
+        (rc = upv(h, (void**)&T.self, self.data(), self.size() * sizeof(int))) ||
+        (rc = upv(h, (void**)&T.row, row.data(), row.size() * sizeof(int))))
+        return rc;
+    return MS_OK;
+}
+
+void ms_tc_tiles_free(TcTiles& T) {
+    cudaFree(T.tile); cudaFree(T.tgt); cudaFree(T.self); cudaFree(T.src); cudaFree(T.row);
+    T = TcTiles{};
+}
+
 // a~ = near-pair Graf sum of the FP32 scaled block xs into dst (written, both waves).
 int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cudaStream_t st) {
     const FmmHost& F = h->fmm;
-    cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
-    k_near_tc<<<dim3(F.ntile, 2), tcp::THREADS, tcp::SMEM, st>>>(
-        xs, h->d.seqm, h->d.seqe, F.near[0].seq, F.near[1].seq, F.near[0].ptr, F.tile, F.ttgt, F.tself, F.tsrc,
-        h->d.expo, dst, h->nc, nrhs, 2 * h->p + 1, h->d.tc_err);
+    const int nc = h->nc;
+    cudaFuncSetAttribute(k_list_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+    for (int b = 0; b < 2; ++b) {
+        ListArgs a{};
+        a.in = xs + (long long)b * nc * nrhs; a.in_stride = 2LL * nc * nrhs;
+        a.out = dst + (long long)b * nc * nrhs; a.out_stride = 2LL * nc * nrhs;
+        a.seqm = h->d.seqm; a.seqe = h->d.seqe;
+        a.tseq = F.near[b].seq; a.tptr = F.near[b].ptr;
+        a.ad = h->d.expo + b * nc; a.ad_stride = 2LL * nc;
+        a.as = h->d.expo + b * nc; a.as_stride = 2LL * nc;
+        a.tiles = F.near_tc.tile; a.ttgt = F.near_tc.tgt; a.tself = F.near_tc.self; a.tsrc = F.near_tc.src;
+        a.trow = nullptr;
+        a.Pd = h->p; a.Ps = h->p; a.K = 2 * h->p + 1; a.nrhs = nrhs;
+        k_list_tc<<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+    }
+    return MS_OK;
+}
+
+// Multipole-to-local of (wave b, level lev) from the FP32 multipole block into the local block.
+int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* lexp, int nrhs, cudaStream_t st) {
+    const FmmHost& F = h->fmm;
+    const int P = F.P[b][lev], nd = 2 * P + 1;
+    if (int rc = ms_check(h, cudaMemsetAsync(lexp, 0, (size_t)F.nbox[lev] * nd * nrhs * sizeof(float2), st)))
+        return rc;
+    const TcTiles& T = F.m2l_tc[b][lev];
+    if (T.n == 0) return MS_OK;
+    cudaFuncSetAttribute(k_list_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+    ListArgs a{};
+    a.in = mexp; a.in_stride = (long long)nd * nrhs;
+    a.out = lexp; a.out_stride = (long long)nd * nrhs;
+    a.seqm = h->d.seqm; a.seqe = h->d.seqe;
+    a.tseq = F.m2l[b][lev].seq; a.tptr = F.m2l[b][lev].ptr;
+    a.ad = F.expo[b][lev]; a.ad_stride = 0;
+    a.as = F.expo[b][lev]; a.as_stride = 0;
+    a.tiles = T.tile; a.ttgt = T.tgt; a.tself = T.self; a.tsrc = F.m2l[b][lev].src; a.trow = T.row;
+    a.Pd = P; a.Ps = P; a.K = 2 * P; a.nrhs = nrhs;
+    k_list_tc<<<T.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
     return ms_check(h, cudaGetLastError());
 }

@@ -1,7 +1,8 @@
 // Fifth-generation tensor-core (tcgen05) building blocks for sm_103a, as inline PTX:
 // tensor-memory allocation, shared-memory matrix descriptors, the kind::tf32 MMA with its
 // instruction descriptor, commit to an mbarrier, tensor-memory loads, bounded mbarrier waits and the
-// fp32 -> tf32 hi/lo split used for FP32-accurate products (3xTF32: a b ~ ah bh + ah bl + al bh).
+// fp32 -> tf32 hi/lo split used for near-FP32 products (3xTF32: a b ~ ah bh + ah bl + al bh, relative
+// error about 2^-21 per product against 2^-24 for an FP32 multiply).
 //
 // Operand layout (no swizzle, K-major): an R x K tile (R rows, K contiguous 32-bit values per row) is
 // stored as 8-row x 16-byte core matrices; core matrix (g, kk) (rows 8g..8g+7, k 4kk..4kk+3) starts at
@@ -39,10 +40,11 @@ __device__ __forceinline__ float tf32_rna(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
-// x = hi + lo with hi exactly representable in tf32
+// x ~ hi + lo with hi and lo both tf32 values (lo rounded rather than left to the hardware's
+// truncation of its low mantissa bits): |x - hi - lo| <= 2^-22 |x|
 __device__ __forceinline__ void split(float x, float& hi, float& lo) {
     hi = tf32_rna(x);
-    lo = x - hi;
+    lo = tf32_rna(x - hi);
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
