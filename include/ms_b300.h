@@ -101,9 +101,10 @@ typedef struct {
                                   d ~ 3 / (horizontal extent) and panels narrow enough for e^{i t dx} */
     int32_t grade;             /* extra panel edges at each branch point +-kp, +-ks of both layers and
                                   at c +- d 2^j, j < grade (default 0: none) */
-    int32_t tensor_cores;      /* MS_PREC_FP32 spectral contractions (M2S, S2L and their adjoints):
-                                  1 = tcgen05 tensor cores, 3xTF32 split with FP32 accumulation;
-                                  0 = CUDA-core FP32 (default).  Costs 16 M N_S bytes of device tables. */
+    int32_t tensor_cores;      /* MS_PREC_FP32 contractions (near-pair Graf sum, FMM M2L, M2S, S2L; the adjoints of the
+                                  spectral maps):
+                                  1 = tcgen05 tensor cores, 3xTF32 split with FP32 accumulation (default);
+                                  0 = CUDA-core FP32.  Costs 16 M N_S bytes of device tables. */
 } ms_options;
 
 typedef struct {

@@ -45,7 +45,7 @@ class Solver:
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
-                 tensor_cores: bool = False):
+                 tensor_cores: bool = True):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)

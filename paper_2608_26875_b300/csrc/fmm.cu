@@ -452,6 +452,13 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
         if ((rc = upload_list(h, hl, h->fmm.near[b]))) return rc;
     }
     if (h->opt.tensor_cores) {
+        // the near sequences of each wave are consecutive (the tensor-core tiles compute offsets)
+        for (int b = 0; b < 2; ++b) {
+            const long long len = 4LL * p + 3;
+            h->fmm.near_seq_base[b] = seq_near[b].empty() ? 0 : seq_near[b][0];
+            for (size_t t = 0; t < seq_near[b].size(); ++t)
+                if (seq_near[b][t] != h->fmm.near_seq_base[b] + (long long)t * len) return MS_ERR_UNSUPPORTED;
+        }
         // tiles of the tensor-core near field (same source order as the near lists above)
         const int tpt = std::max(1, 256 / h->nc);
         std::vector<int4> tinfo;

@@ -64,6 +64,7 @@ struct FmmHost {
     // ptr[m] + s - (s > self position)) and of the M2L lists (256-row ranges of one box)
     TcTiles near_tc;
     TcTiles m2l_tc[2][13];
+    long long near_seq_base[2] = {0, 0};   // near task t's sequence starts at base + t (4p + 3)
 };
 
 struct MsDeviceTables {

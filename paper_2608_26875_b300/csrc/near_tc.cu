@@ -8,7 +8,8 @@
 // leaf against the 3 x 3 leaves around it; the self block is zero), or a row range of one box (M2L:
 // 2P + 1 rows against its interaction list).  Each tile is one dense contraction over (source,
 // order): the input expansions form the 128-row A operand and the Toeplitz blocks the B operand
-// (tc_pipeline.cuh).  Task of target d and source slot s: tptr[d] + s - (s > self(d)).
+// (tc_pipeline.cuh).  Task of target d and source slot s: tptr[d] + s, minus one past the target's
+// own slot self(d) when it has one (near lists; self(d) = -1 for M2L).
 #include <algorithm>
 #include <vector>
 
@@ -28,7 +29,9 @@ struct ListArgs {
     long long out_stride;
     const float2* seqm;
     const int* seqe;
-    const long long* tseq;       // per task: sequence offset
+    const long long* tseq;       // per task: sequence offset (used when seq_len == 0)
+    long long seq_base;          // seq_len > 0: task t's sequence starts at seq_base + t * seq_len
+    int seq_len;
     const int* tptr;             // per target entity: first task
     const int* ad;               // target exponents ad[d * ad_stride + i]
     long long ad_stride;
@@ -42,14 +45,22 @@ struct ListArgs {
     int Pd, Ps, K, nrhs;
 };
 
+constexpr int MAX_TABLE = 64;    // task offsets staged per single-target tile (M2L lists <= 27)
+
 struct ListPolicy {
     const ListArgs& a;
     const int* tgt;
     const int* self;
     const int* src;
+    const long long* toff;       // staged task offsets of a single-target tile, or NULL
     int ntgt, nsrc, nrow, i0, nd, ns;
-    int i, ad_i, ptr_t, self_t;
+    int i, ad_i, ptr_t, self_t, kbase;
     bool valid;
+    // one fetched chunk
+    float2 ya[8];
+    float2 mv[16];
+    int ex[16];
+    unsigned vmask;
 
     __device__ void init() {
         const int row = threadIdx.x;
@@ -64,48 +75,61 @@ struct ListPolicy {
             ptr_t = a.tptr[d];
             self_t = self[tt];
         }
+        kbase = a.K - a.Ps - (i - a.Pd);         // sequence index = task offset + kbase + j
     }
-    __device__ void load_a(const Stage& st, int c) {
+    __device__ long long task_off(int s) const {
+        const int t = ptr_t + s - ((self_t >= 0 && s > self_t) ? 1 : 0);
+        if (a.seq_len > 0) return a.seq_base + (long long)t * a.seq_len;
+        return toff ? toff[s] : a.tseq[t];
+    }
+    __device__ void fetch(int c) {
         const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
         const bool ok = r < a.nrhs;
-        const int f0 = c * KCC + h * 8;
-        int s = f0 / ns, j = f0 - s * ns;
+        const int fa = c * KCC + h * 8;
+        int s = fa / ns, j = fa - s * ns;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float2 y[2];
-#pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                y[v] = make_float2(0.f, 0.f);
-                if (ok && s < nsrc) y[v] = a.in[(long long)src[s] * a.in_stride + (long long)j * a.nrhs + r];
-                if (++j == ns) { j = 0; ++s; }
-            }
-            tcp::put_a(st, rp, h * 4 + u, y[0], y[1]);
+        for (int v = 0; v < 8; ++v) {
+            ya[v] = (ok && s < nsrc) ? a.in[(long long)src[s] * a.in_stride + (long long)j * a.nrhs + r]
+                                     : make_float2(0.f, 0.f);
+            if (++j == ns) { j = 0; ++s; }
         }
-    }
-    __device__ void gen_b(const Stage& st, int c) {
         const int f0 = c * KCC;
-        int s = f0 / ns, j = f0 - s * ns;
+        s = f0 / ns;
+        j = f0 - s * ns;
+        vmask = 0;
         int cs = -1, e = 0;
         long long off = 0;
-        const int kbase = a.K - a.Ps - (i - a.Pd);       // sequence index = off + kbase + j
 #pragma unroll
-        for (int kk = 0; kk < tcp::KC / 4; ++kk) {
+        for (int v = 0; v < 16; ++v) {
+            if (valid && s < nsrc && s != self_t) {
+                if (s != cs) {
+                    cs = s;
+                    e = src[s];
+                    off = task_off(s);
+                }
+                const long long idx = off + kbase + j;
+                vmask |= 1u << v;
+                mv[v] = a.seqm[idx];
+                ex[v] = a.seqe[idx] + a.as[(long long)e * a.as_stride + j];
+            }
+            if (++j == ns) { j = 0; ++s; }
+        }
+    }
+    __device__ void build(const Stage& st) {
+        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
             float2 z[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
+                const int q = 2 * kk + v;
                 z[v] = make_float2(0.f, 0.f);
-                if (valid && s < nsrc && s != self_t) {
-                    if (s != cs) {
-                        cs = s;
-                        e = src[s];
-                        off = a.tseq[ptr_t + s - (s > self_t ? 1 : 0)];
-                    }
-                    const long long idx = off + kbase + j;
-                    const float2 mv = a.seqm[idx];
-                    const float f = pow2f(a.seqe[idx] + ad_i + a.as[(long long)e * a.as_stride + j]);
-                    z[v] = make_float2(mv.x * f, mv.y * f);
+                if ((vmask >> q) & 1u) {
+                    const float f = pow2f(ex[q] + ad_i);
+                    z[v] = make_float2(mv[q].x * f, mv[q].y * f);
                 }
-                if (++j == ns) { j = 0; ++s; }
             }
             tcp::put_b(st, threadIdx.x, kk, z[0], z[1]);
         }
@@ -125,11 +149,19 @@ struct ListPolicy {
 };
 
 __global__ void __launch_bounds__(tcp::THREADS, 1) k_list_tc(ListArgs a, int* err) {
+    __shared__ long long toff[MAX_TABLE];
     const int4 t = a.tiles[blockIdx.x];
     const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1;
     const int i0 = a.trow ? a.trow[blockIdx.x] : 0;
     const int nrow = t.y == 1 ? min(tcp::NMAX, nd - i0) : nd;
-    ListPolicy pol{a, a.ttgt + t.x, a.tself + t.x, a.tsrc + t.z, t.y, t.w, nrow, i0, nd, ns};
+    // single-target lists with looked-up offsets: stage the task offsets once per tile
+    const bool staged = a.seq_len == 0 && t.y == 1 && t.w <= MAX_TABLE;
+    if (staged) {
+        const int p0 = a.tptr[a.ttgt[t.x]];
+        for (int s = threadIdx.x; s < t.w; s += blockDim.x) toff[s] = a.tseq[p0 + s];
+        __syncthreads();
+    }
+    ListPolicy pol{a, a.ttgt + t.x, a.tself + t.x, a.tsrc + t.z, staged ? toff : nullptr, t.y, t.w, nrow, i0, nd, ns};
     pol.init();
     const int n = ((t.y * nrow + 15) / 16) * 16;
     const int nchunks = (t.w * ns + KCC - 1) / KCC;
@@ -189,6 +221,7 @@ int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cud
         a.out = dst + (long long)b * nc * nrhs; a.out_stride = 2LL * nc * nrhs;
         a.seqm = h->d.seqm; a.seqe = h->d.seqe;
         a.tseq = F.near[b].seq; a.tptr = F.near[b].ptr;
+        a.seq_base = F.near_seq_base[b]; a.seq_len = 4 * h->p + 3;
         a.ad = h->d.expo + b * nc; a.ad_stride = 2LL * nc;
         a.as = h->d.expo + b * nc; a.as_stride = 2LL * nc;
         a.tiles = F.near_tc.tile; a.ttgt = F.near_tc.tgt; a.tself = F.near_tc.self; a.tsrc = F.near_tc.src;
@@ -214,6 +247,7 @@ int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* l
     a.out = lexp; a.out_stride = (long long)nd * nrhs;
     a.seqm = h->d.seqm; a.seqe = h->d.seqe;
     a.tseq = F.m2l[b][lev].seq; a.tptr = F.m2l[b][lev].ptr;
+    a.seq_base = 0; a.seq_len = 0;
     a.ad = F.expo[b][lev]; a.ad_stride = 0;
     a.as = F.expo[b][lev]; a.as_stride = 0;
     a.tiles = T.tile; a.ttgt = T.tgt; a.tself = T.self; a.tsrc = F.m2l[b][lev].src; a.trow = T.row;

@@ -214,7 +214,7 @@ extern "C" void ms_default_options(ms_options* o) {
     o->leaf_target = 10;
     o->depth = 0.5;
     o->grade = 0;
-    o->tensor_cores = 0;
+    o->tensor_cores = 1;
 }
 
 // Panel edges of the Sommerfeld rule on [-t_max, t_max]: n uniform panels (edge k at

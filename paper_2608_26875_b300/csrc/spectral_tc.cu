@@ -48,6 +48,10 @@ struct S2LPolicy {
     int M, nc, NSp, nrhs, b, j0, accumulate, conj;
     int j, m, n, a;
     bool valid;
+    // one fetched chunk
+    float2 ya[8];
+    float4 e4[8], q4[8];
+    int2 qe2[8];
 
     __device__ void init() {
         j = j0 + threadIdx.x;
@@ -56,58 +60,48 @@ struct S2LPolicy {
         n = valid ? j - m * nc : 0;
         a = valid ? expo[((size_t)m * 2 + b) * nc + n] : 0;
     }
-    __device__ void load_a(const Stage& st, int c) {
+    __device__ void fetch(int c) {
         const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
-        const bool ok = r < nrhs;
+        const int qa = c * KCC + h * 8;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int kk = h * 4 + u;
-            const int q = c * KCC + 2 * kk;
-            float2 y0 = make_float2(0.f, 0.f), y1 = y0;
-            if (ok) {
-                y0 = D[(size_t)q * nrhs + r];
-                y1 = D[(size_t)(q + 1) * nrhs + r];
+        for (int v = 0; v < 8; ++v) ya[v] = r < nrhs ? D[(size_t)(qa + v) * nrhs + r] : make_float2(0.f, 0.f);
+        if (valid) {
+            const int q0 = c * KCC;
+            const float4* er = reinterpret_cast<const float4*>(E + (size_t)m * NSp + q0);
+            const float4* qr = reinterpret_cast<const float4*>(Qm + (size_t)n * NSp + q0);
+            const int2* xr = reinterpret_cast<const int2*>(Qe + (size_t)n * NSp + q0);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                e4[kk] = er[kk];
+                q4[kk] = qr[kk];
+                qe2[kk] = xr[kk];
             }
-            tcp::put_a(st, rp, kk, y0, y1);
         }
     }
-    __device__ void gen_b(const Stage& st, int c) {
-        const int t = threadIdx.x;
-        const int q0 = c * KCC;
+    __device__ void build(const Stage& st) {
+        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
 #pragma unroll
-        for (int kk = 0; kk < KC / 4; ++kk) {
+        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
             float2 g0 = make_float2(0.f, 0.f), g1 = g0;
             if (valid) {
-                const int q = q0 + 2 * kk;
-                const float4 e = *reinterpret_cast<const float4*>(E + (size_t)m * NSp + q);
-                const float4 qm = *reinterpret_cast<const float4*>(Qm + (size_t)n * NSp + q);
-                const int2 qe = *reinterpret_cast<const int2*>(Qe + (size_t)n * NSp + q);
-                g0 = gen_entry(make_float2(e.x, e.y), make_float2(qm.x, qm.y), qe.x + a, conj);
-                g1 = gen_entry(make_float2(e.z, e.w), make_float2(qm.z, qm.w), qe.y + a, conj);
+                g0 = gen_entry(make_float2(e4[kk].x, e4[kk].y), make_float2(q4[kk].x, q4[kk].y), qe2[kk].x + a, conj);
+                g1 = gen_entry(make_float2(e4[kk].z, e4[kk].w), make_float2(q4[kk].z, q4[kk].w), qe2[kk].y + a, conj);
             }
-            tcp::put_b(st, t, kk, g0, g1);
+            tcp::put_b(st, threadIdx.x, kk, g0, g1);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
         if (!ok) return;
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int quarter = w & 3, half = w >> 2;
-        const int rp = 32 * quarter + lane, r = rp & 63, comp = rp >> 6;
-#pragma unroll 1
-        for (int cb = 0; cb < 8; ++cb) {
-            const int col0 = 128 * half + 16 * cb;
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
-            if (r >= nrhs) continue;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int jj = j0 + col0 + i;
-                if (jj >= M * nc) break;
-                const int m2 = jj / nc, n2 = jj - m2 * nc;
-                float* dst = reinterpret_cast<float*>(out + (((size_t)m2 * 2 + b) * nc + n2) * nrhs + r) + comp;
-                *dst = accumulate ? *dst + v[i] : v[i];
-            }
-        }
+        tcp::for_each_acc(tmem, NT, [&](int rp, int col, float v) {
+            const int r = rp & 63, comp = rp >> 6;
+            const int jj = j0 + col;
+            if (r >= nrhs || jj >= M * nc) return;
+            const int m2 = jj / nc, n2 = jj - m2 * nc;
+            float* dst = reinterpret_cast<float*>(out + (((size_t)m2 * 2 + b) * nc + n2) * nrhs + r) + comp;
+            *dst = accumulate ? *dst + v : v;
+        });
     }
 };
 
@@ -134,81 +128,64 @@ struct M2SPolicy {
     int M, nc, NS, NSp, nrhs, b, q0, i0, i1, split, conj;
     int q;
     bool valid;
+    // one fetched chunk
+    float2 ya[8];
+    float2 ee[16], qm[16];
+    int ex[16];
+    unsigned vmask;
 
     __device__ void init() {
         q = q0 + threadIdx.x;
         valid = q < NS;
     }
-    __device__ void load_a(const Stage& st, int c) {
+    __device__ void fetch(int c) {
         const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
         const bool ok = r < nrhs;
-        const int base = i0 + c * KCC + h * 8;
+        const int ia = i0 + c * KCC + h * 8;
+        int l = ia / nc, n = ia - l * nc;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int kk = h * 4 + u;
-            float2 y[2];
+        for (int v = 0; v < 8; ++v) {
+            ya[v] = (ok && ia + v < i1) ? xs[(((size_t)l * 2 + b) * nc + n) * nrhs + r] : make_float2(0.f, 0.f);
+            if (++n == nc) { n = 0; ++l; }
+        }
+        const int ib = i0 + c * KCC;
+        l = ib / nc;
+        n = ib - l * nc;
+        vmask = 0;
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                const int i = base + 2 * u + v;
-                y[v] = make_float2(0.f, 0.f);
-                if (ok && i < i1) {
-                    const int l = i / nc, n = i - l * nc;
-                    y[v] = xs[(((size_t)l * 2 + b) * nc + n) * nrhs + r];
-                }
+        for (int v = 0; v < 16; ++v) {
+            if (valid && ib + v < i1) {
+                vmask |= 1u << v;
+                ee[v] = E[(size_t)l * NSp + q];
+                qm[v] = Qm[(size_t)q * nc + n];
+                ex[v] = Qe[(size_t)q * nc + n] + expo[((size_t)l * 2 + b) * nc + n];
             }
-            tcp::put_a(st, rp, kk, y[0], y[1]);
+            if (++n == nc) { n = 0; ++l; }
         }
     }
-    __device__ void gen_b(const Stage& st, int c) {
-        const int t = threadIdx.x;
-        const int ib = i0 + c * KCC;
-        int l = ib / nc, n = ib - l * nc;
-        float2 e = make_float2(0.f, 0.f);
-        if (valid && ib < i1) e = E[(size_t)l * NSp + q];
+    __device__ void build(const Stage& st) {
+        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
 #pragma unroll
-        for (int kk = 0; kk < KC / 4; ++kk) {
+        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
             float2 g[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-                const int i = ib + 2 * kk + v;
-                g[v] = make_float2(0.f, 0.f);
-                if (valid && i < i1) {
-                    const float2 qm = Qm[(size_t)q * nc + n];
-                    const int ex = Qe[(size_t)q * nc + n] + expo[((size_t)l * 2 + b) * nc + n];
-                    g[v] = gen_entry(e, qm, ex, conj);
-                }
-                if (++n == nc) {
-                    n = 0;
-                    ++l;
-                    if (valid && i + 1 < i1) e = E[(size_t)l * NSp + q];
-                }
+                const int e = 2 * kk + v;
+                g[v] = (vmask >> e) & 1u ? gen_entry(ee[e], qm[e], ex[e], conj) : make_float2(0.f, 0.f);
             }
-            tcp::put_b(st, t, kk, g[0], g[1]);
+            tcp::put_b(st, threadIdx.x, kk, g[0], g[1]);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int quarter = w & 3, half = w >> 2;
-        const int rp = 32 * quarter + lane, r = rp & 63, comp = rp >> 6;
-#pragma unroll 1
-        for (int cb = 0; cb < 8; ++cb) {
-            const int col0 = 128 * half + 16 * cb;
-            float v[16];
-            if (ok) {
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-            }
-            if (r >= nrhs) continue;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int qq = q0 + col0 + i;
-                if (qq >= NS) break;
-                double* dst = reinterpret_cast<double*>(part + (((size_t)split * 2 + b) * NS + qq) * nrhs + r) + comp;
-                *dst = (double)v[i];
-            }
-        }
+        tcp::for_each_acc(tmem, NT, [&](int rp, int col, float v) {
+            const int r = rp & 63, comp = rp >> 6;
+            const int qq = q0 + col;
+            if (r >= nrhs || qq >= NS) return;
+            double* dst = reinterpret_cast<double*>(part + (((size_t)split * 2 + b) * NS + qq) * nrhs + r) + comp;
+            *dst = ok ? (double)v : 0.0;
+        });
     }
 };
 

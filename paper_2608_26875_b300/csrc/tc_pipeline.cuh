@@ -66,8 +66,10 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// P provides load_a(Stage, chunk), gen_b(Stage, chunk) and epilogue(tmem, ok); n is the MMA N of
-// this tile (a multiple of 16 in [16, 256]).  Sets *err on a timed-out wait.
+// P provides fetch(chunk) (issue the global loads of one K chunk into registers), build(Stage)
+// (write the A and B tiles of the fetched chunk) and epilogue(tmem, ok); n is the MMA N of this
+// tile (a multiple of 16 in [16, 256]).  The loads of chunk c + 1 are issued right after chunk c is
+// built, so their latency overlaps the MMAs in flight.  Sets *err on a timed-out wait.
 template <class P>
 __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -87,12 +89,13 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     tc::fence_after();
     const uint32_t tmem = *tslot;
     int issued = 0;
+    if (nchunks > 0) pol.fetch(0);
     for (int c = 0; c < nchunks; ++c) {
         const int s = c % NSTAGE;
         if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
         const Stage st = stage_ptrs(smem, s);
-        pol.load_a(st, c);
-        pol.gen_b(st, c);
+        pol.build(st);
+        if (c + 1 < nchunks) pol.fetch(c + 1);
         tc::fence_proxy_async();
         __syncthreads();
         if (*fail) break;

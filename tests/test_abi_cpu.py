@@ -59,7 +59,7 @@ def test_default_options(lib):
     import paper_2608_26875_b300 as P
     o = P.default_options()
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
-    assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 0)
+    assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 1)
     assert ctypes.sizeof(o) == 56      # the C struct: 8 int32, 2 doubles, padding
 
 
