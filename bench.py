@@ -308,12 +308,13 @@ def run_solve(args):
     wl = syn.config3(M=args.M, nrhs=args.nrhs) if args.M != 10000 else workload()
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
-                               restart=args.restart, max_iters=args.max_iters)
+                               restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol)
     torch.cuda.synchronize()
     g, info = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
     torch.cuda.synchronize()
     out = {"mode": "solve", "workload": wl.name, "M": wl.M, "nrhs": len(kinds), "tol": 1e-8,
            "restart": args.restart, "max_iters": args.max_iters, "tensor_cores": bool(args.tensor_cores),
+           "inner_tol": args.inner_tol or "default",
            "mixed": info}
     x = torch.empty_like(g)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -330,7 +331,9 @@ def run_solve(args):
     ev1.record()
     torch.cuda.synchronize()
     out["fp32_matvec_s"] = ev0.elapsed_time(ev1) / 1000.0
-    if args.full_fp64:
+    if args.skip_fp64:
+        pass
+    elif args.full_fp64:
         g64, info64 = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP64)
         out["fp64"] = info64
         out["rel_diff_mixed_vs_fp64"] = float(torch.linalg.norm(g - g64) / torch.linalg.norm(g64))
@@ -345,7 +348,8 @@ def run_grad(args):
     32 plane P-waves, 128 receivers on y = -0.5.  The data are the receiver fields of the same discs
     with centres moved by N(0, 0.05^2) (synthetic truth); one gradient is the whole evaluation at the
     current centres: ms_setup, the forward solve, the receiver fields, and ms_grad (adjoint solve plus
-    the centre, radius and frequency derivatives).  Both precisions to relative residual 1e-10."""
+    the centre, radius and frequency derivatives), both solves to --tol with --restart / --max-iters,
+    in the precisions of --grad-prec."""
     import copy
 
     import torch
@@ -355,22 +359,26 @@ def run_grad(args):
     wl = syn.config4()
     rx = wl.receivers
     truth = copy.deepcopy(wl)
-    truth.centres = wl.centres + np.random.default_rng(2006).normal(0.0, 0.05, wl.centres.shape)
+    truth.centres = syn.perturb_centres(wl.centres, wl.radius, 0.05, 3001)
     st = P.Solver.from_workload(truth)
     gt, _ = st.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP64)
     d = st.fields(gt, rx)
     st.close()
     out = {"mode": "grad", "workload": wl.name, "M": wl.M, "nrhs": wl.nrhs, "receivers": int(rx.shape[0])}
-    for name, prec in (("mixed", P.MS_PREC_FP32), ("fp64", P.MS_PREC_FP64)):
+    precs = {"mixed": [("mixed", P.MS_PREC_FP32)], "fp64": [("fp64", P.MS_PREC_FP64)],
+             "both": [("mixed", P.MS_PREC_FP32), ("fp64", P.MS_PREC_FP64)]}[args.grad_prec]
+    out.update({"tol": args.tol, "restart": args.restart, "max_iters": args.max_iters})
+    for name, prec in precs:
         times = []
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores)
-            g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=prec)
+            s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores, restart=args.restart,
+                                       max_iters=args.max_iters)
+            g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=args.tol, prec=prec)
             u = s.fields(g, rx)
             w = (u - d).contiguous()
-            gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-10, prec=prec)
+            gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=args.tol, prec=prec)
             loss = 0.5 * float(torch.sum(torch.abs(w) ** 2))
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
@@ -431,7 +439,11 @@ def main():
     ap.add_argument("--M", type=int, default=2500, help="particles of --profile (default 2500) or --mode solve")
     ap.add_argument("--nrhs", type=int, default=64, help="--mode solve: right-hand sides")
     ap.add_argument("--restart", type=int, default=50, help="--mode solve: GMRES restart length")
-    ap.add_argument("--max-iters", type=int, default=2000, help="--mode solve: GMRES iteration cap")
+    ap.add_argument("--max-iters", type=int, default=2000, help="--mode solve/grad: GMRES iteration cap")
+    ap.add_argument("--tol", type=float, default=1e-8, help="--mode grad: solve tolerance")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="--mode solve: inner GMRES tolerance (0: default)")
+    ap.add_argument("--skip-fp64", action="store_true", help="--mode solve: mixed form only")
+    ap.add_argument("--grad-prec", choices=["mixed", "fp64", "both"], default="mixed")
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
     ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
                     help="FP32 near field and spectral maps on the CUDA cores instead of tcgen05")

@@ -45,7 +45,7 @@ class Solver:
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
-                 tensor_cores: bool = True):
+                 tensor_cores: bool = True, inner_tol: float = 0.0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -76,6 +76,7 @@ class Solver:
         o.use_fmm, o.leaf_target = int(bool(use_fmm)), int(leaf_target)
         o.depth, o.grade = float(depth), int(grade)
         o.tensor_cores = int(bool(tensor_cores))
+        o.inner_tol = float(inner_tol)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")

@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_panels", c_int), ("nodes_per_panel", c_int), ("t_max", ctypes.c_double),
                 ("restart", c_int), ("max_iters", c_int), ("check_geometry", c_int),
                 ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int),
-                ("tensor_cores", c_int)]
+                ("tensor_cores", c_int), ("inner_tol", ctypes.c_double)]
 
 
 class Incidence(ctypes.Structure):

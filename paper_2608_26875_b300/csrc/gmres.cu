@@ -364,7 +364,7 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
     }
     std::vector<double> bn, rn;
     if (!rc) rc = K64.norms(b, bn);
-    const double inner_tol = prec == MS_PREC_FP64 ? 1e-7 : 1e-5;
+    const double inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : (prec == MS_PREC_FP64 ? 1e-7 : 1e-5);
     const int max_ref = 40;
     int left = h->opt.max_iters;
     while (!rc) {

@@ -116,6 +116,38 @@ def place_particles(rng: np.random.Generator, M: int, box, rmin: float, rmax: fl
     return np.stack([cx, cy], axis=1), rr
 
 
+def perturb_centres(centres: np.ndarray, radius: np.ndarray, sigma: float, seed: int,
+                    max_rounds: int = 1000) -> np.ndarray:
+    """Centres moved by N(0, sigma^2) per coordinate; a particle whose move violates the separation
+    rule (or burial) against the already-moved configuration is re-drawn (the inverse-problem
+    truth of the gradient workload)."""
+    rng = np.random.default_rng(seed)
+    c = centres + rng.normal(0.0, sigma, centres.shape)
+
+    def bad_set(c):
+        bad = set(np.where(c[:, 1] + SEP * radius > 0.0)[0].tolist())
+        rmax = float(radius.max())
+        cell = 2.0 * SEP * rmax
+        grid: dict[tuple[int, int], list[int]] = {}
+        keys = np.floor(c / cell).astype(int)
+        for i, (gx, gy) in enumerate(keys):
+            grid.setdefault((gx, gy), []).append(i)
+        for i, (gx, gy) in enumerate(keys):
+            for ix in range(gx - 1, gx + 2):
+                for iy in range(gy - 1, gy + 2):
+                    for j in grid.get((ix, iy), ()):
+                        if j > i and np.sum((c[i] - c[j]) ** 2) < (SEP * (radius[i] + radius[j])) ** 2:
+                            bad.add(j)
+        return sorted(bad)
+
+    for _ in range(max_rounds):
+        bad = bad_set(c)
+        if not bad:
+            return c
+        c[bad] = centres[bad] + rng.normal(0.0, sigma, (len(bad), 2))
+    raise RuntimeError("perturbation could not be made admissible")
+
+
 def receiver_line(R: int, x0: float, x1: float, y: float) -> np.ndarray:
     xs = np.linspace(x0, x1, R)
     return np.stack([xs, np.full(R, y)], axis=1)

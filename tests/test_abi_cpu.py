@@ -60,7 +60,8 @@ def test_default_options(lib):
     o = P.default_options()
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
     assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 1)
-    assert ctypes.sizeof(o) == 56      # the C struct: 8 int32, 2 doubles, padding
+    assert o.inner_tol == 0.0
+    assert ctypes.sizeof(o) == 64      # the C struct: 8 int32, 3 doubles, padding
 
 
 def test_timeout_status_string(lib):
@@ -102,3 +103,14 @@ def test_separation_rule_boundary_is_exact(lib):
     with pytest.raises(P.MsError) as e:
         P.Solver(c, r, np.zeros(3, np.int32), syn.MEDIA_STD, 2.0, 4)
     assert e.value.status == P._native.MS_ERR_NOT_BURIED
+
+
+def test_perturbed_truth_keeps_the_separation_rule():
+    wl = syn.config4(M=300, nrhs=1)
+    c = syn.perturb_centres(wl.centres, wl.radius, 0.05, 3001)
+    assert np.abs(c - wl.centres).max() > 0.05
+    d = np.sqrt(((c[:, None, :] - c[None, :, :]) ** 2).sum(-1))
+    lim = syn.SEP * (wl.radius[:, None] + wl.radius[None, :])
+    np.fill_diagonal(d, np.inf)
+    assert np.all(d >= lim)
+    assert np.all(c[:, 1] + syn.SEP * wl.radius <= 0.0)
