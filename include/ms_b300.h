@@ -106,7 +106,7 @@ typedef struct {
                                   1 = tcgen05 tensor cores, 3xTF32 split with FP32 accumulation (default);
                                   0 = CUDA-core FP32.  Costs 16 M N_S bytes of device tables. */
     double  inner_tol;         /* ms_solve / ms_grad: relative tolerance of each inner GMRES solve of the
-                                  FP64 iterative refinement; 0 = default (1e-5 for MS_PREC_FP32,
+                                  FP64 iterative refinement; 0 = default (1e-3 for MS_PREC_FP32,
                                   1e-7 for MS_PREC_FP64) */
 } ms_options;
 

@@ -56,14 +56,14 @@ struct ListPolicy {
     int ntgt, nsrc, nrow, i0, nd, ns;
     int i, ad_i, ptr_t, self_t, kbase;
     bool valid;
-    // one fetched chunk
-    float2 ya[8];
-    float2 mv[16];
-    int ex[16];
+    // one fetched chunk (this thread's share)
+    float2 ya[4];
+    float2 mv[8];
+    int ex[8];
     unsigned vmask;
 
     __device__ void init() {
-        const int row = threadIdx.x;
+        const int row = tcp::brow();
         const int tt = row / nrow;
         i = i0 + (row - tt * nrow);
         valid = tt < ntgt && i < nd;
@@ -83,24 +83,24 @@ struct ListPolicy {
         return toff ? toff[s] : a.tseq[t];
     }
     __device__ void fetch(int c) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
+        const int r = tcp::arow() & 63;
         const bool ok = r < a.nrhs;
-        const int fa = c * KCC + h * 8;
+        const int fa = c * KCC + 4 * tcp::aq();
         int s = fa / ns, j = fa - s * ns;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < 4; ++v) {
             ya[v] = (ok && s < nsrc) ? a.in[(long long)src[s] * a.in_stride + (long long)j * a.nrhs + r]
                                      : make_float2(0.f, 0.f);
             if (++j == ns) { j = 0; ++s; }
         }
-        const int f0 = c * KCC;
+        const int f0 = c * KCC + 8 * tcp::bhalf();
         s = f0 / ns;
         j = f0 - s * ns;
         vmask = 0;
         int cs = -1, e = 0;
         long long off = 0;
 #pragma unroll
-        for (int v = 0; v < 16; ++v) {
+        for (int v = 0; v < 8; ++v) {
             if (valid && s < nsrc && s != self_t) {
                 if (s != cs) {
                     cs = s;
@@ -116,22 +116,21 @@ struct ListPolicy {
         }
     }
     __device__ void build(const Stage& st) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+        for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        for (int u = 0; u < 4; ++u) {
             float2 z[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-                const int q = 2 * kk + v;
+                const int q = 2 * u + v;
                 z[v] = make_float2(0.f, 0.f);
                 if ((vmask >> q) & 1u) {
                     const float f = pow2f(ex[q] + ad_i);
                     z[v] = make_float2(mv[q].x * f, mv[q].y * f);
                 }
             }
-            tcp::put_b(st, threadIdx.x, kk, z[0], z[1]);
+            tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, z[0], z[1]);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {

@@ -48,48 +48,47 @@ struct S2LPolicy {
     int M, nc, NSp, nrhs, b, j0, accumulate, conj;
     int j, m, n, a;
     bool valid;
-    // one fetched chunk
-    float2 ya[8];
-    float4 e4[8], q4[8];
-    int2 qe2[8];
+    // one fetched chunk (this thread's share)
+    float2 ya[4];
+    float4 e4[4], q4[4];
+    int2 qe2[4];
 
     __device__ void init() {
-        j = j0 + threadIdx.x;
+        j = j0 + tcp::brow();
         valid = j < M * nc;
         m = valid ? j / nc : 0;
         n = valid ? j - m * nc : 0;
         a = valid ? expo[((size_t)m * 2 + b) * nc + n] : 0;
     }
     __device__ void fetch(int c) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
-        const int qa = c * KCC + h * 8;
+        const int r = tcp::arow() & 63;
+        const int qa = c * KCC + 4 * tcp::aq();
 #pragma unroll
-        for (int v = 0; v < 8; ++v) ya[v] = r < nrhs ? D[(size_t)(qa + v) * nrhs + r] : make_float2(0.f, 0.f);
+        for (int v = 0; v < 4; ++v) ya[v] = r < nrhs ? D[(size_t)(qa + v) * nrhs + r] : make_float2(0.f, 0.f);
         if (valid) {
-            const int q0 = c * KCC;
+            const int q0 = c * KCC + 8 * tcp::bhalf();
             const float4* er = reinterpret_cast<const float4*>(E + (size_t)m * NSp + q0);
             const float4* qr = reinterpret_cast<const float4*>(Qm + (size_t)n * NSp + q0);
             const int2* xr = reinterpret_cast<const int2*>(Qe + (size_t)n * NSp + q0);
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                e4[kk] = er[kk];
-                q4[kk] = qr[kk];
-                qe2[kk] = xr[kk];
+            for (int u = 0; u < 4; ++u) {
+                e4[u] = er[u];
+                q4[u] = qr[u];
+                qe2[u] = xr[u];
             }
         }
     }
     __device__ void build(const Stage& st) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+        for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        for (int u = 0; u < 4; ++u) {
             float2 g0 = make_float2(0.f, 0.f), g1 = g0;
             if (valid) {
-                g0 = gen_entry(make_float2(e4[kk].x, e4[kk].y), make_float2(q4[kk].x, q4[kk].y), qe2[kk].x + a, conj);
-                g1 = gen_entry(make_float2(e4[kk].z, e4[kk].w), make_float2(q4[kk].z, q4[kk].w), qe2[kk].y + a, conj);
+                g0 = gen_entry(make_float2(e4[u].x, e4[u].y), make_float2(q4[u].x, q4[u].y), qe2[u].x + a, conj);
+                g1 = gen_entry(make_float2(e4[u].z, e4[u].w), make_float2(q4[u].z, q4[u].w), qe2[u].y + a, conj);
             }
-            tcp::put_b(st, threadIdx.x, kk, g0, g1);
+            tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, g0, g1);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
@@ -121,61 +120,66 @@ k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float
 struct M2SPolicy {
     const float2* xs;      // [M][2][nc][nrhs]
     const float2* E;       // [M][NSp] this wave
-    const float2* Qm;      // [NS][nc] this wave
+    const float2* Qm;      // [nc][NSp] this wave (node-contiguous: neighbouring threads, neighbouring nodes)
     const int* Qe;
     const int* expo;
     double2* part;         // [nsplit][2][NS][nrhs]
     int M, nc, NS, NSp, nrhs, b, q0, i0, i1, split, conj;
     int q;
     bool valid;
-    // one fetched chunk
-    float2 ya[8];
-    float2 ee[16], qm[16];
-    int ex[16];
+    // one fetched chunk (this thread's share)
+    float2 ya[4];
+    float2 ee[8], qm[8];
+    int ex[8];
     unsigned vmask;
 
     __device__ void init() {
-        q = q0 + threadIdx.x;
+        q = q0 + tcp::brow();
         valid = q < NS;
     }
     __device__ void fetch(int c) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7, r = rp & 63;
+        const int r = tcp::arow() & 63;
         const bool ok = r < nrhs;
-        const int ia = i0 + c * KCC + h * 8;
+        const int ia = i0 + c * KCC + 4 * tcp::aq();
         int l = ia / nc, n = ia - l * nc;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < 4; ++v) {
             ya[v] = (ok && ia + v < i1) ? xs[(((size_t)l * 2 + b) * nc + n) * nrhs + r] : make_float2(0.f, 0.f);
             if (++n == nc) { n = 0; ++l; }
         }
-        const int ib = i0 + c * KCC;
+        const int ib = i0 + c * KCC + 8 * tcp::bhalf();
         l = ib / nc;
         n = ib - l * nc;
         vmask = 0;
+        int lc = -1;                 // the particle whose E is held (uniform across the CTA)
+        float2 ec = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int v = 0; v < 16; ++v) {
+        for (int v = 0; v < 8; ++v) {
             if (valid && ib + v < i1) {
                 vmask |= 1u << v;
-                ee[v] = E[(size_t)l * NSp + q];
-                qm[v] = Qm[(size_t)q * nc + n];
-                ex[v] = Qe[(size_t)q * nc + n] + expo[((size_t)l * 2 + b) * nc + n];
+                if (l != lc) {
+                    lc = l;
+                    ec = E[(size_t)l * NSp + q];
+                }
+                ee[v] = ec;
+                qm[v] = Qm[(size_t)n * NSp + q];
+                ex[v] = Qe[(size_t)n * NSp + q] + expo[((size_t)l * 2 + b) * nc + n];
             }
             if (++n == nc) { n = 0; ++l; }
         }
     }
     __device__ void build(const Stage& st) {
-        const int rp = threadIdx.x & 127, h = threadIdx.x >> 7;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) tcp::put_a(st, rp, h * 4 + u, ya[2 * u], ya[2 * u + 1]);
+        for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        for (int u = 0; u < 4; ++u) {
             float2 g[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-                const int e = 2 * kk + v;
+                const int e = 2 * u + v;
                 g[v] = (vmask >> e) & 1u ? gen_entry(ee[e], qm[e], ex[e], conj) : make_float2(0.f, 0.f);
             }
-            tcp::put_b(st, threadIdx.x, kk, g[0], g[1]);
+            tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, g[0], g[1]);
         }
     }
     __device__ void epilogue(uint32_t tmem, bool ok) {
@@ -195,7 +199,7 @@ k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const floa
          int NSp, int nrhs, int rows_per_split, int conj, int* err) {
     const int b = blockIdx.z, split = blockIdx.y;
     const int i0 = split * rows_per_split, i1 = min(M * nc, i0 + rows_per_split);
-    M2SPolicy pol{xs, E + (size_t)b * M * NSp, Qm + (size_t)b * NS * nc, Qe + (size_t)b * NS * nc, expo, part,
+    M2SPolicy pol{xs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp, Qe + (size_t)b * nc * NSp, expo, part,
                   M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
     pol.init();
     const int nchunks = i1 > i0 ? (i1 - i0 + KCC - 1) / KCC : 0;
@@ -315,8 +319,8 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
     nsplit = (rows + per - 1) / per;
     *nchunks = nsplit;
     const MsDeviceTables& d = h->d;
-    k_m2s_tc<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qps_m : d.qpm_m,
-                                                             adj ? d.qps_e : d.qpm_e, d.expo, (double2*)h->ws_part, M,
+    k_m2s_tc<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qpsT_m : d.qpmT_m,
+                                                             adj ? d.qpsT_e : d.qpmT_e, d.expo, (double2*)h->ws_part, M,
                                                              nc, NS, NSp, nrhs, per, adj, d.tc_err);
     return ms_check(h, cudaGetLastError());
 }

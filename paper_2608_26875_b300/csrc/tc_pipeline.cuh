@@ -9,7 +9,7 @@
 //   B[j][2k]    = Re Z(j, kappa),  B[j][2k+1]    =  Im Z(j, kappa)
 // gives C[r][j] = Re sum_kappa Z(j, kappa) Y(kappa, r) and C[64+r][j] = Im of the same.
 // A (the data, M = 128 rows = 2 x 64 columns) and B (the generated operator, N <= 256 rows) are
-// written into shared memory by the CTA's 256 threads one K chunk (16 complex) at a time, in a
+// written into shared memory by the CTA's 512 threads one K chunk (16 complex) at a time, in a
 // two-stage pipeline; one thread issues the MMAs and commits them to the stage's mbarrier, which the
 // threads wait on (time-bounded) before reusing the stage.
 #pragma once
@@ -21,7 +21,7 @@ constexpr int KC = 32;                         // real K per chunk (16 complex)
 constexpr int KCC = KC / 2;
 constexpr int NMAX = 256;                      // MMA N: generated-operator rows per tile (max)
 constexpr int MA = 128;                        // MMA M: 2 x 64 right-hand-side columns
-constexpr int THREADS = 256;
+constexpr int THREADS = 512;                   // 16 warps: two per B row, four per A row
 constexpr int NSTAGE = 2;
 constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
 constexpr uint32_t B_TILE = NMAX * KC * 4;     // 32 KB
@@ -61,6 +61,14 @@ __device__ __forceinline__ void put_a(const Stage& st, int rp, int kk, float2 y0
 __device__ __forceinline__ void put_b(const Stage& st, int j, int kk, float2 z0, float2 z1) {
     put4(st.bh, st.bl, tc::kmajor_off(j, 4 * kk, KC), z0.x, z0.y, z1.x, z1.y);
 }
+
+// Thread roles in building a chunk: B row brow() (one of 256) and its half bhalf() of the 16
+// complex K entries (k-groups 4 bhalf() .. 4 bhalf() + 3); A row arow() (one of 128) and its
+// quarter aq() of the entries (k-groups 2 aq(), 2 aq() + 1).
+__device__ __forceinline__ int brow() { return threadIdx.x & 255; }
+__device__ __forceinline__ int bhalf() { return threadIdx.x >> 8; }
+__device__ __forceinline__ int arow() { return threadIdx.x & 127; }
+__device__ __forceinline__ int aq() { return threadIdx.x >> 7; }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -128,16 +136,16 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     if (tid < 32) tc::tmem_free(tmem, TMEM_COLS);
 }
 
-// Epilogue helper: warp w reads accumulator rows 32 (w & 3) + lane (the A rows rp) and the columns
-// of its half; f(rp, col, value) is called for every column < n.
+// Epilogue helper: warp w reads accumulator rows 32 (w & 3) + lane (the A rows rp) and the 64
+// columns of its block w >> 2; f(rp, col, value) is called for every column < n.
 template <class F>
 __device__ __forceinline__ void for_each_acc(uint32_t tmem, int n, F&& f) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter = w & 3, half = w >> 2;
+    const int quarter = w & 3, blk = w >> 2;
     const int rp = 32 * quarter + lane;
 #pragma unroll 1
-    for (int cb = 0; cb < 8; ++cb) {
-        const int col0 = 128 * half + 16 * cb;
+    for (int cb = 0; cb < 4; ++cb) {
+        const int col0 = 64 * blk + 16 * cb;
         if (col0 >= n) break;                          // uniform per warp
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
