@@ -170,6 +170,7 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
 int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int adj, int accumulate,
                      cudaStream_t st);
 int ms_spectral_tc_status(ms_handle* h, cudaStream_t st);
+bool ms_s2l_tc_ok(const ms_handle* h);
 int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cudaStream_t st);
 int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* lexp, int nrhs, cudaStream_t st);
 int ms_m2l_tc_tiles(ms_handle* h, int b, int lev, const std::vector<int>& ptr);

@@ -511,7 +511,7 @@ int ms_local_scaled(ms_handle* h, const void* xs_, int nrhs, int parts, cudaStre
         }
         if (int rc = ms_reflect_launch(h, (const double2*)h->ws_part, chunks, (double2*)h->ws_u, nrhs, adj, st))
             return rc;
-        if (tcore) {
+        if (tcore && ms_s2l_tc_ok(h)) {
             if (int rc = ms_s2l_tc_launch(h, (const double2*)h->ws_u, (float2*)as, nrhs, adj, have ? 1 : 0, st))
                 return rc;
         } else if (int rc = ms_s2l_launch<T>(h, (const double2*)h->ws_u, as, nrhs, h->d.expo, adj, have ? 1 : 0, st)) {

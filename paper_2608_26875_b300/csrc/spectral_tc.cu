@@ -38,7 +38,20 @@ __device__ __forceinline__ float2 gen_entry(float2 e, float2 qm, int ex, int con
 
 // ------------------------------------------------------------------ S2L-shaped launch
 // out_b[(m,n), r] (+)= sum_q Z(q, m, n) D_b(q, r);  tile = 256 consecutive rows j = m nc + n.
+// The K chunk's distinct operator data -- E of the tile's particles and Q of every order, for the
+// chunk's 16 nodes -- are fetched cooperatively (one or two 16-byte loads per thread) and staged in
+// shared memory: rows of E (16 nodes), Q mantissas (padded to 18 nodes) and Q exponents (padded to
+// 20), so that a warp's 16-byte reads of neighbouring orders spread over the banks.
+constexpr int QS_STRIDE = 18;   // float2 per staged Q row
+constexpr int QE_STRIDE = 20;   // int per staged exponent row
+
+__host__ __device__ inline int s2l_parts_per_tile(int nc) { return (tcp::NMAX + nc - 1) / nc + 1; }
+__host__ __device__ inline size_t s2l_raw_bytes(int nc) {
+    return (size_t)s2l_parts_per_tile(nc) * 16 * 8 + (size_t)nc * QS_STRIDE * 8 + (size_t)nc * QE_STRIDE * 4;
+}
+
 struct S2LPolicy {
+    static constexpr bool kStaged = true;
     const float2* D;       // [NSp][nrhs] this wave (zero beyond NS)
     const float2* E;       // [M][NSp] this wave
     const float2* Qm;      // [nc][NSp] this wave
@@ -46,12 +59,11 @@ struct S2LPolicy {
     const int* expo;       // [M][2][nc]
     float2* out;           // [M][2][nc][nrhs]
     int M, nc, NSp, nrhs, b, j0, accumulate, conj;
-    int j, m, n, a;
+    int j, m, n, a, m0, npt, nitems;
     bool valid;
-    // one fetched chunk (this thread's share)
+    // one fetched chunk: this thread's data rows and its share of the staged items
     float2 ya[4];
-    float4 e4[4], q4[4];
-    int2 qe2[4];
+    float4 it[2];
 
     __device__ void init() {
         j = j0 + tcp::brow();
@@ -59,38 +71,88 @@ struct S2LPolicy {
         m = valid ? j / nc : 0;
         n = valid ? j - m * nc : 0;
         a = valid ? expo[((size_t)m * 2 + b) * nc + n] : 0;
+        m0 = j0 / nc;
+        npt = s2l_parts_per_tile(nc);
+        nitems = npt * 8 + nc * 8 + nc * 4;
+    }
+    // staged item e: E (npt x 8 float4), then Q mantissas (nc x 8 float4), then exponents (nc x 4 int4)
+    __device__ float4 load_item(int e, int q0) const {
+        if (e < npt * 8) {
+            const int mi = e >> 3, part = e & 7;
+            if (m0 + mi >= M) return make_float4(0.f, 0.f, 0.f, 0.f);
+            return *reinterpret_cast<const float4*>(E + (size_t)(m0 + mi) * NSp + q0 + 2 * part);
+        }
+        e -= npt * 8;
+        if (e < nc * 8) return *reinterpret_cast<const float4*>(Qm + (size_t)(e >> 3) * NSp + q0 + 2 * (e & 7));
+        e -= nc * 8;
+        const int4 v = *reinterpret_cast<const int4*>(Qe + (size_t)(e >> 2) * NSp + q0 + 4 * (e & 3));
+        return make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
+    }
+    __device__ void store_item(unsigned char* raw, int e, float4 v) const {
+        float2* Es = reinterpret_cast<float2*>(raw);
+        float2* Qs = Es + npt * 16;
+        int* Qx = reinterpret_cast<int*>(Qs + nc * QS_STRIDE);
+        if (e < npt * 8) {
+            *reinterpret_cast<float4*>(Es + (e >> 3) * 16 + 2 * (e & 7)) = v;
+            return;
+        }
+        e -= npt * 8;
+        if (e < nc * 8) {
+            *reinterpret_cast<float4*>(Qs + (e >> 3) * QS_STRIDE + 2 * (e & 7)) = v;
+            return;
+        }
+        e -= nc * 8;
+        *reinterpret_cast<float4*>(Qx + (e >> 2) * QE_STRIDE + 4 * (e & 3)) = v;
+    }
+    __device__ unsigned char* raw(int c) const {
+        return tcp::raw_base() + (size_t)(c & 1) * ((s2l_raw_bytes(nc) + 15) / 16 * 16);
     }
     __device__ void fetch(int c) {
         const int r = tcp::arow() & 63;
         const int qa = c * KCC + 4 * tcp::aq();
 #pragma unroll
         for (int v = 0; v < 4; ++v) ya[v] = r < nrhs ? D[(size_t)(qa + v) * nrhs + r] : make_float2(0.f, 0.f);
-        if (valid) {
-            const int q0 = c * KCC + 8 * tcp::bhalf();
-            const float4* er = reinterpret_cast<const float4*>(E + (size_t)m * NSp + q0);
-            const float4* qr = reinterpret_cast<const float4*>(Qm + (size_t)n * NSp + q0);
-            const int2* xr = reinterpret_cast<const int2*>(Qe + (size_t)n * NSp + q0);
+        const int q0 = c * KCC;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                e4[u] = er[u];
-                q4[u] = qr[u];
-                qe2[u] = xr[u];
-            }
+        for (int k = 0; k < 2; ++k) {
+            const int e = threadIdx.x + k * tcp::THREADS;
+            if (e < nitems) it[k] = load_item(e, q0);
         }
+    }
+    __device__ void stage(int c) {
+        unsigned char* rb = raw(c);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = threadIdx.x + k * tcp::THREADS;
+            if (e < nitems) store_item(rb, e, it[k]);
+        }
+        cur = rb;
     }
     __device__ void build(const Stage& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
+        // the chunk being built is the one staged last: its buffer is raw(c) with c from the stage call
+        const float2* Es = reinterpret_cast<const float2*>(cur);
+        const float2* Qs = Es + npt * 16;
+        const int* Qx = reinterpret_cast<const int*>(Qs + nc * QS_STRIDE);
+        const int h8 = 8 * tcp::bhalf();
+        const float4* er = reinterpret_cast<const float4*>(Es + (m - m0) * 16 + h8);
+        const float4* qr = reinterpret_cast<const float4*>(Qs + n * QS_STRIDE + h8);
+        const int4* xr = reinterpret_cast<const int4*>(Qx + n * QE_STRIDE + h8);
+        const int4 x0 = xr[0], x1 = xr[1];
+        const int xe[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 g0 = make_float2(0.f, 0.f), g1 = g0;
             if (valid) {
-                g0 = gen_entry(make_float2(e4[u].x, e4[u].y), make_float2(q4[u].x, q4[u].y), qe2[u].x + a, conj);
-                g1 = gen_entry(make_float2(e4[u].z, e4[u].w), make_float2(q4[u].z, q4[u].w), qe2[u].y + a, conj);
+                const float4 e4 = er[u], q4 = qr[u];
+                g0 = gen_entry(make_float2(e4.x, e4.y), make_float2(q4.x, q4.y), xe[2 * u] + a, conj);
+                g1 = gen_entry(make_float2(e4.z, e4.w), make_float2(q4.z, q4.w), xe[2 * u + 1] + a, conj);
             }
             tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, g0, g1);
         }
     }
+    unsigned char* cur = nullptr;   // raw buffer of the chunk last staged
     __device__ void epilogue(uint32_t tmem, bool ok) {
         if (!ok) return;
         tcp::for_each_acc(tmem, NT, [&](int rp, int col, float v) {
@@ -118,6 +180,7 @@ k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float
 // ------------------------------------------------------------------ M2S-shaped launch
 // part[split][b][q][r] = sum_{(l,n) in split's rows} Z(q, l, n) x~_b[(l,n), r];  tile = 256 nodes.
 struct M2SPolicy {
+    static constexpr bool kStaged = false;
     const float2* xs;      // [M][2][nc][nrhs]
     const float2* E;       // [M][NSp] this wave
     const float2* Qm;      // [nc][NSp] this wave (node-contiguous: neighbouring threads, neighbouring nodes)
@@ -334,10 +397,18 @@ int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int
     k_amp_f<<<nblk(2LL * NSp * nrhs, 256), 256, 0, st>>>(ud, uf, NS, NSp, nrhs);
     if (int rc = ms_check(h, cudaGetLastError())) return rc;
     const int ntile = (M * nc + NT - 1) / NT;
-    k_s2l_tc<<<dim3(ntile, 2), THREADS, SMEM, st>>>(uf, adj ? d.em2s : d.es2l, adj ? d.qpmT_m : d.qpsT_m,
+    const size_t smem = SMEM + 2 * ((s2l_raw_bytes(nc) + 15) / 16 * 16);
+    cudaFuncSetAttribute(k_s2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_s2l_tc<<<dim3(ntile, 2), THREADS, smem, st>>>(uf, adj ? d.em2s : d.es2l, adj ? d.qpmT_m : d.qpsT_m,
                                                      adj ? d.qpmT_e : d.qpsT_e, d.expo, out, M, nc, NSp, nrhs,
                                                      accumulate, adj, d.tc_err);
     return ms_check(h, cudaGetLastError());
+}
+
+// The staged Sommerfeld-to-local kernel fits in shared memory for p >= 1 (two raw buffers of E, Q rows).
+bool ms_s2l_tc_ok(const ms_handle* h) {
+    const int nitems = s2l_parts_per_tile(h->nc) * 8 + h->nc * 12;     // staged 16-byte items per chunk
+    return h->p >= 1 && nitems <= 2 * THREADS && SMEM + 2 * ((s2l_raw_bytes(h->nc) + 15) / 16 * 16) <= 227 * 1024;
 }
 
 // Reads and clears the tensor-core kernels' timeout flag (MS_ERR_TIMEOUT if a wait gave up).

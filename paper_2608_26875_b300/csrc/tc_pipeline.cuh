@@ -31,6 +31,13 @@ constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
 constexpr uint32_t TMEM_COLS = 256;
 static_assert(SMEM <= 227 * 1024, "shared memory");
 
+// Shared memory after the stages, the two mbarriers and the tensor-memory slot: raw buffers of
+// policies that stage chunk data (16-byte aligned).
+__device__ __forceinline__ unsigned char* raw_base() {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    return smem + (size_t)NSTAGE * (2 * MA * KC * 4 + 2 * NMAX * KC * 4) + 64;
+}
+
 struct Stage {
     float *ah, *al, *bh, *bl;
 };
@@ -77,7 +84,9 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // P provides fetch(chunk) (issue the global loads of one K chunk into registers), build(Stage)
 // (write the A and B tiles of the fetched chunk) and epilogue(tmem, ok); n is the MMA N of this
 // tile (a multiple of 16 in [16, 256]).  The loads of chunk c + 1 are issued right after chunk c is
-// built, so their latency overlaps the MMAs in flight.  Sets *err on a timed-out wait.
+// built, so their latency overlaps the MMAs in flight.  A policy with kStaged = true also has
+// stage(chunk): it stores the cooperatively fetched data of the chunk into a shared-memory raw
+// buffer (two, alternating) that build() then reads after a barrier.  Sets *err on a timed-out wait.
 template <class P>
 __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -102,6 +111,10 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
         const int s = c % NSTAGE;
         if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
         const Stage st = stage_ptrs(smem, s);
+        if constexpr (P::kStaged) {
+            pol.stage(c);
+            __syncthreads();
+        }
         pol.build(st);
         if (c + 1 < nchunks) pol.fetch(c + 1);
         tc::fence_proxy_async();
