@@ -48,6 +48,7 @@ struct ListArgs {
 constexpr int MAX_TABLE = 64;    // task offsets staged per single-target tile (M2L lists <= 27)
 
 struct ListPolicy {
+    static constexpr bool kStaged = false;
     const ListArgs& a;
     const int* tgt;
     const int* self;
