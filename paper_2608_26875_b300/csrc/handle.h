@@ -103,6 +103,8 @@ struct MsDeviceTables {
     int* qpmT_e = nullptr;
     float2* qpsT_m = nullptr;      // [2][nc][NSp] mantissa / exponent of i^n q^n W_q
     int* qpsT_e = nullptr;
+    float2* rho_m2s = nullptr;     // [2][NSp] -i q_b(xi_q): ratio of consecutive M2S powers
+    float2* rho_s2l = nullptr;     // [2][NSp]  i q_b(xi_q): ratio of consecutive S2L powers
     int* tc_err = nullptr;         // set by a tensor-core kernel whose pipeline wait gave up
 };
 

@@ -179,26 +179,33 @@ k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float
 
 // ------------------------------------------------------------------ M2S-shaped launch
 // part[split][b][q][r] = sum_{(l,n) in split's rows} Z(q, l, n) x~_b[(l,n), r];  tile = 256 nodes.
+// Along the orders of one particle the entries obey Z(q, l, n+1) = Z(q, l, n) rho_q 2^{a(l,n+1) - a(l,n)}
+// with rho_q = -i q (multipole-to-Sommerfeld powers) or i q (the Sommerfeld-to-local ones of the
+// adjoint): a thread reads the power table once per particle segment of its 8 entries and steps the
+// rest by one complex multiply and an exact power-of-two scale (relative error ~1e-6 after 7 steps).
 struct M2SPolicy {
     static constexpr bool kStaged = false;
     const float2* xs;      // [M][2][nc][nrhs]
     const float2* E;       // [M][NSp] this wave
     const float2* Qm;      // [nc][NSp] this wave (node-contiguous: neighbouring threads, neighbouring nodes)
     const int* Qe;
+    const float2* rho;     // [NSp] this wave: ratio of consecutive powers
     const int* expo;
     double2* part;         // [nsplit][2][NS][nrhs]
     int M, nc, NS, NSp, nrhs, b, q0, i0, i1, split, conj;
     int q;
     bool valid;
+    float2 rq;
     // one fetched chunk (this thread's share)
     float2 ya[4];
     float2 ee[8], qm[8];
-    int ex[8];
-    unsigned vmask;
+    int qe[8], ax[8];
+    unsigned vmask, smask;     // entries present; entries that start a particle segment
 
     __device__ void init() {
         q = q0 + tcp::brow();
         valid = q < NS;
+        rq = valid ? rho[q] : make_float2(0.f, 0.f);
     }
     __device__ void fetch(int c) {
         const int r = tcp::arow() & 63;
@@ -213,20 +220,18 @@ struct M2SPolicy {
         const int ib = i0 + c * KCC + 8 * tcp::bhalf();
         l = ib / nc;
         n = ib - l * nc;
-        vmask = 0;
-        int lc = -1;                 // the particle whose E is held (uniform across the CTA)
-        float2 ec = make_float2(0.f, 0.f);
+        vmask = smask = 0;
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             if (valid && ib + v < i1) {
                 vmask |= 1u << v;
-                if (l != lc) {
-                    lc = l;
-                    ec = E[(size_t)l * NSp + q];
+                ax[v] = expo[((size_t)l * 2 + b) * nc + n];
+                if (v == 0 || n == 0) {
+                    smask |= 1u << v;
+                    ee[v] = E[(size_t)l * NSp + q];
+                    qm[v] = Qm[(size_t)n * NSp + q];
+                    qe[v] = Qe[(size_t)n * NSp + q];
                 }
-                ee[v] = ec;
-                qm[v] = Qm[(size_t)n * NSp + q];
-                ex[v] = Qe[(size_t)n * NSp + q] + expo[((size_t)l * 2 + b) * nc + n];
             }
             if (++n == nc) { n = 0; ++l; }
         }
@@ -234,13 +239,26 @@ struct M2SPolicy {
     __device__ void build(const Stage& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
+        float2 w = make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 g[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 const int e = 2 * u + v;
-                g[v] = (vmask >> e) & 1u ? gen_entry(ee[e], qm[e], ex[e], conj) : make_float2(0.f, 0.f);
+                g[v] = make_float2(0.f, 0.f);
+                if ((vmask >> e) & 1u) {
+                    if ((smask >> e) & 1u) {
+                        const float2 t = tcp::cmulf(ee[e], qm[e]);
+                        const float f = pow2f(qe[e] + ax[e]);
+                        w = make_float2(t.x * f, t.y * f);
+                    } else {
+                        const float2 t = tcp::cmulf(w, rq);
+                        const float f = pow2f(ax[e] - ax[e > 0 ? e - 1 : 0]);
+                        w = make_float2(t.x * f, t.y * f);
+                    }
+                    g[v] = conj ? make_float2(w.x, -w.y) : w;
+                }
             }
             tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, g[0], g[1]);
         }
@@ -258,12 +276,13 @@ struct M2SPolicy {
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const float2* __restrict__ Qm,
-         const int* __restrict__ Qe, const int* __restrict__ expo, double2* __restrict__ part, int M, int nc, int NS,
-         int NSp, int nrhs, int rows_per_split, int conj, int* err) {
+         const int* __restrict__ Qe, const float2* __restrict__ rho, const int* __restrict__ expo,
+         double2* __restrict__ part, int M, int nc, int NS, int NSp, int nrhs, int rows_per_split, int conj,
+         int* err) {
     const int b = blockIdx.z, split = blockIdx.y;
     const int i0 = split * rows_per_split, i1 = min(M * nc, i0 + rows_per_split);
-    M2SPolicy pol{xs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp, Qe + (size_t)b * nc * NSp, expo, part,
-                  M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
+    M2SPolicy pol{xs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp, Qe + (size_t)b * nc * NSp,
+                  rho + (size_t)b * NSp, expo, part, M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
     pol.init();
     const int nchunks = i1 > i0 ? (i1 - i0 + KCC - 1) / KCC : 0;
     tcp::run(pol, nchunks, NT, err);
@@ -343,6 +362,22 @@ int ms_spectral_tc_setup(ms_handle* h) {
                 tme[dst] = em[src];
                 tse[dst] = es[src];
             }
+    // ratios of consecutive powers per (wave, node): -i q (M2S table) and i q (S2L table)
+    std::vector<double2> hq((size_t)NS * 2);
+    if (int rc = ms_check(h, cudaMemcpy(hq.data(), d.qq, hq.size() * sizeof(double2), cudaMemcpyDeviceToHost)))
+        return rc;
+    std::vector<float2> rm((size_t)2 * NSp, make_float2(0.f, 0.f)), rs((size_t)2 * NSp, make_float2(0.f, 0.f));
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < NS; ++q) {
+            const double2 v = hq[(size_t)q * 2 + b];
+            rm[(size_t)b * NSp + q] = make_float2((float)v.y, (float)-v.x);
+            rs[(size_t)b * NSp + q] = make_float2((float)-v.y, (float)v.x);
+        }
+    if (cudaMalloc(&d.rho_m2s, rm.size() * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&d.rho_s2l, rs.size() * sizeof(float2)) != cudaSuccess)
+        return MS_ERR_ALLOC;
+    cudaMemcpy(d.rho_m2s, rm.data(), rm.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d.rho_s2l, rs.data(), rs.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (cudaMalloc(&d.qpmT_m, nt * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&d.qpsT_m, nt * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&d.qpmT_e, nt * sizeof(int)) != cudaSuccess || cudaMalloc(&d.qpsT_e, nt * sizeof(int)) != cudaSuccess ||
@@ -367,6 +402,9 @@ void ms_spectral_tc_free(ms_handle* h) {
     cudaFree(d.qpmT_e);
     cudaFree(d.qpsT_e);
     cudaFree(d.tc_err);
+    cudaFree(d.rho_m2s);
+    cudaFree(d.rho_s2l);
+    d.rho_m2s = d.rho_s2l = nullptr;
     d.es2l = d.em2s = d.qpmT_m = d.qpsT_m = nullptr;
     d.qpmT_e = d.qpsT_e = d.tc_err = nullptr;
 }
@@ -383,8 +421,9 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
     *nchunks = nsplit;
     const MsDeviceTables& d = h->d;
     k_m2s_tc<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qpsT_m : d.qpmT_m,
-                                                             adj ? d.qpsT_e : d.qpmT_e, d.expo, (double2*)h->ws_part, M,
-                                                             nc, NS, NSp, nrhs, per, adj, d.tc_err);
+                                                             adj ? d.qpsT_e : d.qpmT_e, adj ? d.rho_s2l : d.rho_m2s,
+                                                             d.expo, (double2*)h->ws_part, M, nc, NS, NSp, nrhs, per,
+                                                             adj, d.tc_err);
     return ms_check(h, cudaGetLastError());
 }
 
