@@ -2,19 +2,23 @@
 """Benchmark: 64-right-hand-side mat-vecs of the layered multiple-scattering operator.
 
 Workload: 10^4 particles (enclosing radius U[0.2, 0.5], packing fraction 0.2), omega = 6,
-expansion order p = 20, 512 Sommerfeld nodes, 64 right-hand sides (synthetic, seeded).  A step
-is one application y = x - S (T + R) x of the whole hot path (precision staging, free-space
-translation, multipole-to-Sommerfeld, reflection, Sommerfeld-to-local, scattering-matrix apply)
-to the 64-column block.  `value` is mat-vecs per second over all ranks with inputs resident in
-HBM; `e2e` repeats the step through the same C-ABI call with the block copied host->device and
-the result device->host inside the timed region.  Inputs (0.84 GB) exceed the 126 MB L2.
+expansion order p = 20, N_S = 4800 Sommerfeld nodes on the contour adapted to the cloud's width,
+64 right-hand sides (synthetic, seeded).  A step is one application y = x - S (T + R) x of the
+whole hot path (precision staging, near-pair translation, FMM far field, multipole-to-Sommerfeld,
+reflection, Sommerfeld-to-local, scattering-matrix apply) to the 64-column block, with the FP32
+operator on the tensor cores (--no-tensor-cores: CUDA cores).  `value` is mat-vecs per second over
+all ranks with inputs resident in HBM; `e2e` repeats the step through the same C-ABI call with the
+block copied host->device and the result device->host inside the timed region.  Inputs (0.84 GB)
+exceed the 126 MB L2.
 
 Multi-GPU: right-hand-side blocks are independent, so each rank applies the operator to its own
 64-column block with no collective (weak scaling, replicas of the geometry).
 
 --impl reference times the FP64 CPU oracle on this host on a bounded sample of the same
 mat-vec (a few target particles of the direct sum plus the full spectral part) and extrapolates
-to one full mat-vec.
+to one full mat-vec.  --mode solve times solves to 1e-8 (mixed, and FP64 with --full-fp64);
+--mode grad times gradient evaluations of the inverse-scattering workload; --profile runs a small
+case for ncu.
 """
 from __future__ import annotations
 
