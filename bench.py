@@ -310,7 +310,7 @@ def run_solve(args):
 
     import paper_2608_26875_b300 as P
     import synthetic as syn
-    wl = syn.config3(M=args.M, nrhs=args.nrhs) if args.M != 10000 else workload()
+    wl = syn.config3(M=args.M, nrhs=args.nrhs) if args.M not in (None, 10000) else workload()
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
                                restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol)
@@ -361,7 +361,7 @@ def run_grad(args):
 
     import paper_2608_26875_b300 as P
     import synthetic as syn
-    wl = syn.config4()
+    wl = syn.config4() if args.M in (None, 2000) else syn.config4(M=args.M)
     rx = wl.receivers
     truth = copy.deepcopy(wl)
     truth.centres = syn.perturb_centres(wl.centres, wl.radius, 0.05, 3001)
@@ -415,7 +415,7 @@ def run_profile(args):
 
     import paper_2608_26875_b300 as P
     import synthetic as syn
-    wl = syn.config3(M=args.M, nrhs=64)
+    wl = syn.config3(M=args.M or 2500, nrhs=64)
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
     s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores)
     x = torch.as_tensor(syn.random_coeffs(5, wl.M, wl.p, 64), device="cuda")
@@ -441,7 +441,8 @@ def main():
     ap.add_argument("--mode", choices=["matvec", "solve", "grad"], default="matvec")
     ap.add_argument("--full-fp64", action="store_true", help="solve mode: run the FP64 solve too")
     ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
-    ap.add_argument("--M", type=int, default=2500, help="particles of --profile (default 2500) or --mode solve")
+    ap.add_argument("--M", type=int, default=None, help="particles: --profile (default 2500), --mode solve "
+                    "(default 10000), --mode grad (default 2000, the inverse-scattering workload)")
     ap.add_argument("--nrhs", type=int, default=64, help="--mode solve: right-hand sides")
     ap.add_argument("--restart", type=int, default=50, help="--mode solve: GMRES restart length")
     ap.add_argument("--max-iters", type=int, default=2000, help="--mode solve/grad: GMRES iteration cap")

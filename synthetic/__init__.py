@@ -118,9 +118,9 @@ def place_particles(rng: np.random.Generator, M: int, box, rmin: float, rmax: fl
 
 def perturb_centres(centres: np.ndarray, radius: np.ndarray, sigma: float, seed: int,
                     max_rounds: int = 1000) -> np.ndarray:
-    """Centres moved by N(0, sigma^2) per coordinate; a particle whose move violates the separation
-    rule (or burial) against the already-moved configuration is re-drawn (the inverse-problem
-    truth of the gradient workload)."""
+    """Centres moved by N(0, sigma^2) per coordinate; both particles of a pair whose moves violate
+    the separation rule, and a particle whose move violates burial, are re-drawn until the moved
+    configuration is admissible (the inverse-problem truth of the gradient workload)."""
     rng = np.random.default_rng(seed)
     c = centres + rng.normal(0.0, sigma, centres.shape)
 
@@ -137,6 +137,7 @@ def perturb_centres(centres: np.ndarray, radius: np.ndarray, sigma: float, seed:
                 for iy in range(gy - 1, gy + 2):
                     for j in grid.get((ix, iy), ()):
                         if j > i and np.sum((c[i] - c[j]) ** 2) < (SEP * (radius[i] + radius[j])) ** 2:
+                            bad.add(i)
                             bad.add(j)
         return sorted(bad)
 
