@@ -393,6 +393,8 @@ def run_grad(args):
         out[name] = {"grads_per_s": len(times) / sum(times), "s_per_grad": sum(times) / len(times),
                      "forward": info, "adjoint": ginfo, "loss": loss,
                      "max_abs_dL_dcentre": float(gc.abs().max()), "dL_domega": gw}
+        # each precision's result as soon as it is known (a slow FP64 pass must not hide the mixed one)
+        print(json.dumps({"partial": name, **out[name]}), file=sys.stderr, flush=True)
     print(json.dumps(out), flush=True)
 
 
