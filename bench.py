@@ -231,7 +231,7 @@ def run_ours(args):
     tf32_peak = float(pk.get("bf16_tflops", 1800.0)) * 0.5             # dense TF32 = bf16 x 1.1/2.25 (nominal)
     tc = args.tensor_cores and prec == P.MS_PREC_FP32
     cand = [("near", t_near, flops_near,
-             "k_near_tc (tcgen05 kind::tf32, 3xTF32) near pairs" if tc else "k_translate<float> near pairs"),
+             "k_list_tc (tcgen05 kind::tf32, 3xTF32) near pairs" if tc else "k_translate<float> near pairs"),
             ("refl", t_refl, flops_refl,
              "k_m2s_tc + k_reflect + k_s2l_tc (tcgen05 kind::tf32, 3xTF32)" if tc else "k_m2s + k_reflect + k_s2l")]
     name, t_dom, flops_dom, kname = max(cand, key=lambda c: c[1])
