@@ -197,6 +197,56 @@ def test_interface_energy_balance(xi0, U):
     assert abs(fin + fr - ft) < 1e-13 * fin
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_normal_incidence_matches_impedance_formulas(kind):
+    """Background field of the right-hand side at normal incidence: a plane P (S) wave from the
+    upper layer reflects and transmits with the one-dimensional displacement coefficients
+    R = (Z_u - Z_l)/(Z_u + Z_l), T = 2 Z_u/(Z_u + Z_l), Z = rho c = sqrt(lam + 2 mu) (sqrt(mu)) at
+    rho = 1, and converts into no wave of the other type."""
+    L = L_STD
+    xi, D, E, I = sommerfeld.plane_wave_incidence(kind, math.pi / 2, L)
+    assert abs(xi) < 1e-15
+    if kind == 0:
+        zu, zl = math.sqrt(L.lam_u + 2 * L.mu_u), math.sqrt(L.lam_l + 2 * L.mu_l)
+        ku, kl = L.kp_u, L.kp_l
+        # y-displacements at y = 0: incident -1, reflected i ku E_P, transmitted -i kl D_P
+        inc, refl, trans = -1.0, 1j * ku * E[0], -1j * kl * D[0]
+        other = (D[1], E[1])
+    else:
+        zu, zl = math.sqrt(L.mu_u), math.sqrt(L.mu_l)
+        ku, kl = L.ks_u, L.ks_l
+        # x-displacements at y = 0: incident 1, reflected -i ku E_S, transmitted i kl D_S
+        inc, refl, trans = 1.0, -1j * ku * E[1], 1j * kl * D[1]
+        other = (D[0], E[0])
+    assert abs(refl / inc - (zu - zl) / (zu + zl)) < 1e-14
+    assert abs(trans / inc - 2 * zu / (zu + zl)) < 1e-14
+    assert max(abs(o) for o in other) < 1e-15
+
+
+@pytest.mark.parametrize("kind,deg", [(0, 60.0), (0, 80.0), (1, 75.0), (1, 85.0)])
+def test_incidence_from_above_energy_balance(kind, deg):
+    """Oblique plane wave from the upper layer, angles at which all four scattered waves
+    propagate: the downward energy flux of the incident wave equals the upward flux of the
+    reflected P and S waves plus the downward flux of the transmitted ones (mode conversion
+    included)."""
+    L = L_STD
+    xi, D, E, I = sommerfeld.plane_wave_incidence(kind, math.radians(deg), L)
+    assert abs(xi) < min(L.kp_u, L.ks_u, L.kp_l, L.ks_l)
+
+    def flux(k, d, lam, mu, amp):
+        u = amp * sommerfeld._pw(k, xi, d)
+        return np.imag(np.vdot(u, sommerfeld._traction_y(u, xi, d, lam, mu)))
+
+    sp, ss = sommerfeld.branch_s(xi, L.kp_l), sommerfeld.branch_s(xi, L.ks_l)
+    spu, ssu = sommerfeld.branch_s(xi, L.kp_u), sommerfeld.branch_s(xi, L.ks_u)
+    f_inc = flux("P", spu, L.lam_u, L.mu_u, I[0]) + flux("S", ssu, L.lam_u, L.mu_u, I[1])
+    f_ref = flux("P", -spu, L.lam_u, L.mu_u, E[0]) + flux("S", -ssu, L.lam_u, L.mu_u, E[1])
+    f_tr = flux("P", sp, L.lam_l, L.mu_l, D[0]) + flux("S", ss, L.lam_l, L.mu_l, D[1])
+    assert f_inc < 0 and f_ref >= 0 and f_tr < 0
+    assert abs(E[1 - kind]) > 1e-3 and abs(D[1 - kind]) > 1e-3      # oblique: both wave types appear
+    assert abs(f_inc + f_ref - f_tr) < 1e-13 * abs(f_inc)
+
+
 @pytest.fixture(scope="module")
 def solved_small():
     wl = syn.small_case(11, 3, 14, omega=2.0, nrhs=2)
