@@ -36,6 +36,9 @@ def gather_columns(local: torch.Tensor, n: int, dim: int = -1) -> torch.Tensor:
     world = dist.get_world_size()
     sizes = [len(rhs_shard(n, r, world)) for r in range(world)]
     dim = dim % local.dim()
+    if local.shape[dim] != sizes[dist.get_rank()]:
+        raise ValueError(f"rank {dist.get_rank()} holds {local.shape[dim]} columns, its shard of {n} has "
+                         f"{sizes[dist.get_rank()]}")
     # all_gather wants equal shapes: pad every shard to the largest, then trim
     big = max(sizes)
     shape = list(local.shape)
