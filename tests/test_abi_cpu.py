@@ -114,3 +114,64 @@ def test_perturbed_truth_keeps_the_separation_rule():
     np.fill_diagonal(d, np.inf)
     assert np.all(d >= lim)
     assert np.all(c[:, 1] + syn.SEP * wl.radius <= 0.0)
+
+
+def _raw_setup(lib, case):
+    """ms_setup through ctypes with one field of config1's arguments made invalid; returns
+    (status, handle pointer value)."""
+    from paper_2608_26875_b300 import _native as nat
+    wl = syn.config1()
+    c = np.ascontiguousarray(wl.centres, dtype=np.float64)
+    r = np.ascontiguousarray(wl.radius, dtype=np.float64)
+    bc = np.ascontiguousarray(wl.bc, dtype=np.int32)
+    proto = np.full(wl.M, -1, dtype=np.int32)
+    g = nat.Geometry()
+    g.M = wl.M
+    g.centres, g.radius, g.bc = c.ctypes.data_as(nat.c_dp), r.ctypes.data_as(nat.c_dp), bc.ctypes.data_as(nat.c_ip)
+    md = nat.Media(wl.media.lam_u, wl.media.mu_u, wl.media.lam_l, wl.media.mu_l)
+    o = nat.Options()
+    lib.ms_default_options(ctypes.byref(o))
+    omega, p = wl.omega, wl.p
+    field, _, value = case.partition("=")
+    if field in ("tensor_cores", "leaf_target", "restart", "max_iters", "n_panels", "nodes_per_panel", "grade"):
+        setattr(o, field, int(value))
+    elif field in ("inner_tol", "t_max", "depth"):
+        setattr(o, field, float(value))
+    elif field in ("mu_u", "mu_l", "lam_l"):
+        setattr(md, field, float(value))
+    elif field == "M":
+        g.M = int(value)
+    elif field == "centre":
+        c[4, 0] = float(value)
+    elif field == "proto":
+        proto[5] = int(value)                  # an index with no prototype table behind it
+        g.proto = proto.ctypes.data_as(nat.c_ip)
+    elif field == "n_proto":
+        g.n_proto = int(value)                 # tables announced, none passed
+    elif field == "p":
+        p = int(value)
+    else:
+        raise AssertionError(case)
+    h = ctypes.c_void_p(12345)
+    st = lib.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o), ctypes.byref(h))
+    return st, h.value
+
+
+@pytest.mark.parametrize("case", [
+    "tensor_cores=2", "tensor_cores=-1", "inner_tol=1.0", "inner_tol=-0.001", "inner_tol=nan",
+    "leaf_target=0", "restart=0", "max_iters=0", "n_panels=0", "nodes_per_panel=0", "t_max=0",
+    "depth=0", "depth=nan", "grade=-1", "grade=31", "mu_u=0", "mu_l=-1", "lam_l=-1.5", "M=0",
+    "centre=nan", "centre=inf", "proto=0", "proto=-2", "n_proto=2", "p=-1"])
+def test_invalid_options_and_media_are_refused_before_device_work(lib, case):
+    """Every ms_options field, the media and the geometry arrays are checked on the host: an
+    invalid value returns MS_ERR_ARG and leaves the handle NULL (the call never reaches CUDA, so
+    this runs without a device)."""
+    from paper_2608_26875_b300 import _native as nat
+    st, h = _raw_setup(lib, case)
+    assert st == nat.MS_ERR_ARG, (case, st)
+    assert h is None
+
+
+def test_setup_refuses_a_null_handle_slot(lib):
+    from paper_2608_26875_b300 import _native as nat
+    assert lib.ms_setup(None, None, 1.0, 4, None, None) == nat.MS_ERR_ARG
