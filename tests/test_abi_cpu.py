@@ -175,3 +175,39 @@ def test_invalid_options_and_media_are_refused_before_device_work(lib, case):
 def test_setup_refuses_a_null_handle_slot(lib):
     from paper_2608_26875_b300 import _native as nat
     assert lib.ms_setup(None, None, 1.0, 4, None, None) == nat.MS_ERR_ARG
+
+
+def test_every_handle_call_refuses_a_null_handle(lib):
+    """Each entry point that takes a handle answers MS_ERR_ARG to a NULL one (all other pointers
+    NULL, sizes 1) without touching memory; ms_destroy(NULL) is a no-op and ms_last_cuda_error(NULL)
+    is 0."""
+    from paper_2608_26875_b300 import _native as nat
+    skip = {"ms_default_options", "ms_setup", "ms_status_string", "ms_destroy", "ms_last_cuda_error"}
+    checked = 0
+    for name, (restype, argtypes) in nat.SIGNATURES.items():
+        if name in skip:
+            continue
+        assert argtypes[0] is ctypes.c_void_p, name          # the handle comes first
+        args = []
+        for t in argtypes:
+            if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+                args.append(1)
+            elif t is ctypes.c_double:
+                args.append(1e-8)
+            else:
+                args.append(None)
+        assert getattr(lib, name)(*args) == nat.MS_ERR_ARG, name
+        checked += 1
+    assert checked == 9          # apply, apply_adjoint, operator, rhs, solve, fields, grad, fields_noalloc, info
+    lib.ms_destroy(None)
+    assert lib.ms_last_cuda_error(None) == 0
+
+
+def test_every_declared_status_has_its_own_message(lib):
+    src = open(os.path.join(ROOT, "include", "ms_b300.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"^#define\s+(MS_(?:OK|NOT_CONVERGED|ERR_\w+))\s+(-?\d+)", src, re.M)}
+    assert len(codes) >= 12
+    msgs = {c: lib.ms_status_string(c) for c in codes}
+    for c, m in msgs.items():
+        assert m and m != b"unknown status", (codes[c], m)
+    assert len(set(msgs.values())) == len(msgs)
