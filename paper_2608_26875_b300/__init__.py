@@ -147,7 +147,9 @@ class Solver:
         return b
 
     def solve(self, kinds, angles, tol: float = 1e-12, prec: int = MS_PREC_FP64, stream=None, out=None):
-        """gamma solving A gamma = S a0 (ms_solve).  Returns (gamma, info dict, status)."""
+        """gamma solving A gamma = S a0 (ms_solve).  Returns (gamma, info), info a dict with the
+        iterations, refinements, mat-vecs, worst relative residual, seconds and the status (MS_OK, or
+        MS_NOT_CONVERGED when a column missed tol within the iteration cap)."""
         inc, keep = self._incidence(kinds, angles)
         g = out if out is not None else self.empty(inc.nrhs)
         info = nat.SolveInfo()
