@@ -294,6 +294,58 @@ def test_interface_continuity_of_assembled_field(solved_small):
     assert np.abs(tl - tu).max() < 1e-8 * np.abs(tl).max()
 
 
+def _betti_on_circles(P, gam, rho=0.6, npts=128):
+    """Betti's reciprocal form I_k = circle integral of u^A . t^B - u^B . t^A (outward normal of the
+    circle) around each of the two centres, for the layered scattered fields of two states given as
+    the two columns of gam."""
+    out = []
+    for m in range(2):
+        th = np.linspace(0, 2 * np.pi, npts, endpoint=False)
+        nx, ny = np.cos(th), np.sin(th)
+        us, gs = P.scattered_field(gam, P.centres[m, 0] + rho * nx, P.centres[m, 1] + rho * ny,
+                                   with_gradient=True)
+        tA = waves.traction(gs[0], nx, ny, P.L.lam_l, P.L.mu_l)
+        tB = waves.traction(gs[1], nx, ny, P.L.lam_l, P.L.mu_l)
+        f = us[0][0] * tB[0] + us[0][1] * tB[1] - us[1][0] * tA[0] - us[1][1] * tA[1]
+        out.append(f.sum() * 2 * np.pi * rho / npts)
+    return out
+
+
+@pytest.fixture(scope="module")
+def two_sources():
+    wl = syn.small_case(21, 2, 5, omega=2.0, nrhs=2)
+    wl.centres = np.array([[-1.5, -2.5], [1.2, -3.1]])
+    wl.radius = np.array([0.3, 0.3])
+    P = system.Problem(wl)
+    rng = np.random.default_rng(5)
+    gam = np.zeros((2, 2, 2 * wl.p + 1, 2), complex)
+    for m in range(2):          # state A: particle 0 radiates alone; state B: particle 1
+        gam[m, :, :, m] = rng.standard_normal((2, 2 * wl.p + 1)) + 1j * rng.standard_normal((2, 2 * wl.p + 1))
+    return P, gam
+
+
+def test_layered_field_is_reciprocal(two_sources):
+    """Elastodynamic reciprocity (Betti) in the welded two-layer medium.  Two states are each the
+    field of one radiating particle: its outgoing multipoles plus the interface-reflected Sommerfeld
+    field.  Betti's form vanishes over the region outside two small circles around the sources:
+    displacement and traction are continuous across the interface and both states radiate.  So
+    the two circle integrals cancel, though each is O(1).  A transposed 2x2 reflection (P->S read
+    as S->P), a flipped order index or x-phase in the multipole-to-Sommerfeld map, or a wrong P/S
+    normalisation there breaks the cancellation."""
+    P, gam = two_sources
+    I1, I2 = _betti_on_circles(P, gam)
+    assert abs(I1) > 1.0
+    assert abs(I1 + I2) < 1e-11 * abs(I1)
+
+
+def test_planted_reflection_transpose_is_caught_by_reciprocity(two_sources, monkeypatch):
+    P, gam = two_sources
+    R = P.reflection_table()
+    monkeypatch.setattr(P, "reflection_table", lambda: np.ascontiguousarray(np.transpose(R, (0, 2, 1))))
+    I1, I2 = _betti_on_circles(P, gam)
+    assert abs(I1 + I2) > 1e-4 * abs(I1)
+
+
 def test_gmres_matches_dense_lu():
     wl = syn.small_case(12, 3, 6, omega=2.0, nrhs=2)
     P = system.Problem(wl)
