@@ -29,6 +29,21 @@ def test_wavenumbers_match_paper_printed_values():
         assert got[1] == pytest.approx(ks, rel=1e-14)
 
 
+@pytest.mark.parametrize("n", [0, 1, -1, 5, -7, 20, 33, -40, 60])
+def test_bessel_and_hankel_against_mpmath(n):
+    """The oracle's J_n and H_n^(1) (every Graf entry, multipole and local expansion goes through
+    them) against mpmath at 30 digits, over the orders and arguments k d of the direct sums
+    (|n| <= 2p = 40 at p = 20, k d up to ~10^3).  J is compared against the envelope |H_n|, so
+    that an argument near a zero of J does not count as a large relative error."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    for x in (0.3, 1.0, 2.7, 9.0, 20.0, 39.5, 150.0, 1200.0):
+        h_ref = complex(mpmath.hankel1(n, x))
+        j_ref = complex(mpmath.besselj(n, x))
+        assert abs(complex(waves.Z("H", n, x)) - h_ref) <= 1e-12 * abs(h_ref), (n, x)
+        assert abs(complex(waves.Z("J", n, x)) - j_ref) <= 1e-12 * abs(h_ref), (n, x)
+
+
 @pytest.mark.parametrize("k", [0.7, 2.0, 6.0])
 def test_graf_translation_pointwise(k):
     """Sec. 4.2: the local expansion T gamma about x_m reproduces the outgoing potential of
