@@ -361,6 +361,88 @@ def test_planted_reflection_transpose_is_caught_by_reciprocity(two_sources, monk
     assert abs(I1 + I2) > 1e-4 * abs(I1)
 
 
+def _manufactured_case(p=10, delta=0.15):
+    """Three discs (rigid, traction-free, rigid), each holding a P + S point source at distance delta
+    from its centre.  The exact scattered field u_ex is the sources' free-space field (H_0 potentials
+    summed directly) plus its interface reflection, taken from the monopole spectral form (som1) and
+    the 2x2 plane-wave reflection.  The boundary data of u_ex (displacement on rigid circles,
+    traction on traction-free ones) are fitted by outgoing waves f^m on each circle.  Then
+    gamma = f + S (T + R) gamma has the exact solution whose field is u_ex: by uniqueness of the
+    exterior problem the solver, through Graf translations, pts1 at every order, Jacobi-Anger and
+    the scattering matrices, must reproduce a field built from none of them."""
+    wl = syn.small_case(31, 3, p, omega=2.0, nrhs=1)
+    wl.centres = np.array([[-2.0, -2.0], [0.5, -3.0], [2.5, -1.8]])
+    wl.radius = np.full(3, 0.5)
+    wl.bc = np.array([0, 1, 0])
+    P = system.Problem(wl)
+    L = P.L
+    rng = np.random.default_rng(7)
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    z = P.centres + delta * np.stack([np.cos(ph), np.sin(ph)], 1)
+    amp = rng.standard_normal((3, 2)) + 1j * rng.standard_normal((3, 2))
+    sp, ss = sommerfeld.branch_s(P.xi, L.kp_l), sommerfeld.branch_s(P.xi, L.ks_l)
+    # som1: H_0(k |x - z|) = sum_q W_q e^{s z_y - i xi z_x} / (i pi s) e^{i xi x - s y} above the source
+    U_P = sum(amp[m, 0] * np.exp(sp * z[m, 1] - 1j * P.xi * z[m, 0]) / (1j * np.pi * sp) for m in range(3))
+    U_S = sum(amp[m, 1] * np.exp(ss * z[m, 1] - 1j * P.xi * z[m, 0]) / (1j * np.pi * ss) for m in range(3))
+    R = P.reflection_table()
+    D_P = R[:, 0, 0] * U_P + R[:, 0, 1] * U_S
+    D_S = R[:, 1, 0] * U_P + R[:, 1, 1] * U_S
+
+    def u_ex(X, Y):
+        u1, u2, g = sommerfeld.downgoing_field(P.xi, P.W, L, D_P, D_S, X, Y)
+        g = [[g[i][j] for j in range(2)] for i in range(2)]
+        for m in range(3):
+            a, b, gg = waves.field_of_coeffs("H", [amp[m, 0]], [amp[m, 1]], 0, L.kp_l, L.ks_l,
+                                             X - z[m, 0], Y - z[m, 1])
+            u1, u2 = u1 + a, u2 + b
+            g = [[g[i][j] + gg[i][j] for j in range(2)] for i in range(2)]
+        return u1, u2, g
+
+    nc = 2 * p + 1
+    f = np.zeros((3, 2, nc, 1), complex)
+    th = np.linspace(0, 2 * np.pi, 96, endpoint=False)
+    nx, ny = np.cos(th), np.sin(th)
+
+    def trace(u1, u2, g, bc):
+        return np.concatenate([u1, u2] if bc == 0 else waves.traction(g, nx, ny, L.lam_l, L.mu_l))
+
+    for m in range(3):
+        X, Y = P.centres[m, 0] + P.radius[m] * nx, P.centres[m, 1] + P.radius[m] * ny
+        data = trace(*u_ex(X, Y), P.bc[m])
+        cols = []
+        for b in range(2):
+            for j in range(nc):
+                c = np.zeros((2, nc), complex)
+                c[b, j] = 1.0
+                cols.append(trace(*waves.field_of_coeffs("H", c[0], c[1], p, L.kp_l, L.ks_l,
+                                                         X - P.centres[m, 0], Y - P.centres[m, 1]), P.bc[m]))
+        A = np.stack(cols, 1)
+        cn = np.linalg.norm(A, axis=0)                # orders differ by many decades at k R < 1
+        sol = np.linalg.lstsq(A / cn, data, rcond=None)[0] / cn
+        # the fit leaves the data's modes above p (about 1e-6 here); they decay like (R/r)^n away from the circle
+        assert np.abs(A @ sol - data).max() < 1e-4 * np.abs(data).max()
+        f[m, :, :, 0] = sol.reshape(2, nc)
+    Xr = np.concatenate([np.linspace(-4, 4, 9), [-0.8, 1.5, 0.0]])
+    Yr = np.concatenate([np.full(9, -0.5), [-2.6, -2.2, -4.5]])
+    return P, f, Xr, Yr, u_ex
+
+
+def test_manufactured_solution_from_interior_sources():
+    P, f, X, Y, u_ex = _manufactured_case()
+    gam = P.solve_lu(f)
+    got = P.scattered_field(gam, X, Y)[0]
+    e1, e2, _ = u_ex(X, Y)
+    want = np.stack([e1, e2])
+    assert np.abs(got - want).max() < 1e-8 * np.abs(want).max()
+
+
+def test_planted_s2l_sign_is_caught_by_manufactured_solution(monkeypatch):
+    orig = sommerfeld.s2l
+    monkeypatch.setattr(sommerfeld, "s2l", lambda *a, **k: -orig(*a, **k))
+    with pytest.raises(AssertionError):
+        test_manufactured_solution_from_interior_sources()
+
+
 def test_gmres_matches_dense_lu():
     wl = syn.small_case(12, 3, 6, omega=2.0, nrhs=2)
     P = system.Problem(wl)
