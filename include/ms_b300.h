@@ -26,7 +26,7 @@
  *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers are
  *     ordinary host memory owned by the caller.  The handle owns its own tables and workspace.
  *   - Work is ordered on the CUDA stream passed in (cudaStream_t as void*, NULL = default stream).
- *     Calls that need host decisions (ms_solve) synchronise that stream.  A handle must not be
+ *     Calls that need host decisions (ms_solve, ms_grad) synchronise that stream.  A handle must not be
  *     used from two threads at once.
  */
 #ifndef MS_B300_H
@@ -129,7 +129,7 @@ typedef struct ms_handle ms_handle;
 /* Fill *o with the defaults listed above. */
 void ms_default_options(ms_options* o);
 
-/* Build a handle for one geometry, medium, frequency omega > 0 and expansion order p >= 0
+/* Build a handle for one geometry, medium, frequency omega > 0 and expansion order 0 <= p <= 30
  * (truncation Z_p of Sec. 4.1): wavenumbers (Sec. 2), scattering matrices (closed-form discs,
  * Sec. 4.1; caller prototypes, Sec. 4.3), the Sommerfeld contour and the 2x2 reflection table per
  * node (Sec. 3, 5.1), and device workspace.  Errors: MS_ERR_ARG, MS_ERR_OVERLAP,
