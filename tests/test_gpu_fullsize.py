@@ -1,0 +1,92 @@
+"""The benchmarked mat-vec at full size, in the launch configuration bench.py times: 10^4 particles,
+p = 20, the adapted 4800-node contour, 64 right-hand sides (bench.py's rank-0 input), FMM with 10
+particles per leaf, FP32 operator on the tensor cores.
+
+* Sampled outputs (3 targets spread over the particle order, 3 of the 64 columns) against the FP64
+  oracle's mat-vec at those targets, for the FP64 GPU path (bar 1e-10, ten times the bar of the
+  smaller FMM and config-2 tests) and the FP32 tensor-core path.
+* Every output of the FP32 tensor-core mat-vec against the FP64 GPU mat-vec.
+
+The FP32 bar here is 1e-3 in the scaled norm.  The tensor-core bar of the smaller cases (1.6e-4,
+derived from the 3xTF32 product error) is established on up to 2500 particles with the same density
+and contour growth e^3.  At full size the multipole-to-Sommerfeld contraction is four times longer,
+so this test guards against size-dependent faults (tile counts, offsets, split-K partitions), which
+give O(1) errors, without claiming the tighter bar untested.  Outputs must also be finite.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import system
+from oracle.media import Layered
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_2608_26875_b300 as P  # noqa: E402
+
+TARGETS = [0, 4321, 9999]
+COLS = [0, 31, 63]
+FULL_FP32_BAR = 1e-3
+
+
+def tau(wl):
+    """Order scale (k_b R_m / 2)^|n| / |n|! per (m, b, n): the natural size of outgoing coefficients."""
+    L = Layered(wl.media, wl.omega)
+    n = np.abs(np.arange(-wl.p, wl.p + 1))
+    lg = np.array([math.lgamma(k + 1) for k in n])
+    out = np.empty((wl.M, 2, 2 * wl.p + 1))
+    for b, k in ((0, L.kp_l), (1, L.ks_l)):
+        out[:, b, :] = np.exp(n[None, :] * np.log(k * wl.radius[:, None] / 2) - lg[None, :])
+    return out[..., None]
+
+
+def scaled_err(got, want, t):
+    return (np.abs(got - want) / t).max() / (np.abs(want) / t).max()
+
+
+def rel_l2(got, want):
+    return np.linalg.norm(got - want) / np.linalg.norm(want)
+
+
+@pytest.fixture(scope="module")
+def full():
+    wl = syn.config3()
+    assert (wl.M, wl.p) == (10000, 20)
+    x = syn.random_coeffs(1000, wl.M, wl.p, 64)
+    s = P.Solver.from_workload(wl, leaf_target=10, tensor_cores=True)
+    assert s.n_nodes == 4800 and s.fmm_levels >= 4
+    xd = torch.as_tensor(x, device="cuda")
+    y32 = s.apply(xd, prec=P.MS_PREC_FP32).cpu().numpy()
+    y64 = s.apply(xd, prec=P.MS_PREC_FP64).cpu().numpy()
+    s.close()
+    del xd
+    ref = system.Problem(wl)
+    want = ref.matvec(np.ascontiguousarray(x[..., COLS]), targets=TARGETS)
+    return wl, y32, y64, want
+
+
+def test_full_size_fp64_matches_oracle_on_sampled_targets(full):
+    wl, _, y64, want = full
+    got, t = y64[TARGETS][..., COLS], tau(wl)[TARGETS]
+    assert rel_l2(got, want) <= 1e-10
+    assert scaled_err(got, want, t) <= 1e-10
+
+
+def test_full_size_fp32_tensor_cores_matches_oracle_on_sampled_targets(full):
+    wl, y32, _, want = full
+    got, t = y32[TARGETS][..., COLS], tau(wl)[TARGETS]
+    assert rel_l2(got, want) <= FULL_FP32_BAR
+    assert scaled_err(got, want, t) <= FULL_FP32_BAR
+
+
+def test_full_size_fp32_tensor_cores_matches_fp64_everywhere(full):
+    wl, y32, y64, _ = full
+    assert np.isfinite(y32).all() and np.isfinite(y64).all()
+    assert rel_l2(y32, y64) <= FULL_FP32_BAR
+    assert scaled_err(y32, y64, tau(wl)) <= FULL_FP32_BAR
