@@ -123,7 +123,7 @@ __global__ void k_add_up_f(double2* __restrict__ x, const float2* __restrict__ d
 
 inline int nb(long long n, int t) { return (int)((n + t - 1) / t); }
 
-// Block GMRES state for nrhs independent columns.
+// GMRES state for nrhs independent columns advanced together (one Krylov space per column).
 template <typename T>
 struct Krylov {
     typedef typename CT<T>::c C;
