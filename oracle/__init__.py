@@ -20,11 +20,15 @@ sommerfeld  contour, branch of sqrt(xi^2-k^2), M2S (pts1/sed1/sed2), S2L (Jacobi
             2x2 interface reflection by the plane-wave route and by the paper's A_xi route (Sec. 3, 5.1, 5.3, 5.4, 7.3)
 system      mat-vec y = gamma - S (T + R) gamma, plane-wave right-hand side, GMRES, dense LU,
             receiver fields, boundary-condition residual                    (Sec. 4.2 mul2, Sec. 5.2 aequ/Schur, Sec. 7.3 bplan)
+adjoint     adjoint gradient of a receiver misfit in centres, radii and omega (inverse scattering, Sec. 7.5)
 
 Pins (tests/test_oracle_*.py, all `-m "not gpu"`) tie each function to something other
-than itself: scipy/DLMF identities, Graf pointwise evaluation, the Sommerfeld identities
-as quadrature, Jacobi-Anger on contour nodes, boundary-condition residuals of the disc
-matrices, two independent derivations of the reflection matrix, identical-media zero
-reflection, plane-wave energy balance, interface continuity of the assembled field,
-boundary-condition residuals of the solved multi-particle system and a dense-LU solve.
+than itself: Bessel and Hankel values against mpmath, Graf pointwise evaluation, the
+Sommerfeld identities as quadrature, Jacobi-Anger on contour nodes, boundary-condition
+residuals of the disc matrices, two independent derivations of the reflection matrix,
+identical-media zero reflection, plane-wave energy balance for incidence from below and
+above, textbook normal-incidence coefficients, interface continuity of the assembled field,
+elastodynamic reciprocity of the layered field, boundary-condition residuals of the solved
+multi-particle system, a manufactured solution from point sources inside the particles, a
+dense-LU solve, and central differences of the loss for the adjoint gradient.
 """
