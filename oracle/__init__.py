@@ -18,8 +18,14 @@ disc        closed-form disc scattering matrix per mode, rigid and traction-free
 graf        M2L translation T^{ml} by Graf's addition theorem          (Sec. 4.2)
 sommerfeld  contour, branch of sqrt(xi^2-k^2), M2S (pts1/sed1/sed2), S2L (Jacobi-Anger, stm/c1/c2),
             2x2 interface reflection by the plane-wave route and by the paper's A_xi route (Sec. 3, 5.1, 5.3, 5.4, 7.3)
+            and the same contour integral by adaptive Gauss-Kronrod quadrature (Sec. 5.1, reading A5)
 system      mat-vec y = gamma - S (T + R) gamma, plane-wave right-hand side, GMRES, dense LU,
             receiver fields, boundary-condition residual                    (Sec. 4.2 mul2, Sec. 5.2 aequ/Schur, Sec. 7.3 bplan)
+nystrom     Nystrom boundary integral solve of one star-shaped particle (Kress log and Hilbert-transform
+            product quadrature), its scattering matrix by the projection formula and by the single-layer
+            coefficient formula, rotated copies                               (Sec. 4.3 bdint, S7, S10; Sec. 7 shapes)
+layered_bie brute-force boundary integral solve of a few particles with the layered Green's function
+            (free-space part plus its Sommerfeld reflection), no scattering matrices (Sec. 7.1 direct method)
 adjoint     adjoint gradient of a receiver misfit in centres, radii and omega (inverse scattering, Sec. 7.5)
 
 Pins (tests/test_oracle_*.py, all `-m "not gpu"`) tie each function to something other
@@ -30,5 +36,11 @@ identical-media zero reflection, plane-wave energy balance for incidence from be
 above, textbook normal-incidence coefficients, interface continuity of the assembled field,
 elastodynamic reciprocity of the layered field, boundary-condition residuals of the solved
 multi-particle system, a manufactured solution from point sources inside the particles, a
-dense-LU solve, and central differences of the loss for the adjoint gradient.
+dense-LU solve, and central differences of the loss for the adjoint gradient.  For the
+non-circular particles (tests/test_oracle_nystrom.py): exactness of the product-quadrature weights
+on trigonometric polynomials, the traction kernel against differences of the fundamental solution,
+the Nystrom matrix on a disc against the closed form, an exact exterior solution from point forces
+inside a star, S7 against S10, the solver on a rotated boundary against the rotation phase, the
+multiple-scattering solve against the brute-force layered boundary integral solve of three stars,
+and the fixed contour rule against adaptive Gauss-Kronrod quadrature.
 """

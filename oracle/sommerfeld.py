@@ -217,6 +217,30 @@ def layered_apply(xi, W, L: Layered, centres, gamma):
     return s2l(xi, W, L, centres, D_P, D_S, p)
 
 
+def layered_apply_adaptive(L: Layered, centres, gamma, t_max: float = 20.0, depth: float = 0.5,
+                           epsrel: float = 1e-12):
+    """The same reflected operator (R gamma) with the contour integral evaluated by adaptive
+    Gauss-Kronrod quadrature (scipy.integrate.quad_vec, 21-point Kronrod rule, error control on the
+    vector of every output coefficient) instead of a fixed rule: xi(t) = t - i depth tanh(t) on
+    |t| <= t_max (Sec. 5.1), with break points at the branch points +-kp, +-ks of both layers.
+    Its difference from the fixed composite rule of `contour` is that rule's discretisation error
+    (reading A5).  Returns (local coefficients (M, 2, 2p+1, nrhs), quad_vec's error estimate)."""
+    from scipy.integrate import quad_vec
+    p = (gamma.shape[2] - 1) // 2
+    M = centres.shape[0]
+
+    def f(t):
+        xi = np.array([t - 1j * depth * np.tanh(t)])
+        dxi = np.array([1.0 - 1j * depth / np.cosh(t) ** 2])
+        U_P, U_S = m2s(xi, L, centres, gamma)
+        D_P, D_S = reflect_nodes(xi, L, U_P, U_S)
+        return s2l(xi, dxi, L, centres, D_P, D_S, p).ravel()
+
+    pts = sorted({s * k for k in (L.kp_u, L.ks_u, L.kp_l, L.ks_l) for s in (-1.0, 1.0) if k < t_max})
+    res, err = quad_vec(f, -t_max, t_max, epsrel=epsrel, epsabs=0.0, points=pts, limit=20000)
+    return res.reshape(M, 2, 2 * p + 1, gamma.shape[3]), err
+
+
 def layered_apply_paper(xi, W, L: Layered, centres, gamma, x0: float = 0.0):
     """Same operator by the paper's route: b1/b2 spectral values -> A_xi sigma = b -> eee1.
 
