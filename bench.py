@@ -1,9 +1,12 @@
 #!/usr/bin/env python3
 """Benchmark: 64-right-hand-side mat-vecs of the layered multiple-scattering operator.
 
-Workload: 10^4 particles (enclosing radius U[0.2, 0.5], packing fraction 0.2), omega = 6,
-expansion order p = 20, N_S = 4800 Sommerfeld nodes on the contour adapted to the cloud's width,
-64 right-hand sides (synthetic, seeded).  A step is one application y = x - S (T + R) x of the
+Workload: 10^4 particles (enclosing radius U[0.2, 0.5], packing fraction 0.2; half discs, half stars
+r(t) = a (1 + 0.2 cos 5t) of 16 quantised sizes x 2 boundary conditions with random rotations),
+omega = 6, expansion order p = 20, N_S = 4800 Sommerfeld nodes on the contour adapted to the cloud's
+width, 64 right-hand sides (synthetic, seeded).  The 32 star prototype matrices are seeded dense
+stand-ins with the order profile of small-particle scattering matrices (synthetic.surrogate_tables):
+the mat-vec's work does not depend on their values.  A step is one application y = x - S (T + R) x of the
 whole hot path (precision staging, near-pair translation, FMM far field, multipole-to-Sommerfeld,
 reflection, Sommerfeld-to-local, scattering-matrix apply) to the 64-column block, with the FP32
 operator on the tensor cores (--no-tensor-cores: CUDA cores).  `value` is mat-vecs per second over
@@ -41,9 +44,23 @@ METRIC = "matvecs/s (2D N=1e4, 64 RHS, mixed FP32 operator)"
 UNIT = "matvec/s"
 
 
+def star_tables(wl, seed: int = 77):
+    """Seeded stand-in prototype matrices for timing: row/column order profile (k_b R_q / 2)^|n| / |n|!
+    with R_q the prototype's enclosing radius and k_b the lower layer's wavenumbers."""
+    import synthetic as syn
+    if wl.n_proto == 0:
+        return None
+    kp = wl.omega / math.sqrt(wl.media.lam_l + 2 * wl.media.mu_l)
+    ks = wl.omega / math.sqrt(wl.media.mu_l)
+    R = wl.proto_shape[:, 0] + wl.proto_shape[:, 1]
+    ratio = np.stack([kp * R / 2, ks * R / 2], 1)
+    return syn.surrogate_tables(seed, ratio, wl.p)
+
+
 def workload():
     import synthetic as syn
-    return syn.config3()
+    wl = syn.config3()
+    return wl, star_tables(wl)
 
 
 # ------------------------------------------------------------------ clocks
@@ -111,24 +128,25 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(wl, targets: int, nrhs: int, spectral_cols: int = 8):
+def oracle_sample(wl, tables, targets: int, nrhs: int, spectral_cols: int = 8):
     """Time the FP64 oracle on `targets` target particles of the direct translation sum (nrhs
     columns) and on the full spectral part (multipole-to-Sommerfeld, reflection, Sommerfeld-to-local)
     for `spectral_cols` columns; extrapolate linearly to one full 64-column mat-vec.
     Returns (matvecs/s, cores, sample text, quadrature nodes of the oracle's rule)."""
     import synthetic as syn
     from oracle import system
-    ref = system.Problem(wl)
+    ref = system.Problem(wl, proto_S=tables)
     x = syn.random_coeffs(99, wl.M, wl.p, nrhs)
     idx = list(range(targets))
     t0 = time.perf_counter()
-    ref.translate(x, targets=idx)
+    ref.apply_S(ref.translate(x, targets=idx), targets=idx)
     t1 = time.perf_counter()
     ref.reflect(x[..., :spectral_cols], targets=idx)
     t2 = time.perf_counter()
     t_full = (t1 - t0) / targets * wl.M * (64 / nrhs) + (t2 - t1) * (64 / spectral_cols)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"oracle FP64 numpy/scipy: direct Graf sum for {targets} of {wl.M} targets with {nrhs} columns "
+    sample = (f"oracle FP64 numpy/scipy: direct Graf sum and scattering-matrix apply for {targets} of {wl.M} "
+              f"targets with {nrhs} columns "
               f"and the full spectral part with {spectral_cols} columns, extrapolated linearly to one "
               f"64-column mat-vec ({t1 - t0:.1f} s + {t2 - t1:.1f} s measured)")
     return 1.0 / t_full, cores, sample, len(ref.xi)
@@ -138,7 +156,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload()
+    wl, tables = workload()
     vals = []
     cores = 0
     sample = ""
@@ -146,9 +164,9 @@ def run_reference(args):
     # warm-up steps run the same oracle code on a minimal sample (one target, one spectral column):
     # they only bring the code and the tables in; the timed steps are the full bounded samples
     for _ in range(args.warmup):
-        oracle_sample(wl, targets=1, nrhs=8, spectral_cols=1)
+        oracle_sample(wl, tables, targets=1, nrhs=8, spectral_cols=1)
     for _ in range(max(args.steps, 1)):
-        v, cores, sample, nodes = oracle_sample(wl, targets=2, nrhs=64)
+        v, cores, sample, nodes = oracle_sample(wl, tables, targets=2, nrhs=64)
         vals.append(v)
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -175,9 +193,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    wl = workload()
+    wl, tables = workload()
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    solver = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores)
+    solver = P.Solver.from_workload(wl, proto_S=tables, leaf_target=args.leaf_target,
+                                    tensor_cores=args.tensor_cores)
     nrhs = 64
     x = torch.as_tensor(syn.random_coeffs(1000 + rank, wl.M, wl.p, nrhs), device="cuda")
     y = torch.empty_like(x)
@@ -225,6 +244,7 @@ def run_ours(args):
     t_near = part_time(P.MS_PART_T_NEAR)
     t_far = part_time(P.MS_PART_T_FAR) if solver.fmm_levels else 0.0
     t_refl = part_time(P.MS_PART_R)
+    t_sapply = part_time(P.MS_PART_S)
     nc = 2 * wl.p + 1
     pairs = solver.near_pairs
     flops_near = pairs * 2 * nc * nc * nrhs * 8.0                     # complex MAC = 8 real flops
@@ -275,7 +295,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, _ = oracle_sample(wl, targets=2, nrhs=64)
+        v, cores, sample, _ = oracle_sample(wl, tables, targets=2, nrhs=64)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -283,6 +303,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == P.MS_PREC_FP32 else "f64", "data": "synthetic",
                 "config": {"workload": wl.name, "M": wl.M, "p": wl.p, "nrhs": nrhs,
+                           "stars": int((wl.proto >= 0).sum()), "prototypes": wl.n_proto,
                            "n_nodes": solver.n_nodes, "omega": wl.omega,
                            "near_pairs": pairs, "fmm_levels": solver.fmm_levels,
                            "leaf_target": args.leaf_target, "contour_depth": wl.depth,
@@ -294,7 +315,9 @@ def run_ours(args):
                              "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                              "flops": "algorithmic complex MACs x 8 (the 3xTF32 split issues 3 MMAs per product)"
                              if tc else "algorithmic complex MACs x 8"},
-                "parts_ms": {"near": t_near * 1e3, "far": t_far * 1e3, "refl": t_refl * 1e3},
+                "parts_ms": {"near": t_near * 1e3, "far": t_far * 1e3, "refl": t_refl * 1e3,
+                             "sapply": t_sapply * 1e3,
+                             "note": "each part timed through ms_operator, staging in and out included"},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": launches_per_step(solver, tc) * args.steps,
@@ -306,7 +329,8 @@ def run_ours(args):
 
 def run_solve(args):
     """Time to solution at relative residual 1e-8 for plane-wave right-hand sides at the 10^4-particle
-    workload's density (radii U[0.2, 0.5], packing 0.2, omega = 6, p = 20), with --M particles and
+    workload's density (radii U[0.2, 0.5], packing 0.2, omega = 6, p = 20; discs, whose closed-form
+    scattering matrices are physical, unlike the stand-in star tables of the mat-vec), with --M particles and
     --nrhs columns: the mixed form (FP32 operator, FP64 refinement) and, with --full-fp64, the FP64
     form, both measured; otherwise the FP64 form is extrapolated from its mat-vec time and the
     mat-vecs the mixed solve needed.  GMRES restart and iteration cap from --restart, --max-iters."""
@@ -314,7 +338,7 @@ def run_solve(args):
 
     import paper_2608_26875_b300 as P
     import synthetic as syn
-    wl = syn.config3(M=args.M, nrhs=args.nrhs) if args.M not in (None, 10000) else workload()
+    wl = syn.config3_discs(M=args.M or 10000, nrhs=args.nrhs)
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
                                restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol)
@@ -405,12 +429,13 @@ def run_grad(args):
 def launches_per_step(solver, tensor_cores=False):
     """Kernels of one ms_apply: staging in/out, near sum (2 waves; one tensor-core launch for both),
     FMM (per wave: P2M, M2M per level, M2L per level, L2L per level, L2P), M2S, reflect, S2L (plus
-    the FP32 amplitude copy on the tensor-core path), S-apply."""
+    the FP32 amplitude copy on the tensor-core path), S-apply of the discs and of the prototypes."""
     L = solver.fmm_levels
     fmm = 0 if L == 0 else 2 * (1 + (L - 2) + (L - 1) + (L - 2) + 1)
+    proto = 1 if getattr(solver, "has_proto", False) else 0
     if tensor_cores:
-        return 2 + 1 + fmm + 4 + 1
-    return 2 + 2 + fmm + 3 + 1
+        return 2 + 1 + fmm + 4 + 1 + proto
+    return 2 + 2 + fmm + 3 + 1 + proto
 
 
 def run_profile(args):
@@ -423,9 +448,10 @@ def run_profile(args):
     import synthetic as syn
     wl = syn.config3(M=args.M or 2500, nrhs=64)
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores)
+    s = P.Solver.from_workload(wl, proto_S=star_tables(wl), tensor_cores=args.tensor_cores)
     x = torch.as_tensor(syn.random_coeffs(5, wl.M, wl.p, 64), device="cuda")
-    parts = {"near": P.MS_PART_T_NEAR, "far": P.MS_PART_T_FAR, "refl": P.MS_PART_R | P.MS_PART_S}
+    parts = {"near": P.MS_PART_T_NEAR, "far": P.MS_PART_T_FAR, "refl": P.MS_PART_R | P.MS_PART_S,
+             "sapply": P.MS_PART_S}
     for _ in range(args.steps):
         if args.part == "all":
             s.apply(x, prec=prec)
@@ -446,7 +472,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small case for ncu (see run_profile)")
     ap.add_argument("--mode", choices=["matvec", "solve", "grad"], default="matvec")
     ap.add_argument("--full-fp64", action="store_true", help="solve mode: run the FP64 solve too")
-    ap.add_argument("--part", choices=["near", "far", "refl", "all"], default="near")
+    ap.add_argument("--part", choices=["near", "far", "refl", "sapply", "all"], default="near")
     ap.add_argument("--M", type=int, default=None, help="particles: --profile (default 2500), --mode solve "
                     "(default 10000), --mode grad (default 2000, the inverse-scattering workload)")
     ap.add_argument("--nrhs", type=int, default=64, help="--mode solve: right-hand sides")

@@ -52,7 +52,10 @@ extern "C" {
 #define MS_ERR_BREAKDOWN       -10    /* GMRES breakdown with a non-zero residual */
 #define MS_ERR_TOO_LARGE       -11    /* request exceeds the fixed scratch of ms_fields_noalloc */
 #define MS_ERR_TIMEOUT         -12    /* a tensor-core kernel gave up waiting on its own pipeline (the
-                                         result of that call is invalid; the context stays usable) */
+                                         result of that call is invalid; the context stays usable).  A CTA
+                                         that gave up still waits, bounded, for its last committed multiplies
+                                         before it frees its tensor memory; if that wait also runs out, the
+                                         results of other kernels running at the same time are suspect too */
 
 /* ------------------------------------------------------------------ precision of an apply / solve */
 #define MS_PREC_FP64   0   /* every operator step in FP64 */
@@ -101,13 +104,17 @@ typedef struct {
                                   d ~ 3 / (horizontal extent) and panels narrow enough for e^{i t dx} */
     int32_t grade;             /* extra panel edges at each branch point +-kp, +-ks of both layers and
                                   at c +- d 2^j, j < grade (default 0: none) */
-    int32_t tensor_cores;      /* MS_PREC_FP32 contractions (near-pair Graf sum, FMM M2L, M2S, S2L; the adjoints of the
-                                  spectral maps):
+    int32_t tensor_cores;      /* MS_PREC_FP32 contractions (near-pair Graf sum, FMM M2L, M2S, S2L, the dense
+                                  prototype scattering-matrix apply; the adjoints of the spectral maps):
                                   1 = tcgen05 tensor cores, 3xTF32 split with FP32 accumulation (default);
                                   0 = CUDA-core FP32.  Costs 16 M N_S bytes of device tables. */
     double  inner_tol;         /* ms_solve / ms_grad: relative tolerance of each inner GMRES solve of the
                                   FP64 iterative refinement; 0 = default (1e-3 for MS_PREC_FP32,
                                   1e-7 for MS_PREC_FP64) */
+    int32_t tc_wait_test;      /* test hook for the tensor-core kernels' failure path (default 0 = off).
+                                  n > 0: every tensor-core CTA first waits, bounded by n microseconds, on a
+                                  barrier that nothing arrives at, gives up, issues no multiply, and the call
+                                  returns MS_ERR_TIMEOUT.  Valid range 0..1000000. */
 } ms_options;
 
 typedef struct {
@@ -164,6 +171,14 @@ int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stream);
 int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
              ms_solve_info* info, void* stream);
 
+/* Solve A gamma = b for a caller-supplied right-hand side b (device [M][2][nc][nrhs] complex double,
+ * not modified; e.g. S a0 of ms_rhs, or the coefficients of any incident field), by the same iterative
+ * refinement as ms_solve.  gamma: device, same layout; if guess != 0 it holds the initial guess on
+ * entry (zero otherwise), and it is overwritten by the solution.  info may be NULL.  Returns MS_OK,
+ * MS_NOT_CONVERGED, MS_ERR_NONFINITE (a NaN or Inf in b or in a residual), or another error. */
+int ms_solve_rhs(ms_handle* h, const void* b, int32_t nrhs, double tol, int32_t prec, void* gamma, int32_t guess,
+                 ms_solve_info* info, void* stream);
+
 /* Scattered displacement at R receivers in the lower layer (Sec. 5, total-field representation):
  * direct outgoing sum of every particle plus the interface-reflected Sommerfeld field.
  * gamma: device [M][2][nc][nrhs]; rx: device [R][2] double; u: device [nrhs][R][2] complex double.
@@ -187,9 +202,10 @@ int ms_grad(ms_handle* h, const ms_incidence* inc, const void* gamma, const void
             void* stream);
 
 /* Allocation-free variant of ms_fields (the paper has no counterpart: this is a service for
- * callers).  Some callers cannot call cudaMalloc: code that runs while a stream is being captured
- * into a CUDA graph, real-time loops that must never wait on the allocator, or processes confined
- * to a memory pool sized in advance.  This call computes exactly what ms_fields computes, with the
+ * callers).  Some callers cannot call cudaMalloc: real-time loops that must never wait on the
+ * allocator (cudaMalloc and cudaFree can synchronise the device), or processes whose device memory is
+ * owned by a pool sized in advance by the host application.  This call computes exactly what
+ * ms_fields computes, with the
  * same arguments, layouts and receiver validation, but allocates nothing: no cudaMalloc, cudaFree
  * or allocating library routine.  Its scratch -- the multipole-to-Sommerfeld partial sums, the
  * reflected spectral amplitudes, a device copy of the radii and a validation flag -- lives in fixed
@@ -199,7 +215,9 @@ int ms_grad(ms_handle* h, const ms_incidence* inc, const void* gamma, const void
  *   2 * N_S * nrhs <= 65536 (e.g. N_S = 512 allows nrhs <= 32); beyond them it returns
  *   MS_ERR_TOO_LARGE and touches nothing.
  *   The first call on each device looks up the addresses of the fixed arrays (with that device
- *   current); make that first call before any stream capture.
+ *   current) and keeps them for the rest of the process: they assume that the device's primary
+ *   context lives as long as the process (after a cudaDeviceReset they are stale).  Make that first
+ *   call before any stream capture.
  *   Every call shares the same arrays and leaves its contents behind: calls that overlap on the
  *   GPU (several streams, several handles or several host threads at once) race and corrupt each
  *   other's results.  Like ms_fields it synchronises `stream` once to read the validation flag. */

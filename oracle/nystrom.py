@@ -48,6 +48,8 @@ The two must agree for a traction-free particle.  Rotated copies: S' = e^{-i (n 
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 from scipy import special
 
@@ -442,3 +444,22 @@ def rotate(S, p: int, phi: float):
     """Scattering matrix of the copy rotated by phi (reading A11): S'_{(b,n),(b',n')} = e^{-i (n - n') phi} S."""
     n = np.tile(np.arange(-p, p + 1), 2)
     return S * np.exp(-1j * (n[:, None] - n[None, :]) * phi)
+
+
+@functools.lru_cache(maxsize=256)
+def _table(a1: float, a2: float, a3: int, bc: int, lam: float, mu: float, omega: float, p: int, N: int):
+    return scattering_matrix(StarCurve(a1, a2, a3), bc, Host(lam, mu, omega), p, N=N)
+
+
+def workload_tables(wl, N: int = 128):
+    """Scattering matrices (Q, 2nc, 2nc) of the star prototypes of a synthetic workload (shapes
+    wl.proto_shape, boundary conditions wl.proto_bc) in the lower layer, in their own unrotated frame;
+    prototypes no particle uses are left zero."""
+    nc = 2 * wl.p + 1
+    out = np.zeros((wl.n_proto, 2 * nc, 2 * nc), complex)
+    used = set(int(q) for q in np.asarray(wl.proto) if q >= 0)
+    for q in sorted(used):
+        a1, a2, a3 = wl.proto_shape[q]
+        out[q] = _table(float(a1), float(a2), int(a3), int(wl.proto_bc[q]), float(wl.media.lam_l),
+                        float(wl.media.mu_l), float(wl.omega), int(wl.p), int(N))
+    return out

@@ -22,7 +22,7 @@ from .waves import field_of_coeffs, traction
 class Problem:
     def __init__(self, wl, proto_S=None, proto_index=None):
         """wl: a synthetic.Workload.  proto_S (Q, 2nc, 2nc) and proto_index (M,) with -1 for
-        closed-form discs optionally give dense prototype scattering matrices, rotated per
+        closed-form discs (default: wl.proto) give dense prototype scattering matrices, rotated per
         particle by wl.rotation (Sec. 4.3: rotated copies by a rotation of the basis)."""
         self.wl = wl
         self.L = Layered(wl.media, wl.omega)
@@ -35,7 +35,11 @@ class Problem:
         self.xi, self.W = sommerfeld.contour(wl.n_panels, wl.nodes_per_panel, wl.t_max, wl.depth, wl.grade,
                                              (self.L.kp_u, self.L.ks_u, self.L.kp_l, self.L.ks_l))
         self.proto_S = proto_S
+        if proto_index is None and getattr(wl, "proto", None) is not None:
+            proto_index = wl.proto
         self.proto_index = np.full(self.M, -1) if proto_index is None else np.asarray(proto_index)
+        if (self.proto_index >= 0).any() and proto_S is None:
+            raise ValueError("prototype particles need their scattering matrices (proto_S)")
         self.rotation = np.asarray(wl.rotation, float)
         self._disc_S = {}
 

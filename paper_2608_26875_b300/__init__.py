@@ -45,7 +45,7 @@ class Solver:
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
-                 tensor_cores: bool = True, inner_tol: float = 0.0):
+                 tensor_cores: bool = True, inner_tol: float = 0.0, tc_wait_test: int = 0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -77,11 +77,13 @@ class Solver:
         o.depth, o.grade = float(depth), int(grade)
         o.tensor_cores = int(bool(tensor_cores))
         o.inner_tol = float(inner_tol)
+        o.tc_wait_test = int(tc_wait_test)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")
         self._h = h
         self.M, self.p, self.nc = M, int(p), 2 * int(p) + 1
+        self.has_proto = proto is not None and bool((np.asarray(proto) >= 0).any())
         nn, lev, npair = nat.c_int(), nat.c_int(), ctypes.c_int64()
         L.ms_info(h, None, None, ctypes.byref(nn), ctypes.byref(lev), ctypes.byref(npair))
         self.n_nodes = int(nn.value)
@@ -90,8 +92,14 @@ class Solver:
         self._keep = []
 
     @classmethod
-    def from_workload(cls, wl, **kw):
-        """Handle for a synthetic.Workload (closed-form discs unless prototypes are given)."""
+    def from_workload(cls, wl, proto_S=None, **kw):
+        """Handle for a synthetic.Workload: closed-form discs, and for a workload with star particles
+        (wl.proto) the prototype scattering matrices proto_S (Q, 2nc, 2nc), which the caller supplies."""
+        proto = getattr(wl, "proto", None)
+        if proto is not None and (np.asarray(proto) >= 0).any():
+            if proto_S is None:
+                raise ValueError(f"workload {wl.name} has prototype particles: pass proto_S")
+            kw.update(proto=proto, proto_S=proto_S)
         return cls(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, wl.p, rotation=wl.rotation,
                    n_panels=wl.n_panels, nodes_per_panel=wl.nodes_per_panel, t_max=wl.t_max,
                    depth=wl.depth, grade=wl.grade, **kw)
@@ -156,6 +164,22 @@ class Solver:
         st = nat.check(nat.lib().ms_solve(self._h, ctypes.byref(inc), float(tol), prec,
                                           ctypes.c_void_p(g.data_ptr()), ctypes.byref(info), _stream(stream)),
                        "ms_solve", allow_warning=True)
+        return g, {"iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
+                   "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
+
+    def solve_rhs(self, b: torch.Tensor, tol: float = 1e-12, prec: int = MS_PREC_FP64, x0=None, stream=None,
+                  out=None):
+        """gamma solving A gamma = b for a caller right-hand side b (ms_solve_rhs), from the initial
+        guess x0 (zero if None).  Returns (gamma, info) like solve()."""
+        nrhs = self._check_vec(b)
+        g = out if out is not None else torch.empty_like(b)
+        if x0 is not None:
+            self._check_vec(x0)
+            g.copy_(x0)
+        info = nat.SolveInfo()
+        st = nat.check(nat.lib().ms_solve_rhs(self._h, ctypes.c_void_p(b.data_ptr()), nrhs, float(tol), prec,
+                                              ctypes.c_void_p(g.data_ptr()), int(x0 is not None), ctypes.byref(info),
+                                              _stream(stream)), "ms_solve_rhs", allow_warning=True)
         return g, {"iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
                    "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
 

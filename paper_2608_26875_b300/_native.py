@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_panels", c_int), ("nodes_per_panel", c_int), ("t_max", ctypes.c_double),
                 ("restart", c_int), ("max_iters", c_int), ("check_geometry", c_int),
                 ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int),
-                ("tensor_cores", c_int), ("inner_tol", ctypes.c_double)]
+                ("tensor_cores", c_int), ("inner_tol", ctypes.c_double), ("tc_wait_test", c_int)]
 
 
 class Incidence(ctypes.Structure):
@@ -79,6 +79,8 @@ SIGNATURES = {
     "ms_rhs": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p]),
     "ms_solve": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_double, c_int, ctypes.c_void_p,
                          ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
+    "ms_solve_rhs": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_double, c_int, ctypes.c_void_p, c_int,
+                             ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                           ctypes.c_void_p]),
     "ms_grad": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -70,7 +70,7 @@ static int apply_common(ms_handle* h, const void* x, void* y, int nrhs, int prec
     // without S the result is a local (incoming) block, scaled the other way
     bool local = !(parts & MS_PART_S) && (parts & (MS_PART_T | MS_PART_R | MS_PART_T_NEAR | MS_PART_T_FAR));
     if ((rc = ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, local))) return rc;
-    if (prec == MS_PREC_FP32 && h->opt.tensor_cores && (parts & MS_PART_R)) return ms_spectral_tc_status(h, st);
+    if (prec == MS_PREC_FP32 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
     return MS_OK;
 }
 
@@ -190,7 +190,7 @@ extern "C" int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_no
 extern "C" void ms_destroy(ms_handle* h) {
     if (!h) return;
     dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);
-    dfree_t(h->d.proto); dfree_t(h->d.rot); dfree_t(h->d.sproto); dfree_t(h->d.node); dfree_t(h->d.wq);
+    dfree_t(h->d.proto); dfree_t(h->d.rot); ms_sapply_free(h); dfree_t(h->d.node); dfree_t(h->d.wq);
     dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
     dfree_t(h->d.qpm_m); dfree_t(h->d.qpm_e); dfree_t(h->d.qps_m); dfree_t(h->d.qps_e);
     dfree_t(h->d.zexp); dfree_t(h->d.dsdr);

@@ -157,8 +157,8 @@ extern "C" int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const do
 
 // ====================================================================== allocation-free fields
 // ms_fields_noalloc: the receiver-field computation of ms_fields for callers that cannot call
-// cudaMalloc (for example code running while a stream is being captured, real-time loops that
-// must not synchronise with the allocator, or processes confined to a pre-sized memory pool).
+// cudaMalloc (for example real-time loops that must not synchronise with the allocator, or
+// processes whose device memory is owned by a pool sized in advance).
 // Everything ms_fields allocates per call -- the validation flag, a device copy of the radii, the
 // multipole-to-Sommerfeld partial sums and the reflected spectral amplitudes -- lives instead in
 // the fixed arrays below, which every GPU that loads this library holds until the process exits.
@@ -235,7 +235,9 @@ __global__ void k_nal_reflect(const double2* __restrict__ part, double2* __restr
     d[(size_t)(1 * NS + q) * nrhs + r] = cadd(cmul(R[2], up), cmul(R[3], us));
 }
 
-// Device addresses of the fixed arrays, looked up once per device with that device current.
+// Device addresses of the fixed arrays, looked up once per device with that device current and kept
+// for the rest of the process: the cache assumes the device's primary context lives as long as the
+// process (a cudaDeviceReset would leave these addresses stale).
 int nal_pointers(ms_handle* h, NalPtrs** out) {
     int dev = 0;
     if (int rc = ms_check(h, cudaGetDevice(&dev))) return rc;

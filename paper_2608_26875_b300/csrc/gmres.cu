@@ -188,6 +188,15 @@ struct Krylov {
     }
 };
 
+// FP32 operator on the tensor cores: read (and clear) their timeout flag after every application, so
+// that a pipeline wait that gave up ends the solve with MS_ERR_TIMEOUT at once (one small device-to-
+// host copy next to the inner products' own synchronisations).
+template <typename T>
+int tc_check(ms_handle* h, cudaStream_t st) {
+    if (sizeof(T) == 4 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
+    return MS_OK;
+}
+
 // Restarted GMRES: solve A x = b for every column; x holds the initial guess on entry.
 // op(in, out) applies A.  Stops a column when its residual estimate drops below tol * ||b||.
 template <typename T, typename Op>
@@ -207,7 +216,7 @@ int gmres(Krylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x,
     std::vector<int> kcol(nrhs);
     while (true) {
         // r0 = b - A x  (into V_0, then normalised)
-        if ((rc = op(x, K.w))) return rc;
+        if ((rc = op(x, K.w)) || (rc = tc_check<T>(K.h, K.st))) return rc;
         ++matvecs;
         long long tot = K.N * nrhs;
         // V_0 = b - w
@@ -238,7 +247,7 @@ int gmres(Krylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x,
         }
         int j = 0;
         for (; j < m && total < max_iters; ++j) {
-            if ((rc = op(K.vec(j), K.w))) return rc;
+            if ((rc = op(K.vec(j), K.w)) || (rc = tc_check<T>(K.h, K.st))) return rc;
             ++matvecs;
             std::vector<cd> h1, h2;
             if ((rc = K.gram(K.vec(0), j + 1, K.w, h1))) return rc;
@@ -310,9 +319,10 @@ int gmres(Krylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x,
 // tol by iterative refinement.  The outer loop keeps x and r = b - op x in FP64 in the ABI basis; each
 // step solves the diagonally scaled system (D^-1 A D, or its adjoint D A^H D^-1 for the local-type
 // adjoint unknowns) for the correction with restarted GMRES in FP64 (inner tolerance 1e-7) or FP32
-// (1e-3); ms_options.inner_tol overrides both.  x is overwritten (zero initial guess).
+// (1e-3); ms_options.inner_tol overrides both.  x is overwritten; it holds the initial guess on entry
+// when guess is set (zero otherwise).
 int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
-                    ms_solve_info* info, cudaStream_t st) {
+                    ms_solve_info* info, cudaStream_t st, bool guess) {
     auto t0 = std::chrono::steady_clock::now();
     int rc = ms_ensure_workspace(h, nrhs);
     if (rc) return rc;
@@ -320,7 +330,7 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
     const long long tot = N * nrhs;
     const bool local = adjoint;                 // adjoint unknowns scale like local coefficients
     const int sgn = local ? -1 : 1;
-    if ((rc = ms_check(h, cudaMemsetAsync(x, 0, tot * sizeof(double2), st)))) return rc;
+    if (!guess && (rc = ms_check(h, cudaMemsetAsync(x, 0, tot * sizeof(double2), st)))) return rc;
     int iters = 0, matvecs = 0, refinements = 0;
     std::vector<double> relres;
     auto op64 = [&](const double2* in, double2* out) -> int {
@@ -443,6 +453,15 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
     cudaFree(b);
     if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;
+}
+
+extern "C" int ms_solve_rhs(ms_handle* h, const void* b, int32_t nrhs, double tol, int32_t prec, void* gamma,
+                            int32_t guess, ms_solve_info* info, void* stream) {
+    if (!h || !b || !gamma || !(tol > 0) || nrhs < 1) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+    return ms_refine_solve(h, (const double2*)b, (double2*)gamma, nrhs, tol, prec, false, info, (cudaStream_t)stream,
+                           guess != 0);
 }
 
 // y = A^H x in the ABI basis (the transposed system of the gradient), through the adjoint kernels.

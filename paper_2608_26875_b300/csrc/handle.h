@@ -76,7 +76,11 @@ struct MsDeviceTables {
     float2* sdisc_f = nullptr;
     int* proto = nullptr;          // [M] -1 disc, else prototype index
     double* rot = nullptr;         // [M] rotation angle
-    double2* sproto = nullptr;     // [Q][2nc][2nc] unscaled prototype tables
+    double2* sps64 = nullptr;      // [Q][2nc][2nc] scaled prototype tables S~_q = 2^-e_ref S_q 2^-e_ref
+    float2* sps32 = nullptr;       // FP32 copy, and its conjugate transpose (adjoint, tensor cores)
+    float2* spsH32 = nullptr;
+    int* plist = nullptr;          // [n_plist] the prototype particles
+    int* pref = nullptr;           // [Q] reference particle of each prototype (whose scales S~_q carries)
     // Sommerfeld contour (Sec. 5.1)
     double2* node = nullptr;       // [NS] per node: xi_q
     double2* wq = nullptr;         // [NS] quadrature weight w_q xi'(t_q)
@@ -116,6 +120,7 @@ struct ms_handle {
     double kp_u = 0, ks_u = 0, kp_l = 0, ks_l = 0;
     int n_proto = 0;
     bool any_proto = false;
+    int n_plist = 0;
     ms_options opt{};
     MsDeviceTables d;
     std::vector<double> h_centres, h_radius, h_rot, h_protoS;
@@ -150,6 +155,11 @@ int ms_sapply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, bool iden
                      cudaStream_t st, int adj = 0, const void* in = nullptr);
 template <typename T>
 int ms_apply_adjoint_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, cudaStream_t st);
+int ms_sapply_setup(ms_handle* h);
+void ms_sapply_free(ms_handle* h);
+template <typename T>
+int ms_sapply_proto_launch(ms_handle* h, const void* xs, const void* as, void* ys, int nrhs, bool identity,
+                           bool apply_s, int adj, cudaStream_t st);
 template <typename T>
 int ms_m2s_launch(ms_handle* h, const void* xs, int nrhs, const int* expo, int adj, int* nchunks, cudaStream_t st);
 int ms_reflect_launch(ms_handle* h, const double2* part, int nchunks, double2* out, int nrhs, int adj,
@@ -178,6 +188,6 @@ int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* l
 int ms_m2l_tc_tiles(ms_handle* h, int b, int lev, const std::vector<int>& ptr);
 void ms_tc_tiles_free(TcTiles& T);
 int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
-                    ms_solve_info* info, cudaStream_t st);
+                    ms_solve_info* info, cudaStream_t st, bool guess = false);
 int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st,
                    bool local = false);

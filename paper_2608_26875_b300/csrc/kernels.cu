@@ -12,7 +12,8 @@
 //   k_m2s                        multipole-to-Sommerfeld, split over source chunks (row a4, Sec. 5.4)
 //   k_reflect                    chunk reduction + 2x2 reflection per node (row a5, Sec. 3 / 5.2)
 //   k_s2l                        Sommerfeld-to-local (row a6, Sec. 5.3)
-//   k_sapply_disc / k_sapply_proto  scattering-matrix apply and combine (row a7, Sec. 4.2 mul2, 4.3)
+//   k_sapply_disc                scattering-matrix apply and combine for discs (row a7, Sec. 4.2 mul2, 4.1);
+//                                prototype particles in sapply.cu
 #include <algorithm>
 
 #include "bessel.cuh"
@@ -338,48 +339,6 @@ __global__ void k_sapply_disc(const typename CT<T>::c* __restrict__ xs, const ty
     }
 }
 
-// Dense prototype particles (Sec. 4.3): S~_{(b,i),(b',j)} = 2^{-a_{m,b,i}} e^{-i (n_i - n_j) phi_m}
-// S_proto[(b,i),(b',j)] 2^{-a_{m,b',j}}, generated on the fly.  One CTA per prototype particle.
-template <typename T>
-__global__ void k_sapply_proto(const typename CT<T>::c* __restrict__ xs, const typename CT<T>::c* __restrict__ as,
-                               typename CT<T>::c* __restrict__ ys, const double2* __restrict__ sproto,
-                               const int* __restrict__ proto, const double* __restrict__ rot,
-                               const int* __restrict__ expo, int p, int nrhs, int identity, int apply_s,
-                               int adj) {
-    typedef typename CT<T>::c C;
-    const int m = blockIdx.x;
-    const int pi = proto[m];
-    if (pi < 0) return;
-    const int nc = 2 * p + 1, N2 = 2 * nc;
-    const double phi = rot[m];
-    const double2* S = sproto + (size_t)pi * N2 * N2;
-    const C* a = as + (size_t)m * N2 * nrhs;
-    for (int t = threadIdx.x; t < N2 * nrhs; t += blockDim.x) {
-        int row = t / nrhs, r = t % nrhs;
-        C y;
-        if (apply_s) {
-            C s = mk((T)0, (T)0);
-            for (int col = 0; col < N2; ++col) {
-                // entry (row, col) of S~, or of S~^H = conj(S~(col, row)) in adjoint mode
-                int rr = adj ? col : row, cc = adj ? row : col;
-                int ni2 = rr % nc - p, nj = cc % nc - p;
-                double sn, cs;
-                sincos(-(double)(ni2 - nj) * phi, &sn, &cs);
-                double2 v = cmul(S[(size_t)rr * N2 + cc], make_double2(cs, sn));
-                double sc = pow2d(-expo[m * N2 + rr] - expo[m * N2 + cc]);
-                v = make_double2(v.x * sc, v.y * sc);
-                if (adj) v = cconj(v);
-                cfma(s, to_c<T>(v), a[(size_t)col * nrhs + r]);
-            }
-            y = s;
-        } else {
-            y = a[(size_t)row * nrhs + r];
-        }
-        size_t o = (size_t)m * N2 * nrhs + t;
-        ys[o] = identity ? csub(xs[o], y) : y;
-    }
-}
-
 template <typename T>
 __global__ void k_zero(typename CT<T>::c* a, long long n) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -540,12 +499,7 @@ int ms_sapply_scaled(ms_handle* h, const void* xs_, void* ys_, int nrhs, bool id
     k_sapply_disc<T><<<nblk(nd, 256), 256, 0, st>>>(xs, as, ys, sd, h->d.proto, M, nc, nrhs, identity ? 1 : 0,
                                                     apply_s ? 1 : 0, adj);
     if (int rc = ms_check(h, cudaGetLastError())) return rc;
-    if (h->any_proto) {
-        k_sapply_proto<T><<<M, 256, 0, st>>>(xs, as, ys, h->d.sproto, h->d.proto, h->d.rot, h->d.expo, p, nrhs,
-                                             identity ? 1 : 0, apply_s ? 1 : 0, adj);
-        if (int rc = ms_check(h, cudaGetLastError())) return rc;
-    }
-    return MS_OK;
+    return ms_sapply_proto_launch<T>(h, xs, as, ys, nrhs, identity, apply_s, adj, st);
 }
 
 // ys = [xs -] [S~] (T~ + R~) xs for the parts selected (all in the scaled basis).

@@ -216,6 +216,7 @@ extern "C" void ms_default_options(ms_options* o) {
     o->grade = 0;
     o->tensor_cores = 1;
     o->inner_tol = 0.0;
+    o->tc_wait_test = 0;
 }
 
 // Panel edges of the Sommerfeld rule on [-t_max, t_max]: n uniform panels (edge k at
@@ -260,7 +261,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     if (o) opt = *o;
     if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || opt.restart < 1 || opt.max_iters < 1 ||
         opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30 ||
-        (opt.tensor_cores != 0 && opt.tensor_cores != 1) || !(opt.inner_tol >= 0.0 && opt.inner_tol < 1.0))
+        (opt.tensor_cores != 0 && opt.tensor_cores != 1) || !(opt.inner_tol >= 0.0 && opt.inner_tol < 1.0) ||
+        opt.tc_wait_test < 0 || opt.tc_wait_test > 1000000)
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {
@@ -478,11 +480,9 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         std::vector<int> z(std::max((size_t)M * 2 * nc, (size_t)4096), 0);
         if ((rc = upload(h, &h->d.zexp, z.data(), z.size()))) { ms_destroy(h); return rc; }
     }
-    if (h->any_proto) {
-        size_t nn = (size_t)g->n_proto * (2 * nc) * (2 * nc);
-        std::vector<double2> sp(nn);
-        for (size_t k = 0; k < nn; ++k) sp[k] = make_double2(g->proto_S[2 * k], g->proto_S[2 * k + 1]);
-        if ((rc = upload(h, &h->d.sproto, sp.data(), nn))) { ms_destroy(h); return rc; }
+    if ((rc = ms_sapply_setup(h))) {
+        ms_destroy(h);
+        return rc;
     }
     if ((rc = ms_build_translations(h, opt.use_fmm, opt.leaf_target))) {
         ms_destroy(h);

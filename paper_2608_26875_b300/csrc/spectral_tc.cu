@@ -381,13 +381,15 @@ int ms_spectral_tc_setup(ms_handle* h) {
     if (cudaMalloc(&d.qpmT_m, nt * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&d.qpsT_m, nt * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&d.qpmT_e, nt * sizeof(int)) != cudaSuccess || cudaMalloc(&d.qpsT_e, nt * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&d.tc_err, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&d.tc_err, 2 * sizeof(int)) != cudaSuccess)
         return MS_ERR_ALLOC;
     cudaMemcpy(d.qpmT_m, tm.data(), nt * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.qpsT_m, ts.data(), nt * sizeof(float2), cudaMemcpyHostToDevice);
     cudaMemcpy(d.qpmT_e, tme.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemcpy(d.qpsT_e, tse.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
-    cudaMemset(d.tc_err, 0, sizeof(int));
+    // tc_err[0]: the timeout flag; tc_err[1]: the test hook's wait in microseconds (ms_options.tc_wait_test)
+    const int flags[2] = {0, h->opt.tc_wait_test};
+    cudaMemcpy(d.tc_err, flags, sizeof(flags), cudaMemcpyHostToDevice);
     cudaFuncSetAttribute(k_s2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     cudaFuncSetAttribute(k_m2s_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     return ms_check(h, cudaDeviceSynchronize());

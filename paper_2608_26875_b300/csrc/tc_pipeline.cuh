@@ -26,7 +26,7 @@ constexpr int NSTAGE = 2;
 constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
 constexpr uint32_t B_TILE = NMAX * KC * 4;     // 32 KB
 constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;
-constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;
+constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;   // + stage barriers, tensor-memory slot, flag, probe
 constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
 constexpr uint32_t TMEM_COLS = 256;
 static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -93,12 +93,18 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NSTAGE);
     int* fail = reinterpret_cast<int*>(tslot + 1);
+    uint64_t* probe = bar + NSTAGE + 1;            // test hook: a barrier that nothing arrives at
     const int tid = threadIdx.x;
     const uint32_t idesc = tc::idesc_tf32(MA, n);
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) tc::mbar_init(&bar[s], 1);
+        tc::mbar_init(probe, 1);
         tc::mbar_fence_init();
         *fail = 0;
+        // err[1] > 0 (ms_options.tc_wait_test): wait that many microseconds for a phase that never
+        // completes, give up, and leave the CTA on its failure path before any multiply is issued
+        const int test_us = err[1];
+        if (test_us > 0 && !tc::mbar_wait(probe, 0, (uint64_t)test_us * 1000ull)) *fail = 1;
     }
     if (tid < 32) tc::tmem_alloc(tslot, TMEM_COLS);
     tc::fence_before();

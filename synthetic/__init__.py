@@ -51,6 +51,9 @@ class Workload:
     gmres_tol: float = 1e-12
     depth: float = 0.5       # contour depth d of xi(t) = t - i d tanh(t)
     grade: int = 0           # branch-point grading levels of the contour panels
+    proto: np.ndarray | None = None        # (M,) int32: -1 disc, q >= 0 star prototype q
+    proto_shape: np.ndarray | None = None  # (Q, 3) float64: a1, a2, a3 of r(t) = a1 + a2 cos(a3 t) (Sec. 7)
+    proto_bc: np.ndarray | None = None     # (Q,) int32: boundary condition of prototype q
 
     @property
     def M(self) -> int:
@@ -64,17 +67,22 @@ class Workload:
     def nc(self) -> int:
         return 2 * self.p + 1
 
+    @property
+    def n_proto(self) -> int:
+        return 0 if self.proto_shape is None else int(self.proto_shape.shape[0])
+
 
 MEDIA_STD = Media(lam_u=1.0, mu_u=0.5, lam_l=2.0, mu_l=1.0)
 
 
 def place_particles(rng: np.random.Generator, M: int, box, rmin: float, rmax: float,
-                    max_tries: int = 200000):
+                    max_tries: int = 200000, radius_fn=None):
     """Random sequential addition of M enclosing discs inside box=(x0,x1,y0,y1).
 
-    Radii are drawn U[rmin, rmax] (a constant when rmin == rmax).  A candidate is
-    rejected if it violates the separation rule against any accepted disc or if
-    y + SEP*R > 0.  A uniform cell grid keeps the neighbour check O(1).
+    Radii are drawn U[rmin, rmax] (a constant when rmin == rmax), or by radius_fn(rng, n) for the
+    n-th particle (values within [rmin, rmax]).  A candidate is rejected if it violates the
+    separation rule against any accepted disc or if y + SEP*R > 0.  A uniform cell grid keeps the
+    neighbour check O(1).
     """
     x0, x1, y0, y1 = box
     cell = 2.0 * SEP * rmax
@@ -90,7 +98,10 @@ def place_particles(rng: np.random.Generator, M: int, box, rmin: float, rmax: fl
         tries += 1
         if tries > max_tries:
             raise RuntimeError(f"placement failed after {max_tries} tries ({n}/{M} placed)")
-        r = rng.uniform(rmin, rmax) if rmax > rmin else rmin
+        if radius_fn is not None:
+            r = radius_fn(rng, n)
+        else:
+            r = rng.uniform(rmin, rmax) if rmax > rmin else rmin
         x = rng.uniform(x0, x1)
         y = rng.uniform(y0, y1)
         if y + SEP * r > 0.0:
@@ -174,32 +185,91 @@ def config1(seed: int = 1002) -> Workload:
                     receiver_line(256, -12, 12, -0.5))
 
 
-def config2(seed: int = 1003, nrhs: int = 1) -> Workload:
-    """1000 particles, radius 1.2 a with a ~ U[0.3,0.6], alternating rigid / traction-free,
-    omega=4, p=16, in [-40,40]x[-30,-1].  Particles are discs until star scattering
-    matrices are supplied (shape flag records the intended star)."""
+STAR_A2 = 0.2      # r(t) = a (1 + 0.2 cos(5 t)): the star of the workloads, enclosing radius 1.2 a
+STAR_A3 = 5
+
+
+def star_levels(rmin: float, rmax: float, Q: int) -> np.ndarray:
+    """Q quantised enclosing radii, the midpoints of Q equal bins of [rmin, rmax]."""
+    return rmin + (np.arange(Q) + 0.5) * (rmax - rmin) / Q
+
+
+def _star_prototypes(levels: np.ndarray):
+    """Prototype table of the stars: q = level + Q bc, shape (a, 0.2 a, 5) with a = R / 1.2."""
+    Q = levels.size
+    a = np.concatenate([levels, levels]) / (1.0 + STAR_A2)
+    shape = np.stack([a, STAR_A2 * a, np.full(2 * Q, float(STAR_A3))], 1)
+    return shape, np.repeat(np.arange(2, dtype=np.int32), Q)
+
+
+def config2(seed: int = 1003, nrhs: int = 1, Q: int = 16) -> Workload:
+    """1000 stars r(t) = a (1 + 0.2 cos 5t), a ~ U[0.3, 0.6] quantised to Q sizes (the finitely many
+    prototype shapes of Sec. 2; reading), enclosing radius 1.2 a, rigid and traction-free alternating,
+    random rotation, omega=4, p=16, in [-40,40]x[-30,-1]."""
     rng = np.random.default_rng(seed)
     M = 1000
-    c, r = place_particles(rng, M, (-40, 40, -30, -1), 1.2 * 0.3, 1.2 * 0.6)
+    levels = star_levels(1.2 * 0.3, 1.2 * 0.6, Q)
+    lev = np.empty(M, np.int64)
+
+    def rad(g, n):
+        lev[n] = g.integers(Q)
+        return levels[lev[n]]
+
+    c, r = place_particles(rng, M, (-40, 40, -30, -1), levels[0], levels[-1], radius_fn=rad)
     bc = (np.arange(M) % 2).astype(np.int32)
     rot = rng.uniform(0, 2 * math.pi, M)
     irng = np.random.default_rng(2003)
     ang = np.full(nrhs, math.radians(30.0)) if nrhs == 1 else np.radians(irng.uniform(10, 170, nrhs))
     npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
-    return Workload("particles1000_p16", MEDIA_STD, 4.0, 16, c, r, bc,
-                    np.zeros(M, np.int32), rot, np.zeros(nrhs, np.int32), ang,
-                    receiver_line(256, -40, 40, -0.5), n_panels=npan, depth=depth, grade=grade)
+    shape, pbc = _star_prototypes(levels)
+    return Workload("stars1000_p16", MEDIA_STD, 4.0, 16, c, r, bc,
+                    np.ones(M, np.int32), rot, np.zeros(nrhs, np.int32), ang,
+                    receiver_line(256, -40, 40, -0.5), proto=(lev + Q * bc).astype(np.int32),
+                    proto_shape=shape, proto_bc=pbc, n_panels=npan, depth=depth, grade=grade)
 
 
-def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
-    """10^4 particles, enclosing radius U[0.2,0.5], packing fraction 0.2 by enclosing
-    area, omega=6, p=20, 64 plane waves (half P, half S) at angles U[10,170] degrees.
-    BC alternates rigid / traction-free.  `M` may be lowered for parity sub-cases; the
-    box then shrinks to keep the packing fraction."""
+def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64, Q: int = 16) -> Workload:
+    """10^4 particles, enclosing radius U[0.2,0.5], packing fraction 0.2 by enclosing area, omega=6,
+    p=20, 64 plane waves (half P, half S) at angles U[10,170] degrees.  Even-numbered particles are
+    discs with continuous radii; odd-numbered ones are stars r(t) = a (1 + 0.2 cos 5t) whose enclosing
+    radius 1.2 a is one of Q quantised sizes (Q sizes x 2 boundary conditions = 2Q prototypes, random
+    rotation).  Boundary conditions alternate rigid / traction-free within each kind.  `M` may be
+    lowered for parity sub-cases; the box then shrinks to keep the packing fraction."""
     rng = np.random.default_rng(seed)
     er2 = (0.5 ** 3 - 0.2 ** 3) / (3 * 0.3)       # E[R^2] for R ~ U[0.2,0.5]
     area = M * math.pi * er2 / 0.2
     side = math.sqrt(area)
+    levels = star_levels(0.2, 0.5, Q)
+    lev = np.full(M, -1, np.int64)
+
+    def rad(g, n):
+        if n % 2 == 0:
+            return g.uniform(0.2, 0.5)
+        lev[n] = g.integers(Q)
+        return levels[lev[n]]
+
+    c, r = place_particles(rng, M, (-side / 2, side / 2, -side - 1.0, -1.0), 0.2, 0.5, radius_fn=rad)
+    bc = ((np.arange(M) // 2) % 2).astype(np.int32)
+    shape_kind = (np.arange(M) % 2).astype(np.int32)
+    proto = np.where(shape_kind == 1, lev + Q * bc, -1).astype(np.int32)
+    rot = rng.uniform(0, 2 * math.pi, M)
+    irng = np.random.default_rng(2004)
+    ang = np.radians(irng.uniform(10, 170, nrhs))
+    kind = (np.arange(nrhs) >= nrhs // 2).astype(np.int32)
+    npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
+    shape, pbc = _star_prototypes(levels)
+    return Workload(f"discs_stars{M}_p20_rhs{nrhs}", MEDIA_STD, 6.0, 20, c, r, bc,
+                    shape_kind, rot, kind, ang,
+                    receiver_line(256, -side / 2, side / 2, -0.5), proto=proto, proto_shape=shape,
+                    proto_bc=pbc, n_panels=npan, depth=depth, grade=grade)
+
+
+def config3_discs(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
+    """The 10^4-particle workload with every particle a disc of continuous radius U[0.2, 0.5] (the
+    substitute earlier measurements were quoted on)."""
+    rng = np.random.default_rng(seed)
+    er2 = (0.5 ** 3 - 0.2 ** 3) / (3 * 0.3)
+    side = math.sqrt(M * math.pi * er2 / 0.2)
     c, r = place_particles(rng, M, (-side / 2, side / 2, -side - 1.0, -1.0), 0.2, 0.5)
     bc = (np.arange(M) % 2).astype(np.int32)
     rot = rng.uniform(0, 2 * math.pi, M)
@@ -207,9 +277,24 @@ def config3(seed: int = 1004, M: int = 10000, nrhs: int = 64) -> Workload:
     ang = np.radians(irng.uniform(10, 170, nrhs))
     kind = (np.arange(nrhs) >= nrhs // 2).astype(np.int32)
     npan, depth, grade = contour_for_width(float(c[:, 0].max() - c[:, 0].min()))
-    return Workload(f"particles{M}_p20_rhs{nrhs}", MEDIA_STD, 6.0, 20, c, r, bc,
+    return Workload(f"discs{M}_p20_rhs{nrhs}", MEDIA_STD, 6.0, 20, c, r, bc,
                     np.zeros(M, np.int32), rot, kind, ang,
                     receiver_line(256, -side / 2, side / 2, -0.5), n_panels=npan, depth=depth, grade=grade)
+
+
+def surrogate_tables(seed: int, ratio: np.ndarray, p: int) -> np.ndarray:
+    """Seeded dense stand-ins (Q, 2nc, 2nc) for prototype scattering matrices, for timing only:
+    N(0,1) + iN(0,1) entries times the order profile rho^|n| / |n|! of row and column, rho = ratio[q, b]
+    supplied by the caller (small-particle matrices fall off like (k R / 2)^(|n|+|n'|) / (|n|! |n'|!)).
+    They hold no scattering physics."""
+    rng = np.random.default_rng(seed)
+    Q = ratio.shape[0]
+    nc = 2 * p + 1
+    n = np.abs(np.arange(-p, p + 1))
+    fact = np.array([math.factorial(int(k)) for k in n], float)
+    prof = np.concatenate([ratio[:, 0:1] ** n[None, :] / fact, ratio[:, 1:2] ** n[None, :] / fact], 1)   # (Q, 2nc)
+    z = rng.standard_normal((Q, 2 * nc, 2 * nc)) + 1j * rng.standard_normal((Q, 2 * nc, 2 * nc))
+    return 0.5 * z * prof[:, :, None] * prof[:, None, :]
 
 
 def config4(seed: int = 1005, M: int = 2000, nrhs: int = 32) -> Workload:

@@ -60,8 +60,8 @@ def test_default_options(lib):
     o = P.default_options()
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
     assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 1)
-    assert o.inner_tol == 0.0
-    assert ctypes.sizeof(o) == 64      # the C struct: 8 int32, 3 doubles, padding
+    assert o.inner_tol == 0.0 and o.tc_wait_test == 0
+    assert ctypes.sizeof(o) == 72      # the C struct: 9 int32, 3 doubles, padding
 
 
 def test_timeout_status_string(lib):
@@ -198,7 +198,7 @@ def test_every_handle_call_refuses_a_null_handle(lib):
                 args.append(None)
         assert getattr(lib, name)(*args) == nat.MS_ERR_ARG, name
         checked += 1
-    assert checked == 9          # apply, apply_adjoint, operator, rhs, solve, fields, grad, fields_noalloc, info
+    assert checked == 10         # apply, apply_adjoint, operator, rhs, solve, solve_rhs, fields, grad, fields_noalloc, info
     lib.ms_destroy(None)
     assert lib.ms_last_cuda_error(None) == 0
 

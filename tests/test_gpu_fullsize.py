@@ -1,17 +1,18 @@
-"""The benchmarked mat-vec at full size, in the launch configuration bench.py times: 10^4 particles,
-p = 20, the adapted 4800-node contour, 64 right-hand sides (bench.py's rank-0 input), FMM with 10
-particles per leaf, FP32 operator on the tensor cores.
+"""The benchmarked mat-vec at full size, in the launch configuration bench.py times: 10^4 particles
+(half discs, half stars of 32 prototypes), p = 20, the adapted 4800-node contour, 64 right-hand sides
+(bench.py's rank-0 input), FMM with 10 particles per leaf, FP32 operator on the tensor cores.  The
+star tables are the oracle's Nystrom matrices.
 
-* Sampled outputs (3 targets spread over the particle order, 3 of the 64 columns) against the FP64
-  oracle's mat-vec at those targets, for the FP64 GPU path (bar 1e-10, ten times the bar of the
-  smaller FMM and config-2 tests) and the FP32 tensor-core path.
+* Sampled outputs (3 targets spread over the particle order, two of them stars, 3 of the 64 columns)
+  against the FP64 oracle's mat-vec at those targets, for the FP64 GPU path (bar 1e-10, ten times the
+  bar of the smaller FMM tests) and the FP32 tensor-core path.
 * Every output of the FP32 tensor-core mat-vec against the FP64 GPU mat-vec.
 
-The FP32 bar here is 1e-3 in the scaled norm.  The tensor-core bar of the smaller cases (1.6e-4,
-derived from the 3xTF32 product error) is established on up to 2500 particles with the same density
-and contour growth e^3.  At full size the multipole-to-Sommerfeld contraction is four times longer,
-so this test guards against size-dependent faults (tile counts, offsets, split-K partitions), which
-give O(1) errors, without claiming the tighter bar untested.  Outputs must also be finite.
+FP32 bar: the tensor-core bar of the smaller cases, 1.6e-4 in the scaled norm (8 x the 2e-5 of FP32
+on the CUDA cores, for the 2^-21 relative error of a 3xTF32 product against 2^-24).  The contractions
+at full size are longer than in any smaller case (4800 nodes x 10^4 particles), but their error
+grows like the square root of the length for independent roundings, and the measured errors are
+printed so that the margin is on record.  Outputs must also be finite.
 """
 import math
 
@@ -19,7 +20,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
-from oracle import system
+from oracle import nystrom, system
 from oracle.media import Layered
 
 torch = pytest.importorskip("torch")
@@ -32,7 +33,7 @@ import paper_2608_26875_b300 as P  # noqa: E402
 
 TARGETS = [0, 4321, 9999]
 COLS = [0, 31, 63]
-FULL_FP32_BAR = 1e-3
+FULL_FP32_BAR = 1.6e-4
 
 
 def tau(wl):
@@ -57,16 +58,17 @@ def rel_l2(got, want):
 @pytest.fixture(scope="module")
 def full():
     wl = syn.config3()
-    assert (wl.M, wl.p) == (10000, 20)
+    assert (wl.M, wl.p) == (10000, 20) and wl.proto[4321] >= 0 and wl.proto[9999] >= 0
+    tabs = nystrom.workload_tables(wl)
     x = syn.random_coeffs(1000, wl.M, wl.p, 64)
-    s = P.Solver.from_workload(wl, leaf_target=10, tensor_cores=True)
+    s = P.Solver.from_workload(wl, proto_S=tabs, leaf_target=10, tensor_cores=True)
     assert s.n_nodes == 4800 and s.fmm_levels >= 4
     xd = torch.as_tensor(x, device="cuda")
     y32 = s.apply(xd, prec=P.MS_PREC_FP32).cpu().numpy()
     y64 = s.apply(xd, prec=P.MS_PREC_FP64).cpu().numpy()
     s.close()
     del xd
-    ref = system.Problem(wl)
+    ref = system.Problem(wl, proto_S=tabs)
     want = ref.matvec(np.ascontiguousarray(x[..., COLS]), targets=TARGETS)
     return wl, y32, y64, want
 
@@ -81,12 +83,14 @@ def test_full_size_fp64_matches_oracle_on_sampled_targets(full):
 def test_full_size_fp32_tensor_cores_matches_oracle_on_sampled_targets(full):
     wl, y32, _, want = full
     got, t = y32[TARGETS][..., COLS], tau(wl)[TARGETS]
-    assert rel_l2(got, want) <= FULL_FP32_BAR
-    assert scaled_err(got, want, t) <= FULL_FP32_BAR
+    e1, e2 = rel_l2(got, want), scaled_err(got, want, t)
+    print(f"full size FP32 tensor cores vs oracle: relative l2 {e1:.3e}, scaled {e2:.3e}")
+    assert e1 <= FULL_FP32_BAR and e2 <= FULL_FP32_BAR
 
 
 def test_full_size_fp32_tensor_cores_matches_fp64_everywhere(full):
     wl, y32, y64, _ = full
     assert np.isfinite(y32).all() and np.isfinite(y64).all()
-    assert rel_l2(y32, y64) <= FULL_FP32_BAR
-    assert scaled_err(y32, y64, tau(wl)) <= FULL_FP32_BAR
+    e1, e2 = rel_l2(y32, y64), scaled_err(y32, y64, tau(wl))
+    print(f"full size FP32 tensor cores vs FP64 everywhere: relative l2 {e1:.3e}, scaled {e2:.3e}")
+    assert e1 <= FULL_FP32_BAR and e2 <= FULL_FP32_BAR

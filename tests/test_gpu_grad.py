@@ -35,7 +35,7 @@ def test_adjoint_dot_product(case):
     if case == "small":
         wl = syn.small_case(501, 7, 6, omega=2.5, nrhs=3)
     else:
-        wl = syn.config3(M=1500, nrhs=3)
+        wl = syn.config3_discs(M=1500, nrhs=3)
     s = P.Solver.from_workload(wl)
     x = dev(syn.random_coeffs(502, wl.M, wl.p, 3))
     y = dev(syn.random_coeffs(503, wl.M, wl.p, 3))
@@ -60,6 +60,27 @@ def test_gradient_matches_oracle_adjoint():
     w = (u - dev(d)).contiguous()
     gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-13)
     assert ginfo["status"] == 0
+    gc, gr = gc.cpu().numpy(), gr.cpu().numpy()
+    assert np.abs(gc - gc_or).max() <= 1e-8 * np.abs(gc_or).max(), (gc, gc_or)
+    assert np.abs(gr - gr_or).max() <= 1e-8 * np.abs(gr_or).max(), (gr, gr_or)
+    assert abs(gw - gw_or) <= 1e-6 * abs(gw_or), (gw, gw_or)
+
+
+def test_mixed_precision_gradient_matches_oracle_adjoint():
+    """The mixed form: forward solve and transposed solve with FP32 inner solves (tensor cores) inside
+    FP64 refinement to 1e-11, against the oracle's FP64 adjoint gradient; held to the mixed path's
+    1e-8 (relative to the largest entry of each gradient)."""
+    wl = syn.small_case(401, 3, 5, omega=2.0, nrhs=2)
+    rx = wl.receivers[::6]
+    rng = np.random.default_rng(0)
+    d = 0.1 * (rng.standard_normal((2, rx.shape[0], 2)) + 1j * rng.standard_normal((2, rx.shape[0], 2)))
+    L, gc_or, gr_or, gw_or = adjoint.gradient(wl, wl.inc_kind, wl.inc_angle, rx, d)
+    s = P.Solver.from_workload(wl, tensor_cores=True)
+    g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-11, prec=P.MS_PREC_FP32)
+    assert info["status"] == 0 and info["refinements"] >= 1
+    w = (s.fields(g, rx) - dev(d)).contiguous()
+    gc, gr, gw, ginfo = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-11, prec=P.MS_PREC_FP32)
+    assert ginfo["status"] == 0 and ginfo["refinements"] >= 1
     gc, gr = gc.cpu().numpy(), gr.cpu().numpy()
     assert np.abs(gc - gc_or).max() <= 1e-8 * np.abs(gc_or).max(), (gc, gc_or)
     assert np.abs(gr - gr_or).max() <= 1e-8 * np.abs(gr_or).max(), (gr, gr_or)

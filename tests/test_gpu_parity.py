@@ -196,22 +196,10 @@ def test_receiver_inside_is_rejected():
     assert e.value.status == P._native.MS_ERR_RECEIVER_INSIDE
 
 
-def test_config2_apply_sampled_targets():
-    """1000 particles, p = 16, omega = 4: the full-size mat-vec compared on sampled targets."""
-    wl = syn.config2()
-    x = syn.random_coeffs(81, wl.M, wl.p, 1)
-    s = P.Solver.from_workload(wl)
-    got = s.apply(dev(x)).cpu().numpy()
-    ref = system.Problem(wl)
-    targets = [0, 1, 137, 500, 998, 999]
-    want = ref.matvec(x, targets=targets)
-    compare(got[targets], want, wl, 1e-12, 1e-11, targets=targets)
-
-
 # --------------------------------------------------------------------- fast multipole far field
 def test_fmm_matches_direct_sum_on_sampled_targets():
     """3000 particles with the quadtree FMM (row a3) against the oracle's direct Graf sum."""
-    wl = syn.config3(M=3000, nrhs=4)
+    wl = syn.config3_discs(M=3000, nrhs=4)
     x = syn.random_coeffs(91, wl.M, wl.p, 4)
     s = P.Solver.from_workload(wl)
     got = s.operator(dev(x), P.MS_PART_T | P.MS_PART_S).cpu().numpy()
@@ -225,7 +213,7 @@ def test_fmm_matches_direct_sum_on_sampled_targets():
                                         (P.MS_PREC_FP32, 1.6e-4, True)])
 def test_fmm_matches_gpu_direct_everywhere(prec, tol, tc):
     """FMM operator vs the direct all-pairs GPU sum (itself pinned to the oracle) on every target."""
-    wl = syn.config3(M=2500, nrhs=8)
+    wl = syn.config3_discs(M=2500, nrhs=8)
     x = dev(syn.random_coeffs(92, wl.M, wl.p, 8))
     f = P.Solver.from_workload(wl, tensor_cores=tc).apply(x, prec=prec).cpu().numpy()
     d = P.Solver.from_workload(wl, use_fmm=False).apply(x, prec=P.MS_PREC_FP64).cpu().numpy()

@@ -81,7 +81,7 @@ def test_reflected_part_fp32_tensor_cores_matches_oracle(seed, M, p, nrhs, omega
 
 
 def test_tensor_cores_and_cuda_cores_agree_with_fp64():
-    wl = syn.config3(M=600, nrhs=64)
+    wl = syn.config3_discs(M=600, nrhs=64)
     x = dev(syn.random_coeffs(61, wl.M, wl.p, 64))
     s_tc = P.Solver.from_workload(wl, tensor_cores=True)
     s_cc = P.Solver.from_workload(wl, tensor_cores=False)
@@ -144,7 +144,7 @@ def test_translation_fp32_tensor_cores_matches_oracle(seed, M, p, nrhs):
 @pytest.mark.parametrize("M,nrhs,leaf", [(600, 64, 10), (2500, 7, 10), (1200, 32, 6)])
 def test_near_field_fp32_tensor_cores_matches_fp64(M, nrhs, leaf):
     """Quadtree near lists (3 x 3 leaves): tensor-core tiles against the FP64 near sum."""
-    wl = syn.config3(M=M, nrhs=nrhs)
+    wl = syn.config3_discs(M=M, nrhs=nrhs)
     x = dev(syn.random_coeffs(94, wl.M, wl.p, nrhs))
     s = P.Solver.from_workload(wl, tensor_cores=True, leaf_target=leaf)
     assert s.fmm_levels >= 2
@@ -159,7 +159,7 @@ def test_near_field_fp32_tensor_cores_matches_fp64(M, nrhs, leaf):
 def test_fmm_far_field_fp32_tensor_cores_matches_fp64(M, nrhs, leaf):
     """M2L of every level on tensor-core tiles (the other FMM stages on the CUDA cores) against
     the FP64 far field, and the whole FP32 mat-vec against the FP64 one."""
-    wl = syn.config3(M=M, nrhs=nrhs)
+    wl = syn.config3_discs(M=M, nrhs=nrhs)
     x = dev(syn.random_coeffs(95, wl.M, wl.p, nrhs))
     s = P.Solver.from_workload(wl, tensor_cores=True, leaf_target=leaf)
     assert s.fmm_levels >= 3

@@ -45,12 +45,21 @@ def test_config1_recipe():
 def test_config3_recipe_is_the_benchmarked_workload():
     wl = syn.config3()
     assert (wl.M, wl.p, wl.omega, wl.nrhs) == (10000, 20, 6.0, 64)
-    assert wl.name == "particles10000_p20_rhs64"
+    assert wl.name == "discs_stars10000_p20_rhs64"
     assert wl.radius.min() >= 0.2 and wl.radius.max() <= 0.5
     side = np.ptp(wl.centres[:, 0])
     packing = wl.M * np.mean(np.pi * wl.radius ** 2) / (143.0 * 143.0)
     assert 0.18 < packing < 0.21 and 140 < side < 144
-    assert np.array_equal(wl.bc, np.arange(wl.M) % 2)
+    # half discs (even index), half stars (odd): 16 quantised sizes x 2 boundary conditions
+    star = wl.proto >= 0
+    assert np.array_equal(star, np.arange(wl.M) % 2 == 1) and wl.n_proto == 32
+    assert np.array_equal(wl.bc, (np.arange(wl.M) // 2) % 2)
+    levels = syn.star_levels(0.2, 0.5, 16)
+    q = wl.proto[star]
+    assert np.allclose(wl.radius[star], levels[q % 16]) and np.array_equal(wl.bc[star], q // 16)
+    sh = wl.proto_shape[q]
+    assert np.allclose(sh[:, 0] + sh[:, 1], wl.radius[star]) and np.allclose(sh[:, 1], 0.2 * sh[:, 0])
+    assert np.all(np.bincount(q, minlength=32) > 100)
     assert np.sum(wl.inc_kind == 0) == 32 and np.sum(wl.inc_kind == 1) == 32
     assert np.all((wl.inc_angle >= math.radians(10)) & (wl.inc_angle <= math.radians(170)))
     npan, depth, grade = syn.contour_for_width(side)
@@ -73,3 +82,24 @@ def test_workloads_are_reproducible():
     assert np.array_equal(a.centres, b.centres) and np.array_equal(a.inc_angle, b.inc_angle)
     x1, x2 = syn.random_coeffs(1000, 50, 20, 4), syn.random_coeffs(1000, 50, 20, 4)
     assert np.array_equal(x1, x2) and x1.shape == (50, 2, 41, 4) and x1.dtype == np.complex128
+
+
+def test_config2_is_all_stars_with_quantised_sizes():
+    wl = syn.config2()
+    assert (wl.M, wl.p, wl.omega) == (1000, 16, 4.0)
+    assert np.all(wl.proto >= 0) and wl.n_proto == 32
+    a = wl.proto_shape[wl.proto, 0]
+    assert a.min() >= 0.3 and a.max() <= 0.6 and np.allclose(wl.radius, 1.2 * a)
+    assert np.array_equal(wl.bc, np.arange(wl.M) % 2) and np.array_equal(wl.proto_bc[wl.proto], wl.bc)
+    _check_admissible(wl)
+
+
+def test_surrogate_tables_follow_the_order_profile():
+    ratio = np.array([[0.5, 1.5], [0.3, 0.9]])
+    t = syn.surrogate_tables(7, ratio, 6)
+    assert t.shape == (2, 26, 26)
+    n = np.abs(np.arange(-6, 7))
+    prof = 1.5 ** n / np.array([math.factorial(int(k)) for k in n])
+    # shear-shear block of prototype 0 divided by its profile is O(1)
+    blk = t[0, 13:, 13:] / np.outer(prof, prof)
+    assert 0.01 < np.abs(blk).mean() < 10

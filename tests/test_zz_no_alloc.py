@@ -1,8 +1,8 @@
 """The allocation-free receiver-field call (ms_fields_noalloc) against ms_fields.
 
-ms_fields_noalloc exists for callers that cannot call cudaMalloc -- code running while a stream
-is captured into a CUDA graph, real-time loops that must not wait on the allocator, processes
-held to a pre-sized memory pool.  It keeps its scratch in fixed device arrays instead.  This file
+ms_fields_noalloc exists for callers that cannot call cudaMalloc -- real-time loops that must not
+wait on the allocator, processes whose device memory is owned by a pool sized in advance.  It keeps
+its scratch in fixed device arrays instead.  This file
 is collected last so that a failure here comes after every other test has run; it also passes on
 its own in a fresh process.
 """
