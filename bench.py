@@ -341,11 +341,13 @@ def run_solve(args):
     wl = syn.config3_discs(M=args.M or 10000, nrhs=args.nrhs)
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
-                               restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol)
+                               restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol,
+                               block_krylov=not args.per_column)
     torch.cuda.synchronize()
     g, info = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
     torch.cuda.synchronize()
     out = {"mode": "solve", "workload": wl.name, "M": wl.M, "nrhs": len(kinds), "tol": 1e-8,
+           "krylov": "per-column GMRES" if args.per_column else "block GMRES over the right-hand sides",
            "restart": args.restart, "max_iters": args.max_iters, "tensor_cores": bool(args.tensor_cores),
            "inner_tol": args.inner_tol or "default",
            "mixed": info}
@@ -476,7 +478,10 @@ def main():
     ap.add_argument("--M", type=int, default=None, help="particles: --profile (default 2500), --mode solve "
                     "(default 10000), --mode grad (default 2000, the inverse-scattering workload)")
     ap.add_argument("--nrhs", type=int, default=64, help="--mode solve: right-hand sides")
-    ap.add_argument("--restart", type=int, default=50, help="--mode solve: GMRES restart length")
+    ap.add_argument("--restart", type=int, default=50, help="--mode solve/grad: GMRES restart length (block "
+                    "iterations with block GMRES)")
+    ap.add_argument("--per-column", action="store_true", help="--mode solve: one Krylov space per column "
+                    "instead of block GMRES")
     ap.add_argument("--max-iters", type=int, default=2000, help="--mode solve/grad: GMRES iteration cap")
     ap.add_argument("--tol", type=float, default=1e-8, help="--mode grad: solve tolerance")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="--mode solve: inner GMRES tolerance (0: default)")

@@ -93,7 +93,7 @@ typedef struct {
     int32_t nodes_per_panel;   /* nodes per panel (default 16); N_S = panels * nodes_per_panel, the panels
                                   being the uniform ones split at the graded edges (see grade) */
     double  t_max;             /* contour xi(t) = t - i tanh(t)/2, |t| <= t_max (Sec. 5.1; default 20) */
-    int32_t restart;           /* GMRES restart length (default 50) */
+    int32_t restart;           /* GMRES restart length (default 50; block iterations with block_krylov) */
     int32_t max_iters;         /* total GMRES iteration cap per solve (default 2000) */
     int32_t check_geometry;    /* 1 = validate separation / burial (default 1) */
     int32_t use_fmm;           /* 1 = quadtree FMM for non-adjacent leaves when M is large enough
@@ -111,6 +111,11 @@ typedef struct {
     double  inner_tol;         /* ms_solve / ms_grad: relative tolerance of each inner GMRES solve of the
                                   FP64 iterative refinement; 0 = default (1e-3 for MS_PREC_FP32,
                                   1e-7 for MS_PREC_FP64) */
+    int32_t block_krylov;      /* ms_solve / ms_solve_rhs / ms_grad: 1 = block GMRES, the right-hand sides
+                                  share one Krylov space (default); 0 = one Krylov space per column.  With
+                                  block GMRES, restart counts block iterations and the basis holds
+                                  (restart + 1) blocks of M (4p + 2) nrhs complex values (FP32 or FP64 as
+                                  the inner precision); if they do not fit, restart is halved until they do */
     int32_t tc_wait_test;      /* test hook for the tensor-core kernels' failure path (default 0 = off).
                                   n > 0: every tensor-core CTA first waits, bounded by n microseconds, on a
                                   barrier that nothing arrives at, gives up, issues no multiply, and the call

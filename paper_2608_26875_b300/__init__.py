@@ -45,7 +45,8 @@ class Solver:
                  proto_S=None, n_panels: int = 32, nodes_per_panel: int = 16, t_max: float = 20.0,
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
-                 tensor_cores: bool = True, inner_tol: float = 0.0, tc_wait_test: int = 0):
+                 tensor_cores: bool = True, inner_tol: float = 0.0, block_krylov: bool = True,
+                 tc_wait_test: int = 0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -77,6 +78,7 @@ class Solver:
         o.depth, o.grade = float(depth), int(grade)
         o.tensor_cores = int(bool(tensor_cores))
         o.inner_tol = float(inner_tol)
+        o.block_krylov = int(bool(block_krylov))
         o.tc_wait_test = int(tc_wait_test)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),

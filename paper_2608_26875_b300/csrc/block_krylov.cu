@@ -1,0 +1,636 @@
+// Block GMRES over the right-hand sides (row a8; Sec. 4.2: the coupled system is solved by GMRES).
+//
+// The plane waves of one solve share one Krylov space: with the s-column residual block R0 = V0 S0,
+//     K_j = span{V0, A V0, ..., A^j V0},  A V_{0:j} = V_{0:j+1} Hbar_j  (block Arnoldi),
+// and each column's iterate minimises its own residual over the shared space.  Every block iteration
+// costs one s-column application of the operator -- the batched mat-vec -- so a block iteration
+// costs what one per-column GMRES iteration costs, and far fewer are needed when the waves excite
+// the same slowly converging multiple-scattering modes.
+//
+// Orthogonalisation is block classical Gram-Schmidt applied twice (CGS2) followed by Cholesky QR
+// applied twice (CholQR2) of the new block; the two dense contractions
+//     G = V_{0:j}^H W   (Gram, contracted over the N rows)      and      W (+)= V_{0:j} H   (update)
+// run on the tensor cores for FP32 bases (tcgen05 kind::tf32, 3xTF32, tc_pipeline.cuh) and on the CUDA
+// cores for FP64 ones.  The small dense work -- Cholesky factors, the block Householder QR of the
+// block Hessenberg matrix, the residual estimates and the final triangular solve -- runs on the host
+// in FP64, parallel over the s columns.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+#include "tc_pipeline.cuh"
+
+typedef std::complex<double> cd;
+
+namespace {
+
+using tcp::KCC;
+using tcp::Stage;
+
+// basis vector k = i s + r of block i, row `row`: V + (i N + row) s + r
+__host__ __device__ __forceinline__ size_t vidx(int k, long long row, long long N, int s) {
+    const int i = k / s, r = k - i * s;
+    return ((size_t)i * N + row) * s + r;
+}
+
+// ------------------------------------------------------------------ tensor cores (FP32 bases)
+// Gram: part[split][k][r] = sum_{row in split} conj(V_k[row]) W[row][r]; tile = 256 basis vectors.
+struct GramPolicy {
+    static constexpr bool kStaged = false;
+    const float2* V;
+    const float2* W;
+    double2* part;
+    long long N, row0, row1;
+    int s, nb, k0, split;
+    int k;
+    bool valid;
+    float2 ya[4];
+    float2 vb[8];
+
+    __device__ void init() {
+        k = k0 + tcp::brow();
+        valid = k < nb;
+    }
+    __device__ void fetch(int c) {
+        const int r = tcp::arow() & 63;
+        const long long ra = row0 + (long long)c * KCC + 4 * tcp::aq();
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            ya[v] = (r < s && ra + v < row1) ? W[(ra + v) * s + r] : make_float2(0.f, 0.f);
+        const long long rb = row0 + (long long)c * KCC + 8 * tcp::bhalf();
+#pragma unroll
+        for (int v = 0; v < 8; ++v) vb[v] = (valid && rb + v < row1) ? V[vidx(k, rb + v, N, s)] : make_float2(0.f, 0.f);
+    }
+    __device__ void build(const Stage& st) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, make_float2(vb[2 * u].x, -vb[2 * u].y),
+                       make_float2(vb[2 * u + 1].x, -vb[2 * u + 1].y));
+    }
+    __device__ void epilogue(uint32_t tmem, bool ok) {
+        const int ncol = min(tcp::NMAX, (nb - k0 + 15) / 16 * 16);
+        tcp::for_each_acc(tmem, ncol, [&](int rp, int col, float v) {
+            const int r = rp & 63, comp = rp >> 6;
+            const int kk = k0 + col;
+            if (r >= s || kk >= nb) return;
+            reinterpret_cast<double*>(part + ((size_t)split * nb + kk) * s + r)[comp] = ok ? (double)v : 0.0;
+        });
+    }
+};
+
+__global__ void __launch_bounds__(tcp::THREADS, 1)
+k_bgram_tc(const float2* __restrict__ V, const float2* __restrict__ W, double2* __restrict__ part, long long N,
+           int s, int nb, long long rows_per_split, int* err) {
+    GramPolicy pol;
+    pol.V = V;
+    pol.W = W;
+    pol.part = part;
+    pol.N = N;
+    pol.s = s;
+    pol.nb = nb;
+    pol.k0 = blockIdx.x * tcp::NMAX;
+    pol.split = blockIdx.y;
+    pol.row0 = (long long)blockIdx.y * rows_per_split;
+    pol.row1 = min(N, pol.row0 + rows_per_split);
+    pol.init();
+    const int nchunks = pol.row1 > pol.row0 ? (int)((pol.row1 - pol.row0 + KCC - 1) / KCC) : 0;
+    tcp::run(pol, nchunks, min(tcp::NMAX, (nb - pol.k0 + 15) / 16 * 16), err);
+}
+
+// Update: out[row][r] = (accumulate ? out : 0) + sign sum_k V_k[row] H[k][r]; tile = 256 rows.
+struct UpdPolicy {
+    static constexpr bool kStaged = false;
+    const float2* V;
+    const float2* H;       // [nb][s]
+    float2* out;
+    long long N, row0;
+    int s, nb, accumulate;
+    float sign;
+    long long row;
+    bool valid;
+    float2 ya[4];
+    float2 vb[8];
+
+    __device__ void init() {
+        row = row0 + tcp::brow();
+        valid = row < N;
+    }
+    __device__ void fetch(int c) {
+        const int r = tcp::arow() & 63;
+        const int ka = c * KCC + 4 * tcp::aq();
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ya[v] = (r < s && ka + v < nb) ? H[(size_t)(ka + v) * s + r] : make_float2(0.f, 0.f);
+        const int kb = c * KCC + 8 * tcp::bhalf();
+#pragma unroll
+        for (int v = 0; v < 8; ++v) vb[v] = (valid && kb + v < nb) ? V[vidx(kb + v, row, N, s)] : make_float2(0.f, 0.f);
+    }
+    __device__ void build(const Stage& st) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tcp::put_b(st, tcp::brow(), 4 * tcp::bhalf() + u, vb[2 * u], vb[2 * u + 1]);
+    }
+    __device__ void epilogue(uint32_t tmem, bool ok) {
+        if (!ok) return;
+        tcp::for_each_acc(tmem, tcp::NMAX, [&](int rp, int col, float v) {
+            const int r = rp & 63, comp = rp >> 6;
+            const long long rr = row0 + col;
+            if (r >= s || rr >= N) return;
+            float* dst = reinterpret_cast<float*>(out + rr * s + r) + comp;
+            *dst = accumulate ? *dst + sign * v : sign * v;
+        });
+    }
+};
+
+__global__ void __launch_bounds__(tcp::THREADS, 1)
+k_bupdate_tc(const float2* V, const float2* __restrict__ H, float2* out, long long N, int s, int nb,
+             int accumulate, float sign, int* err) {
+    UpdPolicy pol;
+    pol.V = V;
+    pol.H = H;
+    pol.out = out;
+    pol.N = N;
+    pol.row0 = (long long)blockIdx.x * tcp::NMAX;
+    pol.s = s;
+    pol.nb = nb;
+    pol.accumulate = accumulate;
+    pol.sign = sign;
+    pol.init();
+    tcp::run(pol, (nb + KCC - 1) / KCC, tcp::NMAX, err);
+}
+
+// ------------------------------------------------------------------ CUDA cores (FP64 and FP32 bases)
+constexpr int CC_T = 16;            // 16 x 16 threads, 4 x 4 outputs each: 64 x 64 output tile
+constexpr int CC_K = 16;            // contracted entries per staged chunk
+
+// part[split][k][r] over a 64-basis-vector x 64-column tile (k = k0 + tk + 16 a, r = tr + 16 b)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_bgram_cc(const typename CT<T>::c* __restrict__ V, const typename CT<T>::c* __restrict__ W,
+           double2* __restrict__ part, long long N, int s, int nb, long long rows_per_split) {
+    typedef typename CT<T>::c C;
+    __shared__ C Vs[CC_K][64];
+    __shared__ C Ws[CC_K][64];
+    const int k0 = blockIdx.x * 64, split = blockIdx.y;
+    const long long row0 = (long long)split * rows_per_split, row1 = min(N, row0 + rows_per_split);
+    const int tk = threadIdx.x / CC_T, tr = threadIdx.x % CC_T;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk((T)0, (T)0);
+    for (long long rc = row0; rc < row1; rc += CC_K) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < CC_K * 64; e += blockDim.x) {
+            const int rr = e / 64, q = e % 64;
+            const long long row = rc + rr;
+            const bool inrow = row < row1;
+            Vs[rr][q] = (inrow && k0 + q < nb) ? cconj(V[vidx(k0 + q, row, N, s)]) : mk((T)0, (T)0);
+            Ws[rr][q] = (inrow && q < s) ? W[row * s + q] : mk((T)0, (T)0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < CC_K; ++rr) {
+            C vv[4], ww[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) vv[a] = Vs[rr][tk + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ww[b] = Ws[rr][tr + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cfma(acc[a][b], vv[a], ww[b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int k = k0 + tk + 16 * a, r = tr + 16 * b;
+            if (k < nb && r < s) part[((size_t)split * nb + k) * s + r] = to_d(acc[a][b]);
+        }
+}
+
+// out[row][r] = (accumulate ? out : 0) + sign sum_k V_k[row] H[k][r] over a 64-row x 64-column tile
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_bupdate_cc(const typename CT<T>::c* V, const typename CT<T>::c* __restrict__ H,
+             typename CT<T>::c* out, long long N, int s, int nb, int accumulate, double sign) {
+    typedef typename CT<T>::c C;
+    __shared__ C Vs[64][CC_K + 1];
+    __shared__ C Hs[CC_K][64];
+    const long long r0 = (long long)blockIdx.x * 64;
+    const int tw = threadIdx.x / CC_T, tr = threadIdx.x % CC_T;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk((T)0, (T)0);
+    for (int kc = 0; kc < nb; kc += CC_K) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * CC_K; e += blockDim.x) {
+            const int w = e / CC_K, kk = e % CC_K;
+            const long long row = r0 + w;
+            Vs[w][kk] = (row < N && kc + kk < nb) ? V[vidx(kc + kk, row, N, s)] : mk((T)0, (T)0);
+        }
+        for (int e = threadIdx.x; e < CC_K * 64; e += blockDim.x) {
+            const int kk = e / 64, q = e % 64;
+            Hs[kk][q] = (kc + kk < nb && q < s) ? H[(size_t)(kc + kk) * s + q] : mk((T)0, (T)0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < CC_K; ++kk) {
+            C vv[4], hh[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) vv[a] = Vs[tw + 16 * a][kk];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) hh[b] = Hs[kk][tr + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cfma(acc[a][b], vv[a], hh[b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const long long row = r0 + tw + 16 * a;
+            const int r = tr + 16 * b;
+            if (row >= N || r >= s) continue;
+            double2 v = to_d(acc[a][b]);
+            v = make_double2(sign * v.x, sign * v.y);
+            C* dst = out + row * s + r;
+            *dst = accumulate ? to_c<T>(cadd(to_d(*dst), v)) : to_c<T>(v);
+        }
+}
+
+// G[k][r] = sum over splits of part[split][k][r]
+__global__ void k_bgram_sum(const double2* __restrict__ part, double2* __restrict__ G, int nsplit, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = make_double2(0, 0);
+    for (int sp = 0; sp < nsplit; ++sp) a = cadd(a, part[(size_t)sp * n + i]);
+    G[i] = a;
+}
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ host: small dense FP64 algebra
+// Upper-triangular R with G = R^H R (G Hermitian positive definite, s x s row-major); a diagonal
+// shift of shift * max diag(G) keeps the factorisation defined for (nearly) dependent blocks.
+bool chol_upper(const std::vector<cd>& G, int s, double shift, std::vector<cd>& R) {
+    double dmax = 0;
+    for (int i = 0; i < s; ++i) dmax = std::max(dmax, G[i * s + i].real());
+    const double add = shift * dmax + 1e-300;
+    R.assign((size_t)s * s, cd(0));
+    for (int i = 0; i < s; ++i) {
+        cd d = G[i * s + i] + add;
+        for (int k = 0; k < i; ++k) d -= std::conj(R[k * s + i]) * R[k * s + i];
+        if (!(d.real() > 0)) return false;
+        const double rii = sqrt(d.real());
+        R[i * s + i] = rii;
+        for (int j = i + 1; j < s; ++j) {
+            cd v = G[i * s + j];
+            for (int k = 0; k < i; ++k) v -= std::conj(R[k * s + i]) * R[k * s + j];
+            R[i * s + j] = v / rii;
+        }
+    }
+    return true;
+}
+
+// inverse of an upper-triangular s x s matrix
+void tri_inv_upper(const std::vector<cd>& R, int s, std::vector<cd>& Ri) {
+    Ri.assign((size_t)s * s, cd(0));
+    for (int j = 0; j < s; ++j) {
+        Ri[j * s + j] = 1.0 / R[j * s + j];
+        for (int i = j - 1; i >= 0; --i) {
+            cd v = 0;
+            for (int k = i + 1; k <= j; ++k) v += R[i * s + k] * Ri[k * s + j];
+            Ri[i * s + j] = -v / R[i * s + i];
+        }
+    }
+}
+
+// C = A B (s x s, row-major)
+std::vector<cd> matmul(const std::vector<cd>& A, const std::vector<cd>& B, int s) {
+    std::vector<cd> C((size_t)s * s, cd(0));
+    for (int i = 0; i < s; ++i)
+        for (int k = 0; k < s; ++k) {
+            const cd a = A[i * s + k];
+            if (a == 0.0) continue;
+            for (int j = 0; j < s; ++j) C[i * s + j] += a * B[k * s + j];
+        }
+    return C;
+}
+
+// Householder reflectors of one block step: acting on rows [j s, (j+2) s) of the block Hessenberg
+// matrix; reflector k has vector v_k (2s entries, zero above k) and factor tau_k: (I - tau v v^H).
+struct StepQR {
+    std::vector<cd> v;      // [s][2s]
+    std::vector<double> tau;
+};
+
+// y (2s entries with stride ys) -= tau v (v^H y) for every reflector of the step, in order
+void apply_step(const StepQR& q, int s, cd* y, long long ys) {
+    for (int k = 0; k < s; ++k) {
+        const cd* v = &q.v[(size_t)k * 2 * s];
+        cd d = 0;
+        for (int i = k; i < 2 * s; ++i) d += std::conj(v[i]) * y[i * ys];
+        d *= q.tau[k];
+        for (int i = k; i < 2 * s; ++i) y[i * ys] -= v[i] * d;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ the block Krylov solver
+template <typename T>
+struct BlockKrylov {
+    typedef typename CT<T>::c C;
+    ms_handle* h;
+    cudaStream_t st;
+    long long N;
+    int s, m;
+    bool tc;
+    C* V = nullptr;          // (m + 1) blocks of N x s
+    C* W = nullptr;          // N x s
+    C* Hd = nullptr;         // (m + 1) s x s coefficients of an update
+    double2* part = nullptr;
+    double2* G = nullptr;
+    int nsplit_max = 1;
+
+    ~BlockKrylov() {
+        cudaFree(V); cudaFree(W); cudaFree(Hd); cudaFree(part); cudaFree(G);
+    }
+    int init() {
+        const size_t blk = (size_t)N * s * sizeof(C);
+        nsplit_max = std::max(1, std::min(2 * 148, (int)((N + 4095) / 4096)));
+        const size_t nbmax = (size_t)(m + 1) * s;
+        // split-K partials: a launch uses nsplit <= 296 / ntile + 1 splits of its nb vectors in tiles of
+        // <= 256, so nsplit * nb <= 296 * 256 + nb + 256
+        const size_t part_cap = ((size_t)2 * 148 * tcp::NMAX + nbmax + tcp::NMAX) * s;
+        if (cudaMalloc(&V, blk * (m + 1)) != cudaSuccess || cudaMalloc(&W, blk) != cudaSuccess ||
+            cudaMalloc(&Hd, nbmax * s * sizeof(C)) != cudaSuccess ||
+            cudaMalloc(&part, part_cap * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc(&G, nbmax * s * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return MS_ERR_ALLOC;
+        }
+        return MS_OK;
+    }
+    C* blk(int i) { return V + (size_t)i * N * s; }
+
+    // out[k * s + r] = <basis_k, Wp[:, r]> for the nb basis vectors starting at block pointer Vb
+    int gram(const C* Vb, int nb, const C* Wp, std::vector<cd>& out) {
+        int nsplit;
+        if (tc) {
+            const int ntile = (nb + tcp::NMAX - 1) / tcp::NMAX;
+            nsplit = std::max(1, std::min(nsplit_max, (2 * 148 + ntile - 1) / ntile));
+            long long per = (N + nsplit - 1) / nsplit;
+            per = (per + KCC - 1) / KCC * KCC;
+            nsplit = (int)((N + per - 1) / per);
+            k_bgram_tc<<<dim3(ntile, nsplit), tcp::THREADS, tcp::SMEM, st>>>(
+                (const float2*)Vb, (const float2*)Wp, part, N, s, nb, per, h->d.tc_err);
+        } else {
+            const int ntile = (nb + 63) / 64;
+            nsplit = std::max(1, std::min(nsplit_max, (2 * 148 + ntile - 1) / ntile));
+            long long per = (N + nsplit - 1) / nsplit;
+            nsplit = (int)((N + per - 1) / per);
+            k_bgram_cc<T><<<dim3(ntile, nsplit), 256, 0, st>>>(Vb, Wp, part, N, s, nb, per);
+        }
+        const int n = nb * s;
+        k_bgram_sum<<<nblk(n, 256), 256, 0, st>>>(part, G, nsplit, n);
+        if (int rc = ms_check(h, cudaGetLastError())) return rc;
+        out.resize(n);
+        if (int rc = ms_check(h, cudaMemcpyAsync(out.data(), G, n * sizeof(double2), cudaMemcpyDeviceToHost, st)))
+            return rc;
+        if (int rc = ms_check(h, cudaStreamSynchronize(st))) return rc;
+        if (tc) return ms_spectral_tc_status(h, st);
+        return MS_OK;
+    }
+    // out (+)= sign * Vb[:, 0:nb] Hc, Hc = nb x s row-major
+    int update(const C* Vb, int nb, const std::vector<cd>& Hc, C* out, bool accumulate, double sign) {
+        std::vector<C> hc((size_t)nb * s);
+        for (size_t i = 0; i < hc.size(); ++i) hc[i] = to_c<T>(make_double2(Hc[i].real(), Hc[i].imag()));
+        if (int rc = ms_check(h, cudaMemcpyAsync(Hd, hc.data(), hc.size() * sizeof(C), cudaMemcpyHostToDevice, st)))
+            return rc;
+        if (tc)
+            k_bupdate_tc<<<nblk(N, tcp::NMAX), tcp::THREADS, tcp::SMEM, st>>>(
+                (const float2*)Vb, (const float2*)Hd, (float2*)out, N, s, nb, accumulate ? 1 : 0, (float)sign,
+                h->d.tc_err);
+        else
+            k_bupdate_cc<T><<<nblk(N, 64), 256, 0, st>>>(Vb, Hd, out, N, s, nb, accumulate ? 1 : 0, sign);
+        // (a copy from pageable host memory returns once the data are staged: hc may go out of scope)
+        return ms_check(h, cudaGetLastError());
+    }
+    // CholQR2: dst R = src with dst orthonormal (dst may equal src); returns R (s x s upper)
+    int cholqr(const C* src, C* dst, std::vector<cd>& R) {
+        const double shift = sizeof(T) == 8 ? 1e-13 : 1e-6;
+        std::vector<cd> Gm, R1, R2, Ri;
+        if (int rc = gram(src, s, src, Gm)) return rc;
+        if (!chol_upper(Gm, s, shift, R1)) return MS_ERR_BREAKDOWN;
+        tri_inv_upper(R1, s, Ri);
+        if (int rc = update(src, s, Ri, dst, false, 1.0)) return rc;
+        if (int rc = gram(dst, s, dst, Gm)) return rc;
+        if (!chol_upper(Gm, s, shift, R2)) return MS_ERR_BREAKDOWN;
+        tri_inv_upper(R2, s, Ri);
+        if (int rc = update(dst, s, Ri, dst, false, 1.0)) return rc;
+        R = matmul(R2, R1, s);
+        return MS_OK;
+    }
+};
+
+// Block GMRES(m): solve A x = b for the s columns of b; x holds the initial guess.  op(in, out)
+// applies A to an s-column block.  Stops when every column's residual estimate is <= tol ||b_c||.
+template <typename T, typename Op>
+int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename CT<T>::c* x, double tol,
+                int max_iters, bool zero_guess, int& iters_out, int& matvecs, std::vector<double>& relres) {
+    typedef typename CT<T>::c C;
+    const int s = K.s, m = K.m;
+    int rc;
+    std::vector<cd> gb;
+    if ((rc = K.gram(b, s, b, gb))) return rc;
+    std::vector<double> bn(s);
+    for (int c = 0; c < s; ++c) {
+        const double g2 = gb[(size_t)c * s + c].real();
+        bn[c] = std::isnan(g2) ? g2 : sqrt(std::max(0.0, g2));      // a NaN must not read as zero
+        if (!std::isfinite(bn[c])) return MS_ERR_NONFINITE;
+    }
+    relres.assign(s, 0.0);
+    int total = 0;
+    bool first = true;
+    while (true) {
+        // R0 = b - A x into V_0 (the first cycle of a zero initial guess needs no product)
+        if (first && zero_guess) {
+            if ((rc = ms_check(K.h, cudaMemcpyAsync(K.blk(0), b, (size_t)K.N * s * sizeof(C),
+                                                    cudaMemcpyDeviceToDevice, K.st))))
+                return rc;
+        } else {
+            if ((rc = op(x, K.W))) return rc;
+            ++matvecs;
+            if ((rc = ms_check(K.h, cudaMemcpyAsync(K.blk(0), b, (size_t)K.N * s * sizeof(C),
+                                                    cudaMemcpyDeviceToDevice, K.st))))
+                return rc;
+            std::vector<cd> I((size_t)s * s, cd(0));
+            for (int c = 0; c < s; ++c) I[(size_t)c * s + c] = 1.0;
+            if ((rc = K.update(K.W, s, I, K.blk(0), true, -1.0))) return rc;
+        }
+        first = false;
+        std::vector<cd> S0;
+        if ((rc = K.cholqr(K.blk(0), K.blk(0), S0))) return rc;
+        // transformed right-hand side of the least-squares problem: (m + 1) s x s, column-major per column c
+        const int rows_max = (m + 1) * s;
+        std::vector<cd> g((size_t)rows_max * s, cd(0));     // g[row * s + c]
+        for (int i = 0; i < s; ++i)
+            for (int c = 0; c < s; ++c) g[(size_t)i * s + c] = S0[(size_t)i * s + c];
+        bool all = true;
+        for (int c = 0; c < s; ++c) {
+            double r2 = 0;
+            for (int i = 0; i < s; ++i) r2 += std::norm(g[(size_t)i * s + c]);
+            relres[c] = bn[c] > 0 ? sqrt(r2) / bn[c] : 0.0;
+            all = all && relres[c] <= tol;
+        }
+        if (all || total >= max_iters) break;
+        std::vector<std::vector<cd>> Rcol;      // R block column j: (j + 1) s x s, row-major
+        std::vector<StepQR> qr;
+        int j = 0;
+        for (; j < m && total < max_iters; ++j) {
+            if ((rc = op(K.blk(j), K.W))) return rc;
+            ++matvecs;
+            const int nb = (j + 1) * s;
+            std::vector<cd> hcol((size_t)(nb + s) * s, cd(0));      // (j + 2) s x s
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<cd> Gp;
+                if ((rc = K.gram(K.blk(0), nb, K.W, Gp))) return rc;
+                if ((rc = K.update(K.blk(0), nb, Gp, K.W, true, -1.0))) return rc;
+                for (size_t i = 0; i < Gp.size(); ++i) hcol[i] += Gp[i];
+            }
+            std::vector<cd> Rn;
+            if ((rc = K.cholqr(K.W, K.blk(j + 1), Rn))) return rc;
+            for (int i = 0; i < s; ++i)
+                for (int c = 0; c < s; ++c) hcol[(size_t)(nb + i) * s + c] = Rn[(size_t)i * s + c];
+            ++total;
+            // previous steps' reflectors on the new block column, then this step's QR
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < s; ++c)
+                for (int i = 0; i < j; ++i) apply_step(qr[i], s, &hcol[(size_t)(i * s) * s + c], s);
+            StepQR q;
+            q.v.assign((size_t)s * 2 * s, cd(0));
+            q.tau.assign(s, 0.0);
+            cd* P = &hcol[(size_t)(j * s) * s];                     // 2s x s panel, row stride s
+            for (int k = 0; k < s; ++k) {
+                double nx = 0;
+                for (int i = k; i < 2 * s; ++i) nx += std::norm(P[(size_t)i * s + k]);
+                nx = sqrt(nx);
+                cd* v = &q.v[(size_t)k * 2 * s];
+                if (nx == 0) continue;
+                const cd x0 = P[(size_t)k * s + k];
+                const cd alpha = -(std::abs(x0) > 0 ? x0 / std::abs(x0) : cd(1.0)) * nx;
+                for (int i = k; i < 2 * s; ++i) v[i] = P[(size_t)i * s + k];
+                v[k] -= alpha;
+                double vn = 0;
+                for (int i = k; i < 2 * s; ++i) vn += std::norm(v[i]);
+                if (vn == 0) continue;
+                q.tau[k] = 2.0 / vn;
+                for (int c = k; c < s; ++c) {
+                    cd d = 0;
+                    for (int i = k; i < 2 * s; ++i) d += std::conj(v[i]) * P[(size_t)i * s + c];
+                    d *= q.tau[k];
+                    for (int i = k; i < 2 * s; ++i) P[(size_t)i * s + c] -= v[i] * d;
+                }
+            }
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < s; ++c) apply_step(q, s, &g[(size_t)(j * s) * s + c], s);
+            qr.push_back(std::move(q));
+            Rcol.emplace_back(hcol.begin(), hcol.begin() + (size_t)nb * s);
+            all = true;
+            for (int c = 0; c < s; ++c) {
+                double r2 = 0;
+                for (int i = 0; i < s; ++i) r2 += std::norm(g[(size_t)(nb + i) * s + c]);
+                relres[c] = bn[c] > 0 ? sqrt(r2) / bn[c] : 0.0;
+                if (!std::isfinite(relres[c])) return MS_ERR_NONFINITE;
+                all = all && relres[c] <= tol;
+            }
+            if (all) {
+                ++j;
+                break;
+            }
+        }
+        // x += V_{0:j} Y with R Y = g[0 : j s] (block upper-triangular back substitution per column)
+        const int nbj = j * s;
+        if (nbj > 0) {
+            std::vector<cd> Y((size_t)nbj * s, cd(0));
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < s; ++c) {
+                for (int row = nbj - 1; row >= 0; --row) {
+                    cd v = g[(size_t)row * s + c];
+                    // entries of row `row` in block columns jj >= its own block
+                    const int jb = row / s;
+                    for (int jj = jb; jj < j; ++jj) {
+                        const std::vector<cd>& Rc = Rcol[jj];
+                        for (int cc = 0; cc < s; ++cc) {
+                            const int col = jj * s + cc;
+                            if (col <= row) continue;
+                            v -= Rc[(size_t)row * s + cc] * Y[(size_t)col * s + c];
+                        }
+                    }
+                    const cd d = Rcol[jb][(size_t)row * s + (row - jb * s)];
+                    Y[(size_t)row * s + c] = d != 0.0 ? v / d : cd(0);
+                }
+            }
+            if ((rc = K.update(K.blk(0), nbj, Y, x, true, 1.0))) return rc;
+        }
+        if (all || total >= max_iters) break;
+    }
+    iters_out = total;
+    return MS_OK;
+}
+
+// Inner solve of the refinement with block GMRES (scaled basis); see ms_refine_solve.
+template <typename T>
+int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds, double tol, int max_iters,
+                   bool adjoint, int& iters, int& matvecs, std::vector<double>& relres, cudaStream_t st,
+                   void** cache) {
+    typedef typename CT<T>::c C;
+    BlockKrylov<T>* K = (BlockKrylov<T>*)*cache;
+    if (!K) {
+        int m = std::max(1, h->opt.restart);
+        while (true) {
+            K = new BlockKrylov<T>{h, st, N, nrhs, m, sizeof(T) == 4 && h->opt.tensor_cores != 0};
+            if (K->init() == MS_OK) break;
+            delete K;
+            K = nullptr;
+            if (m <= 4) return MS_ERR_ALLOC;
+            m /= 2;                     // the basis does not fit: restart more often
+        }
+        *cache = K;
+    }
+    auto op = [&](const C* in, C* out) -> int {
+        int rc = adjoint ? ms_apply_adjoint_scaled<T>(h, in, out, nrhs, st)
+                         : ms_apply_scaled<T>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+        if (rc) return rc;
+        if (sizeof(T) == 4 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
+        return MS_OK;
+    };
+    return block_gmres<T>(*K, op, (const C*)rs, (C*)ds, tol, max_iters, true, iters, matvecs, relres);
+}
+
+template <typename T>
+void ms_block_free(void* cache) {
+    delete (BlockKrylov<T>*)cache;
+}
+
+template int ms_block_inner<double>(ms_handle*, int, long long, const void*, void*, double, int, bool, int&, int&,
+                                    std::vector<double>&, cudaStream_t, void**);
+template int ms_block_inner<float>(ms_handle*, int, long long, const void*, void*, double, int, bool, int&, int&,
+                                   std::vector<double>&, cudaStream_t, void**);
+template void ms_block_free<double>(void*);
+template void ms_block_free<float>(void*);

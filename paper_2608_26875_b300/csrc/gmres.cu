@@ -183,7 +183,8 @@ struct Krylov {
         std::vector<cd> g;
         if (int rc = gram(x, 1, x, g)) return rc;
         out.resize(nrhs);
-        for (int r = 0; r < nrhs; ++r) out[r] = sqrt(std::max(0.0, g[r].real()));
+        // (a NaN inner product must stay NaN: std::max(0.0, NaN) would return 0)
+        for (int r = 0; r < nrhs; ++r) out[r] = std::isnan(g[r].real()) ? g[r].real() : sqrt(std::max(0.0, g[r].real()));
         return MS_OK;
     }
 };
@@ -365,12 +366,16 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
     }
     Krylov<double>* K64i = nullptr;
     Krylov<float>* K32 = nullptr;
-    if (prec == MS_PREC_FP64) {
-        K64i = new Krylov<double>{h, st, N, nrhs, h->opt.restart};
-        rc = K64i->init();
-    } else {
-        K32 = new Krylov<float>{h, st, N, nrhs, h->opt.restart};
-        rc = K32->init();
+    void* bk = nullptr;                      // block Krylov state (allocated by the first inner solve)
+    const bool block = h->opt.block_krylov != 0;
+    if (!rc && !block) {
+        if (prec == MS_PREC_FP64) {
+            K64i = new Krylov<double>{h, st, N, nrhs, h->opt.restart};
+            rc = K64i->init();
+        } else {
+            K32 = new Krylov<float>{h, st, N, nrhs, h->opt.restart};
+            rc = K32->init();
+        }
     }
     std::vector<double> bn, rn;
     if (!rc) rc = K64.norms(b, bn);
@@ -398,18 +403,22 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
         if (prec == MS_PREC_FP64) {
             if ((rc = ms_to_scaled(h, r, rs, nrhs, MS_PREC_FP64, st, local))) break;
             if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
-            if ((rc = gmres<double>(*K64i, op64s, (const double2*)rs, (double2*)ds, inner_tol, left, it, matvecs,
-                                    inner_res)))
-                break;
+            rc = block ? ms_block_inner<double>(h, nrhs, N, rs, ds, inner_tol, left, adjoint, it, matvecs, inner_res,
+                                                st, &bk)
+                       : gmres<double>(*K64i, op64s, (const double2*)rs, (double2*)ds, inner_tol, left, it, matvecs,
+                                       inner_res);
+            if (rc) break;
             if ((rc = ms_from_scaled(h, ds, K64.w, nrhs, MS_PREC_FP64, st, local))) break;
             std::vector<cd> one(nrhs, cd(1.0, 0.0));
             if ((rc = K64.update(K64.w, 1, x, one, -1.0))) break;       // x += D d~ (or D^-1 d~)
         } else {
             k_scale_down_f<<<nb(tot, 256), 256, 0, st>>>(r, (float2*)rs, h->d.expo, tot, nrhs, sgn);
             if ((rc = ms_check(h, cudaMemsetAsync(ds, 0, tot * esz, st)))) break;
-            if ((rc = gmres<float>(*K32, op32, (const float2*)rs, (float2*)ds, inner_tol, left, it, matvecs,
-                                   inner_res)))
-                break;
+            rc = block ? ms_block_inner<float>(h, nrhs, N, rs, ds, inner_tol, left, adjoint, it, matvecs, inner_res, st,
+                                               &bk)
+                       : gmres<float>(*K32, op32, (const float2*)rs, (float2*)ds, inner_tol, left, it, matvecs,
+                                      inner_res);
+            if (rc) break;
             if (h->opt.tensor_cores && (rc = ms_spectral_tc_status(h, st))) break;
             k_add_up_f<<<nb(tot, 256), 256, 0, st>>>(x, (const float2*)ds, h->d.expo, tot, nrhs, sgn);
         }
@@ -419,6 +428,12 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
     }
     delete K64i;
     delete K32;
+    if (bk) {
+        if (prec == MS_PREC_FP64)
+            ms_block_free<double>(bk);
+        else
+            ms_block_free<float>(bk);
+    }
     cudaFree(r); cudaFree(rs); cudaFree(ds);
     cudaStreamSynchronize(st);
     double worst = 0;

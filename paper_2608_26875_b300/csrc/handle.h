@@ -189,5 +189,11 @@ int ms_m2l_tc_tiles(ms_handle* h, int b, int lev, const std::vector<int>& ptr);
 void ms_tc_tiles_free(TcTiles& T);
 int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double tol, int prec, bool adjoint,
                     ms_solve_info* info, cudaStream_t st, bool guess = false);
+template <typename T>
+int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds, double tol, int max_iters,
+                   bool adjoint, int& iters, int& matvecs, std::vector<double>& relres, cudaStream_t st,
+                   void** cache);
+template <typename T>
+void ms_block_free(void* cache);
 int ms_from_scaled(ms_handle* h, const void* ys, void* y, int nrhs, int prec, cudaStream_t st,
                    bool local = false);
