@@ -61,6 +61,11 @@ extern "C" {
 #define MS_PREC_FP64   0   /* every operator step in FP64 */
 #define MS_PREC_FP32   1   /* translations and spectral contractions in FP32 (scaled basis); solves
                               use FP64 iterative refinement around an FP32 inner GMRES */
+#define MS_PREC_BF16   2   /* BF16-split: as MS_PREC_FP32, with the tensor-core contractions of the operator
+                              (near pairs, FMM M2L, M2S, S2L, prototype S-apply) on bf16 hi/lo operands,
+                              three products (hi hi + hi lo + lo hi) accumulated in FP32: about 2^-16
+                              relative error per product.  Needs ms_options.tensor_cores = 1
+                              (MS_ERR_UNSUPPORTED otherwise); solves refine in FP64 as for FP32 */
 
 /* ------------------------------------------------------------------ operator parts (ms_operator) */
 #define MS_PART_T      1   /* free-space particle-to-particle translation sum_{l != m} T^{ml} */

@@ -12,10 +12,10 @@ import numpy as np
 import torch
 
 from . import _native as nat
-from ._native import (MS_PART_R, MS_PART_S, MS_PART_T, MS_PART_T_FAR, MS_PART_T_NEAR, MS_PREC_FP32,
-                      MS_PREC_FP64, MsError)
+from ._native import (MS_PART_R, MS_PART_S, MS_PART_T, MS_PART_T_FAR, MS_PART_T_NEAR, MS_PREC_BF16,
+                      MS_PREC_FP32, MS_PREC_FP64, MsError)
 
-__all__ = ["Solver", "MsError", "MS_PREC_FP64", "MS_PREC_FP32", "MS_PART_T", "MS_PART_R", "MS_PART_S",
+__all__ = ["Solver", "MsError", "MS_PREC_FP64", "MS_PREC_FP32", "MS_PREC_BF16", "MS_PART_T", "MS_PART_R", "MS_PART_S",
            "MS_PART_T_NEAR", "MS_PART_T_FAR", "default_options"]
 
 

@@ -29,6 +29,7 @@ MS_ERR_TIMEOUT = -12
 
 MS_PREC_FP64 = 0
 MS_PREC_FP32 = 1
+MS_PREC_BF16 = 2
 
 MS_PART_T = 1
 MS_PART_R = 2

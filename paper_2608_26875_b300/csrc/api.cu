@@ -53,7 +53,7 @@ int ms_ensure_workspace(ms_handle* h, int nrhs) {
 
 static int check_call(ms_handle* h, const void* x, void* y, int nrhs, int prec) {
     if (!h || !x || !y || nrhs < 1) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;     // (after ms_resolve_prec)
     if (nrhs > 64) return MS_ERR_UNSUPPORTED;
     return ms_ensure_workspace(h, nrhs);
 }
@@ -75,6 +75,8 @@ static int apply_common(ms_handle* h, const void* x, void* y, int nrhs, int prec
 }
 
 extern "C" int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
+    if (!h) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     int rc = check_call(h, x, y, nrhs, prec);
     if (rc) return rc;
     return apply_common(h, x, y, nrhs, prec, MS_PART_T | MS_PART_R | MS_PART_S, true, (cudaStream_t)stream);
@@ -82,6 +84,8 @@ extern "C" int ms_apply(ms_handle* h, const void* x, void* y, int32_t nrhs, int3
 
 extern "C" int ms_operator(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, int32_t parts,
                            void* stream) {
+    if (!h) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     int rc = check_call(h, x, y, nrhs, prec);
     if (rc) return rc;
     if (parts & ~(MS_PART_T | MS_PART_R | MS_PART_S | MS_PART_T_NEAR | MS_PART_T_FAR)) return MS_ERR_ARG;

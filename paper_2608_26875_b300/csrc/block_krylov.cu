@@ -397,6 +397,7 @@ struct BlockKrylov {
             long long per = (N + nsplit - 1) / nsplit;
             per = (per + KCC - 1) / KCC * KCC;
             nsplit = (int)((N + per - 1) / per);
+            cudaFuncSetAttribute(k_bgram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
             k_bgram_tc<<<dim3(ntile, nsplit), tcp::THREADS, tcp::SMEM, st>>>(
                 (const float2*)Vb, (const float2*)Wp, part, N, s, nb, per, h->d.tc_err);
         } else {
@@ -422,11 +423,12 @@ struct BlockKrylov {
         for (size_t i = 0; i < hc.size(); ++i) hc[i] = to_c<T>(make_double2(Hc[i].real(), Hc[i].imag()));
         if (int rc = ms_check(h, cudaMemcpyAsync(Hd, hc.data(), hc.size() * sizeof(C), cudaMemcpyHostToDevice, st)))
             return rc;
-        if (tc)
+        if (tc) {
+            cudaFuncSetAttribute(k_bupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
             k_bupdate_tc<<<nblk(N, tcp::NMAX), tcp::THREADS, tcp::SMEM, st>>>(
                 (const float2*)Vb, (const float2*)Hd, (float2*)out, N, s, nb, accumulate ? 1 : 0, (float)sign,
                 h->d.tc_err);
-        else
+        } else
             k_bupdate_cc<T><<<nblk(N, 64), 256, 0, st>>>(Vb, Hd, out, N, s, nb, accumulate ? 1 : 0, sign);
         // (a copy from pageable host memory returns once the data are staged: hc may go out of scope)
         return ms_check(h, cudaGetLastError());

@@ -452,7 +452,7 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
 extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
                         ms_solve_info* info, void* stream) {
     if (!h || !inc || !gamma || !(tol > 0)) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     const int nrhs = inc->nrhs;
     if (nrhs < 1) return MS_ERR_ARG;
     if (nrhs > 64) return MS_ERR_UNSUPPORTED;
@@ -473,7 +473,7 @@ extern "C" int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32
 extern "C" int ms_solve_rhs(ms_handle* h, const void* b, int32_t nrhs, double tol, int32_t prec, void* gamma,
                             int32_t guess, ms_solve_info* info, void* stream) {
     if (!h || !b || !gamma || !(tol > 0) || nrhs < 1) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     if (nrhs > 64) return MS_ERR_UNSUPPORTED;
     return ms_refine_solve(h, (const double2*)b, (double2*)gamma, nrhs, tol, prec, false, info, (cudaStream_t)stream,
                            guess != 0);
@@ -482,7 +482,7 @@ extern "C" int ms_solve_rhs(ms_handle* h, const void* b, int32_t nrhs, double to
 // y = A^H x in the ABI basis (the transposed system of the gradient), through the adjoint kernels.
 extern "C" int ms_apply_adjoint(ms_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
     if (!h || !x || !y || nrhs < 1) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     if (nrhs > 64) return MS_ERR_UNSUPPORTED;
     int rc = ms_ensure_workspace(h, nrhs);
     if (rc) return rc;

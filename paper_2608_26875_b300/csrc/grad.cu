@@ -340,7 +340,7 @@ extern "C" int ms_grad(ms_handle* h, const ms_incidence* inc, const void* gamma_
                        int32_t R, double tol, int32_t prec, double* g_centres, double* g_radii, double* g_omega,
                        ms_solve_info* info, void* stream) {
     if (!h || !inc || !gamma_ || !w_ || !rx_ || R < 1 || !(tol > 0)) return MS_ERR_ARG;
-    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    if ((prec = ms_resolve_prec(h, prec)) < 0) return prec;
     const int nrhs = inc->nrhs;
     if (nrhs < 1) return MS_ERR_ARG;
     if (nrhs > 64) return MS_ERR_UNSUPPORTED;

@@ -121,6 +121,8 @@ struct ms_handle {
     int n_proto = 0;
     bool any_proto = false;
     int n_plist = 0;
+    int tc_kind = 0;               // operand kind of the tensor-core operator kernels in the current call:
+                                   // 0 3xTF32 (MS_PREC_FP32), 1 BF16-split (MS_PREC_BF16)
     ms_options opt{};
     MsDeviceTables d;
     std::vector<double> h_centres, h_radius, h_rot, h_protoS;
@@ -142,6 +144,19 @@ struct ms_handle {
     int last_cuda = 0;
 };
 
+// MS_PREC_BF16 runs the FP32 data path with BF16-split operands on the tensor cores: sets h->tc_kind
+// and returns the data precision (MS_PREC_FP64 or MS_PREC_FP32), or a negative status.
+inline int ms_resolve_prec(ms_handle* h, int prec) {
+    if (prec == MS_PREC_BF16) {
+        if (!h->opt.tensor_cores) return MS_ERR_UNSUPPORTED;
+        h->tc_kind = 1;
+        return MS_PREC_FP32;
+    }
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
+    h->tc_kind = 0;
+    return prec;
+}
+
 // internal helpers implemented across the .cu files
 int ms_check(ms_handle* h, cudaError_t e);
 int ms_ensure_workspace(ms_handle* h, int nrhs);
@@ -156,6 +171,7 @@ int ms_sapply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, bool iden
 template <typename T>
 int ms_apply_adjoint_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, cudaStream_t st);
 int ms_sapply_setup(ms_handle* h);
+void ms_near_tc_attributes();
 void ms_sapply_free(ms_handle* h);
 template <typename T>
 int ms_sapply_proto_launch(ms_handle* h, const void* xs, const void* as, void* ys, int nrhs, bool identity,

@@ -116,7 +116,8 @@ struct ListPolicy {
             if (++j == ns) { j = 0; ++s; }
         }
     }
-    __device__ void build(const Stage& st) {
+    template <class St>
+    __device__ void build(const St& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
 #pragma unroll
@@ -148,6 +149,7 @@ struct ListPolicy {
     }
 };
 
+template <class K>
 __global__ void __launch_bounds__(tcp::THREADS, 1) k_list_tc(ListArgs a, int* err) {
     __shared__ long long toff[MAX_TABLE];
     const int4 t = a.tiles[blockIdx.x];
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_list_tc(ListArgs a, int* er
     pol.init();
     const int n = ((t.y * nrow + 15) / 16) * 16;
     const int nchunks = (t.w * ns + KCC - 1) / KCC;
-    tcp::run(pol, nchunks, n, err);
+    tcp::run<ListPolicy, K>(pol, nchunks, n, err);
 }
 
 inline int upv(ms_handle* h, void** dst, const void* src, size_t bytes) {
@@ -176,6 +178,12 @@ inline int upv(ms_handle* h, void** dst, const void* src, size_t bytes) {
 }
 
 }  // namespace
+
+// Shared-memory limits of the tensor-core list kernels (both operand kinds), set once at setup.
+void ms_near_tc_attributes() {
+    cudaFuncSetAttribute(k_list_tc<tcp::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+    cudaFuncSetAttribute(k_list_tc<tcp::BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+}
 
 // Tiles of the FMM multipole-to-local stage for (wave b, level lev): one tile per 256-row range of
 // every box that has an interaction list; its sources are the box's M2L tasks.  Boxes without a list
@@ -214,7 +222,6 @@ void ms_tc_tiles_free(TcTiles& T) {
 int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cudaStream_t st) {
     const FmmHost& F = h->fmm;
     const int nc = h->nc;
-    cudaFuncSetAttribute(k_list_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
     for (int b = 0; b < 2; ++b) {
         ListArgs a{};
         a.in = xs + (long long)b * nc * nrhs; a.in_stride = 2LL * nc * nrhs;
@@ -227,7 +234,10 @@ int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cud
         a.tiles = F.near_tc.tile; a.ttgt = F.near_tc.tgt; a.tself = F.near_tc.self; a.tsrc = F.near_tc.src;
         a.trow = nullptr;
         a.Pd = h->p; a.Ps = h->p; a.K = 2 * h->p + 1; a.nrhs = nrhs;
-        k_list_tc<<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
+        if (h->tc_kind)
+            k_list_tc<tcp::BF16><<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
+        else
+            k_list_tc<tcp::TF32><<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
         if (int rc = ms_check(h, cudaGetLastError())) return rc;
     }
     return MS_OK;
@@ -241,7 +251,6 @@ int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* l
         return rc;
     const TcTiles& T = F.m2l_tc[b][lev];
     if (T.n == 0) return MS_OK;
-    cudaFuncSetAttribute(k_list_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
     ListArgs a{};
     a.in = mexp; a.in_stride = (long long)nd * nrhs;
     a.out = lexp; a.out_stride = (long long)nd * nrhs;
@@ -252,6 +261,9 @@ int ms_m2l_tc_launch(ms_handle* h, int b, int lev, const float2* mexp, float2* l
     a.as = F.expo[b][lev]; a.as_stride = 0;
     a.tiles = T.tile; a.ttgt = T.tgt; a.tself = T.self; a.tsrc = F.m2l[b][lev].src; a.trow = T.row;
     a.Pd = P; a.Ps = P; a.K = 2 * P; a.nrhs = nrhs;
-    k_list_tc<<<T.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
+    if (h->tc_kind)
+        k_list_tc<tcp::BF16><<<T.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
+    else
+        k_list_tc<tcp::TF32><<<T.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
     return ms_check(h, cudaGetLastError());
 }

@@ -67,7 +67,8 @@ struct SapplyPolicy {
 #pragma unroll
         for (int v = 0; v < 8; ++v) sb[v] = (j < n2 && k1 + v < n2) ? S[(size_t)j * n2 + k1 + v] : make_float2(0.f, 0.f);
     }
-    __device__ void build(const Stage& st) {
+    template <class St>
+    __device__ void build(const St& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
         const int k1 = (cur_chunk++ * KCC) + 8 * tcp::bhalf();
@@ -96,6 +97,7 @@ struct SapplyPolicy {
     }
 };
 
+template <class K>
 __global__ void __launch_bounds__(tcp::THREADS, 1)
 k_sapply_tc(const float2* __restrict__ a, const float2* __restrict__ x, float2* __restrict__ y,
             const float2* __restrict__ tab, const int* __restrict__ plist, const int* __restrict__ proto,
@@ -131,7 +133,7 @@ k_sapply_tc(const float2* __restrict__ a, const float2* __restrict__ x, float2* 
     }
     const int nchunks = (n2 + KCC - 1) / KCC;
     // (the pipeline's first barrier, after its tensor-memory allocation, publishes colf)
-    tcp::run(pol, nchunks, (n2 + 15) / 16 * 16, err);
+    tcp::run<SapplyPolicy, K>(pol, nchunks, (n2 + 15) / 16 * 16, err);
 }
 
 // ------------------------------------------------------------------ CUDA cores (FP64 / FP32)
@@ -297,8 +299,9 @@ int ms_sapply_proto_launch(ms_handle* h, const void* xs, const void* as, void* y
     }
     if (sizeof(T) == 4 && h->opt.tensor_cores) {
         const size_t smem = tcp::SMEM + (size_t)n2 * sizeof(float2);
-        cudaFuncSetAttribute(k_sapply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_sapply_tc<<<np, tcp::THREADS, smem, st>>>((const float2*)as, (const float2*)xs, (float2*)ys,
+        auto kern = h->tc_kind ? k_sapply_tc<tcp::BF16> : k_sapply_tc<tcp::TF32>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<np, tcp::THREADS, smem, st>>>((const float2*)as, (const float2*)xs, (float2*)ys,
                                                     adj ? h->d.spsH32 : h->d.sps32, h->d.plist, h->d.proto,
                                                     h->d.pref, h->d.rot, h->d.expo, h->p, nrhs, identity ? 1 : 0,
                                                     h->d.tc_err);

@@ -128,7 +128,8 @@ struct S2LPolicy {
         }
         cur = rb;
     }
-    __device__ void build(const Stage& st) {
+    template <class St>
+    __device__ void build(const St& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
         // the chunk being built is the one staged last: its buffer is raw(c) with c from the stage call
@@ -166,6 +167,7 @@ struct S2LPolicy {
     }
 };
 
+template <class K>
 __global__ void __launch_bounds__(THREADS, 1)
 k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float2* __restrict__ Qm,
          const int* __restrict__ Qe, const int* __restrict__ expo, float2* __restrict__ out, int M, int nc, int NSp,
@@ -174,7 +176,7 @@ k_s2l_tc(const float2* __restrict__ D, const float2* __restrict__ E, const float
     S2LPolicy pol{D + (size_t)b * NSp * nrhs, E + (size_t)b * M * NSp, Qm + (size_t)b * nc * NSp,
                   Qe + (size_t)b * nc * NSp, expo, out, M, nc, NSp, nrhs, b, (int)blockIdx.x * NT, accumulate, conj};
     pol.init();
-    tcp::run(pol, NSp / KCC, NT, err);
+    tcp::run<S2LPolicy, K>(pol, NSp / KCC, NT, err);
 }
 
 // ------------------------------------------------------------------ M2S-shaped launch
@@ -236,7 +238,8 @@ struct M2SPolicy {
             if (++n == nc) { n = 0; ++l; }
         }
     }
-    __device__ void build(const Stage& st) {
+    template <class St>
+    __device__ void build(const St& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
         float2 w = make_float2(0.f, 0.f);
@@ -274,6 +277,7 @@ struct M2SPolicy {
     }
 };
 
+template <class K>
 __global__ void __launch_bounds__(THREADS, 1)
 k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const float2* __restrict__ Qm,
          const int* __restrict__ Qe, const float2* __restrict__ rho, const int* __restrict__ expo,
@@ -285,7 +289,7 @@ k_m2s_tc(const float2* __restrict__ xs, const float2* __restrict__ E, const floa
                   rho + (size_t)b * NSp, expo, part, M, nc, NS, NSp, nrhs, b, (int)blockIdx.x * NT, i0, i1, split, conj};
     pol.init();
     const int nchunks = i1 > i0 ? (i1 - i0 + KCC - 1) / KCC : 0;
-    tcp::run(pol, nchunks, NT, err);
+    tcp::run<M2SPolicy, K>(pol, nchunks, NT, err);
 }
 
 // ------------------------------------------------------------------ setup-time tables
@@ -390,8 +394,9 @@ int ms_spectral_tc_setup(ms_handle* h) {
     // tc_err[0]: the timeout flag; tc_err[1]: the test hook's wait in microseconds (ms_options.tc_wait_test)
     const int flags[2] = {0, h->opt.tc_wait_test};
     cudaMemcpy(d.tc_err, flags, sizeof(flags), cudaMemcpyHostToDevice);
-    cudaFuncSetAttribute(k_s2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-    cudaFuncSetAttribute(k_m2s_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaFuncSetAttribute(k_m2s_tc<tcp::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaFuncSetAttribute(k_m2s_tc<tcp::BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    ms_near_tc_attributes();
     return ms_check(h, cudaDeviceSynchronize());
 }
 
@@ -422,10 +427,11 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
     nsplit = (rows + per - 1) / per;
     *nchunks = nsplit;
     const MsDeviceTables& d = h->d;
-    k_m2s_tc<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qpsT_m : d.qpmT_m,
-                                                             adj ? d.qpsT_e : d.qpmT_e, adj ? d.rho_s2l : d.rho_m2s,
-                                                             d.expo, (double2*)h->ws_part, M, nc, NS, NSp, nrhs, per,
-                                                             adj, d.tc_err);
+    auto kern = h->tc_kind ? k_m2s_tc<tcp::BF16> : k_m2s_tc<tcp::TF32>;
+    kern<<<dim3(ntile, nsplit, 2), THREADS, SMEM, st>>>(xs, adj ? d.es2l : d.em2s, adj ? d.qpsT_m : d.qpmT_m,
+                                                        adj ? d.qpsT_e : d.qpmT_e, adj ? d.rho_s2l : d.rho_m2s,
+                                                        d.expo, (double2*)h->ws_part, M, nc, NS, NSp, nrhs, per,
+                                                        adj, d.tc_err);
     return ms_check(h, cudaGetLastError());
 }
 
@@ -439,10 +445,11 @@ int ms_s2l_tc_launch(ms_handle* h, const double2* ud, float2* out, int nrhs, int
     if (int rc = ms_check(h, cudaGetLastError())) return rc;
     const int ntile = (M * nc + NT - 1) / NT;
     const size_t smem = SMEM + 2 * ((s2l_raw_bytes(nc) + 15) / 16 * 16);
-    cudaFuncSetAttribute(k_s2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_s2l_tc<<<dim3(ntile, 2), THREADS, smem, st>>>(uf, adj ? d.em2s : d.es2l, adj ? d.qpmT_m : d.qpsT_m,
-                                                     adj ? d.qpmT_e : d.qpsT_e, d.expo, out, M, nc, NSp, nrhs,
-                                                     accumulate, adj, d.tc_err);
+    auto kern = h->tc_kind ? k_s2l_tc<tcp::BF16> : k_s2l_tc<tcp::TF32>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<dim3(ntile, 2), THREADS, smem, st>>>(uf, adj ? d.em2s : d.es2l, adj ? d.qpmT_m : d.qpsT_m,
+                                                adj ? d.qpmT_e : d.qpsT_e, d.expo, out, M, nc, NSp, nrhs,
+                                                accumulate, adj, d.tc_err);
     return ms_check(h, cudaGetLastError());
 }
 

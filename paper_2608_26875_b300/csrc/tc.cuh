@@ -2,7 +2,8 @@
 // tensor-memory allocation, shared-memory matrix descriptors, the kind::tf32 MMA with its
 // instruction descriptor, commit to an mbarrier, tensor-memory loads, bounded mbarrier waits and the
 // fp32 -> tf32 hi/lo split used for near-FP32 products (3xTF32: a b ~ ah bh + ah bl + al bh, relative
-// error about 2^-21 per product against 2^-24 for an FP32 multiply).
+// error about 2^-21 per product against 2^-24 for an FP32 multiply); the kind::f16 MMA with bf16
+// operands and the fp32 -> bf16 hi/lo split of the BF16-split variant (3 products, about 2^-16).
 //
 // Operand layout (no swizzle, K-major): an R x K tile (R rows, K contiguous 32-bit values per row) is
 // stored as 8-row x 16-byte core matrices; core matrix (g, kk) (rows 8g..8g+7, k 4kk..4kk+3) starts at
@@ -34,6 +35,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f16 instruction descriptor with bf16 A and B: D f32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// element offset of (row, k) in a K-major no-swizzle tile of 16-bit values with K values per row:
+// core matrix = 8 rows x 16 bytes (8 values)
+__device__ __forceinline__ int kmajor_off16(int row, int k, int K) {
+    return ((row >> 3) * (K >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -45,6 +56,19 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __device__ __forceinline__ void split(float x, float& hi, float& lo) {
     hi = tf32_rna(x);
     lo = tf32_rna(x - hi);
+}
+// Two values as a packed pair of bf16 (round to nearest even), low half = a.
+__device__ __forceinline__ uint32_t bf16x2(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
+// (a, b) ~ hi + lo with hi, lo bf16 pairs: |x - hi - lo| <= 2^-17 |x| per value
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t& hi, uint32_t& lo) {
+    hi = bf16x2(a, b);
+    lo = bf16x2(a - bf16_lo(hi), b - bf16_hi(hi));
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -97,6 +121,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// D[tmem] (+)= A[smem] B[smem]^T with bf16 operands (kind::f16, K = 16), issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }

@@ -38,12 +38,40 @@ __device__ __forceinline__ unsigned char* raw_base() {
     return smem + (size_t)NSTAGE * (2 * MA * KC * 4 + 2 * NMAX * KC * 4) + 64;
 }
 
-struct Stage {
-    float *ah, *al, *bh, *bl;
+// Operand kinds.  TF32: 32-bit tf32 hi/lo tiles, kind::tf32 (K = 8 per MMA).  BF16: 16-bit bf16 hi/lo
+// tiles, kind::f16 with bf16 inputs (K = 16 per MMA), half the tile bytes; the BF16-split variant.
+// Both keep the TF32 stage stride, so that the shared-memory map (barriers, raw buffers) is one.
+struct TF32 {
+    static constexpr int ELEM = 4;
+    static constexpr int KMMA = 8;
+    static constexpr uint32_t SBO_ = (KC / 4) * 128;     // 8-row groups: K / 4 core matrices apart
+    __device__ static uint32_t idesc(int M, int N) { return tc::idesc_tf32(M, N); }
+    __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+        tc::mma_tf32(d, a, b, id, acc);
+    }
 };
-__device__ __forceinline__ Stage stage_ptrs(unsigned char* base, int s) {
-    float* p = reinterpret_cast<float*>(base + (size_t)s * STAGE);
-    return {p, p + MA * KC, p + 2 * MA * KC, p + 2 * MA * KC + NMAX * KC};
+struct BF16 {
+    static constexpr int ELEM = 2;
+    static constexpr int KMMA = 16;
+    static constexpr uint32_t SBO_ = (KC / 8) * 128;
+    __device__ static uint32_t idesc(int M, int N) { return tc::idesc_bf16(M, N); }
+    __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+        tc::mma_bf16(d, a, b, id, acc);
+    }
+};
+
+template <class K>
+struct StageT {
+    K* kind_tag;           // (type carrier only)
+    unsigned char *ah, *al, *bh, *bl;
+};
+typedef StageT<TF32> Stage;
+
+template <class K>
+__device__ __forceinline__ StageT<K> stage_ptrs(unsigned char* base, int s) {
+    unsigned char* p = base + (size_t)s * STAGE;
+    const size_t at = (size_t)MA * KC * K::ELEM, bt = (size_t)NMAX * KC * K::ELEM;
+    return {nullptr, p, p + at, p + 2 * at, p + 2 * at + bt};
 }
 
 __device__ __forceinline__ void put4(float* hi, float* lo, int off, float a, float b, float c, float d) {
@@ -56,17 +84,40 @@ __device__ __forceinline__ void put4(float* hi, float* lo, int off, float a, flo
     *reinterpret_cast<float4*>(lo + off) = l;
 }
 
+// four consecutive K values of one row as bf16 hi and lo (8 bytes each)
+__device__ __forceinline__ void put4_bf16(unsigned char* hi, unsigned char* lo, int off, float a, float b, float c,
+                                          float d) {
+    uint2 h, l;
+    tc::split_bf16(a, b, h.x, l.x);
+    tc::split_bf16(c, d, h.y, l.y);
+    *reinterpret_cast<uint2*>(hi + 2 * off) = h;
+    *reinterpret_cast<uint2*>(lo + 2 * off) = l;
+}
+
 // A row rp (= r or 64 + r) of k-group kk from two consecutive complex values y0, y1 of column r
-__device__ __forceinline__ void put_a(const Stage& st, int rp, int kk, float2 y0, float2 y1) {
+__device__ __forceinline__ void put_a(const StageT<TF32>& st, int rp, int kk, float2 y0, float2 y1) {
     const int off = tc::kmajor_off(rp, 4 * kk, KC);
+    float* ah = reinterpret_cast<float*>(st.ah);
+    float* al = reinterpret_cast<float*>(st.al);
     if (rp < 64)
-        put4(st.ah, st.al, off, y0.x, -y0.y, y1.x, -y1.y);
+        put4(ah, al, off, y0.x, -y0.y, y1.x, -y1.y);
     else
-        put4(st.ah, st.al, off, y0.y, y0.x, y1.y, y1.x);
+        put4(ah, al, off, y0.y, y0.x, y1.y, y1.x);
+}
+__device__ __forceinline__ void put_a(const StageT<BF16>& st, int rp, int kk, float2 y0, float2 y1) {
+    const int off = tc::kmajor_off16(rp, 4 * kk, KC);
+    if (rp < 64)
+        put4_bf16(st.ah, st.al, off, y0.x, -y0.y, y1.x, -y1.y);
+    else
+        put4_bf16(st.ah, st.al, off, y0.y, y0.x, y1.y, y1.x);
 }
 // B row j of k-group kk from two consecutive complex operator entries
-__device__ __forceinline__ void put_b(const Stage& st, int j, int kk, float2 z0, float2 z1) {
-    put4(st.bh, st.bl, tc::kmajor_off(j, 4 * kk, KC), z0.x, z0.y, z1.x, z1.y);
+__device__ __forceinline__ void put_b(const StageT<TF32>& st, int j, int kk, float2 z0, float2 z1) {
+    put4(reinterpret_cast<float*>(st.bh), reinterpret_cast<float*>(st.bl), tc::kmajor_off(j, 4 * kk, KC), z0.x,
+         z0.y, z1.x, z1.y);
+}
+__device__ __forceinline__ void put_b(const StageT<BF16>& st, int j, int kk, float2 z0, float2 z1) {
+    put4_bf16(st.bh, st.bl, tc::kmajor_off16(j, 4 * kk, KC), z0.x, z0.y, z1.x, z1.y);
 }
 
 // Thread roles in building a chunk: B row brow() (one of 256) and its half bhalf() of the 16
@@ -87,7 +138,7 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // built, so their latency overlaps the MMAs in flight.  A policy with kStaged = true also has
 // stage(chunk): it stores the cooperatively fetched data of the chunk into a shared-memory raw
 // buffer (two, alternating) that build() then reads after a barrier.  Sets *err on a timed-out wait.
-template <class P>
+template <class P, class K = TF32>
 __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
@@ -95,7 +146,7 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     int* fail = reinterpret_cast<int*>(tslot + 1);
     uint64_t* probe = bar + NSTAGE + 1;            // test hook: a barrier that nothing arrives at
     const int tid = threadIdx.x;
-    const uint32_t idesc = tc::idesc_tf32(MA, n);
+    const uint32_t idesc = K::idesc(MA, n);
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) tc::mbar_init(&bar[s], 1);
         tc::mbar_init(probe, 1);
@@ -116,7 +167,7 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     for (int c = 0; c < nchunks; ++c) {
         const int s = c % NSTAGE;
         if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
-        const Stage st = stage_ptrs(smem, s);
+        const StageT<K> st = stage_ptrs<K>(smem, s);
         if constexpr (P::kStaged) {
             pol.stage(c);
             __syncthreads();
@@ -132,10 +183,11 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
             for (int pass = 0; pass < 3; ++pass) {
                 const uint32_t a0 = tc::smem_u32(pass == 2 ? st.al : st.ah);
                 const uint32_t b0 = tc::smem_u32(pass == 1 ? st.bl : st.bh);
+                // one MMA covers K::KMMA values = two core matrices (256 bytes) along K
 #pragma unroll
-                for (int ks = 0; ks < KC / 8; ++ks)
-                    tc::mma_tf32(tmem, tc::smem_desc(a0 + ks * 256, LBO, SBO), tc::smem_desc(b0 + ks * 256, LBO, SBO),
-                                 idesc, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+                for (int ks = 0; ks < KC / K::KMMA; ++ks)
+                    K::mma(tmem, tc::smem_desc(a0 + ks * 256, LBO, K::SBO_), tc::smem_desc(b0 + ks * 256, LBO, K::SBO_),
+                           idesc, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
             }
             tc::mma_commit(&bar[s]);
         }
