@@ -181,6 +181,14 @@ int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stream);
 int ms_solve(ms_handle* h, const ms_incidence* inc, double tol, int32_t prec, void* gamma,
              ms_solve_info* info, void* stream);
 
+/* b = S a0 for point forces in the upper layer (the point-source incidence of Sec. 7.2): source j at
+ * src[2j], src[2j+1] (host, y > 0) with force vector force[2j], force[2j+1] (host; unit density of the
+ * upper layer's fundamental solution).  Each source's downgoing spectrum (som1) is transmitted through
+ * the welded interface node by node on the handle's contour and expanded about every centre by the
+ * Sommerfeld-to-local map.  b: device [M][2][nc][nsrc] complex double, nsrc <= 64.  Errors: MS_ERR_ARG
+ * (a source not above the interface, non-finite input), MS_ERR_UNSUPPORTED (nsrc > 64). */
+int ms_rhs_point(ms_handle* h, const double* src, const double* force, int32_t nsrc, void* b, void* stream);
+
 /* Solve A gamma = b for a caller-supplied right-hand side b (device [M][2][nc][nrhs] complex double,
  * not modified; e.g. S a0 of ms_rhs, or the coefficients of any incident field), by the same iterative
  * refinement as ms_solve.  gamma: device, same layout; if guess != 0 it holds the initial guess on
@@ -195,6 +203,25 @@ int ms_solve_rhs(ms_handle* h, const void* b, int32_t nrhs, double tol, int32_t 
  * Errors: MS_ERR_RECEIVER_INSIDE if a receiver lies in an enclosing disc or at y >= 0. */
 int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
               void* stream);
+
+/* Scattered displacement at R receivers in the upper layer (y > 0): the particles' upgoing spectra
+ * (multipole-to-Sommerfeld, Sec. 5.4) transmitted through the welded interface (Sec. 3) node by node
+ * and summed as upgoing plane waves of the upper layer.  Same layouts as ms_fields; a receiver with
+ * y <= 0 gives MS_ERR_RECEIVER_INSIDE. */
+int ms_fields_upper(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
+                    void* stream);
+
+/* Time-reversal matrix of a mirror of n points in the upper layer (the DORT method of Sec. 7.5):
+ * trm host [n][2] (y > 0), 2n <= 64.  The 2n incident fields are point forces at the mirror points,
+ * x then y polarised (ms_rhs_point); one batched solve to tol in precision prec; the response
+ *     F[(2i + c)][(2j + d)] = component c at mirror point i of the field scattered under force e_d at point j
+ * (ms_fields_upper), and T = conj(F)^T F.  Outputs (host, any may be NULL but not all):
+ *   F   [2n][2n] complex interleaved;
+ *   eig [2n] eigenvalues of T, descending;
+ *   vec [2n][2n] complex interleaved, column k the eigenvector of eig[k] (the focusing density).
+ * Returns the solve's status (MS_OK or MS_NOT_CONVERGED) or an error. */
+int ms_time_reversal(ms_handle* h, const double* trm, int32_t n, double tol, int32_t prec, double* F, double* eig,
+                     double* vec, ms_solve_info* info, void* stream);
 
 /* Adjoint gradient of a real loss L of the receiver fields u = ms_fields(gamma) of the solution
  * gamma of ms_solve for the same incidences (the inverse-scattering use, Sec. 7.5): given

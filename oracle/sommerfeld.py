@@ -342,6 +342,49 @@ def plane_wave_incidence(kind: int, angle: float, L: Layered):
     return xi, D, E, I
 
 
+def point_force_downgoing(xi, L: Layered, z, q):
+    """Downgoing plane-wave amplitudes (I_P, I_S) per node of the upper-layer field Phi_u(x, z) q of a
+    unit-density point force q at z (z_2 > 0), valid below the source:
+        Phi_u(., z) q = -(i/(4 w^2)) [grad (q . grad) H_0(kp r) + grad_perp (q . grad_perp) H_0(ks r)],
+    with som1 below the source, H_0(k |x - z|) = (1/(i pi)) int e^{i xi (x - z_1) + s (y - z_2)} / s dxi, so that
+    d/dx -> i xi and d/dy -> s.  In the basis grad(e^{i xi x + s_p y}), grad_perp(e^{i xi x + s_s y}):
+        I_P = -(i xi q_1 + s_p q_2) e^{-i xi z_1 - s_p z_2} / (4 pi w^2 s_p),
+        I_S = -(i xi q_2 - s_s q_1) e^{-i xi z_1 - s_s z_2} / (4 pi w^2 s_s)
+    (upper-layer wavenumbers; point sources of Sec. 7.2)."""
+    sp, ss = branch_s(xi, L.kp_u), branch_s(xi, L.ks_u)
+    w2 = L.omega ** 2
+    IP = -(1j * xi * q[0] + sp * q[1]) * np.exp(-1j * xi * z[0] - sp * z[1]) / (4 * np.pi * w2 * sp)
+    IS = -(1j * xi * q[1] - ss * q[0]) * np.exp(-1j * xi * z[0] - ss * z[1]) / (4 * np.pi * w2 * ss)
+    return IP, IS
+
+
+def upper_downgoing_field(xi, W, L: Layered, I_P, I_S, X, Y):
+    """u and grad u of int I_P grad(e^{i xi x + s_p y}) + I_S grad_perp(e^{i xi x + s_s y}) dxi (upper layer)."""
+    X = np.asarray(X, float)[..., None]
+    Y = np.asarray(Y, float)[..., None]
+    sp, ss = branch_s(xi, L.kp_u), branch_s(xi, L.ks_u)
+    ep = W * I_P * np.exp(1j * xi * X + sp * Y)
+    es = W * I_S * np.exp(1j * xi * X + ss * Y)
+    ix = 1j * xi
+    u1 = (ix * ep - ss * es).sum(-1)
+    u2 = (sp * ep + ix * es).sum(-1)
+    g = [[(ix * ix * ep - ss * ix * es).sum(-1), (ix * sp * ep - ss * ss * es).sum(-1)],
+         [(sp * ix * ep + ix * ix * es).sum(-1), (sp * sp * ep + ix * ss * es).sum(-1)]]
+    return u1, u2, g
+
+
+def point_force_transmitted(xi, L: Layered, z, q):
+    """Downgoing lower-layer amplitudes (D_P, D_S) per node of the field of the upper-layer point force
+    transmitted through the welded interface (the background field of point-source incidence)."""
+    IP, IS = point_force_downgoing(xi, L, z, q)
+    DP = np.empty_like(IP)
+    DS = np.empty_like(IS)
+    for k in range(xi.size):
+        D, _ = interface_solve(xi[k], L, U=(0.0, 0.0), I=(IP[k], IS[k]))
+        DP[k], DS[k] = D
+    return DP, DS
+
+
 def local_expansion_of_plane(xi: complex, D, L: Layered, centres, p: int):
     """Incoming coefficients (M, 2, 2p+1) of D_P grad(e^{i xi x + s'_p y}) + D_S grad_perp(e^{i xi x + s'_s y})
     about every centre, by Jacobi-Anger (Sec. 5.3 ja/stm)."""

@@ -122,6 +122,44 @@ class Problem:
         """b = S a0 (right-hand side of mul2)."""
         return self.apply_S(self.incident_local(kinds, angles))
 
+    def point_source_local(self, sources, forces):
+        """Local coefficients a0 (M, 2, nc, nsrc) of point forces in the upper layer (Sec. 7.2): each
+        source's downgoing spectrum transmitted through the interface, expanded about every centre by the
+        Sommerfeld-to-local map on the problem's contour."""
+        cols = []
+        for z, q in zip(np.asarray(sources, float), np.asarray(forces, float)):
+            DP, DS = sommerfeld.point_force_transmitted(self.xi, self.L, z, q)
+            cols.append(sommerfeld.s2l(self.xi, self.W, self.L, self.centres, DP[:, None], DS[:, None], self.p)[..., 0])
+        return np.stack(cols, axis=-1)
+
+    def point_rhs(self, sources, forces):
+        """b = S a0 for upper-layer point forces."""
+        return self.apply_S(self.point_source_local(sources, forces))
+
+    def time_reversal(self, mirror):
+        """Response matrix F of a mirror in the upper layer (Sec. 7.5): column 2j + d is the solve for a
+        point force e_d at mirror point j, row 2i + c component c of its scattered field at mirror point i;
+        returns F and the eigenvalues of T = conj(F)^T F, descending (dense LU solves)."""
+        mirror = np.asarray(mirror, float)
+        n = mirror.shape[0]
+        src = np.repeat(mirror, 2, axis=0)
+        force = np.tile(np.eye(2), (n, 1))
+        gam = self.solve_lu(self.point_rhs(src, force))
+        u = self.upper_field(gam, mirror[:, 0], mirror[:, 1])        # (2n, 2, n)
+        F = u.transpose(2, 1, 0).reshape(2 * n, 2 * n)               # row 2i + c, column 2j + d
+        T = F.conj().T @ F
+        return F, np.sort(np.linalg.eigvalsh(T))[::-1]
+
+    def upper_field(self, gamma, X, Y):
+        """Scattered displacement in the upper layer at (X, Y), Y > 0: the particles' upgoing spectra
+        transmitted through the interface (Sec. 3, 5).  Returns (nrhs, 2, npts)."""
+        (_, _), (E_P, E_S) = self.interface_amplitudes(gamma)
+        out = []
+        for r in range(gamma.shape[3]):
+            u1, u2, _ = sommerfeld.upgoing_upper_field(self.xi, self.W, self.L, E_P[:, r], E_S[:, r], X, Y)
+            out.append(np.stack([u1, u2]))
+        return np.stack(out)
+
     # ------------------------------------------------------------------ solvers
     def solve_gmres(self, b, tol=1e-12, restart=200, maxit=2000):
         """Restarted GMRES (modified Gram-Schmidt, Givens rotations) per right-hand side,

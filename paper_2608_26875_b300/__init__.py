@@ -185,6 +185,45 @@ class Solver:
         return g, {"iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
                    "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
 
+    def rhs_point(self, sources, forces, stream=None) -> torch.Tensor:
+        """b = S a0 for point forces in the upper layer (ms_rhs_point): sources (n, 2) with y > 0,
+        forces (n, 2)."""
+        src = np.ascontiguousarray(sources, dtype=np.float64)
+        fo = np.ascontiguousarray(forces, dtype=np.float64)
+        if src.shape != fo.shape or src.ndim != 2 or src.shape[1] != 2:
+            raise ValueError("sources and forces must both be (n, 2)")
+        b = self.empty(int(src.shape[0]))
+        nat.check(nat.lib().ms_rhs_point(self._h, _dp(src), _dp(fo), int(src.shape[0]), ctypes.c_void_p(b.data_ptr()),
+                                         _stream(stream)), "ms_rhs_point")
+        return b
+
+    def fields_upper(self, gamma: torch.Tensor, receivers, stream=None) -> torch.Tensor:
+        """Scattered displacement (nrhs, R, 2) at receivers (R, 2) in the upper layer (ms_fields_upper)."""
+        nrhs = self._check_vec(gamma)
+        rx = torch.as_tensor(np.ascontiguousarray(receivers, dtype=np.float64), device=gamma.device)
+        R = int(rx.shape[0])
+        u = torch.empty((nrhs, R, 2), dtype=torch.complex128, device=gamma.device)
+        nat.check(nat.lib().ms_fields_upper(self._h, ctypes.c_void_p(gamma.data_ptr()), nrhs,
+                                            ctypes.c_void_p(rx.data_ptr()), R, ctypes.c_void_p(u.data_ptr()),
+                                            _stream(stream)), "ms_fields_upper")
+        return u
+
+    def time_reversal(self, mirror, tol: float = 1e-10, prec: int = MS_PREC_FP64, stream=None):
+        """DORT (ms_time_reversal) for mirror points (n, 2) in the upper layer: returns (F, eigenvalues of
+        conj(F)^T F descending, eigenvectors as columns, info) as numpy arrays."""
+        trm = np.ascontiguousarray(mirror, dtype=np.float64)
+        nr = 2 * int(trm.shape[0])
+        F = np.zeros((nr, nr), np.complex128)
+        ev = np.zeros(nr)
+        V = np.zeros((nr, nr), np.complex128)
+        info = nat.SolveInfo()
+        st = nat.check(nat.lib().ms_time_reversal(self._h, _dp(trm), int(trm.shape[0]), float(tol), prec,
+                                                  F.view(np.float64).ctypes.data_as(nat.c_dp), _dp(ev),
+                                                  V.view(np.float64).ctypes.data_as(nat.c_dp), ctypes.byref(info),
+                                                  _stream(stream)), "ms_time_reversal", allow_warning=True)
+        return F, ev, V, {"iterations": info.iterations, "refinements": info.refinements,
+                          "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
+
     def fields(self, gamma: torch.Tensor, receivers, stream=None) -> torch.Tensor:
         """Scattered displacement (nrhs, R, 2) complex128 at receivers (R, 2) in the lower layer (ms_fields)."""
         nrhs = self._check_vec(gamma)

@@ -81,10 +81,15 @@ SIGNATURES = {
     "ms_rhs": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p]),
     "ms_solve": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_double, c_int, ctypes.c_void_p,
                          ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
+    "ms_rhs_point": (c_int, [ctypes.c_void_p, c_dp, c_dp, c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ms_solve_rhs": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_double, c_int, ctypes.c_void_p, c_int,
                              ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                           ctypes.c_void_p]),
+    "ms_fields_upper": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
+                                ctypes.c_void_p]),
+    "ms_time_reversal": (c_int, [ctypes.c_void_p, c_dp, c_int, ctypes.c_double, c_int, c_dp, c_dp, c_dp,
+                                 ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_grad": (c_int, [ctypes.c_void_p, ctypes.POINTER(Incidence), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         c_int, ctypes.c_double, c_int, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), ctypes.c_void_p]),

@@ -9,6 +9,7 @@
 
 typedef std::complex<double> cd;
 bool ms_plane_wave_transmission(const ms_handle* h, int kind, double angle, double* xi_out, cd D[2]);
+bool ms_point_force_transmission(const ms_handle* h, cd xi, const double z[2], const double q[2], cd D[2]);
 
 int ms_check(ms_handle* h, cudaError_t e) {
     if (e == cudaSuccess) return MS_OK;
@@ -180,6 +181,41 @@ extern "C" int ms_rhs(ms_handle* h, const ms_incidence* inc, void* b, void* stre
     return rc;
 }
 
+// b = S a0 for point forces in the upper layer (Sec. 7.2): per node the transmitted amplitudes of each
+// source (host, FP64), then the Sommerfeld-to-local map and the scattering matrices on the device.
+extern "C" int ms_rhs_point(ms_handle* h, const double* src, const double* force, int32_t nsrc, void* b,
+                            void* stream) {
+    if (!h || !src || !force || !b || nsrc < 1) return MS_ERR_ARG;
+    if (nsrc > 64) return MS_ERR_UNSUPPORTED;
+    for (int j = 0; j < nsrc; ++j)
+        if (!std::isfinite(src[2 * j]) || !(src[2 * j + 1] > 0) || !std::isfinite(src[2 * j + 1]) ||
+            !std::isfinite(force[2 * j]) || !std::isfinite(force[2 * j + 1]))
+            return MS_ERR_ARG;
+    int rc = check_call(h, b, b, nsrc, MS_PREC_FP64);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int NS = h->NS;
+    std::vector<double2> node(NS), ud((size_t)2 * NS * nsrc);
+    if ((rc = ms_check(h, cudaMemcpy(node.data(), h->d.node, NS * sizeof(double2), cudaMemcpyDeviceToHost))))
+        return rc;
+    for (int q = 0; q < NS; ++q) {
+        const cd xi(node[q].x, node[q].y);
+        for (int r = 0; r < nsrc; ++r) {
+            cd D[2];
+            if (!ms_point_force_transmission(h, xi, src + 2 * r, force + 2 * r, D)) return MS_ERR_ARG;
+            ud[((size_t)0 * NS + q) * nsrc + r] = make_double2(D[0].real(), D[0].imag());
+            ud[((size_t)1 * NS + q) * nsrc + r] = make_double2(D[1].real(), D[1].imag());
+        }
+    }
+    if ((rc = ms_check(h, cudaMemcpyAsync(h->ws_u, ud.data(), ud.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                                          st))))
+        return rc;
+    if ((rc = ms_s2l_launch<double>(h, (const double2*)h->ws_u, h->ws_a, nsrc, h->d.expo, 0, 0, st))) return rc;
+    if ((rc = ms_sapply_scaled<double>(h, h->ws_x, h->ws_y, nsrc, false, true, st))) return rc;
+    if ((rc = ms_from_scaled(h, h->ws_y, b, nsrc, MS_PREC_FP64, st))) return rc;
+    return ms_check(h, cudaStreamSynchronize(st));
+}
+
 extern "C" int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,
                        int64_t* near_pairs) {
     if (!h) return MS_ERR_ARG;
@@ -195,7 +231,7 @@ extern "C" void ms_destroy(ms_handle* h) {
     if (!h) return;
     dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);
     dfree_t(h->d.proto); dfree_t(h->d.rot); ms_sapply_free(h); dfree_t(h->d.node); dfree_t(h->d.wq);
-    dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
+    dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.trans); dfree_t(h->d.squ); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
     dfree_t(h->d.qpm_m); dfree_t(h->d.qpm_e); dfree_t(h->d.qps_m); dfree_t(h->d.qps_e);
     dfree_t(h->d.zexp); dfree_t(h->d.dsdr);
     ms_spectral_tc_free(h);

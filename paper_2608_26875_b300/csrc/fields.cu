@@ -116,7 +116,79 @@ __global__ void k_fields_refl(const double2* __restrict__ ud, const double2* __r
     u[((size_t)r * R + k) * 2 + 1] = cadd(u[((size_t)r * R + k) * 2 + 1], u2);
 }
 
+// Upper layer: u = sum_q W_q [E_P (i xi, -s_p) e^{i xi X - s_p Y} + E_S (s_s, i xi) e^{i xi X - s_s Y}] with
+// (E_P, E_S) = T(xi)(U_P, U_S) the transmitted upgoing amplitudes (upper-layer s).
+__global__ void k_fields_upper(const double2* __restrict__ ue, const double2* __restrict__ rx,
+                               const double2* __restrict__ node, const double2* __restrict__ wq,
+                               const double2* __restrict__ squ, double2* __restrict__ u, int NS, int nrhs, int R) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * nrhs) return;
+    int k = i / nrhs, r = i % nrhs;
+    double2 x = rx[k];
+    double2 u1 = make_double2(0, 0), u2 = make_double2(0, 0);
+    for (int q = 0; q < NS; ++q) {
+        double2 xi = node[q], w = wq[q];
+        double2 ixi = make_double2(-xi.y, xi.x);
+        for (int b = 0; b < 2; ++b) {
+            double2 s = squ[q * 2 + b];
+            // exponent i xi X - s Y
+            double re = -xi.y * x.x - s.x * x.y;
+            double im = xi.x * x.x - s.y * x.y;
+            double mag = exp(re), sn, cs;
+            sincos(im, &sn, &cs);
+            double2 e = cmul(cmul(make_double2(mag * cs, mag * sn), w), ue[((size_t)b * NS + q) * nrhs + r]);
+            if (b == 0) {
+                u1 = cadd(u1, cmul(ixi, e));
+                u2 = csub(u2, cmul(s, e));
+            } else {
+                u1 = cadd(u1, cmul(s, e));
+                u2 = cadd(u2, cmul(ixi, e));
+            }
+        }
+    }
+    u[((size_t)r * R + k) * 2 + 0] = u1;
+    u[((size_t)r * R + k) * 2 + 1] = u2;
+}
+
+__global__ void k_check_upper(const double2* __restrict__ rx, int R, int* flag) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < R && !(rx[k].y > 0.0)) atomicExch(flag, 1);
+}
+
 }  // namespace
+
+// Scattered displacement at receivers in the upper layer (shared by ms_fields_upper and the time
+// reversal): multipole-to-Sommerfeld of gamma, transmission per node, the upgoing plane-wave sum.
+int ms_fields_upper_impl(ms_handle* h, const void* gamma, int nrhs, const double* rx, int R, void* u,
+                         cudaStream_t st) {
+    int rc = ms_ensure_workspace(h, nrhs);
+    if (rc) return rc;
+    int* flag = nullptr;
+    if ((rc = ms_check(h, cudaMalloc(&flag, sizeof(int))))) return rc;
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    k_check_upper<<<(R + 255) / 256, 256, 0, st>>>((const double2*)rx, R, flag);
+    int hflag = 0;
+    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    rc = ms_check(h, cudaStreamSynchronize(st));
+    cudaFree(flag);
+    if (rc) return rc;
+    if (hflag) return MS_ERR_RECEIVER_INSIDE;
+    if ((rc = ms_to_scaled(h, gamma, h->ws_x, nrhs, MS_PREC_FP64, st))) return rc;
+    int chunks = 0;
+    if ((rc = ms_m2s_launch<double>(h, h->ws_x, nrhs, h->d.expo, 0, &chunks, st))) return rc;
+    if ((rc = ms_reflect_launch(h, (const double2*)h->ws_part, chunks, (double2*)h->ws_u, nrhs, 0, st, h->d.trans)))
+        return rc;
+    k_fields_upper<<<(R * nrhs + 127) / 128, 128, 0, st>>>((const double2*)h->ws_u, (const double2*)rx, h->d.node,
+                                                           h->d.wq, h->d.squ, (double2*)u, h->NS, nrhs, R);
+    return ms_check(h, cudaGetLastError());
+}
+
+extern "C" int ms_fields_upper(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
+                               void* stream) {
+    if (!h || !gamma || !rx || !u || nrhs < 1 || R < 1) return MS_ERR_ARG;
+    if (nrhs > 64) return MS_ERR_UNSUPPORTED;
+    return ms_fields_upper_impl(h, gamma, nrhs, rx, R, u, (cudaStream_t)stream);
+}
 
 extern "C" int ms_fields(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
                          void* stream) {

@@ -87,6 +87,8 @@ struct MsDeviceTables {
     double2* sq = nullptr;         // [NS][2] s_b(xi_q), b = P, S (lower layer)
     double2* qq = nullptr;         // [NS][2] q_b = (xi_q - s_b)/k_b
     double2* refl = nullptr;       // [NS][2][2] reflection matrix R(xi_q): (U_P,U_S) -> (D_P,D_S)
+    double2* trans = nullptr;      // [NS][2][2] transmission into the upper layer: (U_P,U_S) -> (E_P,E_S)
+    double2* squ = nullptr;        // [NS][2] s_b(xi_q) of the upper layer
     double2* qpow_m2s = nullptr;   // [2][NS][nc] (-i)^n q_b^n / (i pi s_b)
     double2* qpow_s2l = nullptr;   // [2][NS][nc] i^n q_b^n W_q
     float2* qpm_m = nullptr;       // FP32 mantissa / binary exponent copies of the two tables
@@ -179,10 +181,11 @@ int ms_sapply_proto_launch(ms_handle* h, const void* xs, const void* as, void* y
 template <typename T>
 int ms_m2s_launch(ms_handle* h, const void* xs, int nrhs, const int* expo, int adj, int* nchunks, cudaStream_t st);
 int ms_reflect_launch(ms_handle* h, const double2* part, int nchunks, double2* out, int nrhs, int adj,
-                      cudaStream_t st);
+                      cudaStream_t st, const double2* table = nullptr);
 template <typename T>
 int ms_s2l_launch(ms_handle* h, const double2* ud, void* out, int nrhs, const int* expo, int adj, int accumulate,
                   cudaStream_t st);
+int ms_fields_upper_impl(ms_handle* h, const void* gamma, int nrhs, const double* rx, int R, void* u, cudaStream_t st);
 int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target);
 template <typename T>
 int ms_translate_scaled(ms_handle* h, const void* xs, int nrhs, bool near, bool far, cudaStream_t st);

@@ -418,8 +418,9 @@ int ms_m2s_launch(ms_handle* h, const void* xs_, int nrhs, const int* expo, int 
 }
 
 int ms_reflect_launch(ms_handle* h, const double2* part, int nchunks, double2* out, int nrhs, int adj,
-                      cudaStream_t st) {
-    k_reflect<<<nblk((long long)h->NS * nrhs, 256), 256, 0, st>>>(part, out, h->d.refl, nchunks, h->NS, nrhs, adj);
+                      cudaStream_t st, const double2* table) {
+    k_reflect<<<nblk((long long)h->NS * nrhs, 256), 256, 0, st>>>(part, out, table ? table : h->d.refl, nchunks, h->NS,
+                                                                  nrhs, adj);
     return ms_check(h, cudaGetLastError());
 }
 

@@ -140,6 +140,25 @@ bool ms_plane_wave_transmission(const ms_handle* h, int kind, double angle, doub
     return interface_solve(h, xi, U, In, D, E);
 }
 
+// Transmitted (lower, downgoing) amplitudes D at the node xi of the field of a unit point force q at z
+// in the upper layer (Sec. 7.2 point-source incidence).  Below the source its downgoing spectrum in the
+// basis grad(e^{i xi x + s_p y}), grad_perp(e^{i xi x + s_s y}) (upper wavenumbers) is, from som1 with
+// d/dx -> i xi, d/dy -> s applied to Phi = -(i/(4 w^2)) [grad (q.grad) H_0(kp r) + grad_perp (q.grad_perp) H_0(ks r)],
+//   I_P = -(i xi q_1 + s_p q_2) e^{-i xi z_1 - s_p z_2} / (4 pi w^2 s_p),
+//   I_S = -(i xi q_2 - s_s q_1) e^{-i xi z_1 - s_s z_2} / (4 pi w^2 s_s);
+// the welded interface then gives D.
+bool ms_point_force_transmission(const ms_handle* h, cd xi, const double z[2], const double q[2], cd D[2]) {
+    const cd I(0, 1);
+    const cd sp = branch(xi, h->kp_u), ss = branch(xi, h->ks_u);
+    const double f = 1.0 / (4.0 * M_PI * h->omega * h->omega);
+    cd In[2];
+    In[0] = -(I * xi * q[0] + sp * q[1]) * std::exp(-I * xi * z[0] - sp * z[1]) * f / sp;
+    In[1] = -(I * xi * q[1] - ss * q[0]) * std::exp(-I * xi * z[0] - ss * z[1]) * f / ss;
+    const cd U[2] = {0.0, 0.0};
+    cd E[2];
+    return interface_solve(h, xi, U, In, D, E);
+}
+
 // Disc mode matrix (Sec. 4.1; projection-formula matrix of Sec. 4.3 for rigid particles):
 // boundary displacement (rigid) or traction (traction-free) of (P coef, S coef) of mode n at r = R.
 static void disc_mode(int kind, int n, double kp, double ks, double R, int bc, double lam, double mu, cd M[4]) {
@@ -403,7 +422,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     const int npan = (int)edges.size() - 1;
     h->NS = npan * opt.nodes_per_panel;
     const int NS = h->NS;
-    std::vector<double2> node(NS), wq(NS), sq(NS * 2), qq(NS * 2), refl(NS * 4);
+    std::vector<double2> node(NS), wq(NS), sq(NS * 2), qq(NS * 2), refl(NS * 4), trans(NS * 4), squ(NS * 2);
     std::vector<double2> qpm((size_t)2 * NS * nc), qps((size_t)2 * NS * nc);
     for (int pnl = 0; pnl < npan; ++pnl) {
         double a = edges[pnl], width = edges[pnl + 1] - edges[pnl];
@@ -417,15 +436,20 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
             node[q] = d2(xi);
             wq[q] = d2(w * dxi);
             cd U[2], D[2], E[2], In[2] = {0.0, 0.0};
-            cd R[4];
+            cd R[4], Tu[4];
             for (int c = 0; c < 2; ++c) {
                 U[0] = c == 0 ? 1.0 : 0.0;
                 U[1] = c == 1 ? 1.0 : 0.0;
                 if (!interface_solve(h, xi, U, In, D, E)) { ms_destroy(h); return MS_ERR_ARG; }
                 R[0 * 2 + c] = D[0];
                 R[1 * 2 + c] = D[1];
+                Tu[0 * 2 + c] = E[0];
+                Tu[1 * 2 + c] = E[1];
             }
             for (int k = 0; k < 4; ++k) refl[(size_t)q * 4 + k] = d2(R[k]);
+            for (int k = 0; k < 4; ++k) trans[(size_t)q * 4 + k] = d2(Tu[k]);
+            squ[q * 2 + 0] = d2(branch(xi, h->kp_u));
+            squ[q * 2 + 1] = d2(branch(xi, h->ks_u));
             for (int b = 0; b < 2; ++b) {
                 double k = b ? h->ks_l : h->kp_l;
                 cd s = branch(xi, k);
@@ -461,6 +485,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         (rc = upload(h, &h->d.sq, sq.data(), sq.size())) ||
         (rc = upload(h, &h->d.qq, qq.data(), qq.size())) ||
         (rc = upload(h, &h->d.refl, refl.data(), refl.size())) ||
+        (rc = upload(h, &h->d.trans, trans.data(), trans.size())) ||
+        (rc = upload(h, &h->d.squ, squ.data(), squ.size())) ||
         (rc = upload(h, &h->d.qpow_m2s, qpm.data(), qpm.size())) ||
         (rc = upload(h, &h->d.qpow_s2l, qps.data(), qps.size()))) {
         ms_destroy(h);
