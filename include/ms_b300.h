@@ -121,6 +121,12 @@ typedef struct {
                                   block GMRES, restart counts block iterations and the basis holds
                                   (restart + 1) blocks of M (4p + 2) nrhs complex values (FP32 or FP64 as
                                   the inner precision); if they do not fit, restart is halved until they do */
+    int32_t cuda_graph;        /* 1 = the operator's kernel sequence (from the handle's scaled input workspace
+                                  to its output workspace) is captured into a CUDA graph once per column
+                                  count, precision and operator part set, and replayed on the caller's stream
+                                  by ms_apply, ms_operator, ms_apply_adjoint and the solves' inner
+                                  iterations (default 1); 0 = plain launches.  The graphs are rebuilt when
+                                  the workspace grows. */
     int32_t tc_wait_test;      /* test hook for the tensor-core kernels' failure path (default 0 = off).
                                   n > 0: every tensor-core CTA first waits, bounded by n microseconds, on a
                                   barrier that nothing arrives at, gives up, issues no multiply, and the call

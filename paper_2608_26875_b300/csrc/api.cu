@@ -29,6 +29,7 @@ static void dfree_t(X*& p) {
 
 int ms_ensure_workspace(ms_handle* h, int nrhs) {
     if (h->ws_nrhs >= nrhs) return MS_OK;
+    ms_graphs_free(h);              // captured graphs hold the old workspace addresses
     dfree(h->ws_x);
     dfree(h->ws_a);
     dfree(h->ws_y);
@@ -64,9 +65,9 @@ static int apply_common(ms_handle* h, const void* x, void* y, int nrhs, int prec
     int rc;
     if ((rc = ms_to_scaled(h, x, h->ws_x, nrhs, prec, st))) return rc;
     if (prec == MS_PREC_FP64)
-        rc = ms_apply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, parts, identity, st);
+        rc = ms_operator_ws<double>(h, nrhs, parts, identity, false, st);
     else
-        rc = ms_apply_scaled<float>(h, h->ws_x, h->ws_y, nrhs, parts, identity, st);
+        rc = ms_operator_ws<float>(h, nrhs, parts, identity, false, st);
     if (rc) return rc;
     // without S the result is a local (incoming) block, scaled the other way
     bool local = !(parts & MS_PART_S) && (parts & (MS_PART_T | MS_PART_R | MS_PART_T_NEAR | MS_PART_T_FAR));
@@ -234,6 +235,7 @@ extern "C" void ms_destroy(ms_handle* h) {
     dfree_t(h->d.sq); dfree_t(h->d.qq); dfree_t(h->d.refl); dfree_t(h->d.trans); dfree_t(h->d.squ); dfree_t(h->d.qpow_m2s); dfree_t(h->d.qpow_s2l);
     dfree_t(h->d.qpm_m); dfree_t(h->d.qpm_e); dfree_t(h->d.qps_m); dfree_t(h->d.qps_e);
     dfree_t(h->d.zexp); dfree_t(h->d.dsdr);
+    ms_graphs_free(h);
     ms_spectral_tc_free(h);
     ms_fmm_free(h);
     dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u); dfree(h->ws_uf);

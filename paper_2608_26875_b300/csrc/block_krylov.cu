@@ -616,8 +616,7 @@ int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds
         *cache = K;
     }
     auto op = [&](const C* in, C* out) -> int {
-        int rc = adjoint ? ms_apply_adjoint_scaled<T>(h, in, out, nrhs, st)
-                         : ms_apply_scaled<T>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+        int rc = ms_operator_op<T>(h, in, out, nrhs, adjoint, st);
         if (rc) return rc;
         if (sizeof(T) == 4 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
         return MS_OK;

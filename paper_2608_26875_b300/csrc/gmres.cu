@@ -338,22 +338,16 @@ int ms_refine_solve(ms_handle* h, const double2* b, double2* x, int nrhs, double
         int r2;
         if (!adjoint) {
             if ((r2 = ms_to_scaled(h, in, h->ws_x, nrhs, MS_PREC_FP64, st))) return r2;
-            if ((r2 = ms_apply_scaled<double>(h, h->ws_x, h->ws_y, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true,
-                                              st)))
-                return r2;
+            if ((r2 = ms_operator_ws<double>(h, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, false, st))) return r2;
             return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st);
         }
         if ((r2 = ms_to_scaled(h, in, h->ws_y, nrhs, MS_PREC_FP64, st, true))) return r2;
-        if ((r2 = ms_apply_adjoint_scaled<double>(h, h->ws_y, h->ws_y, nrhs, st))) return r2;
+        if ((r2 = ms_operator_ws<double>(h, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, true, st))) return r2;
         return ms_from_scaled(h, h->ws_y, out, nrhs, MS_PREC_FP64, st, true);
     };
-    auto op32 = [&](const float2* in, float2* out) -> int {
-        if (adjoint) return ms_apply_adjoint_scaled<float>(h, in, out, nrhs, st);
-        return ms_apply_scaled<float>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
-    };
+    auto op32 = [&](const float2* in, float2* out) -> int { return ms_operator_op<float>(h, in, out, nrhs, adjoint, st); };
     auto op64s = [&](const double2* in, double2* out) -> int {
-        if (adjoint) return ms_apply_adjoint_scaled<double>(h, in, out, nrhs, st);
-        return ms_apply_scaled<double>(h, in, out, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, st);
+        return ms_operator_op<double>(h, in, out, nrhs, adjoint, st);
     };
     Krylov<double> K64{h, st, N, nrhs, 1};
     double2* r = nullptr;
@@ -489,9 +483,9 @@ extern "C" int ms_apply_adjoint(ms_handle* h, const void* x, void* y, int32_t nr
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = ms_to_scaled(h, x, h->ws_y, nrhs, prec, st, true))) return rc;
     if (prec == MS_PREC_FP64)
-        rc = ms_apply_adjoint_scaled<double>(h, h->ws_y, h->ws_y, nrhs, st);
+        rc = ms_operator_ws<double>(h, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, true, st);
     else
-        rc = ms_apply_adjoint_scaled<float>(h, h->ws_y, h->ws_y, nrhs, st);
+        rc = ms_operator_ws<float>(h, nrhs, MS_PART_T | MS_PART_R | MS_PART_S, true, true, st);
     if (rc) return rc;
     if ((rc = ms_from_scaled(h, h->ws_y, y, nrhs, prec, st, true))) return rc;
     if (prec == MS_PREC_FP32 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);

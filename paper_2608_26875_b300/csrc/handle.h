@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ms_b300.h"
@@ -144,6 +146,10 @@ struct ms_handle {
     void* ws_u = nullptr;          // [2][NS][nrhs] double2 upgoing amplitudes, then reflected D
     void* ws_uf = nullptr;         // [2][NSp][nrhs] float2 copy of the reflected amplitudes (tensor cores)
     int last_cuda = 0;
+    // captured operator graphs (ms_options.cuda_graph): key (nrhs, data precision, operand kind, parts,
+    // identity / adjoint), workspace input ws_x (ws_y for the adjoint) to output ws_y
+    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
 };
 
 // MS_PREC_BF16 runs the FP32 data path with BF16-split operands on the tensor cores: sets h->tc_kind
@@ -173,6 +179,11 @@ int ms_sapply_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, bool iden
 template <typename T>
 int ms_apply_adjoint_scaled(ms_handle* h, const void* xs, void* ys, int nrhs, cudaStream_t st);
 int ms_sapply_setup(ms_handle* h);
+void ms_graphs_free(ms_handle* h);
+template <typename T>
+int ms_operator_ws(ms_handle* h, int nrhs, int parts, bool identity, bool adjoint, cudaStream_t st);
+template <typename T>
+int ms_operator_op(ms_handle* h, const void* in, void* out, int nrhs, bool adjoint, cudaStream_t st);
 void ms_near_tc_attributes();
 void ms_sapply_free(ms_handle* h);
 template <typename T>

@@ -540,3 +540,68 @@ template int ms_apply_adjoint_scaled<double>(ms_handle*, const void*, void*, int
 template int ms_apply_adjoint_scaled<float>(ms_handle*, const void*, void*, int, cudaStream_t);
 template int ms_m2s_launch<double>(ms_handle*, const void*, int, const int*, int, int*, cudaStream_t);
 template int ms_s2l_launch<double>(ms_handle*, const double2*, void*, int, const int*, int, int, cudaStream_t);
+
+// ------------------------------------------------------------------ captured operator graphs
+void ms_graphs_free(ms_handle* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+}
+
+// Workspace to workspace: ws_y = [ws_x -] [S~] (T~ + R~) ws_x for the parts (adjoint: ws_y = A~^H ws_y in
+// place), as a replay of a graph captured on the handle's private stream the first time a key is seen.
+template <typename T>
+int ms_operator_ws(ms_handle* h, int nrhs, int parts, bool identity, bool adjoint, cudaStream_t st) {
+    auto direct = [&](cudaStream_t s) -> int {
+        if (adjoint) return ms_apply_adjoint_scaled<T>(h, h->ws_y, h->ws_y, nrhs, s);
+        return ms_apply_scaled<T>(h, h->ws_x, h->ws_y, nrhs, parts, identity, s);
+    };
+    if (!h->opt.cuda_graph) return direct(st);
+    const auto key = std::make_tuple(nrhs, (int)sizeof(T), h->tc_kind, parts, (identity ? 1 : 0) + (adjoint ? 2 : 0));
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        int rc;
+        if (!h->cap_stream && (rc = ms_check(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking))))
+            return rc;
+        if ((rc = ms_check(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)))) return rc;
+        rc = direct(h->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : ms_check(h, e);
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if ((rc = ms_check(h, e2))) return rc;
+        it = h->graphs.emplace(key, ex).first;
+    }
+    return ms_check(h, cudaGraphLaunch(it->second, st));
+}
+
+// out = A~ in (or A~^H in) for scaled blocks at any address: copied through the workspace so that the
+// captured graph of the whole operator can run (two block copies against the operator's work).
+template <typename T>
+int ms_operator_op(ms_handle* h, const void* in, void* out, int nrhs, bool adjoint, cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const int parts = MS_PART_T | MS_PART_R | MS_PART_S;
+    if (!h->opt.cuda_graph) {
+        if (adjoint) return ms_apply_adjoint_scaled<T>(h, in, out, nrhs, st);
+        return ms_apply_scaled<T>(h, in, out, nrhs, parts, true, st);
+    }
+    const size_t bytes = (size_t)h->M * 2 * h->nc * nrhs * sizeof(C);
+    void* wi = adjoint ? h->ws_y : h->ws_x;
+    int rc;
+    if (in != wi && (rc = ms_check(h, cudaMemcpyAsync(wi, in, bytes, cudaMemcpyDeviceToDevice, st)))) return rc;
+    if ((rc = ms_operator_ws<T>(h, nrhs, parts, true, adjoint, st))) return rc;
+    if (out != h->ws_y) return ms_check(h, cudaMemcpyAsync(out, h->ws_y, bytes, cudaMemcpyDeviceToDevice, st));
+    return MS_OK;
+}
+
+template int ms_operator_ws<double>(ms_handle*, int, int, bool, bool, cudaStream_t);
+template int ms_operator_ws<float>(ms_handle*, int, int, bool, bool, cudaStream_t);
+template int ms_operator_op<double>(ms_handle*, const void*, void*, int, bool, cudaStream_t);
+template int ms_operator_op<float>(ms_handle*, const void*, void*, int, bool, cudaStream_t);

@@ -236,6 +236,7 @@ extern "C" void ms_default_options(ms_options* o) {
     o->tensor_cores = 1;
     o->inner_tol = 0.0;
     o->block_krylov = 1;
+    o->cuda_graph = 1;
     o->tc_wait_test = 0;
 }
 
@@ -282,7 +283,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || opt.restart < 1 || opt.max_iters < 1 ||
         opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30 ||
         (opt.tensor_cores != 0 && opt.tensor_cores != 1) || !(opt.inner_tol >= 0.0 && opt.inner_tol < 1.0) ||
-        opt.tc_wait_test < 0 || opt.tc_wait_test > 1000000 || (opt.block_krylov != 0 && opt.block_krylov != 1))
+        opt.tc_wait_test < 0 || opt.tc_wait_test > 1000000 || (opt.block_krylov != 0 && opt.block_krylov != 1) ||
+        (opt.cuda_graph != 0 && opt.cuda_graph != 1))
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {

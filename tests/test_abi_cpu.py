@@ -60,8 +60,8 @@ def test_default_options(lib):
     o = P.default_options()
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
     assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 1)
-    assert o.inner_tol == 0.0 and o.tc_wait_test == 0 and o.block_krylov == 1
-    assert ctypes.sizeof(o) == 72      # the C struct: 10 int32, 3 doubles
+    assert o.inner_tol == 0.0 and o.tc_wait_test == 0 and o.block_krylov == 1 and o.cuda_graph == 1
+    assert ctypes.sizeof(o) == 80      # the C struct: 11 int32, 3 doubles, padding
 
 
 def test_timeout_status_string(lib):
