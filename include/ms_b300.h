@@ -267,6 +267,18 @@ int ms_grad(ms_handle* h, const ms_incidence* inc, const void* gamma, const void
 int ms_fields_noalloc(ms_handle* h, const void* gamma, int32_t nrhs, const double* rx, int32_t R, void* u,
                       void* stream);
 
+/* Autotuner of the operator's launch shapes for nrhs columns in precision prec: the FMM leaf level (the
+ * candidates M / 4^L for L one below, at and one above the current level) and, for the tensor-core FP32
+ * path, the K-split size of the multipole-to-Sommerfeld contraction (1024, 2048, 4096 or 8192 rows).
+ * Every candidate is timed on this handle (median of three applications of a seeded block after a
+ * warm-up); the fastest is kept in the handle and cached for the process by (M, p, N_S, nrhs,
+ * precision, tensor cores), so that a later call for a handle of the same sizes applies the cached
+ * choice after one timing.  Rebuilding the tree reallocates the handle's translation tables.
+ * Outputs (host, may be NULL): the chosen leaf target and split size, and the time of one application
+ * in milliseconds with them.  Synchronises the stream. */
+int ms_autotune(ms_handle* h, int32_t nrhs, int32_t prec, int32_t* leaf_target, int32_t* m2s_rows,
+                double* ms_per_apply, void* stream);
+
 /* Sizes of the handle: M, p, N_S, FMM levels (0 = direct sum over all pairs) and the number of
  * ordered particle pairs summed directly.  Any output pointer may be NULL. */
 int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,

@@ -273,6 +273,18 @@ class Solver:
                                               _stream(stream)), "ms_fields_noalloc")
         return out
 
+    def autotune(self, nrhs: int = 64, prec: int = MS_PREC_FP32, stream=None):
+        """ms_autotune: time the candidate FMM leaf levels and multipole-to-Sommerfeld split sizes and keep
+        the fastest.  Returns (leaf target, rows per split, ms per application)."""
+        leaf, rows, ms = nat.c_int(), nat.c_int(), ctypes.c_double()
+        nat.check(nat.lib().ms_autotune(self._h, int(nrhs), prec, ctypes.byref(leaf), ctypes.byref(rows),
+                                        ctypes.byref(ms), _stream(stream)), "ms_autotune")
+        lev = nat.c_int()
+        npair = ctypes.c_int64()
+        nat.lib().ms_info(self._h, None, None, None, ctypes.byref(lev), ctypes.byref(npair))
+        self.fmm_levels, self.near_pairs = int(lev.value), int(npair.value)
+        return int(leaf.value), int(rows.value), float(ms.value)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             nat.lib().ms_destroy(self._h)

@@ -95,6 +95,8 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), ctypes.c_void_p]),
     "ms_fields_noalloc": (c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p, c_int, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    "ms_autotune": (c_int, [ctypes.c_void_p, c_int, c_int, c_ip, c_ip, ctypes.POINTER(ctypes.c_double),
+                            ctypes.c_void_p]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),
     "ms_destroy": (None, [ctypes.c_void_p]),
     "ms_status_string": (ctypes.c_char_p, [c_int]),

@@ -125,6 +125,7 @@ struct ms_handle {
     int n_proto = 0;
     bool any_proto = false;
     int n_plist = 0;
+    int m2s_rows = 0;              // tensor-core multipole-to-Sommerfeld: rows per K split (0: 2048)
     int tc_kind = 0;               // operand kind of the tensor-core operator kernels in the current call:
                                    // 0 3xTF32 (MS_PREC_FP32), 1 BF16-split (MS_PREC_BF16)
     ms_options opt{};

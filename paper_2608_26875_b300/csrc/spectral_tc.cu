@@ -421,7 +421,8 @@ int ms_m2s_tc_launch(ms_handle* h, const float2* xs, int nrhs, int adj, int* nch
     const int M = h->M, nc = h->nc, NS = h->NS, NSp = h->NSp;
     const int rows = M * nc;
     const int ntile = (NS + NT - 1) / NT;
-    int nsplit = std::max(1, std::min(64, (rows + 2047) / 2048));
+    const int rows_per = h->m2s_rows > 0 ? h->m2s_rows : 2048;          // ms_autotune may change it
+    int nsplit = std::max(1, std::min(64, (rows + rows_per - 1) / rows_per));
     int per = (rows + nsplit - 1) / nsplit;
     per = (per + KCC - 1) / KCC * KCC;
     nsplit = (rows + per - 1) / per;
