@@ -245,10 +245,11 @@ def run_ours(args):
     t_far = part_time(P.MS_PART_T_FAR) if solver.fmm_levels else 0.0
     t_refl = part_time(P.MS_PART_R)
     t_sapply = part_time(P.MS_PART_S)
-    nc = 2 * wl.p + 1
     pairs = solver.near_pairs
-    flops_near = pairs * 2 * nc * nc * nrhs * 8.0                     # complex MAC = 8 real flops
-    flops_refl = 2 * 2 * solver.n_nodes * wl.M * nc * nrhs * 8.0      # M2S + S2L, both waves
+    work = solver.work()                                              # complex MACs per column, by part
+    flops_near = work["near"] * nrhs * 8.0                            # complex MAC = 8 real flops
+    flops_far = work["far"] * nrhs * 8.0
+    flops_refl = work["refl"] * nrhs * 8.0
     pk, src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12                  # TFLOP/s of the FP32 CUDA-core pipes
@@ -260,6 +261,7 @@ def run_ours(args):
              "k_m2s_tc + k_reflect + k_s2l_tc (tcgen05 kind::tf32, 3xTF32)" if tc else "k_m2s + k_reflect + k_s2l")]
     name, t_dom, flops_dom, kname = max(cand, key=lambda c: c[1])
     achieved = flops_dom / t_dom / 1e12
+    part_peak = tf32_peak if tc else fp32_peak
     if tc:
         peak, bound = tf32_peak, "tensor"
         peak_src = f"TF32 dense = measured bf16 {pk.get('bf16_tflops')} TFLOP/s x 0.5 (nominal ratio); {src}"
@@ -318,6 +320,11 @@ def run_ours(args):
                 "parts_ms": {"near": t_near * 1e3, "far": t_far * 1e3, "refl": t_refl * 1e3,
                              "sapply": t_sapply * 1e3,
                              "note": "each part timed through ms_operator, staging in and out included"},
+                "parts_roofline": {
+                    k: {"tflops_algorithmic": f / 1e12, "achieved_tflops": (f / t / 1e12) if t > 0 else None,
+                        "frac": (f / t / 1e12 / part_peak) if t > 0 else None}
+                    for k, t, f in (("near", t_near, flops_near), ("far", t_far, flops_far),
+                                    ("refl", t_refl, flops_refl))},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": launches_per_step(solver, tc) * args.steps,

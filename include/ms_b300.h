@@ -284,6 +284,13 @@ int ms_autotune(ms_handle* h, int32_t nrhs, int32_t prec, int32_t* leaf_target, 
 int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,
             int64_t* near_pairs);
 
+/* Algorithmic work of one application per right-hand-side column, in complex multiply-adds (a
+ * complex multiply-add is 8 real flops): near, the directly summed near pairs (nc^2 per ordered pair and
+ * wave); far, the FMM's P2M, M2M, M2L, L2L and L2P tasks ((2P_dst + 1)(2P_src + 1) each); refl, the two
+ * spectral maps (2 waves x N_S x M x nc each); sapply, the scattering matrices ((2nc)^2 per prototype
+ * particle, 4 nc per disc).  Any output may be NULL. */
+int ms_work(const ms_handle* h, double* near, double* far, double* refl, double* sapply);
+
 /* Release every device buffer of the handle.  NULL is ignored. */
 void ms_destroy(ms_handle* h);
 

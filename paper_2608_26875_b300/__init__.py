@@ -273,6 +273,12 @@ class Solver:
                                               _stream(stream)), "ms_fields_noalloc")
         return out
 
+    def work(self):
+        """ms_work: algorithmic complex multiply-adds per column of one application, by part."""
+        v = [ctypes.c_double() for _ in range(4)]
+        nat.check(nat.lib().ms_work(self._h, *[ctypes.byref(x) for x in v]), "ms_work")
+        return dict(zip(("near", "far", "refl", "sapply"), (x.value for x in v)))
+
     def autotune(self, nrhs: int = 64, prec: int = MS_PREC_FP32, stream=None):
         """ms_autotune: time the candidate FMM leaf levels and multipole-to-Sommerfeld split sizes and keep
         the fastest.  Returns (leaf target, rows per split, ms per application)."""

@@ -228,6 +228,19 @@ extern "C" int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_no
     return MS_OK;
 }
 
+extern "C" int ms_work(const ms_handle* h, double* near, double* far, double* refl, double* sapply) {
+    if (!h) return MS_ERR_ARG;
+    const double nc = h->nc;
+    if (near) *near = h->fmm.work_near;
+    if (far) *far = h->fmm.work_far;
+    if (refl) *refl = 2.0 * 2.0 * h->NS * h->M * nc;                // M2S and S2L, both waves
+    if (sapply) {
+        const double np = h->n_plist;
+        *sapply = np * (2 * nc) * (2 * nc) + (h->M - np) * nc * 4.0;   // dense prototypes, 2 x 2 disc blocks
+    }
+    return MS_OK;
+}
+
 extern "C" void ms_destroy(ms_handle* h) {
     if (!h) return;
     dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);

@@ -450,6 +450,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
         HostList hl = nearL;
         hl.seq = seq_near[b];
         if ((rc = upload_list(h, hl, h->fmm.near[b]))) return rc;
+        h->fmm.work_near += (double)h->fmm.near[b].ntask * (2 * p + 1) * (2 * p + 1);
     }
     if (h->opt.tensor_cores) {
         // the near sequences of each wave are consecutive (the tensor-core tiles compute offsets)
@@ -548,6 +549,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
             }
             p2m.ptr[nL * nL] = (int)p2m.src.size();
             if ((rc = upload_list(h, p2m, F.p2m[b]))) return rc;
+            F.work_far += (double)F.p2m[b].ntask * (2 * F.P[b][L] + 1) * (2 * p + 1);
             // L2P: particle <- its leaf, v = x_m - c_leaf
             HostList l2p;
             l2p.ptr.assign(M + 1, 0);
@@ -560,6 +562,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
             }
             l2p.ptr[M] = M;
             if ((rc = upload_list(h, l2p, F.l2p[b]))) return rc;
+            F.work_far += (double)F.l2p[b].ntask * (2 * p + 1) * (2 * F.P[b][L] + 1);
             for (int lev = 2; lev <= L; ++lev) {
                 int n = 1 << lev;
                 double w = F.w[lev];
@@ -593,6 +596,7 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                 }
                 m2l.ptr[n * n] = (int)m2l.src.size();
                 if ((rc = upload_list(h, m2l, F.m2l[b][lev]))) return rc;
+                F.work_far += (double)F.m2l[b][lev].ntask * (2 * F.P[b][lev] + 1) * (2 * F.P[b][lev] + 1);
                 if (h->opt.tensor_cores && (rc = ms_m2l_tc_tiles(h, b, lev, m2l.ptr))) return rc;
                 if (lev < L) {
                     // M2M: parent (lev) <- children (lev+1); v = c_parent - c_child = (+-w/4, +-w/4)
@@ -632,6 +636,8 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                     l2l.ptr[nc2 * nc2] = (int)l2l.src.size();
                     if ((rc = upload_list(h, m2m, F.m2m[b][lev])) || (rc = upload_list(h, l2l, F.l2l[b][lev + 1])))
                         return rc;
+                    F.work_far += (double)(F.m2m[b][lev].ntask + F.l2l[b][lev + 1].ntask) * (2 * F.P[b][lev] + 1) *
+                                  (2 * F.P[b][lev + 1] + 1);
                 }
             }
         }
@@ -818,6 +824,7 @@ int ms_fmm_workspace(ms_handle* h, int nrhs) {
 
 void ms_fmm_free(ms_handle* h) {
     FmmHost& F = h->fmm;
+    F.work_near = F.work_far = 0;
     auto fl = [](DevList& D) { cudaFree(D.ptr); cudaFree(D.src); cudaFree(D.seq); D = DevList{}; };
     for (int b = 0; b < 2; ++b) {
         fl(F.near[b]); fl(F.p2m[b]); fl(F.l2p[b]);

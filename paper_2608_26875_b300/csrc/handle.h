@@ -67,6 +67,9 @@ struct FmmHost {
     TcTiles near_tc;
     TcTiles m2l_tc[2][13];
     long long near_seq_base[2] = {0, 0};   // near task t's sequence starts at base + t (4p + 3)
+    // algorithmic complex multiply-adds per right-hand-side column of one application (both waves):
+    // direct near pairs, and the FMM's P2M + M2M + M2L + L2L + L2P tasks
+    double work_near = 0, work_far = 0;
 };
 
 struct MsDeviceTables {

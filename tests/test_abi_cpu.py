@@ -198,8 +198,8 @@ def test_every_handle_call_refuses_a_null_handle(lib):
                 args.append(None)
         assert getattr(lib, name)(*args) == nat.MS_ERR_ARG, name
         checked += 1
-    assert checked == 14         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
-    #                              fields_upper, time_reversal, grad, fields_noalloc, autotune, info
+    assert checked == 15         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
+    #                              fields_upper, time_reversal, grad, fields_noalloc, autotune, info, work
     lib.ms_destroy(None)
     assert lib.ms_last_cuda_error(None) == 0
 
