@@ -402,8 +402,8 @@ def run_grad(args):
     rx = wl.receivers
     truth = copy.deepcopy(wl)
     truth.centres = syn.perturb_centres(wl.centres, wl.radius, 0.05, 3001)
-    st = P.Solver.from_workload(truth)
-    gt, _ = st.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP64)
+    st = P.Solver.from_workload(truth, restart=args.restart)
+    gt, _ = st.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP32)     # refined to 1e-10 in FP64
     d = st.fields(gt, rx)
     st.close()
     out = {"mode": "grad", "workload": wl.name, "M": wl.M, "nrhs": wl.nrhs, "receivers": int(rx.shape[0])}
