@@ -279,6 +279,13 @@ int ms_fields_noalloc(ms_handle* h, const void* gamma, int32_t nrhs, const doubl
 int ms_autotune(ms_handle* h, int32_t nrhs, int32_t prec, int32_t* leaf_target, int32_t* m2s_rows,
                 double* ms_per_apply, void* stream);
 
+/* Dense tensor-core rate of this GPU for the operand kind of prec (MS_PREC_FP32: kind::tf32;
+ * MS_PREC_BF16: kind::f16 with bf16 inputs), measured by a project microkernel with the operator's MMA
+ * shapes (M = 128, N = 256, K-major shared-memory operands, FP32 accumulation): one CTA per SM issues
+ * iters groups of 32-deep MMAs back to back (the current device; no handle needed).  Outputs (host):
+ * TFLOP/s counting 2 M N K flops per MMA, and the milliseconds of the timed launch (may be NULL). */
+int ms_tensor_peak(int32_t prec, int32_t iters, double* tflops, double* ms);
+
 /* Sizes of the handle: M, p, N_S, FMM levels (0 = direct sum over all pairs) and the number of
  * ordered particle pairs summed directly.  Any output pointer may be NULL. */
 int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_t* fmm_levels,

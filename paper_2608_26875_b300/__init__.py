@@ -32,6 +32,13 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def tensor_peak(prec: int = MS_PREC_FP32, iters: int = 200000):
+    """Measured dense tensor-core rate (TFLOP/s) for the operand kind of prec (ms_tensor_peak)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    nat.check(nat.lib().ms_tensor_peak(prec, int(iters), ctypes.byref(tf), ctypes.byref(ms)), "ms_tensor_peak")
+    return float(tf.value), float(ms.value)
+
+
 def default_options() -> nat.Options:
     o = nat.Options()
     nat.lib().ms_default_options(ctypes.byref(o))

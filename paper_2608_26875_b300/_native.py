@@ -99,6 +99,7 @@ SIGNATURES = {
                             ctypes.c_void_p]),
     "ms_work": (c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ms_tensor_peak": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),
     "ms_destroy": (None, [ctypes.c_void_p]),
     "ms_status_string": (ctypes.c_char_p, [c_int]),

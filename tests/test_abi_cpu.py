@@ -182,7 +182,8 @@ def test_every_handle_call_refuses_a_null_handle(lib):
     NULL, sizes 1) without touching memory; ms_destroy(NULL) is a no-op and ms_last_cuda_error(NULL)
     is 0."""
     from paper_2608_26875_b300 import _native as nat
-    skip = {"ms_default_options", "ms_setup", "ms_status_string", "ms_destroy", "ms_last_cuda_error"}
+    skip = {"ms_default_options", "ms_setup", "ms_status_string", "ms_destroy", "ms_last_cuda_error",
+            "ms_tensor_peak"}
     checked = 0
     for name, (restype, argtypes) in nat.SIGNATURES.items():
         if name in skip:
@@ -212,3 +213,14 @@ def test_every_declared_status_has_its_own_message(lib):
     for c, m in msgs.items():
         assert m and m != b"unknown status", (codes[c], m)
     assert len(set(msgs.values())) == len(msgs)
+
+
+def test_tensor_peak_refuses_invalid_arguments(lib):
+    """ms_tensor_peak takes no handle; it refuses an unknown operand kind, a non-positive count and a
+    NULL output before touching the device."""
+    import ctypes as ct
+    from paper_2608_26875_b300 import _native as nat
+    out = ct.c_double()
+    assert lib.ms_tensor_peak(0, 10, ct.byref(out), None) == nat.MS_ERR_ARG      # FP64 has no tensor kind here
+    assert lib.ms_tensor_peak(1, 0, ct.byref(out), None) == nat.MS_ERR_ARG
+    assert lib.ms_tensor_peak(1, 10, None, None) == nat.MS_ERR_ARG

@@ -30,3 +30,12 @@ def test_autotune_keeps_the_operator_and_caches_its_choice():
     s2 = P.Solver.from_workload(wl)
     leaf2, rows2, _ = s2.autotune(16, P.MS_PREC_FP32)
     assert (leaf2, rows2) == (leaf, rows)
+
+
+@pytest.mark.parametrize("prec", [P.MS_PREC_FP32, P.MS_PREC_BF16])
+def test_tensor_peak_microkernel(prec):
+    """The project tcgen05 rate kernel: a positive, repeatable rate, bf16 about twice tf32 per flop."""
+    tf1, _ = P.tensor_peak(prec, 20000)
+    tf2, _ = P.tensor_peak(prec, 20000)
+    print(f"tensor peak, {'tf32' if prec == P.MS_PREC_FP32 else 'bf16'}: {tf1:.1f} / {tf2:.1f} TFLOP/s")
+    assert tf1 > 50 and abs(tf1 - tf2) <= 0.2 * max(tf1, tf2)
