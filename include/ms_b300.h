@@ -131,6 +131,12 @@ typedef struct {
                                   n > 0: every tensor-core CTA first waits, bounded by n microseconds, on a
                                   barrier that nothing arrives at, gives up, issues no multiply, and the call
                                   returns MS_ERR_TIMEOUT.  Valid range 0..1000000. */
+    int32_t store_near;        /* tensor_cores = 1: device-memory budget in GB (0..1024) for the near-pair
+                                  Graf operator of the FP32 path, stored as its 3xTF32 tensor-core tiles at
+                                  setup (and again when ms_autotune rebuilds the tree) instead of being
+                                  generated in every application (default 0 = generate).  Not stored
+                                  (silently) when the tiles need more than the budget or would leave less
+                                  than 8 GB of the device free.  Same arithmetic either way. */
 } ms_options;
 
 typedef struct {
@@ -297,6 +303,10 @@ int ms_info(const ms_handle* h, int32_t* M, int32_t* p, int32_t* n_nodes, int32_
  * spectral maps (2 waves x N_S x M x nc each); sapply, the scattering matrices ((2nc)^2 per prototype
  * particle, 4 nc per disc).  Any output may be NULL. */
 int ms_work(const ms_handle* h, double* near, double* far, double* refl, double* sapply);
+
+/* Device bytes of the stored near-pair operator (ms_options.store_near) into *bytes: 0 when the
+   operator is generated in each application.  MS_ERR_ARG for a NULL argument. */
+int ms_near_stored(const ms_handle* h, int64_t* bytes);
 
 /* Release every device buffer of the handle.  NULL is ignored. */
 void ms_destroy(ms_handle* h);

@@ -53,7 +53,7 @@ class Solver:
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
                  tensor_cores: bool = True, inner_tol: float = 0.0, block_krylov: bool = True,
-                 cuda_graph: bool = True, tc_wait_test: int = 0):
+                 cuda_graph: bool = True, tc_wait_test: int = 0, store_near: int = 0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -88,6 +88,7 @@ class Solver:
         o.block_krylov = int(bool(block_krylov))
         o.cuda_graph = int(bool(cuda_graph))
         o.tc_wait_test = int(tc_wait_test)
+        o.store_near = int(store_near)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")
@@ -285,6 +286,12 @@ class Solver:
         v = [ctypes.c_double() for _ in range(4)]
         nat.check(nat.lib().ms_work(self._h, *[ctypes.byref(x) for x in v]), "ms_work")
         return dict(zip(("near", "far", "refl", "sapply"), (x.value for x in v)))
+
+    def near_stored_bytes(self) -> int:
+        """ms_near_stored: device bytes of the stored near-pair operator (0: generated per application)."""
+        v = ctypes.c_int64()
+        nat.check(nat.lib().ms_near_stored(self._h, ctypes.byref(v)), "ms_near_stored")
+        return int(v.value)
 
     def autotune(self, nrhs: int = 64, prec: int = MS_PREC_FP32, stream=None):
         """ms_autotune: time the candidate FMM leaf levels and multipole-to-Sommerfeld split sizes and keep

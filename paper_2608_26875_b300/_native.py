@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
                 ("restart", c_int), ("max_iters", c_int), ("check_geometry", c_int),
                 ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int),
                 ("tensor_cores", c_int), ("inner_tol", ctypes.c_double), ("block_krylov", c_int),
-                ("cuda_graph", c_int), ("tc_wait_test", c_int)]
+                ("cuda_graph", c_int), ("tc_wait_test", c_int),
+                ("store_near", c_int)]
 
 
 class Incidence(ctypes.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = {
                             ctypes.c_void_p]),
     "ms_work": (c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ms_near_stored": (c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ms_tensor_peak": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),
     "ms_destroy": (None, [ctypes.c_void_p]),

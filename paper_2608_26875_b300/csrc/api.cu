@@ -241,6 +241,12 @@ extern "C" int ms_work(const ms_handle* h, double* near, double* far, double* re
     return MS_OK;
 }
 
+extern "C" int ms_near_stored(const ms_handle* h, int64_t* bytes) {
+    if (!h || !bytes) return MS_ERR_ARG;
+    *bytes = h->fmm.near_store ? 2 * h->fmm.near_store_wave : 0;
+    return MS_OK;
+}
+
 extern "C" void ms_destroy(ms_handle* h) {
     if (!h) return;
     dfree_t(h->d.centre); dfree_t(h->d.expo); dfree_t(h->d.sdisc); dfree_t(h->d.sdisc_f);

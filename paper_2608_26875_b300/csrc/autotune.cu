@@ -37,6 +37,8 @@ int rebuild(ms_handle* h, int leaf) {
     ms_fmm_free(h);
     if (int rc = ms_build_translations(h, h->opt.use_fmm, leaf)) return rc;
     h->opt.leaf_target = leaf;
+    if (h->opt.tensor_cores)
+        if (int rc = ms_near_store_build(h)) return rc;
     return ms_fmm_workspace(h, h->ws_nrhs);
 }
 

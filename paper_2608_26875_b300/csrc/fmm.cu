@@ -835,6 +835,7 @@ void ms_fmm_free(ms_handle* h) {
             F.mexp[b][lev] = F.lexp[b][lev] = nullptr;
         }
     }
+    ms_near_store_free(h);
     ms_tc_tiles_free(F.near_tc);
     for (int b = 0; b < 2; ++b)
         for (int lev = 0; lev <= 12; ++lev) ms_tc_tiles_free(F.m2l_tc[b][lev]);

@@ -70,6 +70,11 @@ struct FmmHost {
     // algorithmic complex multiply-adds per right-hand-side column of one application (both waves):
     // direct near pairs, and the FMM's P2M + M2M + M2L + L2L + L2P tasks
     double work_near = 0, work_far = 0;
+    // stored 3xTF32 B tiles of the near tiles (ms_options.store_near): wave b at near_store + b *
+    // near_store_wave, tile t at near_store_off[t], chunk c at + c * 2 * (n * KC * 4) (hi, then lo)
+    unsigned char* near_store = nullptr;
+    long long* near_store_off = nullptr;
+    long long near_store_wave = 0;
 };
 
 struct MsDeviceTables {
@@ -189,6 +194,8 @@ int ms_operator_ws(ms_handle* h, int nrhs, int parts, bool identity, bool adjoin
 template <typename T>
 int ms_operator_op(ms_handle* h, const void* in, void* out, int nrhs, bool adjoint, cudaStream_t st);
 void ms_near_tc_attributes();
+int ms_near_store_build(ms_handle* h);
+void ms_near_store_free(ms_handle* h);
 void ms_sapply_free(ms_handle* h);
 template <typename T>
 int ms_sapply_proto_launch(ms_handle* h, const void* xs, const void* as, void* ys, int nrhs, bool identity,

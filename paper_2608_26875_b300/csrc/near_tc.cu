@@ -83,9 +83,10 @@ struct ListPolicy {
         if (a.seq_len > 0) return a.seq_base + (long long)t * a.seq_len;
         return toff ? toff[s] : a.tseq[t];
     }
+    bool load_b = true;          // false: the B tiles come from a stored copy (run_stored)
     __device__ void fetch(int c) {
         const int r = tcp::arow() & 63;
-        const bool ok = r < a.nrhs;
+        const bool ok = r < a.nrhs && a.in != nullptr;
         const int fa = c * KCC + 4 * tcp::aq();
         int s = fa / ns, j = fa - s * ns;
 #pragma unroll
@@ -94,6 +95,7 @@ struct ListPolicy {
                                      : make_float2(0.f, 0.f);
             if (++j == ns) { j = 0; ++s; }
         }
+        if (!load_b) return;
         const int f0 = c * KCC + 8 * tcp::bhalf();
         s = f0 / ns;
         j = f0 - s * ns;
@@ -117,9 +119,13 @@ struct ListPolicy {
         }
     }
     template <class St>
-    __device__ void build(const St& st) {
+    __device__ void build_a(const St& st) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) tcp::put_a(st, tcp::arow(), 2 * tcp::aq() + u, ya[2 * u], ya[2 * u + 1]);
+    }
+    template <class St>
+    __device__ void build(const St& st) {
+        build_a(st);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 z[2];
@@ -170,6 +176,54 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_list_tc(ListArgs a, int* er
     tcp::run<ListPolicy, K>(pol, nchunks, n, err);
 }
 
+// Stored operator of the near tiles: one CTA per tile generates every chunk's B tiles exactly as
+// k_list_tc builds them (same policy, same split) and writes rows 0..n-1 of the hi and lo tiles to
+// out + off[tile] + chunk * 2 * half, half = n * KC * ELEM bytes.
+template <class K>
+__global__ void __launch_bounds__(tcp::THREADS, 1) k_list_store(ListArgs a, unsigned char* out,
+                                                                const long long* off) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int4 t = a.tiles[blockIdx.x];
+    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1;
+    const int nrow = nd;
+    ListPolicy pol{a, a.ttgt + t.x, a.tself + t.x, a.tsrc + t.z, nullptr, t.y, t.w, nrow, 0, nd, ns};
+    pol.init();
+    const int n = ((t.y * nrow + 15) / 16) * 16;
+    const size_t half = (size_t)n * tcp::KC * K::ELEM;
+    const int nchunks = (t.w * ns + KCC - 1) / KCC;
+    const tcp::StageT<K> st = tcp::stage_ptrs<K>(smem, 0);
+    unsigned char* dst = out + off[blockIdx.x];
+    for (int c = 0; c < nchunks; ++c) {
+        pol.fetch(c);
+        pol.build(st);
+        __syncthreads();
+        uint4* d = reinterpret_cast<uint4*>(dst + (size_t)c * 2 * half);
+        const uint4* bh = reinterpret_cast<const uint4*>(st.bh);
+        const uint4* bl = reinterpret_cast<const uint4*>(st.bl);
+        for (int i = threadIdx.x; i < (int)(half / 16); i += blockDim.x) {
+            d[i] = bh[i];
+            d[half / 16 + i] = bl[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Near tiles against the stored operator: only the data operand is built in the loop.
+template <class K>
+__global__ void __launch_bounds__(tcp::THREADS, 1) k_list_stored(ListArgs a, const unsigned char* bstore,
+                                                                 const long long* off, int* err) {
+    const int4 t = a.tiles[blockIdx.x];
+    const int nd = 2 * a.Pd + 1, ns = 2 * a.Ps + 1;
+    const int nrow = nd;
+    ListPolicy pol{a, a.ttgt + t.x, a.tself + t.x, a.tsrc + t.z, nullptr, t.y, t.w, nrow, 0, nd, ns};
+    pol.init();
+    pol.load_b = false;
+    const int n = ((t.y * nrow + 15) / 16) * 16;
+    const uint32_t half = (uint32_t)n * tcp::KC * K::ELEM;
+    const int nchunks = (t.w * ns + KCC - 1) / KCC;
+    tcp::run_stored<ListPolicy, K>(pol, nchunks, n, err, bstore + off[blockIdx.x], half);
+}
+
 inline int upv(ms_handle* h, void** dst, const void* src, size_t bytes) {
     *dst = nullptr;
     if (!bytes) return MS_OK;
@@ -183,6 +237,77 @@ inline int upv(ms_handle* h, void** dst, const void* src, size_t bytes) {
 void ms_near_tc_attributes() {
     cudaFuncSetAttribute(k_list_tc<tcp::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
     cudaFuncSetAttribute(k_list_tc<tcp::BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+    cudaFuncSetAttribute(k_list_store<tcp::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+    cudaFuncSetAttribute(k_list_stored<tcp::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcp::SMEM);
+}
+
+namespace {
+void near_args(ms_handle* h, int b, const float2* xs, float2* dst, int nrhs, ListArgs& a) {
+    const FmmHost& F = h->fmm;
+    const int nc = h->nc;
+    a = ListArgs{};
+    a.in = xs ? xs + (long long)b * nc * nrhs : nullptr; a.in_stride = 2LL * nc * nrhs;
+    a.out = dst ? dst + (long long)b * nc * nrhs : nullptr; a.out_stride = 2LL * nc * nrhs;
+    a.seqm = h->d.seqm; a.seqe = h->d.seqe;
+    a.tseq = F.near[b].seq; a.tptr = F.near[b].ptr;
+    a.seq_base = F.near_seq_base[b]; a.seq_len = 4 * h->p + 3;
+    a.ad = h->d.expo + b * nc; a.ad_stride = 2LL * nc;
+    a.as = h->d.expo + b * nc; a.as_stride = 2LL * nc;
+    a.tiles = F.near_tc.tile; a.ttgt = F.near_tc.tgt; a.tself = F.near_tc.self; a.tsrc = F.near_tc.src;
+    a.trow = nullptr;
+    a.Pd = h->p; a.Ps = h->p; a.K = 2 * h->p + 1; a.nrhs = nrhs;
+}
+}  // namespace
+
+// Stored near operator (ms_options.store_near): the 3xTF32 B tiles of every near tile and chunk, for
+// both waves, generated once here.  Skipped (MS_OK, nothing stored) when the tiles exceed the budget
+// of opt.store_near gigabytes or the free device memory.
+int ms_near_store_build(ms_handle* h) {
+    FmmHost& F = h->fmm;
+    ms_near_store_free(h);
+    if (!h->opt.store_near || !h->opt.tensor_cores || F.near_tc.n == 0) return MS_OK;
+    const int nc = h->nc, ntile = F.near_tc.n;
+    std::vector<int4> tiles(ntile);
+    if (int rc = ms_check(h, cudaMemcpy(tiles.data(), F.near_tc.tile, ntile * sizeof(int4), cudaMemcpyDeviceToHost)))
+        return rc;
+    std::vector<long long> off(ntile);
+    long long total = 0;
+    for (int t = 0; t < ntile; ++t) {
+        const long long n = ((long long)tiles[t].y * nc + 15) / 16 * 16;
+        const long long nchunks = ((long long)tiles[t].w * nc + KCC - 1) / KCC;
+        off[t] = total;
+        total += nchunks * 2 * n * tcp::KC * 4;
+    }
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const double budget = (double)h->opt.store_near * 1e9;
+    if ((double)(2 * total) > budget || (size_t)(2 * total) + ((size_t)8 << 30) > freeb) return MS_OK;
+    int rc;
+    if ((rc = ms_check(h, cudaMalloc(&F.near_store, (size_t)2 * total))) ||
+        (rc = ms_check(h, cudaMalloc(&F.near_store_off, ntile * sizeof(long long)))) ||
+        (rc = ms_check(h, cudaMemcpy(F.near_store_off, off.data(), ntile * sizeof(long long),
+                                     cudaMemcpyHostToDevice)))) {
+        ms_near_store_free(h);
+        return rc;
+    }
+    F.near_store_wave = total;
+    for (int b = 0; b < 2; ++b) {
+        ListArgs a;
+        near_args(h, b, nullptr, nullptr, 1, a);
+        k_list_store<tcp::TF32><<<ntile, tcp::THREADS, tcp::SMEM>>>(a, F.near_store + (size_t)b * total,
+                                                                    F.near_store_off);
+        if ((rc = ms_check(h, cudaGetLastError()))) { ms_near_store_free(h); return rc; }
+    }
+    return ms_check(h, cudaDeviceSynchronize());
+}
+
+void ms_near_store_free(ms_handle* h) {
+    FmmHost& F = h->fmm;
+    cudaFree(F.near_store);
+    cudaFree(F.near_store_off);
+    F.near_store = nullptr;
+    F.near_store_off = nullptr;
+    F.near_store_wave = 0;
 }
 
 // Tiles of the FMM multipole-to-local stage for (wave b, level lev): one tile per 256-row range of
@@ -223,18 +348,12 @@ int ms_near_tc_launch(ms_handle* h, const float2* xs, float2* dst, int nrhs, cud
     const FmmHost& F = h->fmm;
     const int nc = h->nc;
     for (int b = 0; b < 2; ++b) {
-        ListArgs a{};
-        a.in = xs + (long long)b * nc * nrhs; a.in_stride = 2LL * nc * nrhs;
-        a.out = dst + (long long)b * nc * nrhs; a.out_stride = 2LL * nc * nrhs;
-        a.seqm = h->d.seqm; a.seqe = h->d.seqe;
-        a.tseq = F.near[b].seq; a.tptr = F.near[b].ptr;
-        a.seq_base = F.near_seq_base[b]; a.seq_len = 4 * h->p + 3;
-        a.ad = h->d.expo + b * nc; a.ad_stride = 2LL * nc;
-        a.as = h->d.expo + b * nc; a.as_stride = 2LL * nc;
-        a.tiles = F.near_tc.tile; a.ttgt = F.near_tc.tgt; a.tself = F.near_tc.self; a.tsrc = F.near_tc.src;
-        a.trow = nullptr;
-        a.Pd = h->p; a.Ps = h->p; a.K = 2 * h->p + 1; a.nrhs = nrhs;
-        if (h->tc_kind)
+        ListArgs a;
+        near_args(h, b, xs, dst, nrhs, a);
+        if (!h->tc_kind && F.near_store)
+            k_list_stored<tcp::TF32><<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(
+                a, F.near_store + (size_t)b * F.near_store_wave, F.near_store_off, h->d.tc_err);
+        else if (h->tc_kind)
             k_list_tc<tcp::BF16><<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);
         else
             k_list_tc<tcp::TF32><<<F.near_tc.n, tcp::THREADS, tcp::SMEM, st>>>(a, h->d.tc_err);

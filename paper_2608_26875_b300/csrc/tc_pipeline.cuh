@@ -26,7 +26,8 @@ constexpr int NSTAGE = 2;
 constexpr uint32_t A_TILE = MA * KC * 4;       // 16 KB (hi or lo)
 constexpr uint32_t B_TILE = NMAX * KC * 4;     // 32 KB
 constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;
-constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;   // + stage barriers, tensor-memory slot, flag, probe
+constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 64;   // + stage barriers, tensor-memory slot, flag, probe,
+                                                         //   copy barriers and the last-commit index
 constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
 constexpr uint32_t TMEM_COLS = 256;
 static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -197,6 +198,98 @@ __device__ __forceinline__ void run(P& pol, int nchunks, int n, int* err) {
     bool ok = !*fail && issued == nchunks;
     if (issued > 0) {
         const int c = issued - 1;
+        if (!tc::mbar_wait(&bar[c % NSTAGE], (c / NSTAGE) & 1)) ok = false;
+    }
+    tc::fence_after();
+    if (!ok && tid == 0) atomicExch(err, 1);
+    pol.epilogue(tmem, ok && nchunks > 0);
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) tc::tmem_free(tmem, TMEM_COLS);
+}
+
+// As run(), for an operator stored in global memory in the stage layout: chunk c's B tiles (hi, then
+// lo, half_bytes each; rows 0..n-1 of the 256-row tile, 8-row groups SBO apart) are at
+// bsrc + c * 2 * half_bytes.  Thread 0 issues two bulk asynchronous copies per chunk into the stage as
+// soon as the multiplies that last read it have completed; they complete on the stage's copy barrier,
+// which thread 0 waits on (bounded) before it issues the chunk's multiplies.  The policy's build_a()
+// writes only the A tiles.  Every wait is bounded; a CTA that gave up waits, bounded, for its issued
+// copies and multiplies before it frees tensor memory.
+template <class P, class K = TF32>
+__device__ __forceinline__ void run_stored(P& pol, int nchunks, int n, int* err, const unsigned char* bsrc,
+                                           uint32_t half_bytes) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NSTAGE);
+    int* fail = reinterpret_cast<int*>(tslot + 1);
+    uint64_t* probe = bar + NSTAGE + 1;
+    uint64_t* cbar = bar + NSTAGE + 2;             // [NSTAGE] copy barriers
+    int* last = reinterpret_cast<int*>(cbar + NSTAGE);   // last committed chunk (thread 0 writes)
+    const int tid = threadIdx.x;
+    const uint32_t idesc = K::idesc(MA, n);
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            tc::mbar_init(&bar[s], 1);
+            tc::mbar_init(&cbar[s], 1);
+        }
+        tc::mbar_init(probe, 1);
+        tc::mbar_fence_init();
+        *fail = 0;
+        *last = -1;
+        const int test_us = err[1];
+        if (test_us > 0 && !tc::mbar_wait(probe, 0, (uint64_t)test_us * 1000ull)) *fail = 1;
+    }
+    if (tid < 32) tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    int copied = -1;                               // thread 0: last chunk whose copies were issued
+    int waited = -1;                               // thread 0: last chunk whose copies were waited for
+    if (nchunks > 0) pol.fetch(0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % NSTAGE;
+        if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
+        const StageT<K> st = stage_ptrs<K>(smem, s);
+        if (tid == 0 && !*fail) {
+            const unsigned char* src = bsrc + (size_t)c * 2 * half_bytes;
+            tc::mbar_expect_tx(&cbar[s], 2 * half_bytes);
+            tc::bulk_g2s(st.bh, src, half_bytes, &cbar[s]);
+            tc::bulk_g2s(st.bl, src + half_bytes, half_bytes, &cbar[s]);
+            copied = c;
+        }
+        pol.build_a(st);
+        if (c + 1 < nchunks) pol.fetch(c + 1);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (*fail) break;
+        if (tid == 0) {
+            if (!tc::mbar_wait(&cbar[s], (c / NSTAGE) & 1)) {
+                *fail = 1;
+            } else {
+                waited = c;
+                tc::fence_after();
+#pragma unroll
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t a0 = tc::smem_u32(pass == 2 ? st.al : st.ah);
+                    const uint32_t b0 = tc::smem_u32(pass == 1 ? st.bl : st.bh);
+#pragma unroll
+                    for (int ks = 0; ks < KC / K::KMMA; ++ks)
+                        K::mma(tmem, tc::smem_desc(a0 + ks * 256, LBO, K::SBO_),
+                               tc::smem_desc(b0 + ks * 256, LBO, K::SBO_), idesc, (c > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&bar[s]);
+                *last = c;
+            }
+        }
+    }
+    if (tid == 0 && copied > waited) {             // copies issued but never waited for (failure path)
+        if (!tc::mbar_wait(&cbar[copied % NSTAGE], (copied / NSTAGE) & 1)) *fail = 1;
+    }
+    __syncthreads();
+    bool ok = !*fail && *last == nchunks - 1;
+    if (*last >= 0) {
+        const int c = *last;
         if (!tc::mbar_wait(&bar[c % NSTAGE], (c / NSTAGE) & 1)) ok = false;
     }
     tc::fence_after();

@@ -133,7 +133,8 @@ def _raw_setup(lib, case):
     lib.ms_default_options(ctypes.byref(o))
     omega, p = wl.omega, wl.p
     field, _, value = case.partition("=")
-    if field in ("tensor_cores", "leaf_target", "restart", "max_iters", "n_panels", "nodes_per_panel", "grade"):
+    if field in ("tensor_cores", "leaf_target", "restart", "max_iters", "n_panels", "nodes_per_panel", "grade",
+                 "store_near"):
         setattr(o, field, int(value))
     elif field in ("inner_tol", "t_max", "depth"):
         setattr(o, field, float(value))
@@ -161,7 +162,8 @@ def _raw_setup(lib, case):
     "tensor_cores=2", "tensor_cores=-1", "inner_tol=1.0", "inner_tol=-0.001", "inner_tol=nan",
     "leaf_target=0", "restart=0", "max_iters=0", "n_panels=0", "nodes_per_panel=0", "t_max=0",
     "depth=0", "depth=nan", "grade=-1", "grade=31", "mu_u=0", "mu_l=-1", "lam_l=-1.5", "M=0",
-    "centre=nan", "centre=inf", "proto=0", "proto=-2", "n_proto=2", "p=-1"])
+    "centre=nan", "centre=inf", "proto=0", "proto=-2", "n_proto=2", "p=-1", "store_near=-1",
+    "store_near=1025"])
 def test_invalid_options_and_media_are_refused_before_device_work(lib, case):
     """Every ms_options field, the media and the geometry arrays are checked on the host: an
     invalid value returns MS_ERR_ARG and leaves the handle NULL (the call never reaches CUDA, so
@@ -199,8 +201,9 @@ def test_every_handle_call_refuses_a_null_handle(lib):
                 args.append(None)
         assert getattr(lib, name)(*args) == nat.MS_ERR_ARG, name
         checked += 1
-    assert checked == 15         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
-    #                              fields_upper, time_reversal, grad, fields_noalloc, autotune, info, work
+    assert checked == 16         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
+    #                              fields_upper, time_reversal, grad, fields_noalloc, autotune, info, work,
+    #                              near_stored
     lib.ms_destroy(None)
     assert lib.ms_last_cuda_error(None) == 0
 
