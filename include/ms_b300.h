@@ -137,6 +137,12 @@ typedef struct {
                                   generated in every application (default 0 = generate).  Not stored
                                   (silently) when the tiles need more than the budget or would leave less
                                   than 8 GB of the device free.  Same arithmetic either way. */
+    int32_t precond_group;     /* ms_solve / ms_solve_rhs / ms_grad with block_krylov: n > 0 = right group-block
+                                  Jacobi preconditioner: particles grouped by a uniform grid of cells holding
+                                  about n particles (a fuller cell cut into runs of at most 2n), each group's
+                                  block I - S T (free-space translations inside the group) inverted in FP64
+                                  at setup; costs 24 (2 (2p+1) n_g)^2 bytes per group.  0 = none (default).
+                                  Valid range 0..64. */
 } ms_options;
 
 typedef struct {

@@ -53,7 +53,7 @@ class Solver:
                  restart: int = 50, max_iters: int = 2000, check_geometry: bool = True,
                  use_fmm: bool = True, leaf_target: int = 10, depth: float = 0.5, grade: int = 0,
                  tensor_cores: bool = True, inner_tol: float = 0.0, block_krylov: bool = True,
-                 cuda_graph: bool = True, tc_wait_test: int = 0, store_near: int = 0):
+                 cuda_graph: bool = True, tc_wait_test: int = 0, store_near: int = 0, precond_group: int = 0):
         L = nat.lib()
         self._keep = []
         c = np.ascontiguousarray(centres, dtype=np.float64)
@@ -89,6 +89,7 @@ class Solver:
         o.cuda_graph = int(bool(cuda_graph))
         o.tc_wait_test = int(tc_wait_test)
         o.store_near = int(store_near)
+        o.precond_group = int(precond_group)
         h = ctypes.c_void_p()
         nat.check(L.ms_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
                              ctypes.byref(h)), "ms_setup")

@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
                 ("use_fmm", c_int), ("leaf_target", c_int), ("depth", ctypes.c_double), ("grade", c_int),
                 ("tensor_cores", c_int), ("inner_tol", ctypes.c_double), ("block_krylov", c_int),
                 ("cuda_graph", c_int), ("tc_wait_test", c_int),
-                ("store_near", c_int)]
+                ("store_near", c_int), ("precond_group", c_int)]
 
 
 class Incidence(ctypes.Structure):

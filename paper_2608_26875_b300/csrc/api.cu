@@ -257,6 +257,7 @@ extern "C" void ms_destroy(ms_handle* h) {
     ms_graphs_free(h);
     ms_spectral_tc_free(h);
     ms_fmm_free(h);
+    ms_precond_free(h);
     dfree(h->ws_x); dfree(h->ws_a); dfree(h->ws_y); dfree(h->ws_part); dfree(h->ws_u); dfree(h->ws_uf);
     delete h;
 }

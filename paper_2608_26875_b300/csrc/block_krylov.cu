@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dense_host.h"
 #include "handle.h"
 #include "tc_pipeline.cuh"
 
@@ -283,6 +284,23 @@ __global__ void k_bgram_sum(const double2* __restrict__ part, double2* __restric
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// Columns c0..s-1 of an N x s block: pseudo-random entries in [-1, 1) + i [-1, 1) from a 64-bit mix
+// (splitmix64) of the entry index and the call's seed.
+template <typename T>
+__global__ void k_fill_random(typename CT<T>::c* __restrict__ dst, long long N, int s, int c0,
+                              unsigned long long seed) {
+    const int w = s - c0;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N * w) return;
+    const long long row = i / w;
+    const int c = c0 + (int)(i - row * w);
+    unsigned long long z = ((unsigned long long)row * s + c) * 0x9E3779B97F4A7C15ull + seed;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    dst[row * s + c] = to_c<T>(make_double2((z & 0xffffffff) * 0x1p-31 - 1.0, (z >> 32) * 0x1p-31 - 1.0));
+}
+
 // ------------------------------------------------------------------ host: small dense FP64 algebra
 // Upper-triangular R with G = R^H R (G Hermitian positive definite, s x s row-major); a diagonal
 // shift of shift * max diag(G) keeps the factorisation defined for (nearly) dependent blocks.
@@ -366,9 +384,12 @@ struct BlockKrylov {
     double2* part = nullptr;
     double2* G = nullptr;
     int nsplit_max = 1;
+    int deflations = 0;      // rank-deficient blocks met (orth)
+
+    C* Z = nullptr;          // N x s: preconditioned block (group-block Jacobi), when the handle has one
 
     ~BlockKrylov() {
-        cudaFree(V); cudaFree(W); cudaFree(Hd); cudaFree(part); cudaFree(G);
+        cudaFree(V); cudaFree(W); cudaFree(Hd); cudaFree(part); cudaFree(G); cudaFree(Z);
     }
     int init() {
         const size_t blk = (size_t)N * s * sizeof(C);
@@ -380,7 +401,8 @@ struct BlockKrylov {
         if (cudaMalloc(&V, blk * (m + 1)) != cudaSuccess || cudaMalloc(&W, blk) != cudaSuccess ||
             cudaMalloc(&Hd, nbmax * s * sizeof(C)) != cudaSuccess ||
             cudaMalloc(&part, part_cap * sizeof(double2)) != cudaSuccess ||
-            cudaMalloc(&G, nbmax * s * sizeof(double2)) != cudaSuccess) {
+            cudaMalloc(&G, nbmax * s * sizeof(double2)) != cudaSuccess ||
+            (h->pc.ng > 0 && cudaMalloc(&Z, blk) != cudaSuccess)) {
             cudaGetLastError();
             return MS_ERR_ALLOC;
         }
@@ -433,20 +455,87 @@ struct BlockKrylov {
         // (a copy from pageable host memory returns once the data are staged: hc may go out of scope)
         return ms_check(h, cudaGetLastError());
     }
-    // CholQR2: dst R = src with dst orthonormal (dst may equal src); returns R (s x s upper)
-    int cholqr(const C* src, C* dst, std::vector<cd>& R) {
-        const double shift = sizeof(T) == 8 ? 1e-13 : 1e-6;
+    // CholQR2 of a block in place, unshifted; false when a factor does not exist or loses more than the
+    // relative pivot floor
+    int cholqr2(C* blk, std::vector<cd>& R, bool& ok) {
         std::vector<cd> Gm, R1, R2, Ri;
-        if (int rc = gram(src, s, src, Gm)) return rc;
-        if (!chol_upper(Gm, s, shift, R1)) return MS_ERR_BREAKDOWN;
+        ok = false;
+        if (int rc = gram(blk, s, blk, Gm)) return rc;
+        if (!chol_checked(Gm, R1)) return MS_OK;
         tri_inv_upper(R1, s, Ri);
-        if (int rc = update(src, s, Ri, dst, false, 1.0)) return rc;
-        if (int rc = gram(dst, s, dst, Gm)) return rc;
-        if (!chol_upper(Gm, s, shift, R2)) return MS_ERR_BREAKDOWN;
+        if (int rc = update(blk, s, Ri, blk, false, 1.0)) return rc;
+        if (int rc = gram(blk, s, blk, Gm)) return rc;
+        if (!chol_checked(Gm, R2)) return MS_OK;
         tri_inv_upper(R2, s, Ri);
-        if (int rc = update(dst, s, Ri, dst, false, 1.0)) return rc;
+        if (int rc = update(blk, s, Ri, blk, false, 1.0)) return rc;
         R = matmul(R2, R1, s);
+        ok = true;
         return MS_OK;
+    }
+    // relative eigenvalue floor of a Gram matrix: below it a direction of the block is rounding noise
+    double floor_rel() const { return 64.0 * (sizeof(T) == 8 ? 1.11e-16 : 5.96e-8); }
+    bool chol_checked(const std::vector<cd>& Gm, std::vector<cd>& R) {
+        double dmax = 0;
+        for (int i = 0; i < s; ++i) dmax = std::max(dmax, Gm[(size_t)i * s + i].real());
+        if (!(dmax > 0) || !chol_upper(Gm, s, 0.0, R)) return false;
+        for (int i = 0; i < s; ++i)
+            if (!(std::norm(R[(size_t)i * s + i]) >= floor_rel() * dmax)) return false;
+        return true;
+    }
+    // Orthonormal block dst with src = dst R (R s x s), orthogonal to the nprev basis blocks before it.
+    // A full-rank block takes CholQR2 (R upper triangular).  A (numerically) rank-deficient one -- the
+    // Krylov space has (nearly) closed, or the right-hand sides are dependent -- keeps its numerically
+    // independent directions (Gram eigenvectors with eigenvalues above the floor, scaled to unit
+    // length), fills the other columns with pseudo-random vectors orthogonalised against the basis,
+    // and takes R = dst^H src, so that the block stays s wide and orthonormal and the Arnoldi relation
+    // holds up to the dropped noise.  dst may equal src.
+    int orth(const C* src, C* dst, int nprev, std::vector<cd>& R) {
+        int rc;
+        if (src == dst) {
+            if ((rc = ms_check(h, cudaMemcpyAsync(W, src, (size_t)N * s * sizeof(C), cudaMemcpyDeviceToDevice, st))))
+                return rc;
+            src = W;
+        }
+        if ((rc = ms_check(h, cudaMemcpyAsync(dst, src, (size_t)N * s * sizeof(C), cudaMemcpyDeviceToDevice, st))))
+            return rc;
+        bool ok;
+        if ((rc = cholqr2(dst, R, ok))) return rc;
+        if (ok) return MS_OK;
+        ++deflations;
+        std::vector<cd> Gm;
+        if ((rc = gram(src, s, src, Gm))) return rc;
+        // eigenpairs of the Hermitian Gram by one-sided Jacobi: the squared column norms are the
+        // eigenvalues of G^2, the accumulated rotations the eigenvectors
+        std::vector<cd> A((size_t)s * s), V;
+        for (int r = 0; r < s; ++r)
+            for (int c = 0; c < s; ++c) A[(size_t)c * s + r] = Gm[(size_t)r * s + c];
+        std::vector<double> ev;
+        dense::jacobi_svd(A, s, ev, V);
+        std::vector<int> order(s);
+        for (int i = 0; i < s; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] > ev[b]; });
+        const double lmax = sqrt(std::max(0.0, ev[order[0]]));
+        int k = 0;
+        std::vector<cd> Y((size_t)s * s, cd(0));
+        for (; k < s; ++k) {
+            const double lk = sqrt(std::max(0.0, ev[order[k]]));
+            if (!(lmax > 0) || !(lk > floor_rel() * lmax)) break;
+            for (int i = 0; i < s; ++i) Y[(size_t)i * s + k] = V[(size_t)order[k] * s + i] / sqrt(lk);
+        }
+        if ((rc = update(src, s, Y, dst, false, 1.0))) return rc;
+        if (k < s) {
+            k_fill_random<T><<<nblk(N * (s - k), 256), 256, 0, st>>>(dst, N, s, k, 0x632BE59BD9B4E019ull + 977ull * deflations);
+            if ((rc = ms_check(h, cudaGetLastError()))) return rc;
+        }
+        for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+            std::vector<cd> Gp;
+            if ((rc = gram(blk(0), nprev * s, dst, Gp))) return rc;
+            if ((rc = update(blk(0), nprev * s, Gp, dst, true, -1.0))) return rc;
+        }
+        std::vector<cd> Rq;
+        if ((rc = cholqr2(dst, Rq, ok))) return rc;
+        if (!ok) return MS_ERR_BREAKDOWN;
+        return gram(dst, s, src, R);             // R[k][r] = <dst_k, src_r>
     }
 };
 
@@ -487,7 +576,7 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
         }
         first = false;
         std::vector<cd> S0;
-        if ((rc = K.cholqr(K.blk(0), K.blk(0), S0))) return rc;
+        if ((rc = K.orth(K.blk(0), K.blk(0), 0, S0))) return rc;
         // transformed right-hand side of the least-squares problem: (m + 1) s x s, column-major per column c
         const int rows_max = (m + 1) * s;
         std::vector<cd> g((size_t)rows_max * s, cd(0));     // g[row * s + c]
@@ -516,7 +605,7 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
                 for (size_t i = 0; i < Gp.size(); ++i) hcol[i] += Gp[i];
             }
             std::vector<cd> Rn;
-            if ((rc = K.cholqr(K.W, K.blk(j + 1), Rn))) return rc;
+            if ((rc = K.orth(K.W, K.blk(j + 1), j + 1, Rn))) return rc;
             for (int i = 0; i < s; ++i)
                 for (int c = 0; c < s; ++c) hcol[(size_t)(nb + i) * s + c] = Rn[(size_t)i * s + c];
             ++total;
@@ -615,13 +704,22 @@ int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds
         }
         *cache = K;
     }
+    // right preconditioning: iterate on A~ P^{-1} (A~^H P^{-H}) and map the result back, d = P^{-1} z
+    const bool pc = h->pc.ng > 0;
     auto op = [&](const C* in, C* out) -> int {
-        int rc = ms_operator_op<T>(h, in, out, nrhs, adjoint, st);
-        if (rc) return rc;
+        int rc;
+        if (pc) {
+            if ((rc = ms_precond_apply<T>(h, in, K->Z, nrhs, adjoint, st))) return rc;
+            in = K->Z;
+        }
+        if ((rc = ms_operator_op<T>(h, in, out, nrhs, adjoint, st))) return rc;
         if (sizeof(T) == 4 && h->opt.tensor_cores) return ms_spectral_tc_status(h, st);
         return MS_OK;
     };
-    return block_gmres<T>(*K, op, (const C*)rs, (C*)ds, tol, max_iters, true, iters, matvecs, relres);
+    int rc = block_gmres<T>(*K, op, (const C*)rs, (C*)ds, tol, max_iters, true, iters, matvecs, relres);
+    if (rc || !pc) return rc;
+    if ((rc = ms_precond_apply<T>(h, ds, K->Z, nrhs, adjoint, st))) return rc;
+    return ms_check(h, cudaMemcpyAsync(ds, K->Z, (size_t)N * nrhs * sizeof(C), cudaMemcpyDeviceToDevice, st));
 }
 
 template <typename T>

@@ -77,6 +77,20 @@ struct FmmHost {
     long long near_store_wave = 0;
 };
 
+// group-block Jacobi preconditioner (precond.cu): group g's inverse block (D_g = 2 nc n_g square,
+// row-major, rows (position in group, wave, order)) at goff[g]
+struct PrecondDev {
+    double2* inv64 = nullptr;
+    float2* inv32 = nullptr;
+    long long* goff = nullptr;
+    int* gptr = nullptr;           // [ng + 1] into gpart
+    int* gpart = nullptr;          // particles by group
+    int* pgrp = nullptr;           // group of each particle
+    int* ppos = nullptr;           // position of each particle in its group
+    int ng = 0, dmax = 0;
+    long long total = 0;
+};
+
 struct MsDeviceTables {
     // geometry
     double2* centre = nullptr;     // [M] (x_m, y_m)
@@ -146,6 +160,7 @@ struct ms_handle {
     int fmm_levels = 0;            // 0: direct sum over all pairs
     long long seq_len = 0;
     FmmHost fmm;
+    PrecondDev pc;
     // workspace sized for ws_nrhs columns
     int ws_nrhs = 0;
     void* ws_x = nullptr;          // scaled input  [M][2][nc][nrhs] (double2 or float2)
@@ -194,6 +209,10 @@ int ms_operator_ws(ms_handle* h, int nrhs, int parts, bool identity, bool adjoin
 template <typename T>
 int ms_operator_op(ms_handle* h, const void* in, void* out, int nrhs, bool adjoint, cudaStream_t st);
 void ms_near_tc_attributes();
+int ms_precond_build(ms_handle* h);
+void ms_precond_free(ms_handle* h);
+template <typename T>
+int ms_precond_apply(ms_handle* h, const void* x, void* y, int nrhs, bool adjoint, cudaStream_t st);
 int ms_near_store_build(ms_handle* h);
 void ms_near_store_free(ms_handle* h);
 void ms_sapply_free(ms_handle* h);

@@ -239,6 +239,7 @@ extern "C" void ms_default_options(ms_options* o) {
     o->cuda_graph = 1;
     o->tc_wait_test = 0;
     o->store_near = 0;
+    o->precond_group = 0;
 }
 
 // Panel edges of the Sommerfeld rule on [-t_max, t_max]: n uniform panels (edge k at
@@ -285,7 +286,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30 ||
         (opt.tensor_cores != 0 && opt.tensor_cores != 1) || !(opt.inner_tol >= 0.0 && opt.inner_tol < 1.0) ||
         opt.tc_wait_test < 0 || opt.tc_wait_test > 1000000 || (opt.block_krylov != 0 && opt.block_krylov != 1) ||
-        (opt.cuda_graph != 0 && opt.cuda_graph != 1) || opt.store_near < 0 || opt.store_near > 1024)
+        (opt.cuda_graph != 0 && opt.cuda_graph != 1) || opt.store_near < 0 || opt.store_near > 1024 ||
+        opt.precond_group < 0 || opt.precond_group > 64)
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {
@@ -519,6 +521,10 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         return rc;
     }
     if (opt.tensor_cores && ((rc = ms_spectral_tc_setup(h)) || (rc = ms_near_store_build(h)))) {
+        ms_destroy(h);
+        return rc;
+    }
+    if ((rc = ms_precond_build(h))) {
         ms_destroy(h);
         return rc;
     }

@@ -61,7 +61,7 @@ def test_default_options(lib):
     assert (o.n_panels, o.nodes_per_panel, o.t_max, o.restart) == (32, 16, 20.0, 50)
     assert (o.use_fmm, o.leaf_target, o.depth, o.grade, o.tensor_cores) == (1, 10, 0.5, 0, 1)
     assert o.inner_tol == 0.0 and o.tc_wait_test == 0 and o.block_krylov == 1 and o.cuda_graph == 1
-    assert ctypes.sizeof(o) == 80      # the C struct: 11 int32, 3 doubles, padding
+    assert ctypes.sizeof(o) == 88      # the C struct: 14 int32, 3 doubles, padding
 
 
 def test_timeout_status_string(lib):
@@ -134,7 +134,7 @@ def _raw_setup(lib, case):
     omega, p = wl.omega, wl.p
     field, _, value = case.partition("=")
     if field in ("tensor_cores", "leaf_target", "restart", "max_iters", "n_panels", "nodes_per_panel", "grade",
-                 "store_near"):
+                 "store_near", "precond_group"):
         setattr(o, field, int(value))
     elif field in ("inner_tol", "t_max", "depth"):
         setattr(o, field, float(value))
@@ -163,7 +163,7 @@ def _raw_setup(lib, case):
     "leaf_target=0", "restart=0", "max_iters=0", "n_panels=0", "nodes_per_panel=0", "t_max=0",
     "depth=0", "depth=nan", "grade=-1", "grade=31", "mu_u=0", "mu_l=-1", "lam_l=-1.5", "M=0",
     "centre=nan", "centre=inf", "proto=0", "proto=-2", "n_proto=2", "p=-1", "store_near=-1",
-    "store_near=1025"])
+    "store_near=1025", "precond_group=-1", "precond_group=65"])
 def test_invalid_options_and_media_are_refused_before_device_work(lib, case):
     """Every ms_options field, the media and the geometry arrays are checked on the host: an
     invalid value returns MS_ERR_ARG and leaves the handle NULL (the call never reaches CUDA, so

@@ -45,7 +45,11 @@ def test_bf16_operator_parts_against_fp64(parts):
         tf = s.operator(x, sel[parts], prec=P.MS_PREC_FP32).cpu().numpy()
     e, e32 = scaled_err(got, want, wl), scaled_err(tf, want, wl)
     print(f"BF16-split {parts}: scaled error {e:.3e} (3xTF32 {e32:.3e})")
-    assert e <= BF16_BAR and e > e32
+    assert e <= BF16_BAR
+    if parts == "near":
+        # the near part is all tensor-core contraction, so the coarser split shows; the far and reflected
+        # parts' error is set by their FP32 CUDA-core stages and FP32 tables, the same for both splits
+        assert e > e32
 
 
 def test_bf16_star_apply_against_oracle():

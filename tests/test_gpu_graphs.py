@@ -40,10 +40,14 @@ def test_graph_replay_is_bitwise_equal_to_plain_launches(pair, prec):
 
 
 def test_graph_solves_match_plain_solves(pair):
-    wl, g, d = pair
+    """Same iterations, status and bits with and without graphs (a capped run: the replayed operator
+    must not change a single iterate, converged or not)."""
+    wl = pair[0]
+    g = P.Solver.from_workload(wl, cuda_graph=True, max_iters=60)
+    d = P.Solver.from_workload(wl, cuda_graph=False, max_iters=60)
     for prec, tol in ((P.MS_PREC_FP64, 1e-12), (P.MS_PREC_FP32, 1e-10)):
         a, ia = g.solve(wl.inc_kind, wl.inc_angle, tol=tol, prec=prec)
         b, ib = d.solve(wl.inc_kind, wl.inc_angle, tol=tol, prec=prec)
-        assert ia["status"] == 0 and ib["status"] == 0
+        assert ia["status"] == ib["status"]
         assert ia["iterations"] == ib["iterations"]
         assert torch.equal(a, b)
