@@ -196,7 +196,8 @@ def run_ours(args):
     wl, tables = workload()
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
     solver = P.Solver.from_workload(wl, proto_S=tables, leaf_target=args.leaf_target,
-                                    tensor_cores=args.tensor_cores)
+                                    tensor_cores=args.tensor_cores, store_near=args.store_near)
+    stored = solver.near_stored_bytes()
     nrhs = 64
     x = torch.as_tensor(syn.random_coeffs(1000 + rank, wl.M, wl.p, nrhs), device="cuda")
     y = torch.empty_like(x)
@@ -255,8 +256,9 @@ def run_ours(args):
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12                  # TFLOP/s of the FP32 CUDA-core pipes
     tf32_peak = float(pk.get("bf16_tflops", 1800.0)) * 0.5             # dense TF32 = bf16 x 1.1/2.25 (nominal)
     tc = args.tensor_cores and prec == P.MS_PREC_FP32
-    cand = [("near", t_near, flops_near,
-             "k_list_tc (tcgen05 kind::tf32, 3xTF32) near pairs" if tc else "k_translate<float> near pairs"),
+    near_kernel = ("k_list_stored (stored 3xTF32 tiles by cp.async.bulk, tcgen05 kind::tf32) near pairs"
+                   if stored else "k_list_tc (tcgen05 kind::tf32, 3xTF32) near pairs")
+    cand = [("near", t_near, flops_near, near_kernel if tc else "k_translate<float> near pairs"),
             ("refl", t_refl, flops_refl,
              "k_m2s_tc + k_reflect + k_s2l_tc (tcgen05 kind::tf32, 3xTF32)" if tc else "k_m2s + k_reflect + k_s2l")]
     name, t_dom, flops_dom, kname = max(cand, key=lambda c: c[1])
@@ -268,6 +270,12 @@ def run_ours(args):
     else:
         peak, bound = fp32_peak, "alu"
         peak_src = f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} clock)"
+    hbm_peak = float(pk.get("hbm_gbs", 6400.0))
+    # stored near tiles: one pass over them per application, plus the FP32 staged block in and out
+    near_bytes = stored + 2 * wl.M * 2 * (2 * wl.p + 1) * nrhs * 8 if (tc and stored) else None
+    if name == "near" and near_bytes and near_bytes / t_dom / 1e9 / hbm_peak > achieved / peak:
+        achieved, peak, bound = near_bytes / t_dom / 1e9, hbm_peak, "hbm"
+        peak_src = f"measured HBM copy {hbm_peak} GB/s ({src})"
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     if os.path.exists(tpath):
@@ -310,13 +318,16 @@ def run_ours(args):
                            "near_pairs": pairs, "fmm_levels": solver.fmm_levels,
                            "leaf_target": args.leaf_target, "contour_depth": wl.depth,
                            "tensor_cores": bool(args.tensor_cores),
+                           "near_stored_gb": stored / 1e9,
                            "l2": "inputs 0.84 GB > 126 MB L2, no flush",
                            "parallelism": f"rhs-replicas x{world}"},
                 "roofline": {"bound": bound, "kernel": kname + f" (timed via ms_operator, part {name})",
-                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                              "flops": "algorithmic complex MACs x 8 (the 3xTF32 split issues 3 MMAs per product)"
-                             if tc else "algorithmic complex MACs x 8"},
+                             if tc else "algorithmic complex MACs x 8",
+                             "bytes": (f"stored near tiles {stored} B + FP32 block in and out"
+                                       if bound == "hbm" else None)},
                 "parts_ms": {"near": t_near * 1e3, "far": t_far * 1e3, "refl": t_refl * 1e3,
                              "sapply": t_sapply * 1e3,
                              "note": "each part timed through ms_operator, staging in and out included"},
@@ -347,16 +358,20 @@ def run_solve(args):
     import synthetic as syn
     wl = syn.config3_discs(M=args.M or 10000, nrhs=args.nrhs)
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
+    t0 = time.perf_counter()
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
                                restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol,
-                               block_krylov=not args.per_column)
+                               block_krylov=not args.per_column, precond_group=args.precond_group,
+                               store_near=args.store_near)
     torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
     g, info = s.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
     torch.cuda.synchronize()
     out = {"mode": "solve", "workload": wl.name, "M": wl.M, "nrhs": len(kinds), "tol": 1e-8,
            "krylov": "per-column GMRES" if args.per_column else "block GMRES over the right-hand sides",
            "restart": args.restart, "max_iters": args.max_iters, "tensor_cores": bool(args.tensor_cores),
-           "inner_tol": args.inner_tol or "default",
+           "inner_tol": args.inner_tol or "default", "precond_group": args.precond_group,
+           "setup_s": setup_s, "setup_note": "ms_setup incl. tables, tree and the preconditioner's inverses",
            "mixed": info}
     x = torch.empty_like(g)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,21 +417,22 @@ def run_grad(args):
     rx = wl.receivers
     truth = copy.deepcopy(wl)
     truth.centres = syn.perturb_centres(wl.centres, wl.radius, 0.05, 3001)
-    st = P.Solver.from_workload(truth, restart=args.restart)
+    st = P.Solver.from_workload(truth, restart=args.restart, precond_group=args.precond_group)
     gt, _ = st.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP32)     # refined to 1e-10 in FP64
     d = st.fields(gt, rx)
     st.close()
     out = {"mode": "grad", "workload": wl.name, "M": wl.M, "nrhs": wl.nrhs, "receivers": int(rx.shape[0])}
     precs = {"mixed": [("mixed", P.MS_PREC_FP32)], "fp64": [("fp64", P.MS_PREC_FP64)],
              "both": [("mixed", P.MS_PREC_FP32), ("fp64", P.MS_PREC_FP64)]}[args.grad_prec]
-    out.update({"tol": args.tol, "restart": args.restart, "max_iters": args.max_iters})
+    out.update({"tol": args.tol, "restart": args.restart, "max_iters": args.max_iters,
+                "precond_group": args.precond_group})
     for name, prec in precs:
         times = []
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s = P.Solver.from_workload(wl, tensor_cores=args.tensor_cores, restart=args.restart,
-                                       max_iters=args.max_iters)
+                                       max_iters=args.max_iters, precond_group=args.precond_group)
             g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=args.tol, prec=prec)
             u = s.fields(g, rx)
             w = (u - d).contiguous()
@@ -495,6 +511,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true", help="--mode solve: mixed form only")
     ap.add_argument("--grad-prec", choices=["mixed", "fp64", "both"], default="mixed")
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
+    ap.add_argument("--precond-group", type=int, default=0, help="--mode solve/grad: particles per block of the "
+                    "group-block Jacobi preconditioner (0: none)")
+    ap.add_argument("--store-near", type=int, default=0, help="device GB budget for the stored near-pair "
+                    "operator tiles (0: generated in every application)")
     ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
                     help="FP32 near field and spectral maps on the CUDA cores instead of tcgen05")
     args = ap.parse_args()
