@@ -27,6 +27,12 @@ nystrom     Nystrom boundary integral solve of one star-shaped particle (Kress l
 layered_bie brute-force boundary integral solve of a few particles with the layered Green's function
             (free-space part plus its Sommerfeld reflection), no scattering matrices (Sec. 7.1 direct method)
 adjoint     adjoint gradient of a receiver misfit in centres, radii and omega (inverse scattering, Sec. 7.5)
+sph3d       3D: spherical harmonics (continued to complex directions), vector spherical wave functions L, M, N,
+            closed-form rigid and traction-free sphere scattering matrices, the plane-wave coefficients a, b, c,
+            and the free-space translation by projection on a sphere about the target      (Sec. 6, 6.3)
+layered3d   3D layered operator: polar Sommerfeld rule, the spectral field of a particle (block B), the
+            P/SV/SH reflection at the interface, the plane-wave expansion about a particle (block C), the
+            mat-vec, plane waves from the upper layer, dense solve and fields               (Sec. 6.1-6.3)
 
 Pins (tests/test_oracle_*.py, all `-m "not gpu"`) tie each function to something other
 than itself: Bessel and Hankel values against mpmath, Graf pointwise evaluation, the
@@ -42,5 +48,10 @@ on trigonometric polynomials, the traction kernel against differences of the fun
 the Nystrom matrix on a disc against the closed form, an exact exterior solution from point forces
 inside a star, S7 against S10, the solver on a rotated boundary against the rotation phase, the
 multiple-scattering solve against the brute-force layered boundary integral solve of three stars,
-and the fixed contour rule against adaptive Gauss-Kronrod quadrature.
+and the fixed contour rule against adaptive Gauss-Kronrod quadrature.  For 3D (tests/test_oracle_3d.py):
+orthonormality and the addition theorem of the harmonics, differences of the harmonics and of the wave
+functions' curls, the exponential itself for the plane-wave coefficients at real and complex
+directions, sphere boundary conditions, the local expansion reproducing the sources' field, the polar
+quadrature of the spectral representation reproducing the outgoing field, zero reflection between
+identical layers, energy balance, and the solved system's boundary residual falling with the order.
 """

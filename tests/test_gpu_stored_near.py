@@ -58,10 +58,13 @@ def test_stored_apply_is_bitwise_equal_to_generated(pair, nrhs):
 
 
 def test_stored_solve_matches_generated(pair):
-    wl, s, g = pair
+    """A capped mixed solve: the same iterates, status and bits from the stored and generated tiles."""
+    wl = pair[0]
+    s = P.Solver.from_workload(wl, store_near=4, max_iters=40)
+    g = P.Solver.from_workload(wl, max_iters=40)
     a, ia = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP32)
     b, ib = g.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP32)
-    assert ia["status"] == 0 and ib["status"] == 0
+    assert ia["status"] == ib["status"]
     assert ia["iterations"] == ib["iterations"]
     assert torch.equal(a, b)
 
