@@ -451,6 +451,62 @@ def run_grad(args):
     print(json.dumps(out), flush=True)
 
 
+def run_3d(args):
+    """The 3D workload (Sec. 6): 500 rigid spheres of radius U[0.3, 0.5] in [-15, 15]^2 x [-12, -1], p = 8,
+    16 plane waves, polar Sommerfeld rule 128 x 64 with contour depth 3 / (horizontal extent) (the 2D
+    reading for wide clouds).  Times the FP64 mat-vec and its parts, then the block-GMRES solve to
+    --tol; algorithmic complex multiply-adds per application are counted from the sizes."""
+    import torch
+
+    import paper_2608_26875_b300 as P
+    import synthetic as syn
+    from paper_2608_26875_b300 import _native as nat
+    wl = syn.spheres3d(M=args.M or 500)
+    ext = float(np.hypot(np.ptp(wl.centres[:, 0]), np.ptp(wl.centres[:, 1])))
+    alpha = min(1.0, 3.0 / ext)
+    t0 = time.perf_counter()
+    s = P.Solver3(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, wl.p, n_r=128, n_theta=64, n_panels=4,
+                  t_max=10.0, alpha=alpha, beta=1.0, restart=args.restart, max_iters=args.max_iters)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    nrhs = wl.nrhs
+    x = s.rhs(wl.inc_kind, wl.inc_theta, wl.inc_phi)
+    y = torch.empty_like(x)
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n / 1000.0
+
+    n = max(1, args.steps)
+    t_all = timed(lambda: s.apply(x, out=y), n)
+    t_T = timed(lambda: s.operator(x, nat.MS3_PART_T, out=y), n)
+    t_R = timed(lambda: s.operator(x, nat.MS3_PART_R, out=y), n)
+    p, M, NS = wl.p, wl.M, s.n_nodes
+    nl, nmn, K2 = (p + 1) ** 2, p * (p + 2), (p + 2) ** 2
+    T = 2 * nmn + nl
+    cmac_T = M * (M - 1) * (3 * K2 * nl + nl * nl) * nrhs
+    cmac_R = NS * M * (nl + 4 * nmn) * nrhs + M * NS * 3 * T * nrhs
+    fp64_peak = 1.13e12           # measured FP64 FMA-chain rate of this GPU (design notes)
+    out = {"mode": "3d", "workload": wl.name, "M": M, "p": p, "nrhs": nrhs, "n_nodes": NS, "contour_alpha": alpha,
+           "setup_s": setup_s, "matvec_s": t_all, "matvecs_per_s": 1.0 / t_all, "free_space_s": t_T,
+           "reflected_s": t_R, "dtype": "f64",
+           "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak / 1e12,
+                        "free_space": {"achieved": 8 * cmac_T / t_T / 1e12, "frac": 8 * cmac_T / t_T / fp64_peak},
+                        "reflected": {"achieved": 8 * cmac_R / t_R / 1e12, "frac": 8 * cmac_R / t_R / fp64_peak},
+                        "flops": "complex MACs of the contractions x 8 (translation-coefficient generation not counted)"}}
+    if not args.skip_fp64:
+        g, info = s.solve(wl.inc_kind, wl.inc_theta, wl.inc_phi, tol=args.tol)
+        out["solve"] = info
+    print(json.dumps(out), flush=True)
+
+
 def launches_per_step(solver, tensor_cores=False):
     """Kernels of one ms_apply: staging in/out, near sum (2 waves; one tensor-core launch for both),
     FMM (per wave: P2M, M2M per level, M2L per level, L2L per level, L2P), M2S, reflect, S2L (plus
@@ -495,7 +551,7 @@ def main():
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small case for ncu (see run_profile)")
-    ap.add_argument("--mode", choices=["matvec", "solve", "grad"], default="matvec")
+    ap.add_argument("--mode", choices=["matvec", "solve", "grad", "3d"], default="matvec")
     ap.add_argument("--full-fp64", action="store_true", help="solve mode: run the FP64 solve too")
     ap.add_argument("--part", choices=["near", "far", "refl", "sapply", "all"], default="near")
     ap.add_argument("--M", type=int, default=None, help="particles: --profile (default 2500), --mode solve "
@@ -524,6 +580,8 @@ def main():
         run_solve(args)
     elif args.mode == "grad":
         run_grad(args)
+    elif args.mode == "3d":
+        run_3d(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

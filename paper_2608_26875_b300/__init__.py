@@ -15,7 +15,7 @@ from . import _native as nat
 from ._native import (MS_PART_R, MS_PART_S, MS_PART_T, MS_PART_T_FAR, MS_PART_T_NEAR, MS_PREC_BF16,
                       MS_PREC_FP32, MS_PREC_FP64, MsError)
 
-__all__ = ["Solver", "MsError", "MS_PREC_FP64", "MS_PREC_FP32", "MS_PREC_BF16", "MS_PART_T", "MS_PART_R", "MS_PART_S",
+__all__ = ["Solver", "Solver3", "MsError", "MS_PREC_FP64", "MS_PREC_FP32", "MS_PREC_BF16", "MS_PART_T", "MS_PART_R", "MS_PART_S",
            "MS_PART_T_NEAR", "MS_PART_T_FAR", "default_options"]
 
 
@@ -309,6 +309,95 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             nat.lib().ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver3:
+    """3D handle (include/ms3_b300.h): spheres below the interface, vector spherical wave expansions,
+    polar Sommerfeld rule.  Blocks are torch CUDA tensors (M, T, nrhs) complex128, T = 2p(p+2) + (p+1)^2,
+    coefficients in the order [alpha (n = 1..p) | beta (n = 1..p) | gamma (n = 0..p)], (n, m) at
+    n^2 + n + m (minus one for alpha and beta)."""
+
+    def __init__(self, centres, radius, bc, media, omega: float, p: int, n_r: int = 128, n_theta: int = 64,
+                 n_panels: int = 4, t_max: float = 10.0, alpha: float = 1.0, beta: float = 1.0, restart: int = 60,
+                 max_iters: int = 1000):
+        L = nat.lib()
+        c = np.ascontiguousarray(centres, dtype=np.float64)
+        r = np.ascontiguousarray(radius, dtype=np.float64)
+        b = np.ascontiguousarray(bc, dtype=np.int32)
+        g = nat.Geometry3()
+        g.M = int(r.shape[0])
+        g.centres, g.radius, g.bc = _dp(c), _dp(r), _ip(b)
+        md = nat.Media(float(media.lam_u), float(media.mu_u), float(media.lam_l), float(media.mu_l))
+        o = nat.Options3()
+        L.ms3_default_options(ctypes.byref(o))
+        o.n_r, o.n_theta, o.n_panels = int(n_r), int(n_theta), int(n_panels)
+        o.t_max, o.alpha, o.beta = float(t_max), float(alpha), float(beta)
+        o.restart, o.max_iters = int(restart), int(max_iters)
+        h = ctypes.c_void_p()
+        nat.check(L.ms3_setup(ctypes.byref(g), ctypes.byref(md), float(omega), int(p), ctypes.byref(o),
+                              ctypes.byref(h)), "ms3_setup")
+        self._h = h
+        self.M, self.p = g.M, int(p)
+        self.T = 2 * self.p * (self.p + 2) + (self.p + 1) ** 2
+        nn = nat.c_int()
+        L.ms3_info(h, None, None, None, ctypes.byref(nn))
+        self.n_nodes = int(nn.value)
+
+    def _check(self, x):
+        if not (x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous()) or x.dim() != 3 or \
+                tuple(x.shape[:2]) != (self.M, self.T):
+            raise ValueError(f"expected a contiguous complex128 CUDA tensor ({self.M}, {self.T}, nrhs)")
+        return int(x.shape[2])
+
+    def apply(self, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """y = x - S (T + R) x (ms3_apply)."""
+        return self.operator(x, nat.MS3_PART_T | nat.MS3_PART_R | nat.MS3_PART_S, out, stream)
+
+    def operator(self, x: torch.Tensor, parts: int, out=None, stream=None) -> torch.Tensor:
+        """The selected parts (ms3_operator): with MS3_PART_S, x - S (parts) x; else (parts) x."""
+        nrhs = self._check(x)
+        y = out if out is not None else torch.empty_like(x)
+        nat.check(nat.lib().ms3_operator(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), nrhs,
+                                         int(parts), _stream(stream)), "ms3_operator")
+        return y
+
+    @staticmethod
+    def _incidence(kinds, thetas, phis):
+        k = np.ascontiguousarray(kinds, dtype=np.int32)
+        t = np.ascontiguousarray(thetas, dtype=np.float64)
+        f = np.ascontiguousarray(phis, dtype=np.float64)
+        inc = nat.Incidence3(int(k.shape[0]), _ip(k), _dp(t), _dp(f))
+        return inc, (k, t, f)
+
+    def rhs(self, kinds, thetas, phis, stream=None) -> torch.Tensor:
+        """b = S a0 for plane waves from the upper layer (kind 0 P, 1 SV, 2 SH; angle from the downward
+        vertical; azimuth) (ms3_rhs)."""
+        inc, keep = self._incidence(kinds, thetas, phis)
+        b = torch.empty((self.M, self.T, inc.nrhs), dtype=torch.complex128, device="cuda")
+        nat.check(nat.lib().ms3_rhs(self._h, ctypes.byref(inc), ctypes.c_void_p(b.data_ptr()), _stream(stream)),
+                  "ms3_rhs")
+        return b
+
+    def solve(self, kinds, thetas, phis, tol: float = 1e-10, stream=None):
+        """tau solving A tau = S a0 (ms3_solve).  Returns (tau, info)."""
+        inc, keep = self._incidence(kinds, thetas, phis)
+        g = torch.empty((self.M, self.T, inc.nrhs), dtype=torch.complex128, device="cuda")
+        info = nat.SolveInfo()
+        st = nat.check(nat.lib().ms3_solve(self._h, ctypes.byref(inc), float(tol), ctypes.c_void_p(g.data_ptr()),
+                                           ctypes.byref(info), _stream(stream)), "ms3_solve", allow_warning=True)
+        return g, {"iterations": info.iterations, "matvecs": info.matvecs, "max_rel_residual": info.max_rel_residual,
+                   "seconds": info.seconds, "status": st}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().ms3_destroy(self._h)
             self._h = None
 
     def __del__(self):

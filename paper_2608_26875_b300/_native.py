@@ -1,4 +1,4 @@
-"""ctypes binding of libms_b300.so (declarations in include/ms_b300.h).
+"""ctypes binding of libms_b300.so (declarations in include/ms_b300.h and include/ms3_b300.h).
 
 Argument marshalling only: every step of the operator, the solve and the fields runs inside
 the CUDA library.  Device buffers are torch tensors (complex128, contiguous, on the CUDA
@@ -37,6 +37,10 @@ MS_PART_S = 4
 MS_PART_T_NEAR = 8
 MS_PART_T_FAR = 16
 
+MS3_PART_T = 1
+MS3_PART_R = 2
+MS3_PART_S = 4
+
 c_int = ctypes.c_int32
 c_dp = ctypes.POINTER(ctypes.c_double)
 c_ip = ctypes.POINTER(ctypes.c_int32)
@@ -45,6 +49,22 @@ c_ip = ctypes.POINTER(ctypes.c_int32)
 class Geometry(ctypes.Structure):
     _fields_ = [("M", c_int), ("centres", c_dp), ("radius", c_dp), ("bc", c_ip), ("proto", c_ip),
                 ("rotation", c_dp), ("n_proto", c_int), ("proto_S", c_dp)]
+
+
+class Geometry3(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("centres", ctypes.POINTER(ctypes.c_double)),
+                ("radius", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Options3(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_panels", ctypes.c_int32),
+                ("t_max", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32)]
+
+
+class Incidence3(ctypes.Structure):
+    _fields_ = [("nrhs", ctypes.c_int32), ("kind", ctypes.POINTER(ctypes.c_int32)),
+                ("theta", ctypes.POINTER(ctypes.c_double)), ("phi", ctypes.POINTER(ctypes.c_double))]
 
 
 class Media(ctypes.Structure):
@@ -104,6 +124,15 @@ SIGNATURES = {
     "ms_tensor_peak": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ms_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip, ctypes.POINTER(ctypes.c_int64)]),
     "ms_destroy": (None, [ctypes.c_void_p]),
+    "ms3_default_options": (None, [ctypes.c_void_p]),
+    "ms3_setup": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ms3_apply": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p]),
+    "ms3_operator": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, ctypes.c_void_p]),
+    "ms3_rhs": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ms3_solve": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p]),
+    "ms3_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip]),
+    "ms3_destroy": (None, [ctypes.c_void_p]),
     "ms_status_string": (ctypes.c_char_p, [c_int]),
     "ms_last_cuda_error": (c_int, [ctypes.c_void_p]),
 }

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <complex>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -288,7 +289,7 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 // (splitmix64) of the entry index and the call's seed.
 template <typename T>
 __global__ void k_fill_random(typename CT<T>::c* __restrict__ dst, long long N, int s, int c0,
-                              unsigned long long seed) {
+                              unsigned long long seed, double scale) {
     const int w = s - c0;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N * w) return;
@@ -298,7 +299,7 @@ __global__ void k_fill_random(typename CT<T>::c* __restrict__ dst, long long N, 
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    dst[row * s + c] = to_c<T>(make_double2((z & 0xffffffff) * 0x1p-31 - 1.0, (z >> 32) * 0x1p-31 - 1.0));
+    dst[row * s + c] = to_c<T>(make_double2(((z & 0xffffffff) * 0x1p-31 - 1.0) * scale, ((z >> 32) * 0x1p-31 - 1.0) * scale));
 }
 
 // ------------------------------------------------------------------ host: small dense FP64 algebra
@@ -474,12 +475,16 @@ struct BlockKrylov {
     }
     // relative eigenvalue floor of a Gram matrix: below it a direction of the block is rounding noise
     double floor_rel() const { return 64.0 * (sizeof(T) == 8 ? 1.11e-16 : 5.96e-8); }
+    // Cholesky factor of a Gram matrix, refused when a column is negligible against the largest or
+    // (nearly) dependent on the columns before it: R_ii^2 below the floor times its own G_ii
     bool chol_checked(const std::vector<cd>& Gm, std::vector<cd>& R) {
         double dmax = 0;
         for (int i = 0; i < s; ++i) dmax = std::max(dmax, Gm[(size_t)i * s + i].real());
         if (!(dmax > 0) || !chol_upper(Gm, s, 0.0, R)) return false;
-        for (int i = 0; i < s; ++i)
-            if (!(std::norm(R[(size_t)i * s + i]) >= floor_rel() * dmax)) return false;
+        for (int i = 0; i < s; ++i) {
+            const double gii = Gm[(size_t)i * s + i].real();
+            if (!(gii >= floor_rel() * dmax) || !(std::norm(R[(size_t)i * s + i]) >= floor_rel() * gii)) return false;
+        }
         return true;
     }
     // Orthonormal block dst with src = dst R (R s x s), orthogonal to the nprev basis blocks before it.
@@ -524,7 +529,9 @@ struct BlockKrylov {
         }
         if ((rc = update(src, s, Y, dst, false, 1.0))) return rc;
         if (k < s) {
-            k_fill_random<T><<<nblk(N * (s - k), 256), 256, 0, st>>>(dst, N, s, k, 0x632BE59BD9B4E019ull + 977ull * deflations);
+            // entries of variance 2/3 per component: unit expected column norm with the 1 / sqrt(4N/3) scale
+            k_fill_random<T><<<nblk(N * (s - k), 256), 256, 0, st>>>(dst, N, s, k, 0x632BE59BD9B4E019ull + 977ull * deflations,
+                                                                     1.0 / sqrt(4.0 * N / 3.0));
             if ((rc = ms_check(h, cudaGetLastError()))) return rc;
         }
         for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
@@ -720,6 +727,28 @@ int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds
     if (rc || !pc) return rc;
     if ((rc = ms_precond_apply<T>(h, ds, K->Z, nrhs, adjoint, st))) return rc;
     return ms_check(h, cudaMemcpyAsync(ds, K->Z, (size_t)N * nrhs * sizeof(C), cudaMemcpyDeviceToDevice, st));
+}
+
+// Block GMRES in FP64 on the CUDA cores for an operator given as a callable (the 3D system): x holds
+// the initial guess (zero here) and receives the solution; restart in block iterations.
+int ms_block_solve_fp64(ms_handle* herr, long long N, int nrhs, int restart,
+                        const std::function<int(const double2*, double2*)>& op, const double2* b, double2* x,
+                        double tol, int max_iters, int& iters, int& matvecs, std::vector<double>& relres,
+                        cudaStream_t st) {
+    int m = std::max(1, restart);
+    BlockKrylov<double>* K = nullptr;
+    while (true) {
+        K = new BlockKrylov<double>{herr, st, N, nrhs, m, false};
+        if (K->init() == MS_OK) break;
+        delete K;
+        K = nullptr;
+        if (m <= 4) return MS_ERR_ALLOC;
+        m /= 2;
+    }
+    auto opc = [&](const double2* in, double2* out) -> int { return op(in, out); };
+    const int rc = block_gmres<double>(*K, opc, b, x, tol, max_iters, true, iters, matvecs, relres);
+    delete K;
+    return rc;
 }
 
 template <typename T>

@@ -1,0 +1,1167 @@
+// 3D extension (Sec. 6): spheres below the interface of two welded elastic half-spaces, vector
+// spherical wave expansions, 2D Sommerfeld integrals in polar form.  FP64 throughout.
+//
+// One application of  y = x - S (T + R) x  (ms3_b300.h) runs as
+//   k3_cart       each sphere's shear field as three Cartesian scalar outgoing expansions (degree <= p+1)
+//   k3_translate  every sphere's Cartesian shear expansions and compressional potential translated to
+//                 regular expansions about every other sphere by the scalar addition theorem, on the fly
+//   k3_uncart     regular Cartesian shear expansions back to the coefficients a (N) and b (M); the
+//                 compressional potential's coefficients are c directly (L = grad v)
+//   k3_m2s        upgoing P, SV, SH amplitudes at every Sommerfeld node (block B, Sec. 6.2)
+//   k3_reflect    the 3 x 3 reflection at z = 0 per node, quadrature weight folded in
+//   k3_s2l        regular expansions of the downgoing waves about every sphere (block C, Sec. 6.3)
+//   k3_sapply     the sphere matrices and the combine y = x - S a
+//
+// Translation (block D).  With x = x' + d, d = c_m - c_l, |x'| < |d|, the scalar addition theorem
+//     h_n(k |x|) Y_n^m(x^) = sum_{nu, mu} A^{n m}_{nu mu}(d) j_nu(k |x'|) Y_nu^mu(x'^),
+//     A^{n m}_{nu mu} = 4 pi sum_q i^{nu - n + q} h_q(k |d|) Y_q^{m - mu}(d^) G(n, m; nu, mu; q),
+//     G = int Y_n^m conj(Y_nu^mu) conj(Y_q^{m - mu}) dOmega   (Gaunt; q = |n - nu|, |n - nu| + 2, ..., n + nu),
+// translates the compressional potential sum gamma v^{kp} (L = grad v, so its regular coefficients are c).
+// The shear field is not a scalar potential; its three Cartesian components are scalar outgoing waves:
+//     N_nm = [(n+1) z_{n-1} V-_nm + n z_{n+1} V+_nm] / (i (2n+1)),   M_nm = z_n X_nm,
+//     V-_nm = n Y rhat + Grad Y (components of degree n-1), V+_nm = (n+1) Y rhat - Grad Y (degree n+1),
+//     X_nm = Grad Y x rhat (degree n),
+// (z_n(kr)/(kr) and z_n' by the three-term relations), so each component is translated as a scalar and
+// the regular coefficients come back by orthogonality of V-, V+ and X on the sphere:
+//     a_Jm = i <V-_Jm, U_{J-1}> / (J (J+1)),   b_Jm = <X_Jm, U_J> / (J (J+1)),
+// U_nu the degree-nu part of the regular Cartesian expansion.  The Gaunt coefficients and the Cartesian
+// maps are computed at setup by exact Gauss quadrature on the sphere.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <functional>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+#include "ms3_b300.h"
+
+typedef std::complex<double> cd;
+
+namespace {
+
+constexpr int P3MAX = 10;               // 4 (p+1)^2 translation threads per CTA <= 512
+constexpr int RC = 16;                 // right-hand sides per translation / m2s chunk
+
+inline int idx(int n, int m) { return n * n + n + m; }
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ host: spherical functions
+// Q[n][m] = d^m P_n / dt^m (0 <= m <= n <= P) at complex t by the recurrence in n at fixed m:
+// Q_m^m = (2m-1)!!, Q_{m+1}^m = (2m+1) t Q_m^m, (n-m+1) Q_{n+1}^m = (2n+1) t Q_n^m - (n+m) Q_{n-1}^m.
+std::vector<cd> qtab(int P, cd t) {
+    std::vector<cd> Q((size_t)(P + 2) * (P + 2), cd(0));
+    auto at = [&](int n, int m) -> cd& { return Q[(size_t)n * (P + 2) + m]; };
+    double df = 1.0;
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) df *= (2.0 * m - 1.0);
+        at(m, m) = df;
+        if (m + 1 <= P) at(m + 1, m) = (2.0 * m + 1.0) * t * df;
+        for (int n = m + 1; n < P; ++n) at(n + 1, m) = ((2.0 * n + 1.0) * t * at(n, m) - (double)(n + m) * at(n - 1, m)) / (double)(n - m + 1);
+    }
+    return Q;
+}
+
+double ynorm(int n, int am) {
+    double r = (2.0 * n + 1.0) / (4.0 * M_PI);
+    for (int k = n - am + 1; k <= n + am; ++k) r /= k;
+    return sqrt(r);
+}
+
+// Y_n^m(d) for n <= P at a unit direction d (d.d = 1, complex allowed): N Q_n^|m|(d_z) (d_x +- i d_y)^|m|
+void ylm_c(int P, const cd d[3], std::vector<cd>& Y) {
+    Y.assign((size_t)(P + 1) * (P + 1), cd(0));
+    const std::vector<cd> Q = qtab(P + 1, d[2]);
+    for (int n = 0; n <= P; ++n)
+        for (int m = -n; m <= n; ++m) {
+            const int am = std::abs(m);
+            const cd w = d[0] + (m >= 0 ? cd(0, 1) : cd(0, -1)) * d[1];
+            Y[idx(n, m)] = ynorm(n, am) * Q[(size_t)n * (P + 3) + am] * std::pow(w, am);
+        }
+}
+
+// Surface gradient Grad Y = grad H - n H d of the solid harmonic H = N w^|m| r^{n-|m|} Q(z/r), at r = 1:
+//   Grad Y = N [ |m| w^{|m|-1} Q grad w - |m| w^|m| Q d + w^|m| Q_n^{|m|+1} (e_z - d_z d) ],  grad w = (1, +-i, 0)
+void grad_ylm_c(int P, const cd d[3], std::vector<cd>& G) {
+    G.assign((size_t)(P + 1) * (P + 1) * 3, cd(0));
+    const std::vector<cd> Q = qtab(P + 1, d[2]);
+    auto q = [&](int n, int m) -> cd { return m > n ? cd(0) : Q[(size_t)n * (P + 3) + m]; };
+    for (int n = 0; n <= P; ++n)
+        for (int m = -n; m <= n; ++m) {
+            const int am = std::abs(m);
+            const cd sg = m >= 0 ? cd(0, 1) : cd(0, -1);
+            const cd w = d[0] + sg * d[1];
+            const double N = ynorm(n, am);
+            const cd wm = std::pow(w, am);
+            const cd wm1 = am > 0 ? (double)am * std::pow(w, am - 1) : cd(0);
+            const cd Qn = q(n, am), Qd = q(n, am + 1);
+            const cd gw[3] = {cd(1), sg, cd(0)};
+            const cd ez[3] = {cd(0), cd(0), cd(1)};
+            for (int i = 0; i < 3; ++i)
+                G[(size_t)idx(n, m) * 3 + i] = N * (wm1 * Qn * gw[i] - (double)am * wm * Qn * d[i] + wm * Qd * (ez[i] - d[2] * d[i]));
+        }
+}
+
+cd dot3(const cd a[3], const cd b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+void cross3(const cd a[3], const cd b[3], cd out[3]) {
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// spherical Bessel and Hankel values z_n, z_n' at real x, n = 0..N
+void sph_jh(int N, double x, std::vector<cd>& j, std::vector<cd>& jd, std::vector<cd>& h, std::vector<cd>& hd) {
+    j.resize(N + 2); jd.resize(N + 1); h.resize(N + 2); hd.resize(N + 1);
+    for (int n = 0; n <= N + 1; ++n) {
+        const double jn = std::sph_bessel((unsigned)n, x), yn = std::sph_neumann((unsigned)n, x);
+        j[n] = jn;
+        h[n] = cd(jn, yn);
+    }
+    for (int n = 0; n <= N; ++n) {
+        // z_n' = n z_n / x - z_{n+1}
+        jd[n] = (double)n * j[n] / x - j[n + 1];
+        hd[n] = (double)n * h[n] / x - h[n + 1];
+    }
+}
+
+// Rigid (bc 0) or traction-free (bc 1) sphere: per n the 2 x 2 map (a, c) -> (alpha, gamma) and the
+// scalar b -> beta, from the boundary condition in the orthogonal components (rhat Y, Grad Y, Grad Y x rhat).
+void sphere_s(int p, double kp, double ks, double lam, double mu, double R, int bc, cd* out /* [p+1][5] */) {
+    std::vector<cd> js, jsd, hs, hsd, jp, jpd, hp, hpd;
+    sph_jh(p, ks * R, js, jsd, hs, hsd);
+    sph_jh(p, kp * R, jp, jpd, hp, hpd);
+    const cd I(0, 1);
+    for (int n = 0; n <= p; ++n) {
+        cd comp[2][5];     // [j or h][Nr, Ng, Mt, Lr, Lg]
+        for (int kind = 0; kind < 2; ++kind) {
+            const cd z = kind ? hs[n] : js[n], zd = kind ? hsd[n] : jsd[n];
+            const cd qv = kind ? hp[n] : jp[n], qd = kind ? hpd[n] : jpd[n];
+            if (bc == 0) {
+                comp[kind][0] = (double)(n * (n + 1)) * z / R / (I * ks);
+                comp[kind][1] = (z + ks * R * zd) / R / (I * ks);
+                comp[kind][2] = z;
+                comp[kind][3] = kp * qd;
+                comp[kind][4] = qv / R;
+            } else {
+                // traction sigma(u) rhat = 2 mu d_r u + lam rhat div u + mu rhat x curl u, with
+                // x^2 z'' = -2 x z' - (x^2 - n(n+1)) z for the second derivatives
+                const double xs = ks * R, xp = kp * R;
+                const cd zdd = (-2.0 * xs * zd - (xs * xs - n * (n + 1.0)) * z) / (xs * xs);
+                const cd qdd = (-2.0 * xp * qd - (xp * xp - n * (n + 1.0)) * qv) / (xp * xp);
+                const cd dra = (double)(n * (n + 1)) * (ks * zd / R - z / (R * R));
+                const cd drb = ks * zd / R - z / (R * R) + ks * ks * zdd;
+                comp[kind][0] = 2.0 * mu * dra / (I * ks);
+                comp[kind][1] = 2.0 * mu * drb / (I * ks) - I * ks * mu * z;
+                comp[kind][2] = mu * (ks * zd - z / R);
+                comp[kind][3] = 2.0 * mu * kp * kp * qdd - lam * kp * kp * qv;
+                comp[kind][4] = 2.0 * mu * (kp * qd / R - qv / (R * R));
+            }
+        }
+        cd* o = out + (size_t)n * 5;
+        for (int k = 0; k < 5; ++k) o[k] = 0;
+        if (n == 0) {
+            o[0] = -comp[0][3] / comp[1][3];
+            continue;
+        }
+        // S2 = -A^{-1} B, A = [[Nr_h, Lr_h], [Ng_h, Lg_h]], B = [[Nr_j, Lr_j], [Ng_j, Lg_j]]
+        const cd a11 = comp[1][0], a12 = comp[1][3], a21 = comp[1][1], a22 = comp[1][4];
+        const cd det = a11 * a22 - a12 * a21;
+        const cd b11 = comp[0][0], b12 = comp[0][3], b21 = comp[0][1], b22 = comp[0][4];
+        o[0] = -(a22 * b11 - a12 * b21) / det;
+        o[1] = -(a22 * b12 - a12 * b22) / det;
+        o[2] = -(-a21 * b11 + a11 * b21) / det;
+        o[3] = -(-a21 * b12 + a11 * b22) / det;
+        o[4] = -comp[0][2] / comp[1][2];
+    }
+}
+
+// small dense complex solve (Gaussian elimination with partial pivoting), A n x n row-major, B n x k
+bool solve_small(std::vector<cd> A, int n, std::vector<cd>& B, int k) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::abs(A[(size_t)r * n + c]) > std::abs(A[(size_t)piv * n + c])) piv = r;
+        if (std::abs(A[(size_t)piv * n + c]) == 0.0) return false;
+        if (piv != c) {
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+            for (int j = 0; j < k; ++j) std::swap(B[(size_t)c * k + j], B[(size_t)piv * k + j]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const cd f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+            for (int j = c; j < n; ++j) A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+            for (int j = 0; j < k; ++j) B[(size_t)r * k + j] -= f * B[(size_t)c * k + j];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c)
+        for (int j = 0; j < k; ++j) {
+            cd v = B[(size_t)c * k + j];
+            for (int r = c + 1; r < n; ++r) v -= A[(size_t)c * n + r] * B[(size_t)r * k + j];
+            B[(size_t)c * k + j] = v / A[(size_t)c * n + c];
+        }
+    return true;
+}
+
+struct Layer {
+    double lam, mu, kp, ks;
+};
+
+// plane wave basis at horizontal wavenumber lam (complex) and azimuth th in a layer: direction, SV, SH
+void pw_basis(double k, cd lam, double th, bool up, cd e[3], cd v[3], cd h[3]) {
+    const cd kz = std::sqrt(k * k - lam * lam);
+    const double c = cos(th), s = sin(th);
+    e[0] = lam * c / k; e[1] = lam * s / k; e[2] = (up ? kz : -kz) / k;
+    h[0] = -s; h[1] = c; h[2] = 0.0;
+    cross3(h, e, v);
+}
+
+// traction sigma e_z of A e^{i kvec.x}: i [lam (k.A) e_z + mu (k A_z + A k_z)]
+void traction(const cd kv[3], const cd A[3], double lam, double mu, cd t[3]) {
+    const cd kA = dot3(kv, A), I(0, 1);
+    for (int i = 0; i < 3; ++i) t[i] = I * (mu * (kv[i] * A[2] + A[i] * kv[2]));
+    t[2] += I * lam * kA;
+}
+
+// displacement and traction columns of the three waves (P, SV, SH) of a layer, up or down
+void wave_cols(const Layer& L, cd lam, double th, bool up, cd U[3][3], cd Tr[3][3]) {
+    cd eP[3], vP[3], hP[3], eS[3], vS[3], hS[3];
+    pw_basis(L.kp, lam, th, up, eP, vP, hP);
+    pw_basis(L.ks, lam, th, up, eS, vS, hS);
+    const cd* pol[3] = {eP, vS, hS};
+    const cd* dir[3] = {eP, eS, eS};
+    const double kk[3] = {L.kp, L.ks, L.ks};
+    for (int w = 0; w < 3; ++w) {
+        cd kv[3];
+        for (int i = 0; i < 3; ++i) {
+            kv[i] = kk[w] * dir[w][i];
+            U[w][i] = pol[w][i];
+        }
+        traction(kv, pol[w], L.lam, L.mu, Tr[w]);
+    }
+}
+
+// interface system at one node: unknowns (lower down P, SV, SH; upper up P, SV, SH), continuity of
+// displacement and traction at z = 0; right-hand columns given as (displacement, traction) pairs
+bool interface_solve(const Layer& lo, const Layer& up, cd lam, double th, std::vector<cd>& rhs, int k) {
+    cd Ud[3][3], Td[3][3], Uu[3][3], Tu[3][3];
+    wave_cols(lo, lam, th, false, Ud, Td);
+    wave_cols(up, lam, th, true, Uu, Tu);
+    std::vector<cd> A(36);
+    for (int w = 0; w < 3; ++w)
+        for (int i = 0; i < 3; ++i) {
+            A[(size_t)i * 6 + w] = Ud[w][i];
+            A[(size_t)(3 + i) * 6 + w] = Td[w][i];
+            A[(size_t)i * 6 + 3 + w] = -Uu[w][i];
+            A[(size_t)(3 + i) * 6 + 3 + w] = -Tu[w][i];
+        }
+    return solve_small(A, 6, rhs, k);
+}
+
+// Regular coefficients (a, b, c) of e^{i k_s x.d} pol (pol . d = 0) or e^{i k_p x.d} d (Sec. 6.3):
+//   a_nm = 4 pi i^n / (n(n+1)) Grad Y_n^{-m}(d) . pol,  b_nm = -4 pi i^n / (n(n+1)) (d x Grad Y_n^{-m}(d)) . pol,
+//   c_nm = -4 pi i^{n+1} / kp Y_n^{-m}(d) (d . pol)
+void plane_coeffs(int p, double kp, const cd d[3], const cd pol[3], cd* out) {
+    std::vector<cd> Y, G;
+    ylm_c(p, d, Y);
+    grad_ylm_c(p, d, G);
+    const int nmn = p * (p + 2);
+    const cd I(0, 1);
+    const cd dp = dot3(d, pol);
+    for (int n = 0; n <= p; ++n) {
+        const cd in = std::pow(I, n);
+        for (int m = -n; m <= n; ++m) {
+            const int k = idx(n, -m);
+            const cd* g = &G[(size_t)k * 3];
+            out[2 * nmn + idx(n, m)] = -4.0 * M_PI * in * I / kp * Y[k] * dp;
+            if (n == 0) continue;
+            cd dxg[3];
+            cross3(d, g, dxg);
+            const double f = 4.0 * M_PI / (n * (n + 1.0));
+            out[idx(n, m) - 1] = f * in * dot3(g, pol);
+            out[nmn + idx(n, m) - 1] = -f * in * dot3(dxg, pol);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ device kernels
+__constant__ int c_deg[(P3MAX + 2) * (P3MAX + 2)];
+__constant__ int c_ord[(P3MAX + 2) * (P3MAX + 2)];
+__constant__ double c_ynorm[(2 * P3MAX + 2) * (2 * P3MAX + 2)];     // N_qk, k >= 0, at [q * (2P+2) + k]
+
+__device__ __forceinline__ int didx(int n, int m) { return n * n + n + m; }
+
+// y = (identity ? x : 0) - S a  (identity) or S a (apply only), per sphere and order
+__global__ void k3_sapply(const double2* __restrict__ x, const double2* __restrict__ a, double2* __restrict__ y,
+                          const double2* __restrict__ Sd, int M, int p, int nrhs, int identity, int apply_s) {
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * T * nrhs) return;
+    const int r = (int)(i % nrhs);
+    const long long mk = i / nrhs;
+    const int m = (int)(mk / T), k = (int)(mk % T);
+    const double2* A = a + (size_t)m * T * nrhs;
+    double2 v;
+    if (!apply_s) {
+        v = A[(size_t)k * nrhs + r];
+    } else {
+        int blk, kk;
+        if (k < nmn) { blk = 0; kk = k + 1; }
+        else if (k < 2 * nmn) { blk = 1; kk = k - nmn + 1; }
+        else { blk = 2; kk = k - 2 * nmn; }
+        const int n = (int)sqrtf((float)kk + 0.5f);
+        const double2* S = Sd + ((size_t)m * (p + 1) + n) * 5;
+        if (blk == 2 && n == 0) {
+            v = cmul(S[0], A[(size_t)k * nrhs + r]);
+        } else if (blk == 1) {
+            v = cmul(S[4], A[(size_t)k * nrhs + r]);
+        } else {
+            const double2 aa = A[(size_t)(kk - 1) * nrhs + r];                // alpha-block entry of (n, m)
+            const double2 ac = A[(size_t)(2 * nmn + kk) * nrhs + r];         // gamma-block entry
+            v = blk == 0 ? cadd(cmul(S[0], aa), cmul(S[1], ac)) : cadd(cmul(S[2], aa), cmul(S[3], ac));
+        }
+    }
+    y[i] = identity ? csub(x[i], v) : v;
+}
+
+// Cartesian outgoing expansions of each sphere's shear field: W[l][c][k'][r] = sum of <= 9 terms
+__global__ void k3_cart(const double2* __restrict__ x, double2* __restrict__ W, const int* __restrict__ midx,
+                        const double2* __restrict__ mcoef, int M, int p, int nrhs) {
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * 3 * K2 * nrhs) return;
+    const int r = (int)(i % nrhs);
+    const long long row = i / nrhs;
+    const int l = (int)(row / (3 * K2)), ck = (int)(row % (3 * K2));
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = 0; t < 9; ++t) {
+        const int s = midx[ck * 9 + t];
+        if (s < 0) break;
+        cfma(acc, mcoef[ck * 9 + t], x[((size_t)l * T + s) * nrhs + r]);
+    }
+    W[i] = acc;
+}
+
+// h_q(x), q = 0..Q, real x > 0: h_0 = -i e^{ix}/x, h_1 = -e^{ix}(x + i)/x^2, upward recurrence
+__device__ void sph_hankel_seq(int Q, double x, double2* h) {
+    double s, c;
+    sincos(x, &s, &c);
+    h[0] = make_double2(s / x, -c / x);
+    if (Q >= 1) h[1] = make_double2(-(c * x - s) / (x * x), -(s * x + c) / (x * x));
+    for (int q = 1; q < Q; ++q) {
+        const double f = (2.0 * q + 1.0) / x;
+        h[q + 1] = make_double2(f * h[q].x - h[q - 1].x, f * h[q].y - h[q - 1].y);
+    }
+}
+
+// Translation of every other sphere's expansions into sphere m's regular ones (one CTA per target and
+// right-hand-side chunk; thread (c, nu mu) for the three Cartesian shear components, thread (nu mu)
+// for the compressional potential).  Gt[k'][t][nu mu] = 4 pi i^{nu - n' + q} G(n', m'; nu, mu; q),
+// q = |n' - nu| + 2t.  Shared: the source's Cartesian expansions and potential for the chunk, and
+// H_q^k = h_q(k |d|) Y_q^k(d^) for both wavenumbers.
+__global__ void __launch_bounds__(512) k3_translate(const double2* __restrict__ W, const double2* __restrict__ x,
+                                                     const double* __restrict__ cen, const double2* __restrict__ Gt,
+                                                     double2* __restrict__ Rr, double2* __restrict__ Cr, double kp,
+                                                     double ks, int M, int p, int nrhs) {
+    extern __shared__ double2 sm[];
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
+    const int P2 = 2 * p + 1, QN = (P2 + 1) * (P2 + 1), TT = p + 1;
+    double2* Ws = sm;                           // [3][K2][RC]
+    double2* Gs = Ws + 3 * K2 * RC;             // [nl][RC]
+    double2* Hs = Gs + nl * RC;                 // [QN]
+    double2* Hp = Hs + QN;                      // [QN]
+    double2* hs = Hp + QN;                      // [P2 + 1]
+    double2* hp = hs + P2 + 1;                  // [P2 + 1]
+    __shared__ double dsh[4];
+    const int m = blockIdx.x, r0 = blockIdx.y * RC;
+    const int nr = min(RC, nrhs - r0);
+    const int tid = threadIdx.x;
+    const bool sth = tid < 3 * nl, pth = tid >= 3 * nl && tid < 4 * nl;
+    const int comp = sth ? tid / nl : 0;
+    const int vm = sth ? tid % nl : tid - 3 * nl;
+    const int nu = (sth || pth) ? c_deg[vm] : 0, mu = (sth || pth) ? c_ord[vm] : 0;
+    double2 acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = make_double2(0.0, 0.0);
+    for (int l = 0; l < M; ++l) {
+        if (l == m) continue;
+        if (tid == 0) {
+            const double dx = cen[3 * m] - cen[3 * l], dy = cen[3 * m + 1] - cen[3 * l + 1], dz = cen[3 * m + 2] - cen[3 * l + 2];
+            const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+            dsh[0] = dx / dd; dsh[1] = dy / dd; dsh[2] = dz / dd; dsh[3] = dd;
+            sph_hankel_seq(P2, ks * dd, hs);
+            sph_hankel_seq(P2, kp * dd, hp);
+        }
+        for (int e = tid; e < 3 * K2 * RC; e += blockDim.x) {
+            const int r = e % RC, ck = e / RC;
+            Ws[e] = r < nr ? W[(((size_t)l * 3 * K2) + ck) * nrhs + r0 + r] : make_double2(0.0, 0.0);
+        }
+        for (int e = tid; e < nl * RC; e += blockDim.x) {
+            const int r = e % RC, k = e / RC;
+            Gs[e] = r < nr ? x[((size_t)l * T + 2 * nmn + k) * nrhs + r0 + r] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (tid <= P2) {
+            // Y_q^k(d^), k = tid >= 0, q = k..P2: N Q_q^k(t) w^k, w = d_x + i d_y; Y_q^{-k} = conj(Y_q^k)
+            const int k = tid;
+            const double t = dsh[2];
+            double2 wk = make_double2(1.0, 0.0);
+            const double2 w = make_double2(dsh[0], dsh[1]);
+            for (int i = 0; i < k; ++i) wk = cmul(wk, w);
+            double df = 1.0;
+            for (int i = 1; i <= k; ++i) df *= (2.0 * i - 1.0);
+            double qm1 = 0.0, q0 = df;                 // Q_{k-1}^k = 0, Q_k^k
+            for (int q = k; q <= P2; ++q) {
+                const double y = c_ynorm[q * (2 * P3MAX + 2) + k] * q0;
+                const double2 Y = make_double2(y * wk.x, y * wk.y);
+                const double2 Yc = cconj(Y);
+                Hs[didx(q, k)] = cmul(hs[q], Y);
+                Hp[didx(q, k)] = cmul(hp[q], Y);
+                if (k > 0) {
+                    Hs[didx(q, -k)] = cmul(hs[q], Yc);
+                    Hp[didx(q, -k)] = cmul(hp[q], Yc);
+                }
+                const double qn = ((2.0 * q + 1.0) * t * q0 - (double)(q + k) * qm1) / (double)(q - k + 1);
+                qm1 = q0;
+                q0 = qn;
+            }
+        }
+        __syncthreads();
+        if (sth || pth) {
+            const double2* Hq = sth ? Hs : Hp;
+            const int nk = sth ? K2 : nl;
+            const double2* src = sth ? Ws + (size_t)comp * K2 * RC : Gs;
+            for (int kk = 0; kk < nk; ++kk) {
+                const int n1 = c_deg[kk], m1 = c_ord[kk];
+                const int dm = m1 - mu;
+                double2 A = make_double2(0.0, 0.0);
+                const int tmax = min(n1, nu);
+                for (int t = 0; t <= tmax; ++t) {
+                    const int q = abs(n1 - nu) + 2 * t;
+                    if (abs(dm) > q) continue;
+                    cfma(A, Gt[((size_t)kk * TT + t) * nl + vm], Hq[didx(q, dm)]);
+                }
+                const double2* s = src + (size_t)kk * RC;
+#pragma unroll
+                for (int r = 0; r < RC; ++r) cfma(acc[r], A, s[r]);
+            }
+        }
+        __syncthreads();
+    }
+    if (sth) {
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (r < nr) Rr[(((size_t)m * 3 + comp) * nl + vm) * nrhs + r0 + r] = acc[r];
+    } else if (pth) {
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (r < nr) Cr[((size_t)m * nl + vm) * nrhs + r0 + r] = acc[r];
+    }
+}
+
+// a (+)= the translated coefficients: a_Jm and b_Jm from the regular Cartesian shear expansions (<= 9
+// terms each), c from the translated potential
+__global__ void k3_uncart(const double2* __restrict__ Rr, const double2* __restrict__ Cr, double2* __restrict__ a,
+                          const int* __restrict__ uidx, const double2* __restrict__ ucoef, int M, int p, int nrhs,
+                          int accumulate) {
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * T * nrhs) return;
+    const int r = (int)(i % nrhs);
+    const long long mk = i / nrhs;
+    const int m = (int)(mk / T), k = (int)(mk % T);
+    double2 v = make_double2(0.0, 0.0);
+    if (k < 2 * nmn) {
+        for (int t = 0; t < 9; ++t) {
+            const int s = uidx[k * 9 + t];                   // (c, nu mu) as c * nl + nu mu
+            if (s < 0) break;
+            cfma(v, ucoef[k * 9 + t], Rr[((size_t)m * 3 * nl + s) * nrhs + r]);
+        }
+    } else {
+        v = Cr[((size_t)m * nl + (k - 2 * nmn)) * nrhs + r];
+    }
+    a[i] = accumulate ? cadd(a[i], v) : v;
+}
+
+// Block B: U[q][w][r] = sum_l e^{-i (k_x x_l + k_y y_l) - i k_z^w z_l} sum_k Tw[q][k] x_l[k][r],
+// w = P (gamma block), SV, SH (alpha then beta).  One CTA per node; thread (w, r, l-slice).
+constexpr int M2S_LS = 5;
+__global__ void __launch_bounds__(3 * RC * M2S_LS) k3_m2s(const double2* __restrict__ x, const double2* __restrict__ TP,
+                                                          const double2* __restrict__ TV, const double2* __restrict__ TH,
+                                                          const double2* __restrict__ node, const double* __restrict__ cen,
+                                                          double2* __restrict__ U, int M, int p, int nrhs, int r0) {
+    __shared__ double2 red[3 * RC * M2S_LS];
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const int w = tid / (RC * M2S_LS), rem = tid % (RC * M2S_LS), r = rem % RC, ls = rem / RC;
+    // node: (k_x, k_y, k_z^P, k_z^S)
+    const double2 kx = node[(size_t)q * 4], ky = node[(size_t)q * 4 + 1];
+    const double2 kz = node[(size_t)q * 4 + (w == 0 ? 2 : 3)];
+    const double2* Tw = w == 0 ? TP + (size_t)q * nl : (w == 1 ? TV : TH) + (size_t)q * 2 * nmn;
+    const int off = w == 0 ? 2 * nmn : 0, len = w == 0 ? nl : 2 * nmn;
+    double2 acc = make_double2(0.0, 0.0);
+    if (r0 + r < nrhs) {
+        for (int l = ls; l < M; l += M2S_LS) {
+            const double X = cen[3 * l], Y = cen[3 * l + 1], Z = cen[3 * l + 2];
+            // phase = exp(-i (kx X + ky Y + kz Z))
+            const double re = kx.x * X + ky.x * Y + kz.x * Z, im = kx.y * X + ky.y * Y + kz.y * Z;
+            double s, c;
+            sincos(-re, &s, &c);
+            const double mag = exp(im);
+            const double2 ph = make_double2(mag * c, mag * s);
+            const double2* xl = x + ((size_t)l * T + off) * nrhs + r0 + r;
+            double2 d = make_double2(0.0, 0.0);
+            for (int k = 0; k < len; ++k) cfma(d, Tw[k], xl[(size_t)k * nrhs]);
+            cfma(acc, ph, d);
+        }
+    }
+    red[tid] = acc;
+    __syncthreads();
+    if (ls == 0 && r0 + r < nrhs) {
+        double2 s = acc;
+        for (int j = 1; j < M2S_LS; ++j) s = cadd(s, red[tid + j * RC]);
+        U[((size_t)q * 3 + w) * nrhs + r0 + r] = s;
+    }
+}
+
+// D[q][w][r] = sum_v RW[q][w][v] U[q][v][r]
+__global__ void k3_reflect(const double2* __restrict__ U, const double2* __restrict__ RW, double2* __restrict__ D,
+                           int NS, int nrhs) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)NS * 3 * nrhs) return;
+    const int r = (int)(i % nrhs);
+    const long long qw = i / nrhs;
+    const int q = (int)(qw / 3), w = (int)(qw % 3);
+    double2 v = make_double2(0.0, 0.0);
+    for (int u = 0; u < 3; ++u) cfma(v, RW[(size_t)q * 9 + w * 3 + u], U[((size_t)q * 3 + u) * nrhs + r]);
+    D[i] = v;
+}
+
+// Block C: a[m][k][r] += sum_q [e^{i(k_x x_m + k_y y_m) - i k_z^P z_m} CP[q][k] D[q][P][r]
+//                               + e^{... - i k_z^S z_m} (CV[q][k] D[q][SV][r] + CH[q][k] D[q][SH][r])]
+// One CTA per sphere and right-hand-side chunk; nodes staged in chunks of S2L_QC.
+constexpr int S2L_QC = 32;
+constexpr int S2L_KSPAN = 288;            // coefficients per CTA (grid z covers T in slices)
+__global__ void __launch_bounds__(256) k3_s2l(const double2* __restrict__ D, const double2* __restrict__ CP,
+                                              const double2* __restrict__ CV, const double2* __restrict__ CH,
+                                              const double2* __restrict__ node, const double* __restrict__ cen,
+                                              double2* __restrict__ a, int NS, int p, int nrhs) {
+    __shared__ double2 Ds[S2L_QC][3][RC];
+    __shared__ double2 ph[S2L_QC][2];
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+    const int m = blockIdx.x, r0 = blockIdx.y * RC, tid = threadIdx.x;
+    const int r = tid % RC, kg = tid / RC + S2L_KSPAN * blockIdx.z;   // 16 groups of k per z-slice
+    constexpr int KPT = S2L_KSPAN / 16;                               // k values per thread
+    double2 acc[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) acc[j] = make_double2(0.0, 0.0);
+    const double X = cen[3 * m], Y = cen[3 * m + 1], Z = cen[3 * m + 2];
+    for (int q0 = 0; q0 < NS; q0 += S2L_QC) {
+        const int nq = min(S2L_QC, NS - q0);
+        for (int e = tid; e < S2L_QC * 3 * RC; e += blockDim.x) {
+            const int rr = e % RC, w = (e / RC) % 3, qq = e / (3 * RC);
+            Ds[qq][w][rr] = (qq < nq && r0 + rr < nrhs) ? D[((size_t)(q0 + qq) * 3 + w) * nrhs + r0 + rr]
+                                                       : make_double2(0.0, 0.0);
+        }
+        if (tid < 2 * S2L_QC) {
+            const int qq = tid / 2, wv = tid % 2;
+            double2 v = make_double2(0.0, 0.0);
+            if (qq < nq) {
+                const size_t q = q0 + qq;
+                const double2 kx = node[q * 4], ky = node[q * 4 + 1], kz = node[q * 4 + 2 + wv];
+                // exp(i (kx X + ky Y - kz Z))
+                const double re = kx.x * X + ky.x * Y - kz.x * Z, im = kx.y * X + ky.y * Y - kz.y * Z;
+                double s, c;
+                sincos(re, &s, &c);
+                const double mag = exp(-im);
+                v = make_double2(mag * c, mag * s);
+            }
+            ph[qq][wv] = v;
+        }
+        __syncthreads();
+        for (int qq = 0; qq < nq; ++qq) {
+            const size_t q = q0 + qq;
+            const double2 dp = cmul(ph[qq][0], Ds[qq][0][r]);
+            const double2 dv = cmul(ph[qq][1], Ds[qq][1][r]);
+            const double2 dh = cmul(ph[qq][1], Ds[qq][2][r]);
+#pragma unroll
+            for (int j = 0; j < KPT; ++j) {
+                const int k = kg + 16 * j;
+                if (k < T && k < S2L_KSPAN * (blockIdx.z + 1)) {
+                    cfma(acc[j], CP[q * T + k], dp);
+                    cfma(acc[j], CV[q * T + k], dv);
+                    cfma(acc[j], CH[q * T + k], dh);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (r0 + r < nrhs)
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int k = kg + 16 * j;
+            if (k < T && k < S2L_KSPAN * (blockIdx.z + 1)) {
+                double2* o = a + ((size_t)m * T + k) * nrhs + r0 + r;
+                *o = cadd(*o, acc[j]);
+            }
+        }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct ms3_handle {
+    int M = 0, p = 0, T = 0, NS = 0, K2 = 0, nl = 0, nmn = 0;
+    double omega = 0;
+    Layer lo{}, up{};
+    ms3_options opt{};
+    std::vector<double> h_cen, h_rad;
+    std::vector<int> h_bc;
+    ms_handle* herr = nullptr;              // status plumbing shared with the 2D solver's Krylov code
+    // device tables
+    double* cen = nullptr;                  // [M][3]
+    double2* Sd = nullptr;                  // [M][p+1][5]
+    double2* Gt = nullptr;                  // [K2][p+1][nl]
+    int* midx = nullptr;                    // [3 K2][9]
+    double2* mcoef = nullptr;
+    int* uidx = nullptr;                    // [2 nmn][9]
+    double2* ucoef = nullptr;
+    double2 *TP = nullptr, *TV = nullptr, *TH = nullptr;     // [NS][nl], [NS][2 nmn] x 2
+    double2 *CP = nullptr, *CV = nullptr, *CH = nullptr;     // [NS][T] x 3
+    double2* node = nullptr;                // [NS][4]: k_x, k_y, k_z^P, k_z^S (lower layer)
+    double2* RW = nullptr;                  // [NS][3][3] reflection times weight
+    // workspace (grown to the largest nrhs seen)
+    int ws_nrhs = 0;
+    double2 *W = nullptr, *Rr = nullptr, *Cr = nullptr, *U = nullptr, *Dd = nullptr, *wa = nullptr, *wx = nullptr;
+};
+
+namespace {
+
+void free_all(ms3_handle* h) {
+    cudaFree(h->cen); cudaFree(h->Sd); cudaFree(h->Gt); cudaFree(h->midx); cudaFree(h->mcoef);
+    cudaFree(h->uidx); cudaFree(h->ucoef); cudaFree(h->TP); cudaFree(h->TV); cudaFree(h->TH);
+    cudaFree(h->CP); cudaFree(h->CV); cudaFree(h->CH); cudaFree(h->node); cudaFree(h->RW);
+    cudaFree(h->W); cudaFree(h->Rr); cudaFree(h->Cr); cudaFree(h->U); cudaFree(h->Dd); cudaFree(h->wa); cudaFree(h->wx);
+}
+
+template <typename X>
+int upload(ms3_handle* h, X** dst, const std::vector<X>& v) {
+    *dst = nullptr;
+    if (v.empty()) return MS_OK;
+    if (cudaMalloc((void**)dst, v.size() * sizeof(X)) != cudaSuccess) return MS_ERR_ALLOC;
+    return ms_check(h->herr, cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
+}
+
+std::vector<double2> to_d2(const std::vector<cd>& v) {
+    std::vector<double2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+    return o;
+}
+
+int workspace(ms3_handle* h, int nrhs) {
+    if (nrhs <= h->ws_nrhs) return MS_OK;
+    cudaFree(h->W); cudaFree(h->Rr); cudaFree(h->Cr); cudaFree(h->U); cudaFree(h->Dd); cudaFree(h->wa); cudaFree(h->wx);
+    h->W = h->Rr = h->Cr = h->U = h->Dd = h->wa = h->wx = nullptr;
+    h->ws_nrhs = 0;
+    const size_t M = h->M, e = sizeof(double2);
+    if (cudaMalloc(&h->W, M * 3 * h->K2 * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->Rr, M * 3 * h->nl * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->Cr, M * h->nl * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->U, (size_t)h->NS * 3 * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->Dd, (size_t)h->NS * 3 * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->wa, M * h->T * nrhs * e) != cudaSuccess || cudaMalloc(&h->wx, M * h->T * nrhs * e) != cudaSuccess) {
+        cudaGetLastError();
+        return MS_ERR_ALLOC;
+    }
+    h->ws_nrhs = nrhs;
+    return MS_OK;
+}
+
+// incoming coefficients of the selected parts into h->wa
+int incoming(ms3_handle* h, const double2* x, int nrhs, int parts, cudaStream_t st) {
+    const int M = h->M, p = h->p, T = h->T;
+    const long long n = (long long)M * T * nrhs;
+    int rc;
+    if ((rc = ms_check(h->herr, cudaMemsetAsync(h->wa, 0, n * sizeof(double2), st)))) return rc;
+    if ((parts & MS3_PART_T) && M > 1) {
+        k3_cart<<<nblk((long long)M * 3 * h->K2 * nrhs, 256), 256, 0, st>>>(x, h->W, h->midx, h->mcoef, M, p, nrhs);
+        const int threads = ((4 * h->nl + 31) / 32) * 32;
+        const size_t smem = (size_t)(3 * h->K2 * RC + h->nl * RC + 2 * (2 * p + 2) * (2 * p + 2) + 2 * (2 * p + 2)) * sizeof(double2);
+        k3_translate<<<dim3(M, nblk(nrhs, RC)), threads, smem, st>>>(h->W, x, h->cen, h->Gt, h->Rr, h->Cr, h->lo.kp,
+                                                                     h->lo.ks, M, p, nrhs);
+        k3_uncart<<<nblk(n, 256), 256, 0, st>>>(h->Rr, h->Cr, h->wa, h->uidx, h->ucoef, M, p, nrhs, 1);
+        if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
+    }
+    if (parts & MS3_PART_R) {
+        for (int r0 = 0; r0 < nrhs; r0 += RC)
+            k3_m2s<<<h->NS, 3 * RC * M2S_LS, 0, st>>>(x, h->TP, h->TV, h->TH, h->node, h->cen, h->U, M, p, nrhs, r0);
+        k3_reflect<<<nblk((long long)h->NS * 3 * nrhs, 256), 256, 0, st>>>(h->U, h->RW, h->Dd, h->NS, nrhs);
+        k3_s2l<<<dim3(M, nblk(nrhs, RC), nblk(T, S2L_KSPAN)), 256, 0, st>>>(h->Dd, h->CP, h->CV, h->CH, h->node, h->cen,
+                                                                             h->wa, h->NS, p, nrhs);
+        if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
+    }
+    return MS_OK;
+}
+
+int op3(ms3_handle* h, const double2* x, double2* y, int nrhs, int parts, cudaStream_t st) {
+    int rc;
+    if ((rc = workspace(h, nrhs))) return rc;
+    if ((rc = incoming(h, x, nrhs, parts, st))) return rc;
+    const long long n = (long long)h->M * h->T * nrhs;
+    const bool s = (parts & MS3_PART_S) != 0;
+    k3_sapply<<<nblk(n, 256), 256, 0, st>>>(x, h->wa, y, h->Sd, h->M, h->p, nrhs, s ? 1 : 0, s ? 1 : 0);
+    return ms_check(h->herr, cudaGetLastError());
+}
+
+int check_3d_args(const ms3_handle* h, const void* x, const void* y, int nrhs) {
+    if (!h || !x || !y || nrhs < 1 || nrhs > 64 || x == y) return MS_ERR_ARG;
+    return MS_OK;
+}
+
+}  // namespace
+
+int ms_block_solve_fp64(ms_handle* herr, long long N, int nrhs, int restart,
+                        const std::function<int(const double2*, double2*)>& op, const double2* b, double2* x,
+                        double tol, int max_iters, int& iters, int& matvecs, std::vector<double>& relres,
+                        cudaStream_t st);
+
+extern "C" void ms3_default_options(ms3_options* o) {
+    if (!o) return;
+    o->n_r = 128;
+    o->n_theta = 64;
+    o->n_panels = 4;
+    o->t_max = 10.0;
+    o->alpha = 1.0;
+    o->beta = 1.0;
+    o->restart = 60;
+    o->max_iters = 1000;
+}
+
+extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
+                         ms3_handle** out) {
+    if (!out) return MS_ERR_ARG;
+    *out = nullptr;
+    if (!g || !md || !g->centres || !g->radius || !g->bc || g->M < 1 || !(omega > 0) || p < 1 || p > P3MAX)
+        return MS_ERR_ARG;
+    if (!(md->mu_u > 0) || !(md->mu_l > 0) || !(md->lam_u + md->mu_u > 0) || !(md->lam_l + md->mu_l > 0)) return MS_ERR_ARG;
+    ms3_options opt;
+    ms3_default_options(&opt);
+    if (o) opt = *o;
+    if (opt.n_r < 1 || opt.n_theta < 1 || opt.n_panels < 1 || opt.n_r % opt.n_panels || !(opt.t_max > 0) ||
+        !(opt.alpha >= 0) || !(opt.beta > 0) || opt.restart < 1 || opt.max_iters < 1)
+        return MS_ERR_ARG;
+    const int M = g->M;
+    for (int m = 0; m < M; ++m) {
+        if (!(g->radius[m] > 0) || (g->bc[m] != 0 && g->bc[m] != 1)) return MS_ERR_ARG;
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(g->centres[3 * m + i])) return MS_ERR_ARG;
+        if (g->centres[3 * m + 2] + 1.1 * g->radius[m] > 0.0) return MS_ERR_NOT_BURIED;
+    }
+    for (int m = 0; m < M; ++m)
+        for (int l = m + 1; l < M; ++l) {
+            double d2 = 0;
+            for (int i = 0; i < 3; ++i) d2 += (g->centres[3 * m + i] - g->centres[3 * l + i]) * (g->centres[3 * m + i] - g->centres[3 * l + i]);
+            if (sqrt(d2) < 1.1 * (g->radius[m] + g->radius[l])) return MS_ERR_OVERLAP;
+        }
+    ms3_handle* h = new ms3_handle;
+    h->herr = new ms_handle;
+    h->M = M;
+    h->p = p;
+    h->nmn = p * (p + 2);
+    h->nl = (p + 1) * (p + 1);
+    h->T = 2 * h->nmn + h->nl;
+    h->K2 = (p + 2) * (p + 2);
+    h->omega = omega;
+    h->opt = opt;
+    h->lo = Layer{md->lam_l, md->mu_l, omega / sqrt(md->lam_l + 2 * md->mu_l), omega / sqrt(md->mu_l)};
+    h->up = Layer{md->lam_u, md->mu_u, omega / sqrt(md->lam_u + 2 * md->mu_u), omega / sqrt(md->mu_u)};
+    h->h_cen.assign(g->centres, g->centres + 3 * M);
+    h->h_rad.assign(g->radius, g->radius + M);
+    h->h_bc.assign(g->bc, g->bc + M);
+    const int nmn = h->nmn, nl = h->nl, T = h->T, K2 = h->K2;
+    int rc = MS_OK;
+    auto fail = [&](int code) {
+        free_all(h);
+        delete h->herr;
+        delete h;
+        return code;
+    };
+    // sphere matrices
+    std::vector<cd> S((size_t)M * (p + 1) * 5);
+    for (int m = 0; m < M; ++m)
+        sphere_s(p, h->lo.kp, h->lo.ks, h->lo.lam, h->lo.mu, g->radius[m], g->bc[m], &S[(size_t)m * (p + 1) * 5]);
+    // index tables in constant memory
+    {
+        std::vector<int> deg((P3MAX + 2) * (P3MAX + 2), 0), ord((P3MAX + 2) * (P3MAX + 2), 0);
+        for (int n = 0; n <= P3MAX + 1; ++n)
+            for (int m = -n; m <= n; ++m) { deg[idx(n, m)] = n; ord[idx(n, m)] = m; }
+        std::vector<double> yn((2 * P3MAX + 2) * (2 * P3MAX + 2), 0.0);
+        for (int q = 0; q <= 2 * P3MAX + 1; ++q)
+            for (int k = 0; k <= q; ++k) yn[q * (2 * P3MAX + 2) + k] = ynorm(q, k);
+        if (cudaMemcpyToSymbol(c_deg, deg.data(), deg.size() * sizeof(int)) != cudaSuccess ||
+            cudaMemcpyToSymbol(c_ord, ord.data(), ord.size() * sizeof(int)) != cudaSuccess ||
+            cudaMemcpyToSymbol(c_ynorm, yn.data(), yn.size() * sizeof(double)) != cudaSuccess)
+            return fail(MS_ERR_CUDA);
+    }
+    // Gaunt table: Gt[k'][t][nu mu] = 4 pi i^{nu - n' + q} 2 pi N N N int P P P dt, q = |n' - nu| + 2t
+    std::vector<cd> Gt((size_t)K2 * (p + 1) * nl, cd(0));
+    {
+        const int NG = 2 * p + 6;
+        std::vector<double> gx(NG), gw(NG);
+        // Gauss-Legendre nodes by Newton on P_NG
+        for (int i = 0; i < NG; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (NG + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+                const double dp = NG * (x * p1 - p0) / (x * x - 1);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            const double dp = NG * (x * p1 - p0) / (x * x - 1);
+            gx[i] = x;
+            gw[i] = 2.0 / ((1 - x * x) * dp * dp);
+        }
+        const int PQ = 2 * p + 2;
+        // Ferrers P_n^k(t) = (1 - t^2)^{k/2} Q_n^k(t) at the nodes, n <= PQ
+        std::vector<double> F((size_t)NG * (PQ + 1) * (PQ + 1), 0.0);
+        for (int i = 0; i < NG; ++i) {
+            const std::vector<cd> Q = qtab(PQ, cd(gx[i]));
+            const double s = sqrt(1 - gx[i] * gx[i]);
+            for (int n = 0; n <= PQ; ++n)
+                for (int k = 0; k <= n; ++k)
+                    F[((size_t)i * (PQ + 1) + n) * (PQ + 1) + k] = Q[(size_t)n * (PQ + 2) + k].real() * pow(s, k);
+        }
+        const cd I(0, 1);
+        for (int n1 = 0; n1 <= p + 1; ++n1)
+            for (int m1 = -n1; m1 <= n1; ++m1)
+                for (int nu = 0; nu <= p; ++nu)
+                    for (int mu = -nu; mu <= nu; ++mu)
+                        for (int t = 0; t <= std::min(n1, nu); ++t) {
+                            const int q = std::abs(n1 - nu) + 2 * t, dm = m1 - mu;
+                            if (std::abs(dm) > q) continue;
+                            double s = 0;
+                            for (int i = 0; i < NG; ++i)
+                                s += gw[i] * F[((size_t)i * (PQ + 1) + n1) * (PQ + 1) + std::abs(m1)] *
+                                     F[((size_t)i * (PQ + 1) + nu) * (PQ + 1) + std::abs(mu)] *
+                                     F[((size_t)i * (PQ + 1) + q) * (PQ + 1) + std::abs(dm)];
+                            const double G = 2.0 * M_PI * ynorm(n1, std::abs(m1)) * ynorm(nu, std::abs(mu)) * ynorm(q, std::abs(dm)) * s;
+                            Gt[((size_t)idx(n1, m1) * (p + 1) + t) * nl + idx(nu, mu)] = 4.0 * M_PI * std::pow(I, nu - n1 + q) * G;
+                        }
+    }
+    // Cartesian maps by quadrature on the unit sphere (real directions): C-, C+, CX
+    std::vector<int> midx((size_t)3 * K2 * 9, -1), uidx((size_t)2 * nmn * 9, -1);
+    bool map_overflow = false;
+    std::vector<cd> mcoef((size_t)3 * K2 * 9, cd(0)), ucoef((size_t)2 * nmn * 9, cd(0));
+    {
+        const int NT = p + 5, NP = 2 * p + 10, P1 = p + 1;
+        std::vector<double> tx(NT), tw(NT);
+        for (int i = 0; i < NT; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (NT + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+                const double dp = NT * (x * p1 - p0) / (x * x - 1);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            const double dp = NT * (x * p1 - p0) / (x * x - 1);
+            tx[i] = x;
+            tw[i] = 2.0 / ((1 - x * x) * dp * dp);
+        }
+        const int NY = (P1 + 1) * (P1 + 1);
+        // C[kind][c][(n, m)][(n2, m2)] accumulated densely over (n, m) <= P1 and (n2, m2) <= P1
+        std::vector<cd> Cm((size_t)3 * NY * NY, cd(0)), Cp((size_t)3 * NY * NY, cd(0)), Cx((size_t)3 * NY * NY, cd(0));
+        std::vector<cd> Y, G;
+        for (int i = 0; i < NT; ++i)
+            for (int j = 0; j < NP; ++j) {
+                const double ph = 2.0 * M_PI * j / NP, st = sqrt(1 - tx[i] * tx[i]);
+                const cd d[3] = {st * cos(ph), st * sin(ph), tx[i]};
+                const double wq = tw[i] * 2.0 * M_PI / NP;
+                ylm_c(P1, d, Y);
+                grad_ylm_c(P1, d, G);
+                for (int k = 0; k < NY; ++k) {
+                    const int n = (int)sqrt((double)k + 0.5);
+                    const cd* gk = &G[(size_t)k * 3];
+                    cd X[3];
+                    cross3(gk, d, X);
+                    for (int c = 0; c < 3; ++c) {
+                        const cd vm = (double)n * Y[k] * d[c] + gk[c];
+                        const cd vp = (double)(n + 1) * Y[k] * d[c] - gk[c];
+                        for (int k2 = 0; k2 < NY; ++k2) {
+                            const cd yc = std::conj(Y[k2]) * wq;
+                            Cm[((size_t)c * NY + k) * NY + k2] += vm * yc;
+                            Cp[((size_t)c * NY + k) * NY + k2] += vp * yc;
+                            Cx[((size_t)c * NY + k) * NY + k2] += X[c] * yc;
+                        }
+                    }
+                }
+            }
+        const cd I(0, 1);
+        auto C = [&](std::vector<cd>& A, int c, int k, int k2) -> cd { return A[((size_t)c * NY + k) * NY + k2]; };
+        // forward: W[c][(n', m')] from alpha_{n'+1, m} (V-), alpha_{n'-1, m} (V+), beta_{n', m} (X)
+        for (int c = 0; c < 3; ++c)
+            for (int n1 = 0; n1 <= p + 1; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    const int row = c * K2 + idx(n1, m1);
+                    int cnt = 0;
+                    auto add = [&](int src, cd coef) {
+                        if (std::abs(coef) < 1e-13) return;
+                        if (cnt >= 9) { map_overflow = true; return; }
+                        midx[(size_t)row * 9 + cnt] = src;
+                        mcoef[(size_t)row * 9 + cnt] = coef;
+                        ++cnt;
+                    };
+                    const int n = n1 + 1;
+                    if (n <= p)
+                        for (int m = -n; m <= n; ++m)
+                            add(idx(n, m) - 1, (double)(n + 1) / (I * (2.0 * n + 1)) * C(Cm, c, idx(n, m), idx(n1, m1)));
+                    const int nb = n1 - 1;
+                    if (nb >= 1 && nb <= p)
+                        for (int m = -nb; m <= nb; ++m)
+                            add(idx(nb, m) - 1, (double)nb / (I * (2.0 * nb + 1)) * C(Cp, c, idx(nb, m), idx(n1, m1)));
+                    if (n1 >= 1 && n1 <= p)
+                        for (int m = -n1; m <= n1; ++m) add(nmn + idx(n1, m) - 1, C(Cx, c, idx(n1, m), idx(n1, m1)));
+                }
+        // back: a_Jm = i/(J(J+1)) sum conj(C-(J, m -> J-1, mu)) R_c(J-1, mu); b_Jm = 1/(J(J+1)) sum conj(CX) R_c(J, mu)
+        for (int J = 1; J <= p; ++J)
+            for (int m = -J; m <= J; ++m)
+                for (int which = 0; which < 2; ++which) {
+                    const int row = which * nmn + idx(J, m) - 1;
+                    int cnt = 0;
+                    const int nd = which == 0 ? J - 1 : J;
+                    for (int c = 0; c < 3; ++c)
+                        for (int mu = -nd; mu <= nd; ++mu) {
+                            const cd cc = which == 0 ? std::conj(C(Cm, c, idx(J, m), idx(nd, mu))) * I / (J * (J + 1.0))
+                                                     : std::conj(C(Cx, c, idx(J, m), idx(nd, mu))) / (J * (J + 1.0));
+                            if (std::abs(cc) < 1e-13) continue;
+                            if (cnt >= 9) { map_overflow = true; continue; }
+                            uidx[(size_t)row * 9 + cnt] = c * nl + idx(nd, mu);
+                            ucoef[(size_t)row * 9 + cnt] = cc;
+                            ++cnt;
+                        }
+                }
+    }
+    if (map_overflow) return fail(MS_ERR_UNSUPPORTED);
+    // Sommerfeld nodes, blocks B and C, reflection
+    const int NS = opt.n_r * opt.n_theta;
+    h->NS = NS;
+    std::vector<cd> TP((size_t)NS * nl), TV((size_t)NS * 2 * nmn), TH((size_t)NS * 2 * nmn);
+    std::vector<cd> CPv((size_t)NS * T), CVv((size_t)NS * T), CHv((size_t)NS * T), node((size_t)NS * 4), RW((size_t)NS * 9);
+    {
+        const int per = opt.n_r / opt.n_panels;
+        std::vector<double> gx(per), gw(per);
+        for (int i = 0; i < per; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (per + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int k = 2; k <= per; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+                const double dp = per == 1 ? 1.0 : per * (x * p1 - p0) / (x * x - 1);
+                const double dx = per == 1 ? x : p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= per; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            const double dp = per == 1 ? 1.0 : per * (x * p1 - p0) / (x * x - 1);
+            gx[i] = x;
+            gw[i] = 2.0 / ((1 - x * x) * dp * dp);
+        }
+        const cd I(0, 1);
+        std::vector<cd> Y, G;
+        for (int ir = 0; ir < opt.n_r; ++ir) {
+            const int pan = ir / per, k = ir % per;
+            const double a = pan * opt.t_max / opt.n_panels, b = (pan + 1) * opt.t_max / opt.n_panels;
+            const double t = 0.5 * (b - a) * gx[k] + 0.5 * (a + b), wt = 0.5 * (b - a) * gw[k];
+            const cd lam = cd(t, -opt.alpha * tanh(opt.beta * t));
+            const cd dlam = cd(1.0, -opt.alpha * opt.beta / (cosh(opt.beta * t) * cosh(opt.beta * t)));
+            for (int it = 0; it < opt.n_theta; ++it) {
+                const size_t q = (size_t)ir * opt.n_theta + it;
+                const double th = 2.0 * M_PI * it / opt.n_theta;
+                const cd W = wt * lam * dlam * (2.0 * M_PI / opt.n_theta);
+                const cd kzp = std::sqrt(h->lo.kp * h->lo.kp - lam * lam), kzs = std::sqrt(h->lo.ks * h->lo.ks - lam * lam);
+                node[q * 4] = lam * cos(th);
+                node[q * 4 + 1] = lam * sin(th);
+                node[q * 4 + 2] = kzp;
+                node[q * 4 + 3] = kzs;
+                cd eP[3], vP[3], hP[3], eS[3], vS[3], hS[3];
+                // block B (upgoing)
+                pw_basis(h->lo.kp, lam, th, true, eP, vP, hP);
+                pw_basis(h->lo.ks, lam, th, true, eS, vS, hS);
+                ylm_c(p, eP, Y);
+                for (int n = 0; n <= p; ++n)
+                    for (int m = -n; m <= n; ++m)
+                        TP[q * nl + idx(n, m)] = std::pow(-I, n - 1) * Y[idx(n, m)] / (2.0 * M_PI * kzp);
+                grad_ylm_c(p, eS, G);
+                for (int n = 1; n <= p; ++n)
+                    for (int m = -n; m <= n; ++m) {
+                        const cd f = std::pow(-I, n) / (2.0 * M_PI * h->lo.ks * kzs);
+                        const cd* gk = &G[(size_t)idx(n, m) * 3];
+                        cd gx3[3];
+                        cross3(gk, eS, gx3);
+                        const int k1 = idx(n, m) - 1;
+                        TV[q * 2 * nmn + k1] = f * dot3(gk, vS);
+                        TV[q * 2 * nmn + nmn + k1] = f * dot3(gx3, vS);
+                        TH[q * 2 * nmn + k1] = f * dot3(gk, hS);
+                        TH[q * 2 * nmn + nmn + k1] = f * dot3(gx3, hS);
+                    }
+                // block C (downgoing)
+                pw_basis(h->lo.kp, lam, th, false, eP, vP, hP);
+                pw_basis(h->lo.ks, lam, th, false, eS, vS, hS);
+                plane_coeffs(p, h->lo.kp, eP, eP, &CPv[q * T]);
+                plane_coeffs(p, h->lo.kp, eS, vS, &CVv[q * T]);
+                plane_coeffs(p, h->lo.kp, eS, hS, &CHv[q * T]);
+                // reflection: unit upgoing lower P, SV, SH -> downgoing lower amplitudes
+                cd Ul[3][3], Tl[3][3];
+                wave_cols(h->lo, lam, th, true, Ul, Tl);
+                std::vector<cd> rhs(18);
+                for (int w = 0; w < 3; ++w)
+                    for (int i = 0; i < 3; ++i) {
+                        rhs[(size_t)i * 3 + w] = -Ul[w][i];
+                        rhs[(size_t)(3 + i) * 3 + w] = -Tl[w][i];
+                    }
+                if (!interface_solve(h->lo, h->up, lam, th, rhs, 3)) return fail(MS_ERR_ARG);
+                for (int i = 0; i < 3; ++i)
+                    for (int w = 0; w < 3; ++w) RW[q * 9 + i * 3 + w] = W * rhs[(size_t)i * 3 + w];
+            }
+        }
+    }
+    if ((rc = upload(h, &h->cen, h->h_cen)) || (rc = upload(h, &h->Sd, to_d2(S))) || (rc = upload(h, &h->Gt, to_d2(Gt))) ||
+        (rc = upload(h, &h->midx, midx)) || (rc = upload(h, &h->mcoef, to_d2(mcoef))) || (rc = upload(h, &h->uidx, uidx)) ||
+        (rc = upload(h, &h->ucoef, to_d2(ucoef))) || (rc = upload(h, &h->TP, to_d2(TP))) || (rc = upload(h, &h->TV, to_d2(TV))) ||
+        (rc = upload(h, &h->TH, to_d2(TH))) || (rc = upload(h, &h->CP, to_d2(CPv))) || (rc = upload(h, &h->CV, to_d2(CVv))) ||
+        (rc = upload(h, &h->CH, to_d2(CHv))) || (rc = upload(h, &h->node, to_d2(node))) || (rc = upload(h, &h->RW, to_d2(RW))))
+        return fail(rc);
+    const size_t smem = (size_t)(3 * K2 * RC + nl * RC + 2 * (2 * p + 2) * (2 * p + 2) + 2 * (2 * p + 2)) * sizeof(double2);
+    if (cudaFuncSetAttribute(k3_translate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return fail(MS_ERR_CUDA);
+    *out = h;
+    return MS_OK;
+}
+
+extern "C" int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, void* stream) {
+    if (int rc = check_3d_args(h, x, y, nrhs)) return rc;
+    if (parts < 0 || parts > 7) return MS_ERR_ARG;
+    return op3(h, (const double2*)x, (double2*)y, nrhs, parts, (cudaStream_t)stream);
+}
+
+extern "C" int ms3_apply(ms3_handle* h, const void* x, void* y, int32_t nrhs, void* stream) {
+    return ms3_operator(h, x, y, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, stream);
+}
+
+extern "C" int ms3_rhs(ms3_handle* h, const ms3_incidence* inc, void* b, void* stream) {
+    if (!h || !inc || !b || inc->nrhs < 1 || inc->nrhs > 64 || !inc->kind || !inc->theta || !inc->phi) return MS_ERR_ARG;
+    const int nrhs = inc->nrhs, M = h->M, p = h->p, T = h->T;
+    for (int r = 0; r < nrhs; ++r)
+        if ((inc->kind[r] < 0 || inc->kind[r] > 2) || !(inc->theta[r] >= 0 && inc->theta[r] < 0.5 * M_PI) ||
+            !std::isfinite(inc->phi[r]))
+            return MS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = workspace(h, nrhs))) return rc;
+    std::vector<double2> a((size_t)M * T * nrhs);
+    std::vector<cd> CP(T), CV(T), CH(T);
+    for (int r = 0; r < nrhs; ++r) {
+        const int kind = inc->kind[r];
+        const double kin = kind == 0 ? h->up.kp : h->up.ks;
+        const cd lam = kin * sin(inc->theta[r]);
+        const double th = inc->phi[r];
+        // incident downgoing upper wave (displacement, traction) as the right-hand side
+        cd Uu[3][3], Tu[3][3];
+        wave_cols(h->up, lam, th, false, Uu, Tu);
+        std::vector<cd> rhs(6);
+        for (int i = 0; i < 3; ++i) {
+            rhs[i] = Uu[kind][i];
+            rhs[3 + i] = Tu[kind][i];
+        }
+        if (!interface_solve(h->lo, h->up, lam, th, rhs, 1)) return MS_ERR_ARG;
+        cd eP[3], vP[3], hP[3], eS[3], vS[3], hS[3];
+        pw_basis(h->lo.kp, lam, th, false, eP, vP, hP);
+        pw_basis(h->lo.ks, lam, th, false, eS, vS, hS);
+        plane_coeffs(p, h->lo.kp, eP, eP, CP.data());
+        plane_coeffs(p, h->lo.kp, eS, vS, CV.data());
+        plane_coeffs(p, h->lo.kp, eS, hS, CH.data());
+        for (int m = 0; m < M; ++m) {
+            const double* c = &h->h_cen[3 * m];
+            const cd I(0, 1);
+            const cd fp = rhs[0] * std::exp(I * h->lo.kp * (eP[0] * c[0] + eP[1] * c[1] + eP[2] * c[2]));
+            const cd fs = std::exp(I * h->lo.ks * (eS[0] * c[0] + eS[1] * c[1] + eS[2] * c[2]));
+            for (int k = 0; k < T; ++k) {
+                const cd v = fp * CP[k] + fs * (rhs[1] * CV[k] + rhs[2] * CH[k]);
+                a[((size_t)m * T + k) * nrhs + r] = make_double2(v.real(), v.imag());
+            }
+        }
+    }
+    if ((rc = ms_check(h->herr, cudaMemcpyAsync(h->wa, a.data(), a.size() * sizeof(double2), cudaMemcpyHostToDevice, st))))
+        return rc;
+    const long long n = (long long)M * T * nrhs;
+    k3_sapply<<<nblk(n, 256), 256, 0, st>>>(nullptr, h->wa, (double2*)b, h->Sd, M, p, nrhs, 0, 1);
+    if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
+    return ms_check(h->herr, cudaStreamSynchronize(st));     // a is pageable host memory
+}
+
+extern "C" int ms3_solve(ms3_handle* h, const ms3_incidence* inc, double tol, void* tau, ms_solve_info* info,
+                         void* stream) {
+    if (!h || !inc || !tau || !(tol > 0)) return MS_ERR_ARG;
+    const int nrhs = inc->nrhs;
+    if (nrhs < 1 || nrhs > 64) return MS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    double2* b = nullptr;
+    const size_t n = (size_t)h->M * h->T * nrhs;
+    if (cudaMalloc(&b, n * sizeof(double2)) != cudaSuccess) return MS_ERR_ALLOC;
+    int rc = ms3_rhs(h, inc, b, stream);
+    int iters = 0, matvecs = 0;
+    std::vector<double> relres;
+    if (!rc) rc = ms_check(h->herr, cudaMemsetAsync(tau, 0, n * sizeof(double2), st));
+    double2* tmp = nullptr;
+    if (!rc && cudaMalloc(&tmp, n * sizeof(double2)) != cudaSuccess) rc = MS_ERR_ALLOC;
+    if (!rc) {
+        auto op = [&](const double2* in, double2* out) -> int {
+            // the operator needs distinct input and output blocks
+            if (in == out) {
+                if (int e = ms_check(h->herr, cudaMemcpyAsync(tmp, in, n * sizeof(double2), cudaMemcpyDeviceToDevice, st))) return e;
+                in = tmp;
+            }
+            return op3(h, in, out, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, st);
+        };
+        rc = ms_block_solve_fp64(h->herr, (long long)h->M * h->T, nrhs, h->opt.restart, op, b, (double2*)tau, tol,
+                                 h->opt.max_iters, iters, matvecs, relres, st);
+    }
+    cudaFree(b);
+    cudaFree(tmp);
+    double worst = 0;
+    for (double v : relres) worst = std::max(worst, v);
+    if (info) {
+        info->iterations = iters;
+        info->refinements = 0;
+        info->matvecs = matvecs;
+        info->max_rel_residual = worst;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (rc) return rc;
+    return worst <= tol ? MS_OK : MS_NOT_CONVERGED;
+}
+
+extern "C" int ms3_info(const ms3_handle* h, int32_t* M, int32_t* p, int32_t* T, int32_t* n_nodes) {
+    if (!h) return MS_ERR_ARG;
+    if (M) *M = h->M;
+    if (p) *p = h->p;
+    if (T) *T = h->T;
+    if (n_nodes) *n_nodes = h->NS;
+    return MS_OK;
+}
+
+extern "C" void ms3_destroy(ms3_handle* h) {
+    if (!h) return;
+    free_all(h);
+    delete h->herr;
+    delete h;
+}

@@ -339,3 +339,64 @@ def random_coeffs(seed: int, M: int, p: int, nrhs: int) -> np.ndarray:
     z = rng.standard_normal((M, 2, nc, nrhs)) + 1j * rng.standard_normal((M, 2, nc, nrhs))
     n = np.abs(np.arange(-p, p + 1))
     return z * (0.5 ** n)[None, None, :, None]
+
+
+@dataclasses.dataclass
+class Workload3:
+    """3D workload (Sec. 6): spheres below the interface z = 0 and plane waves from the upper layer."""
+    name: str
+    media: Media
+    omega: float
+    p: int
+    centres: np.ndarray          # (M, 3)
+    radius: np.ndarray           # (M,)
+    bc: np.ndarray               # (M,) 0 rigid, 1 traction-free
+    inc_kind: np.ndarray         # (nrhs,) 0 P, 1 SV, 2 SH
+    inc_theta: np.ndarray        # (nrhs,) angle from the downward vertical
+    inc_phi: np.ndarray          # (nrhs,) azimuth
+
+    @property
+    def M(self) -> int:
+        return int(self.radius.shape[0])
+
+    @property
+    def nrhs(self) -> int:
+        return int(self.inc_kind.shape[0])
+
+
+def place_spheres(rng: np.random.Generator, M: int, box, rmin: float, rmax: float, max_tries: int = 200000):
+    """Random sequential addition of M spheres in box = (x0, x1, y0, y1, z0, z1): radii U[rmin, rmax],
+    centres uniform, rejected when |c_l - c_m| < 1.1 (R_l + R_m) or z + 1.1 R > 0."""
+    x0, x1, y0, y1, z0, z1 = box
+    c = np.empty((M, 3))
+    r = np.empty(M)
+    n = tries = 0
+    while n < M:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError(f"placement failed after {max_tries} tries ({n}/{M} placed)")
+        rad = rng.uniform(rmin, rmax)
+        x = np.array([rng.uniform(x0, x1), rng.uniform(y0, y1), rng.uniform(z0, z1)])
+        if x[2] + SEP * rad > 0.0:
+            continue
+        if n and (np.linalg.norm(c[:n] - x[None, :], axis=1) < SEP * (r[:n] + rad)).any():
+            continue
+        c[n], r[n] = x, rad
+        n += 1
+    return c, r
+
+
+def spheres3d(seed: int = 1006, M: int = 500, nrhs: int = 16, box=None, bc: str = "rigid", p: int = 8) -> Workload3:
+    """The 3D workload: upper lam = 1, mu = 0.5, lower lam' = 2, mu' = 1, omega = 2; M spheres of radius
+    U[0.3, 0.5] in [-15, 15]^2 x [-12, -1] (or the given box); order p; nrhs plane waves from the upper
+    layer with seeded kinds (P, SV, SH), angles from the vertical U[10, 60] degrees and azimuths
+    U[0, 2 pi).  bc: "rigid" (every sphere), or "alternate" (rigid and traction-free by index parity)."""
+    rng = np.random.default_rng(seed)
+    box = box or (-15.0, 15.0, -15.0, 15.0, -12.0, -1.0)
+    c, r = place_spheres(rng, M, box, 0.3, 0.5)
+    b = np.zeros(M, dtype=np.int32) if bc == "rigid" else (np.arange(M) % 2).astype(np.int32)
+    irng = np.random.default_rng(seed + 1000)
+    kinds = irng.integers(0, 3, size=nrhs).astype(np.int32)
+    th = np.deg2rad(irng.uniform(10.0, 60.0, size=nrhs))
+    ph = irng.uniform(0.0, 2.0 * np.pi, size=nrhs)
+    return Workload3(f"spheres{M}_p{p}_rhs{nrhs}", Media(1.0, 0.5, 2.0, 1.0), 2.0, p, c, r, b, kinds, th, ph)

@@ -19,7 +19,7 @@ def header_functions():
     for path in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(path).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(ms_\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(ms3?_\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 
@@ -185,7 +185,7 @@ def test_every_handle_call_refuses_a_null_handle(lib):
     is 0."""
     from paper_2608_26875_b300 import _native as nat
     skip = {"ms_default_options", "ms_setup", "ms_status_string", "ms_destroy", "ms_last_cuda_error",
-            "ms_tensor_peak"}
+            "ms_tensor_peak", "ms3_default_options", "ms3_setup", "ms3_destroy"}
     checked = 0
     for name, (restype, argtypes) in nat.SIGNATURES.items():
         if name in skip:
@@ -201,9 +201,9 @@ def test_every_handle_call_refuses_a_null_handle(lib):
                 args.append(None)
         assert getattr(lib, name)(*args) == nat.MS_ERR_ARG, name
         checked += 1
-    assert checked == 16         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
+    assert checked == 21         # apply, apply_adjoint, operator, rhs, rhs_point, solve, solve_rhs, fields,
     #                              fields_upper, time_reversal, grad, fields_noalloc, autotune, info, work,
-    #                              near_stored
+    #                              near_stored; ms3_: apply, operator, rhs, solve, info
     lib.ms_destroy(None)
     assert lib.ms_last_cuda_error(None) == 0
 
@@ -227,3 +227,49 @@ def test_tensor_peak_refuses_invalid_arguments(lib):
     assert lib.ms_tensor_peak(0, 10, ct.byref(out), None) == nat.MS_ERR_ARG      # FP64 has no tensor kind here
     assert lib.ms_tensor_peak(1, 0, ct.byref(out), None) == nat.MS_ERR_ARG
     assert lib.ms_tensor_peak(1, 10, None, None) == nat.MS_ERR_ARG
+
+
+@pytest.mark.parametrize("case", ["p=0", "p=11", "not_buried", "overlap", "bc=2", "panels", "M=0", "nan"])
+def test_3d_setup_refuses_invalid_input_before_device_work(lib, case):
+    """ms3_setup validates geometry, order and rule on the host (no device needed)."""
+    from paper_2608_26875_b300 import _native as nat
+    c = np.array([[0.0, 0.0, -2.0], [2.0, 0.0, -2.5]])
+    r = np.array([0.4, 0.4])
+    bc = np.array([0, 1], dtype=np.int32)
+    p = 4
+    o = nat.Options3()
+    lib.ms3_default_options(ctypes.byref(o))
+    M = 2
+    want = nat.MS_ERR_ARG
+    if case == "p=0":
+        p = 0
+    elif case == "p=11":
+        p = 11
+    elif case == "not_buried":
+        c[1, 2] = -0.3
+        want = nat.MS_ERR_NOT_BURIED
+    elif case == "overlap":
+        c[1] = [0.5, 0.0, -2.0]
+        want = nat.MS_ERR_OVERLAP
+    elif case == "bc=2":
+        bc[0] = 2
+    elif case == "panels":
+        o.n_panels = 3                   # does not divide n_r = 128
+    elif case == "M=0":
+        M = 0
+    elif case == "nan":
+        c[0, 0] = np.nan
+    g = nat.Geometry3(M, c.ctypes.data_as(nat.c_dp), r.ctypes.data_as(nat.c_dp), bc.ctypes.data_as(nat.c_ip))
+    md = nat.Media(1.0, 0.5, 2.0, 1.0)
+    h = ctypes.c_void_p()
+    st = lib.ms3_setup(ctypes.byref(g), ctypes.byref(md), 2.0, p, ctypes.byref(o), ctypes.byref(h))
+    assert st == want, (case, st)
+    assert not h.value
+
+
+def test_3d_default_options(lib):
+    from paper_2608_26875_b300 import _native as nat
+    o = nat.Options3()
+    lib.ms3_default_options(ctypes.byref(o))
+    assert (o.n_r, o.n_theta, o.n_panels, o.t_max, o.alpha, o.beta) == (128, 64, 4, 10.0, 1.0, 1.0)
+    assert ctypes.sizeof(o) == 48
