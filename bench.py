@@ -529,7 +529,8 @@ def run_profile(args):
     import synthetic as syn
     wl = syn.config3(M=args.M or 2500, nrhs=64)
     prec = P.MS_PREC_FP32 if args.prec == "fp32" else P.MS_PREC_FP64
-    s = P.Solver.from_workload(wl, proto_S=star_tables(wl), tensor_cores=args.tensor_cores)
+    s = P.Solver.from_workload(wl, proto_S=star_tables(wl), tensor_cores=args.tensor_cores,
+                               store_near=args.store_near)
     x = torch.as_tensor(syn.random_coeffs(5, wl.M, wl.p, 64), device="cuda")
     parts = {"near": P.MS_PART_T_NEAR, "far": P.MS_PART_T_FAR, "refl": P.MS_PART_R | P.MS_PART_S,
              "sapply": P.MS_PART_S}
@@ -569,8 +570,8 @@ def main():
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
     ap.add_argument("--precond-group", type=int, default=0, help="--mode solve/grad: particles per block of the "
                     "group-block Jacobi preconditioner (0: none)")
-    ap.add_argument("--store-near", type=int, default=0, help="device GB budget for the stored near-pair "
-                    "operator tiles (0: generated in every application)")
+    ap.add_argument("--store-near", type=int, default=96, help="device GB budget for the stored near-pair "
+                    "operator tiles (0: generated in every application; the 10^4-particle workload stores 48 GB)")
     ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
                     help="FP32 near field and spectral maps on the CUDA cores instead of tcgen05")
     args = ap.parse_args()

@@ -172,14 +172,17 @@ k_bupdate_tc(const float2* V, const float2* __restrict__ H, float2* out, long lo
 constexpr int CC_T = 16;            // 16 x 16 threads, 4 x 4 outputs each: 64 x 64 output tile
 constexpr int CC_K = 16;            // contracted entries per staged chunk
 
-// part[split][k][r] over a 64-basis-vector x 64-column tile (k = k0 + tk + 16 a, r = tr + 16 b)
-template <typename T>
+// part[split][k][r] over a 64-basis-vector x 64-column tile (k = k0 + tk + 16 a, r = tr + 16 b), with
+// products and sums in the accumulation type A (double for the exact Gram of an FP32 block: FP32
+// products are exact in FP64)
+template <typename T, typename A = T>
 __global__ void __launch_bounds__(256)
 k_bgram_cc(const typename CT<T>::c* __restrict__ V, const typename CT<T>::c* __restrict__ W,
            double2* __restrict__ part, long long N, int s, int nb, long long rows_per_split) {
-    typedef typename CT<T>::c C;
-    __shared__ C Vs[CC_K][64];
-    __shared__ C Ws[CC_K][64];
+    typedef typename CT<T>::c CI;
+    typedef typename CT<A>::c C;
+    __shared__ CI Vs[CC_K][64];
+    __shared__ CI Ws[CC_K][64];
     const int k0 = blockIdx.x * 64, split = blockIdx.y;
     const long long row0 = (long long)split * rows_per_split, row1 = min(N, row0 + rows_per_split);
     const int tk = threadIdx.x / CC_T, tr = threadIdx.x % CC_T;
@@ -187,7 +190,7 @@ k_bgram_cc(const typename CT<T>::c* __restrict__ V, const typename CT<T>::c* __r
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = mk((T)0, (T)0);
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk((A)0, (A)0);
     for (long long rc = row0; rc < row1; rc += CC_K) {
         __syncthreads();
         for (int e = threadIdx.x; e < CC_K * 64; e += blockDim.x) {
@@ -202,9 +205,9 @@ k_bgram_cc(const typename CT<T>::c* __restrict__ V, const typename CT<T>::c* __r
         for (int rr = 0; rr < CC_K; ++rr) {
             C vv[4], ww[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) vv[a] = Vs[rr][tk + 16 * a];
+            for (int a = 0; a < 4; ++a) vv[a] = to_c<A>(to_d(Vs[rr][tk + 16 * a]));
 #pragma unroll
-            for (int b = 0; b < 4; ++b) ww[b] = Ws[rr][tr + 16 * b];
+            for (int b = 0; b < 4; ++b) ww[b] = to_c<A>(to_d(Ws[rr][tr + 16 * b]));
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -386,6 +389,7 @@ struct BlockKrylov {
     double2* G = nullptr;
     int nsplit_max = 1;
     int deflations = 0;      // rank-deficient blocks met (orth)
+    int exhausted = 0;       // of which the basis left no room for filler columns
 
     C* Z = nullptr;          // N x s: preconditioned block (group-block Jacobi), when the handle has one
 
@@ -411,10 +415,11 @@ struct BlockKrylov {
     }
     C* blk(int i) { return V + (size_t)i * N * s; }
 
-    // out[k * s + r] = <basis_k, Wp[:, r]> for the nb basis vectors starting at block pointer Vb
-    int gram(const C* Vb, int nb, const C* Wp, std::vector<cd>& out) {
+    // out[k * s + r] = <basis_k, Wp[:, r]> for the nb basis vectors starting at block pointer Vb; exact:
+    // on the CUDA cores with FP64 products and sums whatever the basis precision
+    int gram(const C* Vb, int nb, const C* Wp, std::vector<cd>& out, bool exact = false) {
         int nsplit;
-        if (tc) {
+        if (tc && !exact) {
             const int ntile = (nb + tcp::NMAX - 1) / tcp::NMAX;
             nsplit = std::max(1, std::min(nsplit_max, (2 * 148 + ntile - 1) / ntile));
             long long per = (N + nsplit - 1) / nsplit;
@@ -428,7 +433,10 @@ struct BlockKrylov {
             nsplit = std::max(1, std::min(nsplit_max, (2 * 148 + ntile - 1) / ntile));
             long long per = (N + nsplit - 1) / nsplit;
             nsplit = (int)((N + per - 1) / per);
-            k_bgram_cc<T><<<dim3(ntile, nsplit), 256, 0, st>>>(Vb, Wp, part, N, s, nb, per);
+            if (exact)
+                k_bgram_cc<T, double><<<dim3(ntile, nsplit), 256, 0, st>>>(Vb, Wp, part, N, s, nb, per);
+            else
+                k_bgram_cc<T><<<dim3(ntile, nsplit), 256, 0, st>>>(Vb, Wp, part, N, s, nb, per);
         }
         const int n = nb * s;
         k_bgram_sum<<<nblk(n, 256), 256, 0, st>>>(part, G, nsplit, n);
@@ -437,7 +445,7 @@ struct BlockKrylov {
         if (int rc = ms_check(h, cudaMemcpyAsync(out.data(), G, n * sizeof(double2), cudaMemcpyDeviceToHost, st)))
             return rc;
         if (int rc = ms_check(h, cudaStreamSynchronize(st))) return rc;
-        if (tc) return ms_spectral_tc_status(h, st);
+        if (tc && !exact) return ms_spectral_tc_status(h, st);
         return MS_OK;
     }
     // out (+)= sign * Vb[:, 0:nb] Hc, Hc = nb x s row-major
@@ -456,44 +464,66 @@ struct BlockKrylov {
         // (a copy from pageable host memory returns once the data are staged: hc may go out of scope)
         return ms_check(h, cudaGetLastError());
     }
-    // CholQR2 of a block in place, unshifted; false when a factor does not exist or loses more than the
-    // relative pivot floor
-    int cholqr2(C* blk, std::vector<cd>& R, bool& ok) {
-        std::vector<cd> Gm, R1, R2, Ri;
-        ok = false;
-        if (int rc = gram(blk, s, blk, Gm)) return rc;
-        if (!chol_checked(Gm, R1)) return MS_OK;
-        tri_inv_upper(R1, s, Ri);
-        if (int rc = update(blk, s, Ri, blk, false, 1.0)) return rc;
-        if (int rc = gram(blk, s, blk, Gm)) return rc;
-        if (!chol_checked(Gm, R2)) return MS_OK;
-        tri_inv_upper(R2, s, Ri);
-        if (int rc = update(blk, s, Ri, blk, false, 1.0)) return rc;
-        R = matmul(R2, R1, s);
-        ok = true;
-        return MS_OK;
+    // relative eigenvalue floor of a Gram matrix: below it a direction of the block is rounding noise.
+    // For a Gram from the tensor cores (FP32 sums) 64 u of the FP32 basis; for an exact Gram (FP64
+    // products and sums) (64 u)^2 for an FP32 basis -- the block's own rounding -- and 64 u for FP64.
+    double floor_rel(bool exact = false) const {
+        const double u = sizeof(T) == 8 ? 1.11e-16 : 5.96e-8;
+        return (exact && sizeof(T) == 4) ? (64.0 * u) * (64.0 * u) : 64.0 * u;
     }
-    // relative eigenvalue floor of a Gram matrix: below it a direction of the block is rounding noise
-    double floor_rel() const { return 64.0 * (sizeof(T) == 8 ? 1.11e-16 : 5.96e-8); }
-    // Cholesky factor of a Gram matrix, refused when a column is negligible against the largest or
-    // (nearly) dependent on the columns before it: R_ii^2 below the floor times its own G_ii
-    bool chol_checked(const std::vector<cd>& Gm, std::vector<cd>& R) {
+    // Cholesky factor of the leading k x k block of a Gram matrix, refused when a column is negligible
+    // against the largest or (nearly) dependent on the columns before it (R_ii^2 below the floor times
+    // its own G_ii).  Returns R (k x k, row-major).
+    bool chol_checked(const std::vector<cd>& Gm, int k, double floor, std::vector<cd>& R) {
+        std::vector<cd> Gk((size_t)k * k);
         double dmax = 0;
-        for (int i = 0; i < s; ++i) dmax = std::max(dmax, Gm[(size_t)i * s + i].real());
-        if (!(dmax > 0) || !chol_upper(Gm, s, 0.0, R)) return false;
-        for (int i = 0; i < s; ++i) {
-            const double gii = Gm[(size_t)i * s + i].real();
-            if (!(gii >= floor_rel() * dmax) || !(std::norm(R[(size_t)i * s + i]) >= floor_rel() * gii)) return false;
+        for (int i = 0; i < k; ++i) {
+            for (int j = 0; j < k; ++j) Gk[(size_t)i * k + j] = Gm[(size_t)i * s + j];
+            dmax = std::max(dmax, Gm[(size_t)i * s + i].real());
+        }
+        if (!(dmax > 0) || !chol_upper(Gk, k, 0.0, R)) return false;
+        for (int i = 0; i < k; ++i) {
+            const double gii = Gk[(size_t)i * k + i].real();
+            if (!(gii >= floor * dmax) || !(std::norm(R[(size_t)i * k + i]) >= floor * gii)) return false;
         }
         return true;
     }
+    // the s x s matrix [R_k^{-1} 0; 0 0] that orthonormalises the leading k columns and zeroes the rest
+    std::vector<cd> inv_lead(const std::vector<cd>& Rk, int k) {
+        std::vector<cd> Ri, out((size_t)s * s, cd(0));
+        tri_inv_upper(Rk, k, Ri);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) out[(size_t)i * s + j] = Ri[(size_t)i * k + j];
+        return out;
+    }
+    // Cholesky QR of the leading k columns of a block in place (the rest zeroed), twice; the first
+    // factor from G1 when given.  ok = false when a factor is refused.
+    // With k = s and Rout given, Rout = R2 R1 (blk_in = blk_out Rout).
+    int cholqr2_lead(C* blk, int k, const std::vector<cd>* G1, double floor1, bool& ok,
+                     std::vector<cd>* Rout = nullptr) {
+        std::vector<cd> Gm, R1, R2;
+        ok = false;
+        if (G1) Gm = *G1;
+        else if (int rc = gram(blk, s, blk, Gm)) return rc;
+        if (!chol_checked(Gm, k, floor1, R1)) return MS_OK;
+        if (int rc = update(blk, s, inv_lead(R1, k), blk, false, 1.0)) return rc;
+        if (int rc = gram(blk, s, blk, Gm)) return rc;
+        if (!chol_checked(Gm, k, floor_rel(), R2)) return MS_OK;
+        if (int rc = update(blk, s, inv_lead(R2, k), blk, false, 1.0)) return rc;
+        if (Rout && k == s) *Rout = matmul(R2, R1, s);
+        ok = true;
+        return MS_OK;
+    }
     // Orthonormal block dst with src = dst R (R s x s), orthogonal to the nprev basis blocks before it.
-    // A full-rank block takes CholQR2 (R upper triangular).  A (numerically) rank-deficient one -- the
-    // Krylov space has (nearly) closed, or the right-hand sides are dependent -- keeps its numerically
-    // independent directions (Gram eigenvectors with eigenvalues above the floor, scaled to unit
-    // length), fills the other columns with pseudo-random vectors orthogonalised against the basis,
-    // and takes R = dst^H src, so that the block stays s wide and orthonormal and the Arnoldi relation
-    // holds up to the dropped noise.  dst may equal src.
+    //  1. CholQR2 with tensor-core Grams (well-conditioned blocks).
+    //  2. CholQR2 whose first factor comes from an exact Gram (FP64 products and sums): FP32 blocks with
+    //     condition numbers up to ~1/u.
+    //  3. A (numerically) rank-deficient block -- the Krylov space has (nearly) closed, or the
+    //     right-hand sides are dependent: the exact Gram's eigenvectors with eigenvalues above the floor
+    //     give its independent directions at unit length; the other columns take pseudo-random vectors
+    //     orthogonalised against the basis, or, when the basis leaves no room for them (it spans the
+    //     space), zeros.
+    // R = dst^H src throughout, so the Arnoldi relation holds up to the dropped noise.  dst may equal src.
     int orth(const C* src, C* dst, int nprev, std::vector<cd>& R) {
         int rc;
         if (src == dst) {
@@ -501,19 +531,24 @@ struct BlockKrylov {
                 return rc;
             src = W;
         }
-        if ((rc = ms_check(h, cudaMemcpyAsync(dst, src, (size_t)N * s * sizeof(C), cudaMemcpyDeviceToDevice, st))))
-            return rc;
+        auto restart_from_src = [&]() {
+            return ms_check(h, cudaMemcpyAsync(dst, src, (size_t)N * s * sizeof(C), cudaMemcpyDeviceToDevice, st));
+        };
+        if ((rc = restart_from_src())) return rc;
         bool ok;
-        if ((rc = cholqr2(dst, R, ok))) return rc;
+        if ((rc = cholqr2_lead(dst, s, nullptr, floor_rel(), ok, &R))) return rc;
+        if (ok) return MS_OK;
+        std::vector<cd> Gx;
+        if ((rc = gram(src, s, src, Gx, true))) return rc;
+        if ((rc = restart_from_src())) return rc;
+        if ((rc = cholqr2_lead(dst, s, &Gx, floor_rel(true), ok, &R))) return rc;
         if (ok) return MS_OK;
         ++deflations;
-        std::vector<cd> Gm;
-        if ((rc = gram(src, s, src, Gm))) return rc;
         // eigenpairs of the Hermitian Gram by one-sided Jacobi: the squared column norms are the
         // eigenvalues of G^2, the accumulated rotations the eigenvectors
         std::vector<cd> A((size_t)s * s), V;
         for (int r = 0; r < s; ++r)
-            for (int c = 0; c < s; ++c) A[(size_t)c * s + r] = Gm[(size_t)r * s + c];
+            for (int c = 0; c < s; ++c) A[(size_t)c * s + r] = Gx[(size_t)r * s + c];
         std::vector<double> ev;
         dense::jacobi_svd(A, s, ev, V);
         std::vector<int> order(s);
@@ -524,9 +559,17 @@ struct BlockKrylov {
         std::vector<cd> Y((size_t)s * s, cd(0));
         for (; k < s; ++k) {
             const double lk = sqrt(std::max(0.0, ev[order[k]]));
-            if (!(lmax > 0) || !(lk > floor_rel() * lmax)) break;
+            if (!(lmax > 0) || !(lk > floor_rel(true) * lmax)) break;
             for (int i = 0; i < s; ++i) Y[(size_t)i * s + k] = V[(size_t)order[k] * s + i] / sqrt(lk);
         }
+        auto project_out = [&]() -> int {
+            for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+                std::vector<cd> Gp;
+                if (int e = gram(blk(0), nprev * s, dst, Gp)) return e;
+                if (int e = update(blk(0), nprev * s, Gp, dst, true, -1.0)) return e;
+            }
+            return MS_OK;
+        };
         if ((rc = update(src, s, Y, dst, false, 1.0))) return rc;
         if (k < s) {
             // entries of variance 2/3 per component: unit expected column norm with the 1 / sqrt(4N/3) scale
@@ -534,14 +577,18 @@ struct BlockKrylov {
                                                                      1.0 / sqrt(4.0 * N / 3.0));
             if ((rc = ms_check(h, cudaGetLastError()))) return rc;
         }
-        for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
-            std::vector<cd> Gp;
-            if ((rc = gram(blk(0), nprev * s, dst, Gp))) return rc;
-            if ((rc = update(blk(0), nprev * s, Gp, dst, true, -1.0))) return rc;
+        if ((rc = project_out())) return rc;
+        if ((rc = cholqr2_lead(dst, s, nullptr, floor_rel(), ok))) return rc;
+        if (!ok) {
+            // no room for the filler columns: keep the k independent directions, zero the rest
+            ++exhausted;
+            if ((rc = update(src, s, Y, dst, false, 1.0))) return rc;
+            if ((rc = project_out())) return rc;
+            if (k > 0) {
+                if ((rc = cholqr2_lead(dst, k, nullptr, floor_rel(), ok))) return rc;
+                if (!ok) return MS_ERR_BREAKDOWN;
+            }
         }
-        std::vector<cd> Rq;
-        if ((rc = cholqr2(dst, Rq, ok))) return rc;
-        if (!ok) return MS_ERR_BREAKDOWN;
         return gram(dst, s, src, R);             // R[k][r] = <dst_k, src_r>
     }
 };

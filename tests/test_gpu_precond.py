@@ -76,9 +76,9 @@ def test_preconditioned_gradient_matches_plain():
     for group in (0, 10):
         s = P.Solver.from_workload(wl, precond_group=group)
         g, info = s.solve(wl.inc_kind, wl.inc_angle, tol=1e-10, prec=P.MS_PREC_FP64)
-        assert info["status"] == 0
-        gc, gr, go, gi = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-10, prec=P.MS_PREC_FP64)
-        assert gi["status"] == 0
+        assert info["status"] == 0, (group, info)
+        gc, gr, go, gi = s.grad(wl.inc_kind, wl.inc_angle, g, w, rx, tol=1e-9, prec=P.MS_PREC_FP64)
+        assert gi["status"] == 0, (group, gi)
         out.append((gc.cpu().numpy(), gr.cpu().numpy(), go))
     for a, b in zip(out[0][:2], out[1][:2]):
         assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(a)
