@@ -143,7 +143,7 @@ class Problem3:
     rule parameters; the mat-vec y = gamma - S (T + R) gamma and the dense solve."""
 
     def __init__(self, md: Media3, centres, radii, bc, p: int, n_r=48, n_theta=24, t_max=10.0, alpha=1.0,
-                 beta=1.0, n_panels=1, ntheta_proj=24, rho_frac=0.5):
+                 beta=1.0, n_panels=1, ntheta_proj=40, rho_frac=0.5):
         self.md = md
         self.c = np.asarray(centres, dtype=float)
         self.R = np.asarray(radii, dtype=float)

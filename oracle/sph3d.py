@@ -316,11 +316,14 @@ def project_regular(p: int, kp: float, ks: float, rho: float, u, dirs, wts):
     return out if not vec else out[:, 0]
 
 
-def translate(p: int, kp: float, ks: float, src_centres, src_coeffs, tgt_centre, rho: float, ntheta: int = 24):
+def translate(p: int, kp: float, ks: float, src_centres, src_coeffs, tgt_centre, rho: float, ntheta: int = 40):
     """Local (regular) coefficients about tgt_centre of the outgoing fields of the given sources
     (centres (L, 3), coefficient blocks (L, total[, nrhs])): the summed field evaluated on the sphere of
     radius rho about the target and projected (project_regular).  rho must be below the distance to
-    every source; ntheta sets the rule (exact to degree 2 ntheta - 1)."""
+    every source; ntheta sets the rule (exact to degree 2 ntheta - 1).  The field on the sphere holds
+    every degree, decaying like (rho/d)^n for a source at distance d: degrees beyond the rule alias into
+    the projected ones, so at rho/d = 1/2 the rule needs 2 ntheta - 1 - p >~ 70 (ntheta = 40 gives 1e-13
+    at p <= 8; 24 nodes leave 1e-7 at p = 4 and 4e-4 at p = 8)."""
     dirs, wts = sphere_rule(ntheta)
     pts = np.asarray(tgt_centre)[None, :] + rho * dirs
     u = 0.0

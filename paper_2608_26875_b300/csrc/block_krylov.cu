@@ -390,11 +390,13 @@ struct BlockKrylov {
     int nsplit_max = 1;
     int deflations = 0;      // rank-deficient blocks met (orth)
     int exhausted = 0;       // of which the basis left no room for filler columns
+    int reverted = 0;        // restart cycles undone by the residual safeguard
 
     C* Z = nullptr;          // N x s: preconditioned block (group-block Jacobi), when the handle has one
+    C* Xprev = nullptr;      // N x s: the iterate before the last restart cycle's update
 
     ~BlockKrylov() {
-        cudaFree(V); cudaFree(W); cudaFree(Hd); cudaFree(part); cudaFree(G); cudaFree(Z);
+        cudaFree(V); cudaFree(W); cudaFree(Hd); cudaFree(part); cudaFree(G); cudaFree(Z); cudaFree(Xprev);
     }
     int init() {
         const size_t blk = (size_t)N * s * sizeof(C);
@@ -406,7 +408,7 @@ struct BlockKrylov {
         if (cudaMalloc(&V, blk * (m + 1)) != cudaSuccess || cudaMalloc(&W, blk) != cudaSuccess ||
             cudaMalloc(&Hd, nbmax * s * sizeof(C)) != cudaSuccess ||
             cudaMalloc(&part, part_cap * sizeof(double2)) != cudaSuccess ||
-            cudaMalloc(&G, nbmax * s * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc(&G, nbmax * s * sizeof(double2)) != cudaSuccess || cudaMalloc(&Xprev, blk) != cudaSuccess ||
             (h->pc.ng > 0 && cudaMalloc(&Z, blk) != cudaSuccess)) {
             cudaGetLastError();
             return MS_ERR_ALLOC;
@@ -612,6 +614,10 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
     relres.assign(s, 0.0);
     int total = 0;
     bool first = true;
+    // safeguard: a restart cycle whose update raised the worst true residual (an inaccurate basis or
+    // least-squares solution) is undone and the solve returns the previous iterate
+    std::vector<double> prev_res;
+    double prev_worst = 0;
     while (true) {
         // R0 = b - A x into V_0 (the first cycle of a zero initial guess needs no product)
         if (first && zero_guess) {
@@ -637,12 +643,24 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
         for (int i = 0; i < s; ++i)
             for (int c = 0; c < s; ++c) g[(size_t)i * s + c] = S0[(size_t)i * s + c];
         bool all = true;
+        double worst = 0;
         for (int c = 0; c < s; ++c) {
             double r2 = 0;
             for (int i = 0; i < s; ++i) r2 += std::norm(g[(size_t)i * s + c]);
             relres[c] = bn[c] > 0 ? sqrt(r2) / bn[c] : 0.0;
             all = all && relres[c] <= tol;
+            worst = std::max(worst, relres[c]);
         }
+        if (!prev_res.empty() && !(worst <= 1.05 * prev_worst)) {
+            if ((rc = ms_check(K.h, cudaMemcpyAsync(x, K.Xprev, (size_t)K.N * s * sizeof(C), cudaMemcpyDeviceToDevice,
+                                                    K.st))))
+                return rc;
+            relres = prev_res;
+            ++K.reverted;
+            break;
+        }
+        prev_res = relres;
+        prev_worst = worst;
         if (all || total >= max_iters) break;
         std::vector<std::vector<cd>> Rcol;      // R block column j: (j + 1) s x s, row-major
         std::vector<StepQR> qr;
@@ -713,6 +731,11 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
         const int nbj = j * s;
         if (nbj > 0) {
             std::vector<cd> Y((size_t)nbj * s, cd(0));
+            // truncated back substitution: a diagonal entry below the floor times the largest is a direction
+            // the basis cannot resolve (deflated or stagnant), and its component is left at zero
+            double dmax = 0;
+            for (int row = 0; row < nbj; ++row) dmax = std::max(dmax, std::abs(Rcol[row / s][(size_t)row * s + (row % s)]));
+            const double dfloor = K.floor_rel() * dmax;
 #pragma omp parallel for schedule(static)
             for (int c = 0; c < s; ++c) {
                 for (int row = nbj - 1; row >= 0; --row) {
@@ -728,9 +751,12 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
                         }
                     }
                     const cd d = Rcol[jb][(size_t)row * s + (row - jb * s)];
-                    Y[(size_t)row * s + c] = d != 0.0 ? v / d : cd(0);
+                    Y[(size_t)row * s + c] = std::abs(d) > dfloor ? v / d : cd(0);
                 }
             }
+            if ((rc = ms_check(K.h, cudaMemcpyAsync(K.Xprev, x, (size_t)K.N * s * sizeof(C), cudaMemcpyDeviceToDevice,
+                                                    K.st))))
+                return rc;
             if ((rc = K.update(K.blk(0), nbj, Y, x, true, 1.0))) return rc;
         }
         if (all || total >= max_iters) break;

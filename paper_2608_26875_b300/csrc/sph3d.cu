@@ -208,9 +208,17 @@ struct Layer {
     double lam, mu, kp, ks;
 };
 
+// k_z = sqrt(k^2 - lam^2) on the branch Im k_z >= 0 (k_z >= 0 when real): the principal root, with
+// the sign fixed explicitly because a real lam gives the argument a signed zero imaginary part
+cd kz_of(double k, cd lam) {
+    cd z = std::sqrt(cd(k * k) - lam * lam);
+    if (z.imag() < 0.0 || (z.imag() == 0.0 && z.real() < 0.0)) z = -z;
+    return z;
+}
+
 // plane wave basis at horizontal wavenumber lam (complex) and azimuth th in a layer: direction, SV, SH
 void pw_basis(double k, cd lam, double th, bool up, cd e[3], cd v[3], cd h[3]) {
-    const cd kz = std::sqrt(k * k - lam * lam);
+    const cd kz = kz_of(k, lam);
     const double c = cos(th), s = sin(th);
     e[0] = lam * c / k; e[1] = lam * s / k; e[2] = (up ? kz : -kz) / k;
     h[0] = -s; h[1] = c; h[2] = 0.0;
@@ -283,6 +291,167 @@ void plane_coeffs(int p, double kp, const cd d[3], const cd pol[3], cd* out) {
             out[nmn + idx(n, m) - 1] = -f * in * dot3(dxg, pol);
         }
     }
+}
+
+// Gaunt table: Gt[k'][t][nu mu] = 4 pi i^{nu - n' + q} 2 pi N N N int P P P dt, q = |n' - nu| + 2t (exact
+// Gauss-Legendre in cos(theta); the phi integral is 2 pi)
+std::vector<cd> build_gaunt(int p) {
+    const int K2 = (p + 2) * (p + 2), nl = (p + 1) * (p + 1);
+    std::vector<cd> Gt((size_t)K2 * (p + 1) * nl, cd(0));
+    {
+        const int NG = 2 * p + 6;
+        std::vector<double> gx(NG), gw(NG);
+        // Gauss-Legendre nodes by Newton on P_NG
+        for (int i = 0; i < NG; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (NG + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+                const double dp = NG * (x * p1 - p0) / (x * x - 1);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            const double dp = NG * (x * p1 - p0) / (x * x - 1);
+            gx[i] = x;
+            gw[i] = 2.0 / ((1 - x * x) * dp * dp);
+        }
+        const int PQ = 2 * p + 2;
+        // Ferrers P_n^k(t) = (1 - t^2)^{k/2} Q_n^k(t) at the nodes, n <= PQ
+        std::vector<double> F((size_t)NG * (PQ + 1) * (PQ + 1), 0.0);
+        for (int i = 0; i < NG; ++i) {
+            const std::vector<cd> Q = qtab(PQ, cd(gx[i]));
+            const double s = sqrt(1 - gx[i] * gx[i]);
+            for (int n = 0; n <= PQ; ++n)
+                for (int k = 0; k <= n; ++k)
+                    F[((size_t)i * (PQ + 1) + n) * (PQ + 1) + k] = Q[(size_t)n * (PQ + 2) + k].real() * pow(s, k);
+        }
+        const cd I(0, 1);
+        for (int n1 = 0; n1 <= p + 1; ++n1)
+            for (int m1 = -n1; m1 <= n1; ++m1)
+                for (int nu = 0; nu <= p; ++nu)
+                    for (int mu = -nu; mu <= nu; ++mu)
+                        for (int t = 0; t <= std::min(n1, nu); ++t) {
+                            const int q = std::abs(n1 - nu) + 2 * t, dm = m1 - mu;
+                            if (std::abs(dm) > q) continue;
+                            double s = 0;
+                            for (int i = 0; i < NG; ++i)
+                                s += gw[i] * F[((size_t)i * (PQ + 1) + n1) * (PQ + 1) + std::abs(m1)] *
+                                     F[((size_t)i * (PQ + 1) + nu) * (PQ + 1) + std::abs(mu)] *
+                                     F[((size_t)i * (PQ + 1) + q) * (PQ + 1) + std::abs(dm)];
+                            const double G = 2.0 * M_PI * ynorm(n1, std::abs(m1)) * ynorm(nu, std::abs(mu)) * ynorm(q, std::abs(dm)) * s;
+                            Gt[((size_t)idx(n1, m1) * (p + 1) + t) * nl + idx(nu, mu)] = 4.0 * M_PI * std::pow(I, nu - n1 + q) * G;
+                        }
+    }
+    return Gt;
+}
+
+// Sparse Cartesian maps (<= 9 terms per row) by exact quadrature on the unit sphere (real directions):
+// forward, the outgoing Cartesian expansions W[c][(n', m')] of the shear coefficients; back, a and b from
+// the regular Cartesian expansions.  Returns false if a row needs more than 9 terms.
+bool build_cart_maps(int p, std::vector<int>& midx, std::vector<cd>& mcoef, std::vector<int>& uidx,
+                     std::vector<cd>& ucoef) {
+    const int K2 = (p + 2) * (p + 2), nl = (p + 1) * (p + 1), nmn = p * (p + 2);
+    midx.assign((size_t)3 * K2 * 9, -1);
+    uidx.assign((size_t)2 * nmn * 9, -1);
+    mcoef.assign((size_t)3 * K2 * 9, cd(0));
+    ucoef.assign((size_t)2 * nmn * 9, cd(0));
+    bool map_overflow = false;
+    {
+        const int NT = p + 5, NP = 2 * p + 10, P1 = p + 1;
+        std::vector<double> tx(NT), tw(NT);
+        for (int i = 0; i < NT; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (NT + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+                const double dp = NT * (x * p1 - p0) / (x * x - 1);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            const double dp = NT * (x * p1 - p0) / (x * x - 1);
+            tx[i] = x;
+            tw[i] = 2.0 / ((1 - x * x) * dp * dp);
+        }
+        const int NY = (P1 + 1) * (P1 + 1);
+        // C[kind][c][(n, m)][(n2, m2)] accumulated densely over (n, m) <= P1 and (n2, m2) <= P1
+        std::vector<cd> Cm((size_t)3 * NY * NY, cd(0)), Cp((size_t)3 * NY * NY, cd(0)), Cx((size_t)3 * NY * NY, cd(0));
+        std::vector<cd> Y, G;
+        for (int i = 0; i < NT; ++i)
+            for (int j = 0; j < NP; ++j) {
+                const double ph = 2.0 * M_PI * j / NP, st = sqrt(1 - tx[i] * tx[i]);
+                const cd d[3] = {st * cos(ph), st * sin(ph), tx[i]};
+                const double wq = tw[i] * 2.0 * M_PI / NP;
+                ylm_c(P1, d, Y);
+                grad_ylm_c(P1, d, G);
+                for (int k = 0; k < NY; ++k) {
+                    const int n = (int)sqrt((double)k + 0.5);
+                    const cd* gk = &G[(size_t)k * 3];
+                    cd X[3];
+                    cross3(gk, d, X);
+                    for (int c = 0; c < 3; ++c) {
+                        const cd vm = (double)n * Y[k] * d[c] + gk[c];
+                        const cd vp = (double)(n + 1) * Y[k] * d[c] - gk[c];
+                        for (int k2 = 0; k2 < NY; ++k2) {
+                            const cd yc = std::conj(Y[k2]) * wq;
+                            Cm[((size_t)c * NY + k) * NY + k2] += vm * yc;
+                            Cp[((size_t)c * NY + k) * NY + k2] += vp * yc;
+                            Cx[((size_t)c * NY + k) * NY + k2] += X[c] * yc;
+                        }
+                    }
+                }
+            }
+        const cd I(0, 1);
+        auto C = [&](std::vector<cd>& A, int c, int k, int k2) -> cd { return A[((size_t)c * NY + k) * NY + k2]; };
+        // forward: W[c][(n', m')] from alpha_{n'+1, m} (V-), alpha_{n'-1, m} (V+), beta_{n', m} (X)
+        for (int c = 0; c < 3; ++c)
+            for (int n1 = 0; n1 <= p + 1; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    const int row = c * K2 + idx(n1, m1);
+                    int cnt = 0;
+                    auto add = [&](int src, cd coef) {
+                        if (std::abs(coef) < 1e-13) return;
+                        if (cnt >= 9) { map_overflow = true; return; }
+                        midx[(size_t)row * 9 + cnt] = src;
+                        mcoef[(size_t)row * 9 + cnt] = coef;
+                        ++cnt;
+                    };
+                    const int n = n1 + 1;
+                    if (n <= p)
+                        for (int m = -n; m <= n; ++m)
+                            add(idx(n, m) - 1, (double)(n + 1) / (I * (2.0 * n + 1)) * C(Cm, c, idx(n, m), idx(n1, m1)));
+                    const int nb = n1 - 1;
+                    if (nb >= 1 && nb <= p)
+                        for (int m = -nb; m <= nb; ++m)
+                            add(idx(nb, m) - 1, (double)nb / (I * (2.0 * nb + 1)) * C(Cp, c, idx(nb, m), idx(n1, m1)));
+                    if (n1 >= 1 && n1 <= p)
+                        for (int m = -n1; m <= n1; ++m) add(nmn + idx(n1, m) - 1, C(Cx, c, idx(n1, m), idx(n1, m1)));
+                }
+        // back: a_Jm = i/(J(J+1)) sum conj(C-(J, m -> J-1, mu)) R_c(J-1, mu); b_Jm = 1/(J(J+1)) sum conj(CX) R_c(J, mu)
+        for (int J = 1; J <= p; ++J)
+            for (int m = -J; m <= J; ++m)
+                for (int which = 0; which < 2; ++which) {
+                    const int row = which * nmn + idx(J, m) - 1;
+                    int cnt = 0;
+                    const int nd = which == 0 ? J - 1 : J;
+                    for (int c = 0; c < 3; ++c)
+                        for (int mu = -nd; mu <= nd; ++mu) {
+                            const cd cc = which == 0 ? std::conj(C(Cm, c, idx(J, m), idx(nd, mu))) * I / (J * (J + 1.0))
+                                                     : std::conj(C(Cx, c, idx(J, m), idx(nd, mu))) / (J * (J + 1.0));
+                            if (std::abs(cc) < 1e-13) continue;
+                            if (cnt >= 9) { map_overflow = true; continue; }
+                            uidx[(size_t)row * 9 + cnt] = c * nl + idx(nd, mu);
+                            ucoef[(size_t)row * 9 + cnt] = cc;
+                            ++cnt;
+                        }
+                }
+    }
+    return !map_overflow;
 }
 
 // ------------------------------------------------------------------ device kernels
@@ -804,152 +973,10 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
             cudaMemcpyToSymbol(c_ynorm, yn.data(), yn.size() * sizeof(double)) != cudaSuccess)
             return fail(MS_ERR_CUDA);
     }
-    // Gaunt table: Gt[k'][t][nu mu] = 4 pi i^{nu - n' + q} 2 pi N N N int P P P dt, q = |n' - nu| + 2t
-    std::vector<cd> Gt((size_t)K2 * (p + 1) * nl, cd(0));
-    {
-        const int NG = 2 * p + 6;
-        std::vector<double> gx(NG), gw(NG);
-        // Gauss-Legendre nodes by Newton on P_NG
-        for (int i = 0; i < NG; ++i) {
-            double x = cos(M_PI * (i + 0.75) / (NG + 0.5));
-            for (int it = 0; it < 100; ++it) {
-                double p0 = 1, p1 = x;
-                for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-                const double dp = NG * (x * p1 - p0) / (x * x - 1);
-                const double dx = p1 / dp;
-                x -= dx;
-                if (fabs(dx) < 1e-16) break;
-            }
-            double p0 = 1, p1 = x;
-            for (int k = 2; k <= NG; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-            const double dp = NG * (x * p1 - p0) / (x * x - 1);
-            gx[i] = x;
-            gw[i] = 2.0 / ((1 - x * x) * dp * dp);
-        }
-        const int PQ = 2 * p + 2;
-        // Ferrers P_n^k(t) = (1 - t^2)^{k/2} Q_n^k(t) at the nodes, n <= PQ
-        std::vector<double> F((size_t)NG * (PQ + 1) * (PQ + 1), 0.0);
-        for (int i = 0; i < NG; ++i) {
-            const std::vector<cd> Q = qtab(PQ, cd(gx[i]));
-            const double s = sqrt(1 - gx[i] * gx[i]);
-            for (int n = 0; n <= PQ; ++n)
-                for (int k = 0; k <= n; ++k)
-                    F[((size_t)i * (PQ + 1) + n) * (PQ + 1) + k] = Q[(size_t)n * (PQ + 2) + k].real() * pow(s, k);
-        }
-        const cd I(0, 1);
-        for (int n1 = 0; n1 <= p + 1; ++n1)
-            for (int m1 = -n1; m1 <= n1; ++m1)
-                for (int nu = 0; nu <= p; ++nu)
-                    for (int mu = -nu; mu <= nu; ++mu)
-                        for (int t = 0; t <= std::min(n1, nu); ++t) {
-                            const int q = std::abs(n1 - nu) + 2 * t, dm = m1 - mu;
-                            if (std::abs(dm) > q) continue;
-                            double s = 0;
-                            for (int i = 0; i < NG; ++i)
-                                s += gw[i] * F[((size_t)i * (PQ + 1) + n1) * (PQ + 1) + std::abs(m1)] *
-                                     F[((size_t)i * (PQ + 1) + nu) * (PQ + 1) + std::abs(mu)] *
-                                     F[((size_t)i * (PQ + 1) + q) * (PQ + 1) + std::abs(dm)];
-                            const double G = 2.0 * M_PI * ynorm(n1, std::abs(m1)) * ynorm(nu, std::abs(mu)) * ynorm(q, std::abs(dm)) * s;
-                            Gt[((size_t)idx(n1, m1) * (p + 1) + t) * nl + idx(nu, mu)] = 4.0 * M_PI * std::pow(I, nu - n1 + q) * G;
-                        }
-    }
-    // Cartesian maps by quadrature on the unit sphere (real directions): C-, C+, CX
-    std::vector<int> midx((size_t)3 * K2 * 9, -1), uidx((size_t)2 * nmn * 9, -1);
-    bool map_overflow = false;
-    std::vector<cd> mcoef((size_t)3 * K2 * 9, cd(0)), ucoef((size_t)2 * nmn * 9, cd(0));
-    {
-        const int NT = p + 5, NP = 2 * p + 10, P1 = p + 1;
-        std::vector<double> tx(NT), tw(NT);
-        for (int i = 0; i < NT; ++i) {
-            double x = cos(M_PI * (i + 0.75) / (NT + 0.5));
-            for (int it = 0; it < 100; ++it) {
-                double p0 = 1, p1 = x;
-                for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-                const double dp = NT * (x * p1 - p0) / (x * x - 1);
-                const double dx = p1 / dp;
-                x -= dx;
-                if (fabs(dx) < 1e-16) break;
-            }
-            double p0 = 1, p1 = x;
-            for (int k = 2; k <= NT; ++k) { const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-            const double dp = NT * (x * p1 - p0) / (x * x - 1);
-            tx[i] = x;
-            tw[i] = 2.0 / ((1 - x * x) * dp * dp);
-        }
-        const int NY = (P1 + 1) * (P1 + 1);
-        // C[kind][c][(n, m)][(n2, m2)] accumulated densely over (n, m) <= P1 and (n2, m2) <= P1
-        std::vector<cd> Cm((size_t)3 * NY * NY, cd(0)), Cp((size_t)3 * NY * NY, cd(0)), Cx((size_t)3 * NY * NY, cd(0));
-        std::vector<cd> Y, G;
-        for (int i = 0; i < NT; ++i)
-            for (int j = 0; j < NP; ++j) {
-                const double ph = 2.0 * M_PI * j / NP, st = sqrt(1 - tx[i] * tx[i]);
-                const cd d[3] = {st * cos(ph), st * sin(ph), tx[i]};
-                const double wq = tw[i] * 2.0 * M_PI / NP;
-                ylm_c(P1, d, Y);
-                grad_ylm_c(P1, d, G);
-                for (int k = 0; k < NY; ++k) {
-                    const int n = (int)sqrt((double)k + 0.5);
-                    const cd* gk = &G[(size_t)k * 3];
-                    cd X[3];
-                    cross3(gk, d, X);
-                    for (int c = 0; c < 3; ++c) {
-                        const cd vm = (double)n * Y[k] * d[c] + gk[c];
-                        const cd vp = (double)(n + 1) * Y[k] * d[c] - gk[c];
-                        for (int k2 = 0; k2 < NY; ++k2) {
-                            const cd yc = std::conj(Y[k2]) * wq;
-                            Cm[((size_t)c * NY + k) * NY + k2] += vm * yc;
-                            Cp[((size_t)c * NY + k) * NY + k2] += vp * yc;
-                            Cx[((size_t)c * NY + k) * NY + k2] += X[c] * yc;
-                        }
-                    }
-                }
-            }
-        const cd I(0, 1);
-        auto C = [&](std::vector<cd>& A, int c, int k, int k2) -> cd { return A[((size_t)c * NY + k) * NY + k2]; };
-        // forward: W[c][(n', m')] from alpha_{n'+1, m} (V-), alpha_{n'-1, m} (V+), beta_{n', m} (X)
-        for (int c = 0; c < 3; ++c)
-            for (int n1 = 0; n1 <= p + 1; ++n1)
-                for (int m1 = -n1; m1 <= n1; ++m1) {
-                    const int row = c * K2 + idx(n1, m1);
-                    int cnt = 0;
-                    auto add = [&](int src, cd coef) {
-                        if (std::abs(coef) < 1e-13) return;
-                        if (cnt >= 9) { map_overflow = true; return; }
-                        midx[(size_t)row * 9 + cnt] = src;
-                        mcoef[(size_t)row * 9 + cnt] = coef;
-                        ++cnt;
-                    };
-                    const int n = n1 + 1;
-                    if (n <= p)
-                        for (int m = -n; m <= n; ++m)
-                            add(idx(n, m) - 1, (double)(n + 1) / (I * (2.0 * n + 1)) * C(Cm, c, idx(n, m), idx(n1, m1)));
-                    const int nb = n1 - 1;
-                    if (nb >= 1 && nb <= p)
-                        for (int m = -nb; m <= nb; ++m)
-                            add(idx(nb, m) - 1, (double)nb / (I * (2.0 * nb + 1)) * C(Cp, c, idx(nb, m), idx(n1, m1)));
-                    if (n1 >= 1 && n1 <= p)
-                        for (int m = -n1; m <= n1; ++m) add(nmn + idx(n1, m) - 1, C(Cx, c, idx(n1, m), idx(n1, m1)));
-                }
-        // back: a_Jm = i/(J(J+1)) sum conj(C-(J, m -> J-1, mu)) R_c(J-1, mu); b_Jm = 1/(J(J+1)) sum conj(CX) R_c(J, mu)
-        for (int J = 1; J <= p; ++J)
-            for (int m = -J; m <= J; ++m)
-                for (int which = 0; which < 2; ++which) {
-                    const int row = which * nmn + idx(J, m) - 1;
-                    int cnt = 0;
-                    const int nd = which == 0 ? J - 1 : J;
-                    for (int c = 0; c < 3; ++c)
-                        for (int mu = -nd; mu <= nd; ++mu) {
-                            const cd cc = which == 0 ? std::conj(C(Cm, c, idx(J, m), idx(nd, mu))) * I / (J * (J + 1.0))
-                                                     : std::conj(C(Cx, c, idx(J, m), idx(nd, mu))) / (J * (J + 1.0));
-                            if (std::abs(cc) < 1e-13) continue;
-                            if (cnt >= 9) { map_overflow = true; continue; }
-                            uidx[(size_t)row * 9 + cnt] = c * nl + idx(nd, mu);
-                            ucoef[(size_t)row * 9 + cnt] = cc;
-                            ++cnt;
-                        }
-                }
-    }
-    if (map_overflow) return fail(MS_ERR_UNSUPPORTED);
+    const std::vector<cd> Gt = build_gaunt(p);
+    std::vector<int> midx, uidx;
+    std::vector<cd> mcoef, ucoef;
+    if (!build_cart_maps(p, midx, mcoef, uidx, ucoef)) return fail(MS_ERR_UNSUPPORTED);
     // Sommerfeld nodes, blocks B and C, reflection
     const int NS = opt.n_r * opt.n_theta;
     h->NS = NS;
@@ -986,7 +1013,7 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
                 const size_t q = (size_t)ir * opt.n_theta + it;
                 const double th = 2.0 * M_PI * it / opt.n_theta;
                 const cd W = wt * lam * dlam * (2.0 * M_PI / opt.n_theta);
-                const cd kzp = std::sqrt(h->lo.kp * h->lo.kp - lam * lam), kzs = std::sqrt(h->lo.ks * h->lo.ks - lam * lam);
+                const cd kzp = kz_of(h->lo.kp, lam), kzs = kz_of(h->lo.ks, lam);
                 node[q * 4] = lam * cos(th);
                 node[q * 4 + 1] = lam * sin(th);
                 node[q * 4 + 2] = kzp;

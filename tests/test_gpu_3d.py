@@ -41,7 +41,7 @@ def case(request):
     p = request.param
     wl = syn.spheres3d(M=5, seed=71, box=(-2.0, 2.0, -2.0, 2.0, -3.5, -1.0), bc="alternate")
     md = L3.Media3(wl.media.lam_u, wl.media.mu_u, wl.media.lam_l, wl.media.mu_l, wl.omega)
-    ref = L3.Problem3(md, wl.centres, wl.radius, wl.bc, p, ntheta_proj=20, **RULE)
+    ref = L3.Problem3(md, wl.centres, wl.radius, wl.bc, p, ntheta_proj=40, **RULE)
     gpu = P.Solver3(wl.centres, wl.radius, wl.bc, wl.media, wl.omega, p, **RULE)
     return wl, p, ref, gpu
 
@@ -90,5 +90,5 @@ def test_full_size_translation_on_sampled_targets():
     for m in (0, wl.M // 2):
         others = [l for l in range(wl.M) if l != m]
         dmin = min(np.linalg.norm(wl.centres[l] - wl.centres[m]) for l in others)
-        want = S3.translate(p, md.kp_l, md.ks_l, wl.centres[others], x[others], wl.centres[m], 0.5 * dmin, 20)
+        want = S3.translate(p, md.kp_l, md.ks_l, wl.centres[others], x[others], wl.centres[m], 0.5 * dmin, 40)
         assert rel(t[m], want) <= 1e-10

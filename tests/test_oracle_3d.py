@@ -256,3 +256,37 @@ def test_solved_system_boundary_residual_falls_with_the_order():
                 worst = max(worst, abs(P3.incident_field(*inc[r], X) + P3.scattered_field(g[..., r], X)).max())
         res.append(worst)
     assert res[1] < 0.1 * res[0] and res[2] < res[1] and res[2] < 1e-4, res
+
+
+def test_projection_translation_against_the_addition_theorem_series():
+    """The projection (sph3d.translate) against the scalar addition theorem for the compressional part,
+    written independently: h_n Y_n^m about the source = sum 4 pi i^{nu-n+q} h_q(k d) Y_q^{m-mu}(d^) G
+    j_nu Y_nu^mu about the target, G = int Y_n^m conj(Y_nu^mu) conj(Y_q^{m-mu}) by sphere quadrature."""
+    p, kp = 4, KP
+    nmn, nl, tot = S.sizes(p)
+    rng = np.random.default_rng(11)
+    g = np.zeros(tot, complex)
+    g[2 * nmn:] = rng.normal(size=nl) + 1j * rng.normal(size=nl)     # compressional part only
+    src, tgt = np.array([0.2, -0.1, -2.0]), np.array([1.3, -0.4, -2.6])
+    d = tgt - src
+    dn = np.linalg.norm(d)
+    P2 = 2 * p
+    dirs, w = S.sphere_rule(24)
+    Y = S.ylm(P2, dirs)
+    hq, _ = S.radial(P2, kp * dn, "h")
+    Yd = S.ylm(P2, d / dn)
+    want = np.zeros(nl, complex)
+    for n in range(p + 1):
+        for m in range(-n, n + 1):
+            for nu in range(p + 1):
+                for mu in range(-nu, nu + 1):
+                    s = 0
+                    for q in range(abs(n - nu), n + nu + 1, 2):
+                        if abs(m - mu) > q:
+                            continue
+                        G = np.sum(w * Y[:, S.idx(n, m)] * Y[:, S.idx(nu, mu)].conj() * Y[:, S.idx(q, m - mu)].conj())
+                        s += 4 * np.pi * 1j ** (nu - n + q) * hq[q] * Yd[S.idx(q, m - mu)] * G
+                    want[S.idx(nu, mu)] += s * g[2 * nmn + S.idx(n, m)]
+    got = S.translate(p, KP, KS, [src], [g], tgt, 0.5 * dn)
+    assert abs(got[2 * nmn:] - want).max() < 1e-11 * abs(want).max()
+    assert abs(got[:2 * nmn]).max() < 1e-11 * abs(want).max()
