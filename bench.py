@@ -485,6 +485,7 @@ def run_3d(args):
         return e0.elapsed_time(e1) / n / 1000.0
 
     n = max(1, args.steps)
+    t_all32 = timed(lambda: s.apply(x, prec=P.MS_PREC_FP32, out=y), n)
     t_all = timed(lambda: s.apply(x, out=y), n)
     t_T = timed(lambda: s.operator(x, nat.MS3_PART_T, out=y), n)
     t_R = timed(lambda: s.operator(x, nat.MS3_PART_R, out=y), n)
@@ -495,15 +496,19 @@ def run_3d(args):
     cmac_R = NS * M * (nl + 4 * nmn) * nrhs + M * NS * 3 * T * nrhs
     fp64_peak = 1.13e12           # measured FP64 FMA-chain rate of this GPU (design notes)
     out = {"mode": "3d", "workload": wl.name, "M": M, "p": p, "nrhs": nrhs, "n_nodes": NS, "contour_alpha": alpha,
-           "setup_s": setup_s, "matvec_s": t_all, "matvecs_per_s": 1.0 / t_all, "free_space_s": t_T,
+           "setup_s": setup_s, "matvec_s": t_all, "matvecs_per_s": 1.0 / t_all, "fp32_matvec_s": t_all32,
+           "free_space_s": t_T,
            "reflected_s": t_R, "dtype": "f64",
            "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak / 1e12,
                         "free_space": {"achieved": 8 * cmac_T / t_T / 1e12, "frac": 8 * cmac_T / t_T / fp64_peak},
                         "reflected": {"achieved": 8 * cmac_R / t_R / 1e12, "frac": 8 * cmac_R / t_R / fp64_peak},
                         "flops": "complex MACs of the contractions x 8 (translation-coefficient generation not counted)"}}
+    gm, info_m = s.solve(wl.inc_kind, wl.inc_theta, wl.inc_phi, tol=args.tol, prec=P.MS_PREC_FP32)
+    out["solve_mixed"] = info_m
     if not args.skip_fp64:
         g, info = s.solve(wl.inc_kind, wl.inc_theta, wl.inc_phi, tol=args.tol)
-        out["solve"] = info
+        out["solve_fp64"] = info
+        out["rel_diff_mixed_vs_fp64"] = float(torch.linalg.norm(gm - g) / torch.linalg.norm(g))
     print(json.dumps(out), flush=True)
 
 

@@ -80,21 +80,25 @@ void ms3_default_options(ms3_options* o);
 int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
               ms3_handle** out);
 
-/* y = x - S (T + R) x for nrhs (1..64) columns, FP64.  x, y: device [M][T][nrhs], y != x. */
-int ms3_apply(ms3_handle* h, const void* x, void* y, int32_t nrhs, void* stream);
+/* y = x - S (T + R) x for nrhs (1..64) columns: prec MS_PREC_FP64 (FP64 tables and arithmetic) or
+ * MS_PREC_FP32 (FP32 tables and arithmetic, blocks converted on the way in and out).
+ * x, y: device [M][T][nrhs] complex double, y != x. */
+int ms3_apply(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream);
 
 /* The parts selected by MS3_PART_* bits: with MS3_PART_S, y = x - S (sum of parts) x; without it,
- * y = (sum of parts) x (incoming coefficients).  Same layouts and limits as ms3_apply. */
-int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, void* stream);
+ * y = (sum of parts) x (incoming coefficients).  Same layouts, precisions and limits as ms3_apply. */
+int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, int32_t prec, void* stream);
 
 /* b = S a0 for plane waves from the upper layer (their transmitted field's regular expansion about each
  * sphere).  b: device [M][T][inc->nrhs]. */
 int ms3_rhs(ms3_handle* h, const ms3_incidence* inc, void* b, void* stream);
 
-/* Solve A tau = S a0 to relative residual tol per column with block GMRES over the columns (FP64).
- * tau: device [M][T][nrhs], overwritten.  info may be NULL.  MS_OK, MS_NOT_CONVERGED or an error.
- * Synchronises the stream. */
-int ms3_solve(ms3_handle* h, const ms3_incidence* inc, double tol, void* tau, ms_solve_info* info, void* stream);
+/* Solve A tau = S a0 to relative residual tol per column (FP64 residuals) with block GMRES over the
+ * columns: prec MS_PREC_FP64 (FP64 operator and basis) or MS_PREC_FP32 (FP64 iterative refinement around
+ * FP32 block GMRES solves to 1e-3).  tau: device [M][T][nrhs], overwritten.  info may be NULL.  MS_OK,
+ * MS_NOT_CONVERGED or an error.  Synchronises the stream. */
+int ms3_solve(ms3_handle* h, const ms3_incidence* inc, double tol, int32_t prec, void* tau, ms_solve_info* info,
+              void* stream);
 
 /* M, p, coefficients per sphere T, Sommerfeld nodes N_S.  Any output may be NULL. */
 int ms3_info(const ms3_handle* h, int32_t* M, int32_t* p, int32_t* T, int32_t* n_nodes);

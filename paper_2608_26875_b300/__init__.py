@@ -356,16 +356,16 @@ class Solver3:
             raise ValueError(f"expected a contiguous complex128 CUDA tensor ({self.M}, {self.T}, nrhs)")
         return int(x.shape[2])
 
-    def apply(self, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
-        """y = x - S (T + R) x (ms3_apply)."""
-        return self.operator(x, nat.MS3_PART_T | nat.MS3_PART_R | nat.MS3_PART_S, out, stream)
+    def apply(self, x: torch.Tensor, prec: int = MS_PREC_FP64, out=None, stream=None) -> torch.Tensor:
+        """y = x - S (T + R) x (ms3_apply), FP64 or FP32 arithmetic."""
+        return self.operator(x, nat.MS3_PART_T | nat.MS3_PART_R | nat.MS3_PART_S, prec, out, stream)
 
-    def operator(self, x: torch.Tensor, parts: int, out=None, stream=None) -> torch.Tensor:
+    def operator(self, x: torch.Tensor, parts: int, prec: int = MS_PREC_FP64, out=None, stream=None) -> torch.Tensor:
         """The selected parts (ms3_operator): with MS3_PART_S, x - S (parts) x; else (parts) x."""
         nrhs = self._check(x)
         y = out if out is not None else torch.empty_like(x)
         nat.check(nat.lib().ms3_operator(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), nrhs,
-                                         int(parts), _stream(stream)), "ms3_operator")
+                                         int(parts), int(prec), _stream(stream)), "ms3_operator")
         return y
 
     @staticmethod
@@ -385,15 +385,17 @@ class Solver3:
                   "ms3_rhs")
         return b
 
-    def solve(self, kinds, thetas, phis, tol: float = 1e-10, stream=None):
-        """tau solving A tau = S a0 (ms3_solve).  Returns (tau, info)."""
+    def solve(self, kinds, thetas, phis, tol: float = 1e-10, prec: int = MS_PREC_FP64, stream=None):
+        """tau solving A tau = S a0 (ms3_solve): FP64, or FP32 inner solves with FP64 refinement.
+        Returns (tau, info)."""
         inc, keep = self._incidence(kinds, thetas, phis)
         g = torch.empty((self.M, self.T, inc.nrhs), dtype=torch.complex128, device="cuda")
         info = nat.SolveInfo()
-        st = nat.check(nat.lib().ms3_solve(self._h, ctypes.byref(inc), float(tol), ctypes.c_void_p(g.data_ptr()),
-                                           ctypes.byref(info), _stream(stream)), "ms3_solve", allow_warning=True)
-        return g, {"iterations": info.iterations, "matvecs": info.matvecs, "max_rel_residual": info.max_rel_residual,
-                   "seconds": info.seconds, "status": st}
+        st = nat.check(nat.lib().ms3_solve(self._h, ctypes.byref(inc), float(tol), int(prec),
+                                           ctypes.c_void_p(g.data_ptr()), ctypes.byref(info), _stream(stream)),
+                       "ms3_solve", allow_warning=True)
+        return g, {"iterations": info.iterations, "refinements": info.refinements, "matvecs": info.matvecs,
+                   "max_rel_residual": info.max_rel_residual, "seconds": info.seconds, "status": st}
 
     def close(self):
         if getattr(self, "_h", None):

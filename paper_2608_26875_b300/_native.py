@@ -126,11 +126,12 @@ SIGNATURES = {
     "ms_destroy": (None, [ctypes.c_void_p]),
     "ms3_default_options": (None, [ctypes.c_void_p]),
     "ms3_setup": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, c_int, ctypes.c_void_p, ctypes.c_void_p]),
-    "ms3_apply": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, ctypes.c_void_p]),
-    "ms3_operator": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, ctypes.c_void_p]),
+    "ms3_apply": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, ctypes.c_void_p]),
+    "ms3_operator": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int, c_int, c_int,
+                             ctypes.c_void_p]),
     "ms3_rhs": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "ms3_solve": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
-                          ctypes.c_void_p]),
+    "ms3_solve": (c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, c_int, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p]),
     "ms3_info": (c_int, [ctypes.c_void_p, c_ip, c_ip, c_ip, c_ip]),
     "ms3_destroy": (None, [ctypes.c_void_p]),
     "ms_status_string": (ctypes.c_char_p, [c_int]),

@@ -802,27 +802,33 @@ int ms_block_inner(ms_handle* h, int nrhs, long long N, const void* rs, void* ds
     return ms_check(h, cudaMemcpyAsync(ds, K->Z, (size_t)N * nrhs * sizeof(C), cudaMemcpyDeviceToDevice, st));
 }
 
-// Block GMRES in FP64 on the CUDA cores for an operator given as a callable (the 3D system): x holds
-// the initial guess (zero here) and receives the solution; restart in block iterations.
-int ms_block_solve_fp64(ms_handle* herr, long long N, int nrhs, int restart,
-                        const std::function<int(const double2*, double2*)>& op, const double2* b, double2* x,
-                        double tol, int max_iters, int& iters, int& matvecs, std::vector<double>& relres,
-                        cudaStream_t st) {
+// Block GMRES on the CUDA cores (FP64 or FP32 basis) for an operator given as a callable (the 3D
+// system): x holds the initial guess (zero here) and receives the solution; restart in block iterations.
+template <typename T>
+int ms_block_solve(ms_handle* herr, long long N, int nrhs, int restart,
+                   const std::function<int(const typename CT<T>::c*, typename CT<T>::c*)>& op,
+                   const typename CT<T>::c* b, typename CT<T>::c* x, double tol, int max_iters, int& iters, int& matvecs,
+                   std::vector<double>& relres, cudaStream_t st) {
     int m = std::max(1, restart);
-    BlockKrylov<double>* K = nullptr;
+    BlockKrylov<T>* K = nullptr;
     while (true) {
-        K = new BlockKrylov<double>{herr, st, N, nrhs, m, false};
+        K = new BlockKrylov<T>{herr, st, N, nrhs, m, false};
         if (K->init() == MS_OK) break;
         delete K;
         K = nullptr;
         if (m <= 4) return MS_ERR_ALLOC;
         m /= 2;
     }
-    auto opc = [&](const double2* in, double2* out) -> int { return op(in, out); };
-    const int rc = block_gmres<double>(*K, opc, b, x, tol, max_iters, true, iters, matvecs, relres);
+    auto opc = [&](const typename CT<T>::c* in, typename CT<T>::c* out) -> int { return op(in, out); };
+    const int rc = block_gmres<T>(*K, opc, b, x, tol, max_iters, true, iters, matvecs, relres);
     delete K;
     return rc;
 }
+
+template int ms_block_solve<double>(ms_handle*, long long, int, int, const std::function<int(const double2*, double2*)>&,
+                                    const double2*, double2*, double, int, int&, int&, std::vector<double>&, cudaStream_t);
+template int ms_block_solve<float>(ms_handle*, long long, int, int, const std::function<int(const float2*, float2*)>&,
+                                   const float2*, float2*, double, int, int&, int&, std::vector<double>&, cudaStream_t);
 
 template <typename T>
 void ms_block_free(void* cache) {

@@ -454,24 +454,31 @@ bool build_cart_maps(int p, std::vector<int>& midx, std::vector<cd>& mcoef, std:
     return !map_overflow;
 }
 
-// ------------------------------------------------------------------ device kernels
+// ------------------------------------------------------------------ device kernels (T = double or float)
 __constant__ int c_deg[(P3MAX + 2) * (P3MAX + 2)];
 __constant__ int c_ord[(P3MAX + 2) * (P3MAX + 2)];
 __constant__ double c_ynorm[(2 * P3MAX + 2) * (2 * P3MAX + 2)];     // N_qk, k >= 0, at [q * (2P+2) + k]
 
 __device__ __forceinline__ int didx(int n, int m) { return n * n + n + m; }
+__device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
 
 // y = (identity ? x : 0) - S a  (identity) or S a (apply only), per sphere and order
-__global__ void k3_sapply(const double2* __restrict__ x, const double2* __restrict__ a, double2* __restrict__ y,
-                          const double2* __restrict__ Sd, int M, int p, int nrhs, int identity, int apply_s) {
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+template <typename T>
+__global__ void k3_sapply(const typename CT<T>::c* __restrict__ x, const typename CT<T>::c* __restrict__ a,
+                          typename CT<T>::c* __restrict__ y, const typename CT<T>::c* __restrict__ Sd, int M, int p,
+                          int nrhs, int identity, int apply_s) {
+    typedef typename CT<T>::c C;
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)M * T * nrhs) return;
+    if (i >= (long long)M * T3 * nrhs) return;
     const int r = (int)(i % nrhs);
     const long long mk = i / nrhs;
-    const int m = (int)(mk / T), k = (int)(mk % T);
-    const double2* A = a + (size_t)m * T * nrhs;
-    double2 v;
+    const int m = (int)(mk / T3), k = (int)(mk % T3);
+    const C* A = a + (size_t)m * T3 * nrhs;
+    C v;
     if (!apply_s) {
         v = A[(size_t)k * nrhs + r];
     } else {
@@ -480,14 +487,14 @@ __global__ void k3_sapply(const double2* __restrict__ x, const double2* __restri
         else if (k < 2 * nmn) { blk = 1; kk = k - nmn + 1; }
         else { blk = 2; kk = k - 2 * nmn; }
         const int n = (int)sqrtf((float)kk + 0.5f);
-        const double2* S = Sd + ((size_t)m * (p + 1) + n) * 5;
+        const C* S = Sd + ((size_t)m * (p + 1) + n) * 5;
         if (blk == 2 && n == 0) {
             v = cmul(S[0], A[(size_t)k * nrhs + r]);
         } else if (blk == 1) {
             v = cmul(S[4], A[(size_t)k * nrhs + r]);
         } else {
-            const double2 aa = A[(size_t)(kk - 1) * nrhs + r];                // alpha-block entry of (n, m)
-            const double2 ac = A[(size_t)(2 * nmn + kk) * nrhs + r];         // gamma-block entry
+            const C aa = A[(size_t)(kk - 1) * nrhs + r];                // alpha-block entry of (n, m)
+            const C ac = A[(size_t)(2 * nmn + kk) * nrhs + r];         // gamma-block entry
             v = blk == 0 ? cadd(cmul(S[0], aa), cmul(S[1], ac)) : cadd(cmul(S[2], aa), cmul(S[3], ac));
         }
     }
@@ -495,32 +502,36 @@ __global__ void k3_sapply(const double2* __restrict__ x, const double2* __restri
 }
 
 // Cartesian outgoing expansions of each sphere's shear field: W[l][c][k'][r] = sum of <= 9 terms
-__global__ void k3_cart(const double2* __restrict__ x, double2* __restrict__ W, const int* __restrict__ midx,
-                        const double2* __restrict__ mcoef, int M, int p, int nrhs) {
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
+template <typename T>
+__global__ void k3_cart(const typename CT<T>::c* __restrict__ x, typename CT<T>::c* __restrict__ W,
+                        const int* __restrict__ midx, const typename CT<T>::c* __restrict__ mcoef, int M, int p,
+                        int nrhs) {
+    typedef typename CT<T>::c C;
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)M * 3 * K2 * nrhs) return;
     const int r = (int)(i % nrhs);
     const long long row = i / nrhs;
     const int l = (int)(row / (3 * K2)), ck = (int)(row % (3 * K2));
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = mk((T)0, (T)0);
     for (int t = 0; t < 9; ++t) {
         const int s = midx[ck * 9 + t];
         if (s < 0) break;
-        cfma(acc, mcoef[ck * 9 + t], x[((size_t)l * T + s) * nrhs + r]);
+        cfma(acc, mcoef[ck * 9 + t], x[((size_t)l * T3 + s) * nrhs + r]);
     }
     W[i] = acc;
 }
 
 // h_q(x), q = 0..Q, real x > 0: h_0 = -i e^{ix}/x, h_1 = -e^{ix}(x + i)/x^2, upward recurrence
-__device__ void sph_hankel_seq(int Q, double x, double2* h) {
-    double s, c;
-    sincos(x, &s, &c);
-    h[0] = make_double2(s / x, -c / x);
-    if (Q >= 1) h[1] = make_double2(-(c * x - s) / (x * x), -(s * x + c) / (x * x));
+template <typename T>
+__device__ void sph_hankel_seq(int Q, T x, typename CT<T>::c* h) {
+    T s, c;
+    sc(x, &s, &c);
+    h[0] = mk(s / x, -c / x);
+    if (Q >= 1) h[1] = mk(-(c * x - s) / (x * x), -(s * x + c) / (x * x));
     for (int q = 1; q < Q; ++q) {
-        const double f = (2.0 * q + 1.0) / x;
-        h[q + 1] = make_double2(f * h[q].x - h[q - 1].x, f * h[q].y - h[q - 1].y);
+        const T f = (T)(2 * q + 1) / x;
+        h[q + 1] = mk(f * h[q].x - h[q - 1].x, f * h[q].y - h[q - 1].y);
     }
 }
 
@@ -529,20 +540,24 @@ __device__ void sph_hankel_seq(int Q, double x, double2* h) {
 // for the compressional potential).  Gt[k'][t][nu mu] = 4 pi i^{nu - n' + q} G(n', m'; nu, mu; q),
 // q = |n' - nu| + 2t.  Shared: the source's Cartesian expansions and potential for the chunk, and
 // H_q^k = h_q(k |d|) Y_q^k(d^) for both wavenumbers.
-__global__ void __launch_bounds__(512) k3_translate(const double2* __restrict__ W, const double2* __restrict__ x,
-                                                     const double* __restrict__ cen, const double2* __restrict__ Gt,
-                                                     double2* __restrict__ Rr, double2* __restrict__ Cr, double kp,
-                                                     double ks, int M, int p, int nrhs) {
-    extern __shared__ double2 sm[];
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
+template <typename T>
+__global__ void __launch_bounds__(512) k3_translate(const typename CT<T>::c* __restrict__ W,
+                                                    const typename CT<T>::c* __restrict__ x, const T* __restrict__ cen,
+                                                    const typename CT<T>::c* __restrict__ Gt,
+                                                    typename CT<T>::c* __restrict__ Rr, typename CT<T>::c* __restrict__ Cr,
+                                                    T kp, T ks, int M, int p, int nrhs) {
+    typedef typename CT<T>::c C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sm = reinterpret_cast<C*>(sm_raw);
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl, K2 = (p + 2) * (p + 2);
     const int P2 = 2 * p + 1, QN = (P2 + 1) * (P2 + 1), TT = p + 1;
-    double2* Ws = sm;                           // [3][K2][RC]
-    double2* Gs = Ws + 3 * K2 * RC;             // [nl][RC]
-    double2* Hs = Gs + nl * RC;                 // [QN]
-    double2* Hp = Hs + QN;                      // [QN]
-    double2* hs = Hp + QN;                      // [P2 + 1]
-    double2* hp = hs + P2 + 1;                  // [P2 + 1]
-    __shared__ double dsh[4];
+    C* Ws = sm;                           // [3][K2][RC]
+    C* Gs = Ws + 3 * K2 * RC;             // [nl][RC]
+    C* Hs = Gs + nl * RC;                 // [QN]
+    C* Hp = Hs + QN;                      // [QN]
+    C* hs = Hp + QN;                      // [P2 + 1]
+    C* hp = hs + P2 + 1;                  // [P2 + 1]
+    __shared__ T dsh[4];
     const int m = blockIdx.x, r0 = blockIdx.y * RC;
     const int nr = min(RC, nrhs - r0);
     const int tid = threadIdx.x;
@@ -550,68 +565,68 @@ __global__ void __launch_bounds__(512) k3_translate(const double2* __restrict__ 
     const int comp = sth ? tid / nl : 0;
     const int vm = sth ? tid % nl : tid - 3 * nl;
     const int nu = (sth || pth) ? c_deg[vm] : 0, mu = (sth || pth) ? c_ord[vm] : 0;
-    double2 acc[RC];
+    C acc[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = make_double2(0.0, 0.0);
+    for (int r = 0; r < RC; ++r) acc[r] = mk((T)0, (T)0);
     for (int l = 0; l < M; ++l) {
         if (l == m) continue;
         if (tid == 0) {
-            const double dx = cen[3 * m] - cen[3 * l], dy = cen[3 * m + 1] - cen[3 * l + 1], dz = cen[3 * m + 2] - cen[3 * l + 2];
-            const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+            const T dx = cen[3 * m] - cen[3 * l], dy = cen[3 * m + 1] - cen[3 * l + 1], dz = cen[3 * m + 2] - cen[3 * l + 2];
+            const T dd = sqrt(dx * dx + dy * dy + dz * dz);
             dsh[0] = dx / dd; dsh[1] = dy / dd; dsh[2] = dz / dd; dsh[3] = dd;
-            sph_hankel_seq(P2, ks * dd, hs);
-            sph_hankel_seq(P2, kp * dd, hp);
+            sph_hankel_seq<T>(P2, ks * dd, hs);
+            sph_hankel_seq<T>(P2, kp * dd, hp);
         }
         for (int e = tid; e < 3 * K2 * RC; e += blockDim.x) {
             const int r = e % RC, ck = e / RC;
-            Ws[e] = r < nr ? W[(((size_t)l * 3 * K2) + ck) * nrhs + r0 + r] : make_double2(0.0, 0.0);
+            Ws[e] = r < nr ? W[(((size_t)l * 3 * K2) + ck) * nrhs + r0 + r] : mk((T)0, (T)0);
         }
         for (int e = tid; e < nl * RC; e += blockDim.x) {
             const int r = e % RC, k = e / RC;
-            Gs[e] = r < nr ? x[((size_t)l * T + 2 * nmn + k) * nrhs + r0 + r] : make_double2(0.0, 0.0);
+            Gs[e] = r < nr ? x[((size_t)l * T3 + 2 * nmn + k) * nrhs + r0 + r] : mk((T)0, (T)0);
         }
         __syncthreads();
         if (tid <= P2) {
             // Y_q^k(d^), k = tid >= 0, q = k..P2: N Q_q^k(t) w^k, w = d_x + i d_y; Y_q^{-k} = conj(Y_q^k)
             const int k = tid;
-            const double t = dsh[2];
-            double2 wk = make_double2(1.0, 0.0);
-            const double2 w = make_double2(dsh[0], dsh[1]);
+            const T t = dsh[2];
+            C wk = mk((T)1, (T)0);
+            const C w = mk(dsh[0], dsh[1]);
             for (int i = 0; i < k; ++i) wk = cmul(wk, w);
-            double df = 1.0;
-            for (int i = 1; i <= k; ++i) df *= (2.0 * i - 1.0);
-            double qm1 = 0.0, q0 = df;                 // Q_{k-1}^k = 0, Q_k^k
+            T df = 1;
+            for (int i = 1; i <= k; ++i) df *= (T)(2 * i - 1);
+            T qm1 = 0, q0 = df;                 // Q_{k-1}^k = 0, Q_k^k
             for (int q = k; q <= P2; ++q) {
-                const double y = c_ynorm[q * (2 * P3MAX + 2) + k] * q0;
-                const double2 Y = make_double2(y * wk.x, y * wk.y);
-                const double2 Yc = cconj(Y);
+                const T y = (T)c_ynorm[q * (2 * P3MAX + 2) + k] * q0;
+                const C Y = mk(y * wk.x, y * wk.y);
+                const C Yc = cconj(Y);
                 Hs[didx(q, k)] = cmul(hs[q], Y);
                 Hp[didx(q, k)] = cmul(hp[q], Y);
                 if (k > 0) {
                     Hs[didx(q, -k)] = cmul(hs[q], Yc);
                     Hp[didx(q, -k)] = cmul(hp[q], Yc);
                 }
-                const double qn = ((2.0 * q + 1.0) * t * q0 - (double)(q + k) * qm1) / (double)(q - k + 1);
+                const T qn = ((T)(2 * q + 1) * t * q0 - (T)(q + k) * qm1) / (T)(q - k + 1);
                 qm1 = q0;
                 q0 = qn;
             }
         }
         __syncthreads();
         if (sth || pth) {
-            const double2* Hq = sth ? Hs : Hp;
+            const C* Hq = sth ? Hs : Hp;
             const int nk = sth ? K2 : nl;
-            const double2* src = sth ? Ws + (size_t)comp * K2 * RC : Gs;
+            const C* src = sth ? Ws + (size_t)comp * K2 * RC : Gs;
             for (int kk = 0; kk < nk; ++kk) {
                 const int n1 = c_deg[kk], m1 = c_ord[kk];
                 const int dm = m1 - mu;
-                double2 A = make_double2(0.0, 0.0);
+                C A = mk((T)0, (T)0);
                 const int tmax = min(n1, nu);
                 for (int t = 0; t <= tmax; ++t) {
                     const int q = abs(n1 - nu) + 2 * t;
                     if (abs(dm) > q) continue;
                     cfma(A, Gt[((size_t)kk * TT + t) * nl + vm], Hq[didx(q, dm)]);
                 }
-                const double2* s = src + (size_t)kk * RC;
+                const C* s = src + (size_t)kk * RC;
 #pragma unroll
                 for (int r = 0; r < RC; ++r) cfma(acc[r], A, s[r]);
             }
@@ -631,16 +646,18 @@ __global__ void __launch_bounds__(512) k3_translate(const double2* __restrict__ 
 
 // a (+)= the translated coefficients: a_Jm and b_Jm from the regular Cartesian shear expansions (<= 9
 // terms each), c from the translated potential
-__global__ void k3_uncart(const double2* __restrict__ Rr, const double2* __restrict__ Cr, double2* __restrict__ a,
-                          const int* __restrict__ uidx, const double2* __restrict__ ucoef, int M, int p, int nrhs,
-                          int accumulate) {
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+template <typename T>
+__global__ void k3_uncart(const typename CT<T>::c* __restrict__ Rr, const typename CT<T>::c* __restrict__ Cr,
+                          typename CT<T>::c* __restrict__ a, const int* __restrict__ uidx,
+                          const typename CT<T>::c* __restrict__ ucoef, int M, int p, int nrhs, int accumulate) {
+    typedef typename CT<T>::c C;
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)M * T * nrhs) return;
+    if (i >= (long long)M * T3 * nrhs) return;
     const int r = (int)(i % nrhs);
-    const long long mk = i / nrhs;
-    const int m = (int)(mk / T), k = (int)(mk % T);
-    double2 v = make_double2(0.0, 0.0);
+    const long long mk_ = i / nrhs;
+    const int m = (int)(mk_ / T3), k = (int)(mk_ % T3);
+    C v = mk((T)0, (T)0);
     if (k < 2 * nmn) {
         for (int t = 0; t < 9; ++t) {
             const int s = uidx[k * 9 + t];                   // (c, nu mu) as c * nl + nu mu
@@ -656,31 +673,36 @@ __global__ void k3_uncart(const double2* __restrict__ Rr, const double2* __restr
 // Block B: U[q][w][r] = sum_l e^{-i (k_x x_l + k_y y_l) - i k_z^w z_l} sum_k Tw[q][k] x_l[k][r],
 // w = P (gamma block), SV, SH (alpha then beta).  One CTA per node; thread (w, r, l-slice).
 constexpr int M2S_LS = 5;
-__global__ void __launch_bounds__(3 * RC * M2S_LS) k3_m2s(const double2* __restrict__ x, const double2* __restrict__ TP,
-                                                          const double2* __restrict__ TV, const double2* __restrict__ TH,
-                                                          const double2* __restrict__ node, const double* __restrict__ cen,
-                                                          double2* __restrict__ U, int M, int p, int nrhs, int r0) {
-    __shared__ double2 red[3 * RC * M2S_LS];
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+template <typename T>
+__global__ void __launch_bounds__(3 * RC * M2S_LS) k3_m2s(const typename CT<T>::c* __restrict__ x,
+                                                          const typename CT<T>::c* __restrict__ TP,
+                                                          const typename CT<T>::c* __restrict__ TV,
+                                                          const typename CT<T>::c* __restrict__ TH,
+                                                          const typename CT<T>::c* __restrict__ node,
+                                                          const T* __restrict__ cen, typename CT<T>::c* __restrict__ U,
+                                                          int M, int p, int nrhs, int r0) {
+    typedef typename CT<T>::c C;
+    __shared__ C red[3 * RC * M2S_LS];
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl;
     const int q = blockIdx.x, tid = threadIdx.x;
     const int w = tid / (RC * M2S_LS), rem = tid % (RC * M2S_LS), r = rem % RC, ls = rem / RC;
     // node: (k_x, k_y, k_z^P, k_z^S)
-    const double2 kx = node[(size_t)q * 4], ky = node[(size_t)q * 4 + 1];
-    const double2 kz = node[(size_t)q * 4 + (w == 0 ? 2 : 3)];
-    const double2* Tw = w == 0 ? TP + (size_t)q * nl : (w == 1 ? TV : TH) + (size_t)q * 2 * nmn;
+    const C kx = node[(size_t)q * 4], ky = node[(size_t)q * 4 + 1];
+    const C kz = node[(size_t)q * 4 + (w == 0 ? 2 : 3)];
+    const C* Tw = w == 0 ? TP + (size_t)q * nl : (w == 1 ? TV : TH) + (size_t)q * 2 * nmn;
     const int off = w == 0 ? 2 * nmn : 0, len = w == 0 ? nl : 2 * nmn;
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = mk((T)0, (T)0);
     if (r0 + r < nrhs) {
         for (int l = ls; l < M; l += M2S_LS) {
-            const double X = cen[3 * l], Y = cen[3 * l + 1], Z = cen[3 * l + 2];
+            const T X = cen[3 * l], Y = cen[3 * l + 1], Z = cen[3 * l + 2];
             // phase = exp(-i (kx X + ky Y + kz Z))
-            const double re = kx.x * X + ky.x * Y + kz.x * Z, im = kx.y * X + ky.y * Y + kz.y * Z;
-            double s, c;
-            sincos(-re, &s, &c);
-            const double mag = exp(im);
-            const double2 ph = make_double2(mag * c, mag * s);
-            const double2* xl = x + ((size_t)l * T + off) * nrhs + r0 + r;
-            double2 d = make_double2(0.0, 0.0);
+            const T re = kx.x * X + ky.x * Y + kz.x * Z, im = kx.y * X + ky.y * Y + kz.y * Z;
+            T s, c;
+            sc(-re, &s, &c);
+            const T mag = ex(im);
+            const C ph = mk(mag * c, mag * s);
+            const C* xl = x + ((size_t)l * T3 + off) * nrhs + r0 + r;
+            C d = mk((T)0, (T)0);
             for (int k = 0; k < len; ++k) cfma(d, Tw[k], xl[(size_t)k * nrhs]);
             cfma(acc, ph, d);
         }
@@ -688,79 +710,83 @@ __global__ void __launch_bounds__(3 * RC * M2S_LS) k3_m2s(const double2* __restr
     red[tid] = acc;
     __syncthreads();
     if (ls == 0 && r0 + r < nrhs) {
-        double2 s = acc;
+        C s = acc;
         for (int j = 1; j < M2S_LS; ++j) s = cadd(s, red[tid + j * RC]);
         U[((size_t)q * 3 + w) * nrhs + r0 + r] = s;
     }
 }
 
 // D[q][w][r] = sum_v RW[q][w][v] U[q][v][r]
-__global__ void k3_reflect(const double2* __restrict__ U, const double2* __restrict__ RW, double2* __restrict__ D,
-                           int NS, int nrhs) {
+template <typename T>
+__global__ void k3_reflect(const typename CT<T>::c* __restrict__ U, const typename CT<T>::c* __restrict__ RW,
+                           typename CT<T>::c* __restrict__ D, int NS, int nrhs) {
+    typedef typename CT<T>::c C;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)NS * 3 * nrhs) return;
     const int r = (int)(i % nrhs);
     const long long qw = i / nrhs;
     const int q = (int)(qw / 3), w = (int)(qw % 3);
-    double2 v = make_double2(0.0, 0.0);
+    C v = mk((T)0, (T)0);
     for (int u = 0; u < 3; ++u) cfma(v, RW[(size_t)q * 9 + w * 3 + u], U[((size_t)q * 3 + u) * nrhs + r]);
     D[i] = v;
 }
 
 // Block C: a[m][k][r] += sum_q [e^{i(k_x x_m + k_y y_m) - i k_z^P z_m} CP[q][k] D[q][P][r]
 //                               + e^{... - i k_z^S z_m} (CV[q][k] D[q][SV][r] + CH[q][k] D[q][SH][r])]
-// One CTA per sphere and right-hand-side chunk; nodes staged in chunks of S2L_QC.
+// One CTA per sphere, right-hand-side chunk and slice of 288 coefficients; nodes staged in chunks.
 constexpr int S2L_QC = 32;
 constexpr int S2L_KSPAN = 288;            // coefficients per CTA (grid z covers T in slices)
-__global__ void __launch_bounds__(256) k3_s2l(const double2* __restrict__ D, const double2* __restrict__ CP,
-                                              const double2* __restrict__ CV, const double2* __restrict__ CH,
-                                              const double2* __restrict__ node, const double* __restrict__ cen,
-                                              double2* __restrict__ a, int NS, int p, int nrhs) {
-    __shared__ double2 Ds[S2L_QC][3][RC];
-    __shared__ double2 ph[S2L_QC][2];
-    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T = 2 * nmn + nl;
+template <typename T>
+__global__ void __launch_bounds__(256) k3_s2l(const typename CT<T>::c* __restrict__ D, const typename CT<T>::c* __restrict__ CP,
+                                              const typename CT<T>::c* __restrict__ CV,
+                                              const typename CT<T>::c* __restrict__ CH,
+                                              const typename CT<T>::c* __restrict__ node, const T* __restrict__ cen,
+                                              typename CT<T>::c* __restrict__ a, int NS, int p, int nrhs) {
+    typedef typename CT<T>::c C;
+    __shared__ C Ds[S2L_QC][3][RC];
+    __shared__ C ph[S2L_QC][2];
+    const int nmn = p * (p + 2), nl = (p + 1) * (p + 1), T3 = 2 * nmn + nl;
     const int m = blockIdx.x, r0 = blockIdx.y * RC, tid = threadIdx.x;
     const int r = tid % RC, kg = tid / RC + S2L_KSPAN * blockIdx.z;   // 16 groups of k per z-slice
     constexpr int KPT = S2L_KSPAN / 16;                               // k values per thread
-    double2 acc[KPT];
+    C acc[KPT];
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) acc[j] = make_double2(0.0, 0.0);
-    const double X = cen[3 * m], Y = cen[3 * m + 1], Z = cen[3 * m + 2];
+    for (int j = 0; j < KPT; ++j) acc[j] = mk((T)0, (T)0);
+    const T X = cen[3 * m], Y = cen[3 * m + 1], Z = cen[3 * m + 2];
     for (int q0 = 0; q0 < NS; q0 += S2L_QC) {
         const int nq = min(S2L_QC, NS - q0);
         for (int e = tid; e < S2L_QC * 3 * RC; e += blockDim.x) {
             const int rr = e % RC, w = (e / RC) % 3, qq = e / (3 * RC);
-            Ds[qq][w][rr] = (qq < nq && r0 + rr < nrhs) ? D[((size_t)(q0 + qq) * 3 + w) * nrhs + r0 + rr]
-                                                       : make_double2(0.0, 0.0);
+            Ds[qq][w][rr] = (qq < nq && r0 + rr < nrhs) ? D[((size_t)(q0 + qq) * 3 + w) * nrhs + r0 + rr] : mk((T)0, (T)0);
         }
         if (tid < 2 * S2L_QC) {
             const int qq = tid / 2, wv = tid % 2;
-            double2 v = make_double2(0.0, 0.0);
+            C v = mk((T)0, (T)0);
             if (qq < nq) {
                 const size_t q = q0 + qq;
-                const double2 kx = node[q * 4], ky = node[q * 4 + 1], kz = node[q * 4 + 2 + wv];
+                const C kx = node[q * 4], ky = node[q * 4 + 1], kz = node[q * 4 + 2 + wv];
                 // exp(i (kx X + ky Y - kz Z))
-                const double re = kx.x * X + ky.x * Y - kz.x * Z, im = kx.y * X + ky.y * Y - kz.y * Z;
-                double s, c;
-                sincos(re, &s, &c);
-                const double mag = exp(-im);
-                v = make_double2(mag * c, mag * s);
+                const T re = kx.x * X + ky.x * Y - kz.x * Z, im = kx.y * X + ky.y * Y - kz.y * Z;
+                T s, c;
+                sc(re, &s, &c);
+                const T mag = ex(-im);
+                v = mk(mag * c, mag * s);
             }
             ph[qq][wv] = v;
         }
         __syncthreads();
         for (int qq = 0; qq < nq; ++qq) {
             const size_t q = q0 + qq;
-            const double2 dp = cmul(ph[qq][0], Ds[qq][0][r]);
-            const double2 dv = cmul(ph[qq][1], Ds[qq][1][r]);
-            const double2 dh = cmul(ph[qq][1], Ds[qq][2][r]);
+            const C dp = cmul(ph[qq][0], Ds[qq][0][r]);
+            const C dv = cmul(ph[qq][1], Ds[qq][1][r]);
+            const C dh = cmul(ph[qq][1], Ds[qq][2][r]);
 #pragma unroll
             for (int j = 0; j < KPT; ++j) {
                 const int k = kg + 16 * j;
-                if (k < T && k < S2L_KSPAN * (blockIdx.z + 1)) {
-                    cfma(acc[j], CP[q * T + k], dp);
-                    cfma(acc[j], CV[q * T + k], dv);
-                    cfma(acc[j], CH[q * T + k], dh);
+                if (k < T3 && k < S2L_KSPAN * (blockIdx.z + 1)) {
+                    cfma(acc[j], CP[q * T3 + k], dp);
+                    cfma(acc[j], CV[q * T3 + k], dv);
+                    cfma(acc[j], CH[q * T3 + k], dh);
                 }
             }
         }
@@ -770,16 +796,68 @@ __global__ void __launch_bounds__(256) k3_s2l(const double2* __restrict__ D, con
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             const int k = kg + 16 * j;
-            if (k < T && k < S2L_KSPAN * (blockIdx.z + 1)) {
-                double2* o = a + ((size_t)m * T + k) * nrhs + r0 + r;
+            if (k < T3 && k < S2L_KSPAN * (blockIdx.z + 1)) {
+                C* o = a + ((size_t)m * T3 + k) * nrhs + r0 + r;
                 *o = cadd(*o, acc[j]);
             }
         }
 }
 
+// FP64 <-> FP32 blocks and y = b - y (FP64), column squared norms
+__global__ void k3_to_f32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k3_add_f32(double2* __restrict__ x, const float2* __restrict__ d, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = make_double2(x[i].x + (double)d[i].x, x[i].y + (double)d[i].y);
+}
+__global__ void k3_from_f32(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+__global__ void k3_residual(const double2* __restrict__ b, double2* __restrict__ y, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = csub(b[i], y[i]);
+}
+__global__ void k3_colnorm2(const double2* __restrict__ v, double* __restrict__ out, long long rows, int nrhs) {
+    __shared__ double part[256];
+    const int r = blockIdx.y;
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x)
+        s += cabs2(v[i * nrhs + r]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&out[r], part[0]);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ handle
+// device tables of one precision
+template <typename T>
+struct Tab3 {
+    typedef typename CT<T>::c C;
+    T* cen = nullptr;                       // [M][3]
+    C* Sd = nullptr;                        // [M][p+1][5]
+    C* Gt = nullptr;                        // [K2][p+1][nl]
+    C* mcoef = nullptr;                     // [3 K2][9]
+    C* ucoef = nullptr;                     // [2 nmn][9]
+    C *TP = nullptr, *TV = nullptr, *TH = nullptr;     // [NS][nl], [NS][2 nmn] x 2
+    C *CP = nullptr, *CV = nullptr, *CH = nullptr;     // [NS][T] x 3
+    C* node = nullptr;                      // [NS][4]: k_x, k_y, k_z^P, k_z^S (lower layer)
+    C* RW = nullptr;                        // [NS][3][3] reflection times weight
+    void release() {
+        cudaFree(cen); cudaFree(Sd); cudaFree(Gt); cudaFree(mcoef); cudaFree(ucoef); cudaFree(TP); cudaFree(TV);
+        cudaFree(TH); cudaFree(CP); cudaFree(CV); cudaFree(CH); cudaFree(node); cudaFree(RW);
+        *this = Tab3{};
+    }
+};
+
 struct ms3_handle {
     int M = 0, p = 0, T = 0, NS = 0, K2 = 0, nl = 0, nmn = 0;
     double omega = 0;
@@ -788,30 +866,34 @@ struct ms3_handle {
     std::vector<double> h_cen, h_rad;
     std::vector<int> h_bc;
     ms_handle* herr = nullptr;              // status plumbing shared with the 2D solver's Krylov code
-    // device tables
-    double* cen = nullptr;                  // [M][3]
-    double2* Sd = nullptr;                  // [M][p+1][5]
-    double2* Gt = nullptr;                  // [K2][p+1][nl]
     int* midx = nullptr;                    // [3 K2][9]
-    double2* mcoef = nullptr;
     int* uidx = nullptr;                    // [2 nmn][9]
-    double2* ucoef = nullptr;
-    double2 *TP = nullptr, *TV = nullptr, *TH = nullptr;     // [NS][nl], [NS][2 nmn] x 2
-    double2 *CP = nullptr, *CV = nullptr, *CH = nullptr;     // [NS][T] x 3
-    double2* node = nullptr;                // [NS][4]: k_x, k_y, k_z^P, k_z^S (lower layer)
-    double2* RW = nullptr;                  // [NS][3][3] reflection times weight
-    // workspace (grown to the largest nrhs seen)
+    Tab3<double> t64;
+    Tab3<float> t32;
+    // workspace (sized in complex doubles, reused for FP32; grown to the largest nrhs seen)
     int ws_nrhs = 0;
-    double2 *W = nullptr, *Rr = nullptr, *Cr = nullptr, *U = nullptr, *Dd = nullptr, *wa = nullptr, *wx = nullptr;
+    void *W = nullptr, *Rr = nullptr, *Cr = nullptr, *U = nullptr, *Dd = nullptr, *wa = nullptr, *wx = nullptr,
+         *wy = nullptr;
+    template <typename T> Tab3<T>& tab();
 };
+template <> Tab3<double>& ms3_handle::tab<double>() { return t64; }
+template <> Tab3<float>& ms3_handle::tab<float>() { return t32; }
 
 namespace {
 
-void free_all(ms3_handle* h) {
-    cudaFree(h->cen); cudaFree(h->Sd); cudaFree(h->Gt); cudaFree(h->midx); cudaFree(h->mcoef);
-    cudaFree(h->uidx); cudaFree(h->ucoef); cudaFree(h->TP); cudaFree(h->TV); cudaFree(h->TH);
-    cudaFree(h->CP); cudaFree(h->CV); cudaFree(h->CH); cudaFree(h->node); cudaFree(h->RW);
+void free_ws(ms3_handle* h) {
     cudaFree(h->W); cudaFree(h->Rr); cudaFree(h->Cr); cudaFree(h->U); cudaFree(h->Dd); cudaFree(h->wa); cudaFree(h->wx);
+    cudaFree(h->wy);
+    h->W = h->Rr = h->Cr = h->U = h->Dd = h->wa = h->wx = h->wy = nullptr;
+    h->ws_nrhs = 0;
+}
+
+void free_all(ms3_handle* h) {
+    h->t64.release();
+    h->t32.release();
+    cudaFree(h->midx); cudaFree(h->uidx);
+    h->midx = h->uidx = nullptr;
+    free_ws(h);
 }
 
 template <typename X>
@@ -822,78 +904,129 @@ int upload(ms3_handle* h, X** dst, const std::vector<X>& v) {
     return ms_check(h->herr, cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
 }
 
-std::vector<double2> to_d2(const std::vector<cd>& v) {
-    std::vector<double2> o(v.size());
-    for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+template <typename T>
+std::vector<typename CT<T>::c> to_dev(const std::vector<cd>& v) {
+    std::vector<typename CT<T>::c> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = to_c<T>(make_double2(v[i].real(), v[i].imag()));
     return o;
+}
+
+template <typename T>
+int upload_tables(ms3_handle* h, const std::vector<cd>& S, const std::vector<cd>& Gt, const std::vector<cd>& mcoef,
+                  const std::vector<cd>& ucoef, const std::vector<cd>& TP, const std::vector<cd>& TV,
+                  const std::vector<cd>& TH, const std::vector<cd>& CPv, const std::vector<cd>& CVv,
+                  const std::vector<cd>& CHv, const std::vector<cd>& node, const std::vector<cd>& RW) {
+    Tab3<T>& t = h->tab<T>();
+    std::vector<T> cen(h->h_cen.begin(), h->h_cen.end());
+    int rc;
+    if ((rc = upload(h, &t.cen, cen)) || (rc = upload(h, &t.Sd, to_dev<T>(S))) || (rc = upload(h, &t.Gt, to_dev<T>(Gt))) ||
+        (rc = upload(h, &t.mcoef, to_dev<T>(mcoef))) || (rc = upload(h, &t.ucoef, to_dev<T>(ucoef))) ||
+        (rc = upload(h, &t.TP, to_dev<T>(TP))) || (rc = upload(h, &t.TV, to_dev<T>(TV))) ||
+        (rc = upload(h, &t.TH, to_dev<T>(TH))) || (rc = upload(h, &t.CP, to_dev<T>(CPv))) ||
+        (rc = upload(h, &t.CV, to_dev<T>(CVv))) || (rc = upload(h, &t.CH, to_dev<T>(CHv))) ||
+        (rc = upload(h, &t.node, to_dev<T>(node))) || (rc = upload(h, &t.RW, to_dev<T>(RW))))
+        return rc;
+    return MS_OK;
 }
 
 int workspace(ms3_handle* h, int nrhs) {
     if (nrhs <= h->ws_nrhs) return MS_OK;
-    cudaFree(h->W); cudaFree(h->Rr); cudaFree(h->Cr); cudaFree(h->U); cudaFree(h->Dd); cudaFree(h->wa); cudaFree(h->wx);
-    h->W = h->Rr = h->Cr = h->U = h->Dd = h->wa = h->wx = nullptr;
-    h->ws_nrhs = 0;
+    free_ws(h);
     const size_t M = h->M, e = sizeof(double2);
     if (cudaMalloc(&h->W, M * 3 * h->K2 * nrhs * e) != cudaSuccess ||
         cudaMalloc(&h->Rr, M * 3 * h->nl * nrhs * e) != cudaSuccess ||
         cudaMalloc(&h->Cr, M * h->nl * nrhs * e) != cudaSuccess ||
         cudaMalloc(&h->U, (size_t)h->NS * 3 * nrhs * e) != cudaSuccess ||
         cudaMalloc(&h->Dd, (size_t)h->NS * 3 * nrhs * e) != cudaSuccess ||
-        cudaMalloc(&h->wa, M * h->T * nrhs * e) != cudaSuccess || cudaMalloc(&h->wx, M * h->T * nrhs * e) != cudaSuccess) {
+        cudaMalloc(&h->wa, M * h->T * nrhs * e) != cudaSuccess || cudaMalloc(&h->wx, M * h->T * nrhs * e) != cudaSuccess ||
+        cudaMalloc(&h->wy, M * h->T * nrhs * e) != cudaSuccess) {
         cudaGetLastError();
+        free_ws(h);
         return MS_ERR_ALLOC;
     }
     h->ws_nrhs = nrhs;
     return MS_OK;
 }
 
-// incoming coefficients of the selected parts into h->wa
-int incoming(ms3_handle* h, const double2* x, int nrhs, int parts, cudaStream_t st) {
-    const int M = h->M, p = h->p, T = h->T;
-    const long long n = (long long)M * T * nrhs;
+template <typename T>
+size_t translate_smem(int p) {
+    return (size_t)(3 * (p + 2) * (p + 2) * RC + (p + 1) * (p + 1) * RC + 2 * (2 * p + 2) * (2 * p + 2) + 2 * (2 * p + 2)) *
+           sizeof(typename CT<T>::c);
+}
+
+// incoming coefficients of the selected parts into h->wa (precision T)
+template <typename T>
+int incoming(ms3_handle* h, const typename CT<T>::c* x, int nrhs, int parts, cudaStream_t st) {
+    typedef typename CT<T>::c C;
+    const Tab3<T>& t = h->tab<T>();
+    const int M = h->M, p = h->p, T3 = h->T;
+    C* wa = (C*)h->wa;
+    const long long n = (long long)M * T3 * nrhs;
     int rc;
-    if ((rc = ms_check(h->herr, cudaMemsetAsync(h->wa, 0, n * sizeof(double2), st)))) return rc;
+    if ((rc = ms_check(h->herr, cudaMemsetAsync(wa, 0, n * sizeof(C), st)))) return rc;
     if ((parts & MS3_PART_T) && M > 1) {
-        k3_cart<<<nblk((long long)M * 3 * h->K2 * nrhs, 256), 256, 0, st>>>(x, h->W, h->midx, h->mcoef, M, p, nrhs);
+        k3_cart<T><<<nblk((long long)M * 3 * h->K2 * nrhs, 256), 256, 0, st>>>(x, (C*)h->W, h->midx, t.mcoef, M, p, nrhs);
         const int threads = ((4 * h->nl + 31) / 32) * 32;
-        const size_t smem = (size_t)(3 * h->K2 * RC + h->nl * RC + 2 * (2 * p + 2) * (2 * p + 2) + 2 * (2 * p + 2)) * sizeof(double2);
-        k3_translate<<<dim3(M, nblk(nrhs, RC)), threads, smem, st>>>(h->W, x, h->cen, h->Gt, h->Rr, h->Cr, h->lo.kp,
-                                                                     h->lo.ks, M, p, nrhs);
-        k3_uncart<<<nblk(n, 256), 256, 0, st>>>(h->Rr, h->Cr, h->wa, h->uidx, h->ucoef, M, p, nrhs, 1);
+        k3_translate<T><<<dim3(M, nblk(nrhs, RC)), threads, translate_smem<T>(p), st>>>(
+            (const C*)h->W, x, t.cen, t.Gt, (C*)h->Rr, (C*)h->Cr, (T)h->lo.kp, (T)h->lo.ks, M, p, nrhs);
+        k3_uncart<T><<<nblk(n, 256), 256, 0, st>>>((const C*)h->Rr, (const C*)h->Cr, wa, h->uidx, t.ucoef, M, p, nrhs, 1);
         if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
     }
     if (parts & MS3_PART_R) {
         for (int r0 = 0; r0 < nrhs; r0 += RC)
-            k3_m2s<<<h->NS, 3 * RC * M2S_LS, 0, st>>>(x, h->TP, h->TV, h->TH, h->node, h->cen, h->U, M, p, nrhs, r0);
-        k3_reflect<<<nblk((long long)h->NS * 3 * nrhs, 256), 256, 0, st>>>(h->U, h->RW, h->Dd, h->NS, nrhs);
-        k3_s2l<<<dim3(M, nblk(nrhs, RC), nblk(T, S2L_KSPAN)), 256, 0, st>>>(h->Dd, h->CP, h->CV, h->CH, h->node, h->cen,
-                                                                             h->wa, h->NS, p, nrhs);
+            k3_m2s<T><<<h->NS, 3 * RC * M2S_LS, 0, st>>>(x, t.TP, t.TV, t.TH, t.node, t.cen, (C*)h->U, M, p, nrhs, r0);
+        k3_reflect<T><<<nblk((long long)h->NS * 3 * nrhs, 256), 256, 0, st>>>((const C*)h->U, t.RW, (C*)h->Dd, h->NS, nrhs);
+        k3_s2l<T><<<dim3(M, nblk(nrhs, RC), nblk(T3, S2L_KSPAN)), 256, 0, st>>>((const C*)h->Dd, t.CP, t.CV, t.CH, t.node,
+                                                                                 t.cen, wa, h->NS, p, nrhs);
         if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
     }
     return MS_OK;
 }
 
-int op3(ms3_handle* h, const double2* x, double2* y, int nrhs, int parts, cudaStream_t st) {
+// y = x - S (parts) x (with MS3_PART_S) or (parts) x, x and y of precision T, y != x, neither a workspace
+template <typename T>
+int op3(ms3_handle* h, const typename CT<T>::c* x, typename CT<T>::c* y, int nrhs, int parts, cudaStream_t st) {
+    typedef typename CT<T>::c C;
     int rc;
     if ((rc = workspace(h, nrhs))) return rc;
-    if ((rc = incoming(h, x, nrhs, parts, st))) return rc;
+    if ((rc = incoming<T>(h, x, nrhs, parts, st))) return rc;
     const long long n = (long long)h->M * h->T * nrhs;
     const bool s = (parts & MS3_PART_S) != 0;
-    k3_sapply<<<nblk(n, 256), 256, 0, st>>>(x, h->wa, y, h->Sd, h->M, h->p, nrhs, s ? 1 : 0, s ? 1 : 0);
+    k3_sapply<T><<<nblk(n, 256), 256, 0, st>>>(x, (const C*)h->wa, y, h->tab<T>().Sd, h->M, h->p, nrhs, s ? 1 : 0,
+                                                s ? 1 : 0);
     return ms_check(h->herr, cudaGetLastError());
 }
 
-int check_3d_args(const ms3_handle* h, const void* x, const void* y, int nrhs) {
+int check_3d_args(const ms3_handle* h, const void* x, const void* y, int nrhs, int prec) {
     if (!h || !x || !y || nrhs < 1 || nrhs > 64 || x == y) return MS_ERR_ARG;
+    if (prec != MS_PREC_FP64 && prec != MS_PREC_FP32) return MS_ERR_ARG;
     return MS_OK;
+}
+
+// max over columns of ||v_c|| / ||b_c|| (FP64 blocks of rows x nrhs), norms of b in bn
+int rel_norms(ms3_handle* h, const double2* v, long long rows, int nrhs, std::vector<double>& out, cudaStream_t st) {
+    double* d = nullptr;
+    if (cudaMalloc(&d, nrhs * sizeof(double)) != cudaSuccess) return MS_ERR_ALLOC;
+    int rc = ms_check(h->herr, cudaMemsetAsync(d, 0, nrhs * sizeof(double), st));
+    if (!rc) {
+        k3_colnorm2<<<dim3(std::min<long long>(1184, (rows + 255) / 256), nrhs), 256, 0, st>>>(v, d, rows, nrhs);
+        rc = ms_check(h->herr, cudaGetLastError());
+    }
+    out.assign(nrhs, 0.0);
+    if (!rc) rc = ms_check(h->herr, cudaMemcpyAsync(out.data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = ms_check(h->herr, cudaStreamSynchronize(st));
+    cudaFree(d);
+    for (double& x : out) x = sqrt(x);
+    return rc;
 }
 
 }  // namespace
 
-int ms_block_solve_fp64(ms_handle* herr, long long N, int nrhs, int restart,
-                        const std::function<int(const double2*, double2*)>& op, const double2* b, double2* x,
-                        double tol, int max_iters, int& iters, int& matvecs, std::vector<double>& relres,
-                        cudaStream_t st);
+template <typename T>
+int ms_block_solve(ms_handle* herr, long long N, int nrhs, int restart,
+                   const std::function<int(const typename CT<T>::c*, typename CT<T>::c*)>& op,
+                   const typename CT<T>::c* b, typename CT<T>::c* x, double tol, int max_iters, int& iters, int& matvecs,
+                   std::vector<double>& relres, cudaStream_t st);
 
 extern "C" void ms3_default_options(ms3_options* o) {
     if (!o) return;
@@ -1060,27 +1193,37 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
             }
         }
     }
-    if ((rc = upload(h, &h->cen, h->h_cen)) || (rc = upload(h, &h->Sd, to_d2(S))) || (rc = upload(h, &h->Gt, to_d2(Gt))) ||
-        (rc = upload(h, &h->midx, midx)) || (rc = upload(h, &h->mcoef, to_d2(mcoef))) || (rc = upload(h, &h->uidx, uidx)) ||
-        (rc = upload(h, &h->ucoef, to_d2(ucoef))) || (rc = upload(h, &h->TP, to_d2(TP))) || (rc = upload(h, &h->TV, to_d2(TV))) ||
-        (rc = upload(h, &h->TH, to_d2(TH))) || (rc = upload(h, &h->CP, to_d2(CPv))) || (rc = upload(h, &h->CV, to_d2(CVv))) ||
-        (rc = upload(h, &h->CH, to_d2(CHv))) || (rc = upload(h, &h->node, to_d2(node))) || (rc = upload(h, &h->RW, to_d2(RW))))
+    if ((rc = upload(h, &h->midx, midx)) || (rc = upload(h, &h->uidx, uidx)) ||
+        (rc = upload_tables<double>(h, S, Gt, mcoef, ucoef, TP, TV, TH, CPv, CVv, CHv, node, RW)) ||
+        (rc = upload_tables<float>(h, S, Gt, mcoef, ucoef, TP, TV, TH, CPv, CVv, CHv, node, RW)))
         return fail(rc);
-    const size_t smem = (size_t)(3 * K2 * RC + nl * RC + 2 * (2 * p + 2) * (2 * p + 2) + 2 * (2 * p + 2)) * sizeof(double2);
-    if (cudaFuncSetAttribute(k3_translate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k3_translate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)translate_smem<double>(p)) != cudaSuccess ||
+        cudaFuncSetAttribute(k3_translate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)translate_smem<float>(p)) != cudaSuccess)
         return fail(MS_ERR_CUDA);
     *out = h;
     return MS_OK;
 }
 
-extern "C" int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, void* stream) {
-    if (int rc = check_3d_args(h, x, y, nrhs)) return rc;
+extern "C" int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, int32_t prec,
+                            void* stream) {
+    if (int rc = check_3d_args(h, x, y, nrhs, prec)) return rc;
     if (parts < 0 || parts > 7) return MS_ERR_ARG;
-    return op3(h, (const double2*)x, (double2*)y, nrhs, parts, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == MS_PREC_FP64) return op3<double>(h, (const double2*)x, (double2*)y, nrhs, parts, st);
+    // FP32 operator on FP64 blocks: staged through the FP32 workspace
+    int rc;
+    if ((rc = workspace(h, nrhs))) return rc;
+    const long long n = (long long)h->M * h->T * nrhs;
+    k3_to_f32<<<nblk(n, 256), 256, 0, st>>>((const double2*)x, (float2*)h->wx, n);
+    if ((rc = op3<float>(h, (const float2*)h->wx, (float2*)h->wy, nrhs, parts, st))) return rc;
+    k3_from_f32<<<nblk(n, 256), 256, 0, st>>>((const float2*)h->wy, (double2*)y, n);
+    return ms_check(h->herr, cudaGetLastError());
 }
 
-extern "C" int ms3_apply(ms3_handle* h, const void* x, void* y, int32_t nrhs, void* stream) {
-    return ms3_operator(h, x, y, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, stream);
+extern "C" int ms3_apply(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
+    return ms3_operator(h, x, y, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, prec, stream);
 }
 
 extern "C" int ms3_rhs(ms3_handle* h, const ms3_incidence* inc, void* b, void* stream) {
@@ -1129,46 +1272,89 @@ extern "C" int ms3_rhs(ms3_handle* h, const ms3_incidence* inc, void* b, void* s
     if ((rc = ms_check(h->herr, cudaMemcpyAsync(h->wa, a.data(), a.size() * sizeof(double2), cudaMemcpyHostToDevice, st))))
         return rc;
     const long long n = (long long)M * T * nrhs;
-    k3_sapply<<<nblk(n, 256), 256, 0, st>>>(nullptr, h->wa, (double2*)b, h->Sd, M, p, nrhs, 0, 1);
+    k3_sapply<double><<<nblk(n, 256), 256, 0, st>>>(nullptr, (const double2*)h->wa, (double2*)b, h->t64.Sd, M, p, nrhs, 0, 1);
     if ((rc = ms_check(h->herr, cudaGetLastError()))) return rc;
     return ms_check(h->herr, cudaStreamSynchronize(st));     // a is pageable host memory
 }
 
-extern "C" int ms3_solve(ms3_handle* h, const ms3_incidence* inc, double tol, void* tau, ms_solve_info* info,
-                         void* stream) {
-    if (!h || !inc || !tau || !(tol > 0)) return MS_ERR_ARG;
+// FP64: block GMRES on the FP64 operator.  FP32: iterative refinement -- the FP64 residual r = b - A x,
+// an FP32 block GMRES solve of A d = r to 1e-3 relative (FP32 operator and basis), x += d -- until every
+// column's FP64 relative residual is <= tol or the iteration cap is spent.
+extern "C" int ms3_solve(ms3_handle* h, const ms3_incidence* inc, double tol, int32_t prec, void* tau,
+                         ms_solve_info* info, void* stream) {
+    if (!h || !inc || !tau || !(tol > 0) || (prec != MS_PREC_FP64 && prec != MS_PREC_FP32)) return MS_ERR_ARG;
     const int nrhs = inc->nrhs;
     if (nrhs < 1 || nrhs > 64) return MS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const auto t0 = std::chrono::steady_clock::now();
-    double2* b = nullptr;
-    const size_t n = (size_t)h->M * h->T * nrhs;
-    if (cudaMalloc(&b, n * sizeof(double2)) != cudaSuccess) return MS_ERR_ALLOC;
-    int rc = ms3_rhs(h, inc, b, stream);
-    int iters = 0, matvecs = 0;
-    std::vector<double> relres;
+    const long long rows = (long long)h->M * h->T;
+    const size_t n = (size_t)rows * nrhs;
+    double2 *b = nullptr, *tmp = nullptr, *r = nullptr;
+    float2 *r32 = nullptr, *d32 = nullptr, *tmp32 = nullptr;
+    int rc = MS_OK;
+    if (cudaMalloc(&b, n * sizeof(double2)) != cudaSuccess || cudaMalloc(&tmp, n * sizeof(double2)) != cudaSuccess)
+        rc = MS_ERR_ALLOC;
+    if (!rc) rc = ms3_rhs(h, inc, b, stream);
+    int iters = 0, matvecs = 0, refinements = 0;
+    std::vector<double> relres(nrhs, 1.0);
     if (!rc) rc = ms_check(h->herr, cudaMemsetAsync(tau, 0, n * sizeof(double2), st));
-    double2* tmp = nullptr;
-    if (!rc && cudaMalloc(&tmp, n * sizeof(double2)) != cudaSuccess) rc = MS_ERR_ALLOC;
-    if (!rc) {
-        auto op = [&](const double2* in, double2* out) -> int {
-            // the operator needs distinct input and output blocks
+    if (!rc && prec == MS_PREC_FP64) {
+        std::function<int(const double2*, double2*)> op = [&](const double2* in, double2* out) -> int {
             if (in == out) {
                 if (int e = ms_check(h->herr, cudaMemcpyAsync(tmp, in, n * sizeof(double2), cudaMemcpyDeviceToDevice, st))) return e;
                 in = tmp;
             }
-            return op3(h, in, out, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, st);
+            return op3<double>(h, in, out, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, st);
         };
-        rc = ms_block_solve_fp64(h->herr, (long long)h->M * h->T, nrhs, h->opt.restart, op, b, (double2*)tau, tol,
-                                 h->opt.max_iters, iters, matvecs, relres, st);
+        rc = ms_block_solve<double>(h->herr, rows, nrhs, h->opt.restart, op, b, (double2*)tau, tol, h->opt.max_iters,
+                                    iters, matvecs, relres, st);
+    } else if (!rc) {
+        if (cudaMalloc(&r, n * sizeof(double2)) != cudaSuccess || cudaMalloc(&r32, n * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&d32, n * sizeof(float2)) != cudaSuccess || cudaMalloc(&tmp32, n * sizeof(float2)) != cudaSuccess)
+            rc = MS_ERR_ALLOC;
+        std::vector<double> bn, rn;
+        if (!rc) rc = rel_norms(h, b, rows, nrhs, bn, st);
+        std::function<int(const float2*, float2*)> op32 = [&](const float2* in, float2* out) -> int {
+            if (in == out) {
+                if (int e = ms_check(h->herr, cudaMemcpyAsync(tmp32, in, n * sizeof(float2), cudaMemcpyDeviceToDevice, st))) return e;
+                in = tmp32;
+            }
+            return op3<float>(h, in, out, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, st);
+        };
+        while (!rc) {
+            // r = b - A x in FP64
+            if ((rc = op3<double>(h, (const double2*)tau, r, nrhs, MS3_PART_T | MS3_PART_R | MS3_PART_S, st))) break;
+            ++matvecs;
+            k3_residual<<<nblk((long long)n, 256), 256, 0, st>>>(b, r, (long long)n);
+            if ((rc = rel_norms(h, r, rows, nrhs, rn, st))) break;
+            bool all = true;
+            for (int c = 0; c < nrhs; ++c) {
+                relres[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+                if (!std::isfinite(relres[c])) rc = MS_ERR_NONFINITE;
+                all = all && relres[c] <= tol;
+            }
+            if (rc || all || iters >= h->opt.max_iters) break;
+            k3_to_f32<<<nblk((long long)n, 256), 256, 0, st>>>(r, r32, (long long)n);
+            if ((rc = ms_check(h->herr, cudaMemsetAsync(d32, 0, n * sizeof(float2), st)))) break;
+            int it = 0, mv = 0;
+            std::vector<double> inner;
+            rc = ms_block_solve<float>(h->herr, rows, nrhs, h->opt.restart, op32, r32, d32, 1e-3, h->opt.max_iters - iters,
+                                       it, mv, inner, st);
+            if (rc) break;
+            iters += it;
+            matvecs += mv;
+            ++refinements;
+            k3_add_f32<<<nblk((long long)n, 256), 256, 0, st>>>((double2*)tau, d32, (long long)n);
+            if ((rc = ms_check(h->herr, cudaGetLastError()))) break;
+            if (it == 0) break;                          // no progress possible
+        }
     }
-    cudaFree(b);
-    cudaFree(tmp);
+    cudaFree(b); cudaFree(tmp); cudaFree(r); cudaFree(r32); cudaFree(d32); cudaFree(tmp32);
     double worst = 0;
     for (double v : relres) worst = std::max(worst, v);
     if (info) {
         info->iterations = iters;
-        info->refinements = 0;
+        info->refinements = refinements;
         info->matvecs = matvecs;
         info->max_rel_residual = worst;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -66,7 +66,24 @@ def test_rhs_and_solve_match_oracle(case):
     assert rel(b, want_b) <= 1e-12
     g, info = gpu.solve(kinds, th, ph, tol=1e-12)
     assert info["status"] == 0, info
-    assert rel(g.cpu().numpy(), ref.solve_lu(want_b)) <= 1e-9
+    want = ref.solve_lu(want_b)
+    assert rel(g.cpu().numpy(), want) <= 1e-9
+    gm, im = gpu.solve(kinds, th, ph, tol=1e-10, prec=P.MS_PREC_FP32)      # FP32 inner solves, FP64 refinement
+    assert im["status"] == 0 and im["refinements"] >= 2, im
+    assert rel(gm.cpu().numpy(), want) <= 1e-8
+
+
+def test_fp32_operator_against_fp64(case):
+    """The FP32 tables and arithmetic: relative l2 against the FP64 operator at the FP32 bar 2e-5 (FP32
+    entries and accumulation; the coefficient block's orders span many decades, so the bar is on the
+    whole block)."""
+    wl, p, ref, gpu = case
+    x = torch.as_tensor(scaled_random(300 + p, wl.M, p, 5), device="cuda")
+    a = gpu.apply(x, prec=P.MS_PREC_FP64)
+    b = gpu.apply(x, prec=P.MS_PREC_FP32)
+    e = float(torch.linalg.norm(a - b) / torch.linalg.norm(a))
+    print(f"3D FP32 operator p = {p}: relative error {e:.2e}")
+    assert e <= 2e-5
 
 
 def test_single_column_and_ragged_blocks(case):
