@@ -358,6 +358,18 @@ def run_solve(args):
     import synthetic as syn
     wl = syn.config3_discs(M=args.M or 10000, nrhs=args.nrhs)
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
+    if args.iter_sweep:
+        rows = []
+        for cap in [int(c) for c in args.iter_sweep.split(",")]:
+            sw = P.Solver.from_workload(wl, leaf_target=args.leaf_target, restart=args.restart, max_iters=cap,
+                                        precond_group=args.precond_group, store_near=args.store_near)
+            _, inf = sw.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
+            rows.append({"max_iters": cap, **inf})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            sw.close()
+        print(json.dumps({"mode": "solve-sweep", "workload": wl.name, "restart": args.restart,
+                          "precond_group": args.precond_group, "rows": rows}), flush=True)
+        return
     t0 = time.perf_counter()
     s = P.Solver.from_workload(wl, leaf_target=args.leaf_target, tensor_cores=args.tensor_cores,
                                restart=args.restart, max_iters=args.max_iters, inner_tol=args.inner_tol,
@@ -571,6 +583,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8, help="--mode grad: solve tolerance")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="--mode solve: inner GMRES tolerance (0: default)")
     ap.add_argument("--skip-fp64", action="store_true", help="--mode solve: mixed form only")
+    ap.add_argument("--iter-sweep", type=str, default="", help="--mode solve: comma-separated iteration caps; "
+                    "reports the mixed solve's FP64 residual after each cap (a fresh handle per cap)")
     ap.add_argument("--grad-prec", choices=["mixed", "fp64", "both"], default="mixed")
     ap.add_argument("--leaf-target", type=int, default=10, help="FMM particles per leaf box")
     ap.add_argument("--precond-group", type=int, default=0, help="--mode solve/grad: particles per block of the "

@@ -759,7 +759,35 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
                 return rc;
             if ((rc = K.update(K.blk(0), nbj, Y, x, true, 1.0))) return rc;
         }
-        if (all || total >= max_iters) break;
+        if (all) break;
+        if (total >= max_iters) {
+            // the cap ended a cycle: its update is checked against the true residual like any other
+            if ((rc = op(x, K.W))) return rc;
+            ++matvecs;
+            if ((rc = ms_check(K.h, cudaMemcpyAsync(K.blk(0), b, (size_t)K.N * s * sizeof(C), cudaMemcpyDeviceToDevice,
+                                                    K.st))))
+                return rc;
+            std::vector<cd> I((size_t)s * s, cd(0));
+            for (int c = 0; c < s; ++c) I[(size_t)c * s + c] = 1.0;
+            if ((rc = K.update(K.W, s, I, K.blk(0), true, -1.0))) return rc;
+            std::vector<cd> gr;
+            if ((rc = K.gram(K.blk(0), s, K.blk(0), gr, true))) return rc;
+            double worst = 0;
+            std::vector<double> now(s);
+            for (int c = 0; c < s; ++c) {
+                now[c] = bn[c] > 0 ? sqrt(std::max(0.0, gr[(size_t)c * s + c].real())) / bn[c] : 0.0;
+                worst = std::max(worst, now[c]);
+            }
+            if (!(worst <= 1.05 * prev_worst)) {
+                if ((rc = ms_check(K.h, cudaMemcpyAsync(x, K.Xprev, (size_t)K.N * s * sizeof(C), cudaMemcpyDeviceToDevice,
+                                                        K.st))))
+                    return rc;
+                ++K.reverted;
+            } else {
+                relres = now;
+            }
+            break;
+        }
     }
     iters_out = total;
     return MS_OK;
