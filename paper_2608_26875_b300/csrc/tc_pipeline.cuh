@@ -246,18 +246,21 @@ __device__ __forceinline__ void run_stored(P& pol, int nchunks, int n, int* err,
     const uint32_t tmem = *tslot;
     int copied = -1;                               // thread 0: last chunk whose copies were issued
     int waited = -1;                               // thread 0: last chunk whose copies were waited for
+    // thread 0 issues the hi and lo copies of chunk c into stage c % NSTAGE
+    auto issue_copy = [&](int c) {
+        const StageT<K> st = stage_ptrs<K>(smem, c % NSTAGE);
+        const unsigned char* src = bsrc + (size_t)c * 2 * half_bytes;
+        tc::mbar_expect_tx(&cbar[c % NSTAGE], 2 * half_bytes);
+        tc::bulk_g2s(st.bh, src, half_bytes, &cbar[c % NSTAGE]);
+        tc::bulk_g2s(st.bl, src + half_bytes, half_bytes, &cbar[c % NSTAGE]);
+        copied = c;
+    };
     if (nchunks > 0) pol.fetch(0);
+    if (tid == 0 && nchunks > 0 && !*fail) issue_copy(0);
     for (int c = 0; c < nchunks; ++c) {
         const int s = c % NSTAGE;
         if (c >= NSTAGE && !tc::mbar_wait(&bar[s], ((c / NSTAGE) - 1) & 1)) *fail = 1;
         const StageT<K> st = stage_ptrs<K>(smem, s);
-        if (tid == 0 && !*fail) {
-            const unsigned char* src = bsrc + (size_t)c * 2 * half_bytes;
-            tc::mbar_expect_tx(&cbar[s], 2 * half_bytes);
-            tc::bulk_g2s(st.bh, src, half_bytes, &cbar[s]);
-            tc::bulk_g2s(st.bl, src + half_bytes, half_bytes, &cbar[s]);
-            copied = c;
-        }
         pol.build_a(st);
         if (c + 1 < nchunks) pol.fetch(c + 1);
         tc::fence_proxy_async();
@@ -280,6 +283,15 @@ __device__ __forceinline__ void run_stored(P& pol, int nchunks, int n, int* err,
                 }
                 tc::mma_commit(&bar[s]);
                 *last = c;
+                // the next chunk's copies go out now, overlapping this chunk's multiplies; its stage is free
+                // once the multiplies of chunk c + 1 - NSTAGE have completed
+                const int cn = c + 1;
+                if (cn < nchunks) {
+                    if (cn >= NSTAGE && !tc::mbar_wait(&bar[cn % NSTAGE], ((cn / NSTAGE) - 1) & 1))
+                        *fail = 1;
+                    else
+                        issue_copy(cn);
+                }
             }
         }
     }
