@@ -363,7 +363,16 @@ def run_solve(args):
         for cap in [int(c) for c in args.iter_sweep.split(",")]:
             sw = P.Solver.from_workload(wl, leaf_target=args.leaf_target, restart=args.restart, max_iters=cap,
                                         precond_group=args.precond_group, store_near=args.store_near)
-            _, inf = sw.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
+            xs, inf = sw.solve(kinds, angles, tol=1e-8, prec=P.MS_PREC_FP32)
+            # how far the FP32 operator is from the FP64 one on this iterate, part by part
+            parts = {"near": P.MS_PART_T_NEAR | P.MS_PART_S, "far": P.MS_PART_T_FAR | P.MS_PART_S,
+                     "refl": P.MS_PART_R | P.MS_PART_S, "all": P.MS_PART_T | P.MS_PART_R | P.MS_PART_S}
+            disc = {}
+            for k, pt in parts.items():
+                y64 = sw.operator(xs, pt, prec=P.MS_PREC_FP64)
+                y32 = sw.operator(xs, pt, prec=P.MS_PREC_FP32)
+                disc[k] = float(torch.linalg.norm(y64 - y32) / torch.linalg.norm(y64))
+            inf["fp32_vs_fp64_operator_on_iterate"] = disc
             rows.append({"max_iters": cap, **inf})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
             sw.close()
