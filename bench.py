@@ -358,6 +358,24 @@ def run_solve(args):
     import synthetic as syn
     wl = syn.config3_discs(M=args.M or 10000, nrhs=args.nrhs)
     kinds, angles = wl.inc_kind[:args.nrhs], wl.inc_angle[:args.nrhs]
+    if args.far_diag:
+        # FP32-vs-FP64 far field on the physical right-hand side b and on the library's test blocks, for
+        # tree variants: the default, the CUDA-core M2L, and larger leaves (fewer levels)
+        out = []
+        for name, kw in (("default", {}), ("cuda-core", {"tensor_cores": False}), ("leaf40", {"leaf_target": 40})):
+            sw = P.Solver.from_workload(wl, store_near=0, **kw)
+            b = sw.rhs(kinds, angles)
+            xr = torch.as_tensor(syn.random_coeffs(7, wl.M, wl.p, len(kinds)), device="cuda")
+            row = {"variant": name, "fmm_levels": sw.fmm_levels}
+            for lab, v in (("rhs", b), ("random", xr)):
+                y64 = sw.operator(v, P.MS_PART_T_FAR, prec=P.MS_PREC_FP64)
+                y32 = sw.operator(v, P.MS_PART_T_FAR, prec=P.MS_PREC_FP32)
+                row[lab] = float(torch.linalg.norm(y64 - y32) / torch.linalg.norm(y64))
+            out.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            sw.close()
+        print(json.dumps({"mode": "far-diag", "workload": wl.name, "rows": out}), flush=True)
+        return
     if args.iter_sweep:
         rows = []
         for cap in [int(c) for c in args.iter_sweep.split(",")]:
@@ -592,6 +610,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8, help="--mode grad: solve tolerance")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="--mode solve: inner GMRES tolerance (0: default)")
     ap.add_argument("--skip-fp64", action="store_true", help="--mode solve: mixed form only")
+    ap.add_argument("--far-diag", action="store_true", help="--mode solve: FP32-vs-FP64 far-field discrepancy")
     ap.add_argument("--iter-sweep", type=str, default="", help="--mode solve: comma-separated iteration caps; "
                     "reports the mixed solve's FP64 residual after each cap (a fresh handle per cap)")
     ap.add_argument("--grad-prec", choices=["mixed", "fp64", "both"], default="mixed")
