@@ -522,12 +522,16 @@ int ms_build_translations(ms_handle* h, int use_fmm, int leaf_target) {
                 int P = (int)fmm_order_tail(kb[b], rho, 2.0 * F.w[lev]);
                 P = std::min(P, 480);
                 F.P[b][lev] = P;
-                // scale exponents of the box expansions: round(log2((k rho / 2)^|n| / |n|!))
+                // scale exponents of the box expansions: round(log2((k rho / 2)^|n| / |n|!)) where that is
+                // below 1, else 0.  Box expansions of a physical field are O(1) up to |n| ~ k rho and decay
+                // like the profile beyond; scaling the lower orders up as well (by up to 2^108 on the
+                // 36-wide boxes of the 10^4-particle cloud) pushes the products of two profiles in the M2L
+                // entries past the FP32 exponent range
                 std::vector<int> e(2 * P + 1);
                 for (int i = 0; i <= 2 * P; ++i) {
                     int n = abs(i - P);
                     double l2 = n * log2(kb[b] * rho / 2.0) - lgamma(n + 1.0) / log(2.0);
-                    e[i] = (int)std::max(-900L, std::min(900L, lround(l2)));
+                    e[i] = (int)std::max(-900L, std::min(0L, lround(l2)));
                 }
                 if ((rc = up(h, &F.expo[b][lev], e))) return rc;
             }

@@ -94,3 +94,18 @@ def test_full_size_fp32_tensor_cores_matches_fp64_everywhere(full):
     e1, e2 = rel_l2(y32, y64), scaled_err(y32, y64, tau(wl))
     print(f"full size FP32 tensor cores vs FP64 everywhere: relative l2 {e1:.3e}, scaled {e2:.3e}")
     assert e1 <= FULL_FP32_BAR and e2 <= FULL_FP32_BAR
+
+
+def test_fp32_far_field_on_the_physical_right_hand_side():
+    """The FP32 FMM (5 levels, box orders up to a few hundred on the coarse levels) against the FP64 one
+    on the plane-wave right-hand side b = S a0, whose coefficients follow the physical decay with the
+    order -- the input the mixed solve's inner iterations see -- at the FP32 tensor-core bar."""
+    wl = syn.config3_discs(M=10000, nrhs=8)
+    s = P.Solver.from_workload(wl)
+    assert s.fmm_levels >= 5
+    b = s.rhs(wl.inc_kind[:8], wl.inc_angle[:8])
+    y64 = s.operator(b, P.MS_PART_T_FAR, prec=P.MS_PREC_FP64)
+    y32 = s.operator(b, P.MS_PART_T_FAR, prec=P.MS_PREC_FP32)
+    e = float(torch.linalg.norm(y64 - y32) / torch.linalg.norm(y64))
+    print(f"FP32 far field on b: relative error {e:.2e}")
+    assert e <= FULL_FP32_BAR
