@@ -163,8 +163,14 @@ def field(p: int, kp: float, ks: float, x, coeffs, kind: str = "h"):
     if c.ndim == 1:
         return (np.einsum("...ki,k->...i", N, c[:nmn]) + np.einsum("...ki,k->...i", M, c[nmn:2 * nmn])
                 + np.einsum("...ki,k->...i", L, c[2 * nmn:]))
-    return (np.einsum("...ki,kr->...ir", N, c[:nmn]) + np.einsum("...ki,kr->...ir", M, c[nmn:2 * nmn])
-            + np.einsum("...ki,kr->...ir", L, c[2 * nmn:]))
+    return _mode_sum(N, c[:nmn]) + _mode_sum(M, c[nmn:2 * nmn]) + _mode_sum(L, c[2 * nmn:])
+
+
+def _mode_sum(V, c):
+    """sum_k V[..., k, i] c[k, r] -> (..., 3, nrhs), as one matrix product."""
+    lead = V.shape[:-2]
+    Vt = np.moveaxis(V, -2, -1).reshape(-1, V.shape[-2])
+    return (Vt @ c).reshape(lead + (V.shape[-1], c.shape[-1]))
 
 
 # ------------------------------------------------------------------ traction on a sphere
@@ -296,9 +302,9 @@ def project_regular(p: int, kp: float, ks: float, rho: float, u, dirs, wts):
     ur = np.einsum("ki,kir->kr", dirs.astype(complex), u)
     n, _ = orders(p)
     nn1 = np.where(n > 0, n * (n + 1), 1)
-    f = np.einsum("k,kj,kr->jr", wts, Y.conj(), ur)
-    g = np.einsum("k,kji,kir->jr", wts, G.conj(), u) / nn1[:, None]
-    h = np.einsum("k,kji,kir->jr", wts, X.conj(), u) / nn1[:, None]
+    f = (Y.conj() * wts[:, None]).T @ ur                                        # sum_k w_k Y*_kj ur_kr
+    g = np.tensordot(G.conj() * wts[:, None, None], u, axes=([0, 2], [0, 1])) / nn1[:, None]
+    h = np.tensordot(X.conj() * wts[:, None, None], u, axes=([0, 2], [0, 1])) / nn1[:, None]
     zs, zsd = radial(p, ks * rho, "j")
     zp, zpd = radial(p, kp * rho, "j")
     out = np.zeros((tot, u.shape[-1]), dtype=complex)
