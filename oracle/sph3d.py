@@ -85,14 +85,15 @@ def grad_ylm(p: int, d):
     d = np.asarray(d)
     x, y, z = d[..., 0], d[..., 1], d[..., 2]
     out = np.zeros(d.shape[:-1] + (nlm(p), 3), dtype=complex)
+    zp = [z ** j for j in range(p + 1)]                                  # z^j, j = 0..p
     for n, m, am, norm, q in _ylm_poly(p):
         sg = 1j if m >= 0 else -1j
         w = x + sg * y
         j = np.arange(len(q))
         k = (n - am - j) / 2.0
-        s0 = sum(q[i] * z ** j[i] for i in range(len(q)))
-        s1 = sum(q[i] * k[i] * z ** j[i] for i in range(len(q)))
-        s2 = sum(q[i] * j[i] * z ** (j[i] - 1) for i in range(len(q)) if j[i] > 0) if len(q) > 1 else 0.0 * z
+        s0 = sum(q[i] * zp[i] for i in range(len(q)))
+        s1 = sum(q[i] * k[i] * zp[i] for i in range(len(q)))
+        s2 = sum(q[i] * j[i] * zp[i - 1] for i in range(1, len(q))) if len(q) > 1 else 0.0 * z
         wm = w ** am
         wm1 = am * w ** (am - 1) if am > 0 else 0.0 * w
         H = norm * wm * s0
