@@ -48,7 +48,7 @@ typedef struct {
 
 typedef struct {
     int32_t n_r;               /* Gauss-Legendre nodes in t on [0, t_max] (default 128) */
-    int32_t n_theta;           /* equispaced angles (default 64) */
+    int32_t n_theta;           /* equispaced angles (default 64); n_r * n_theta <= 2^18 */
     int32_t n_panels;          /* equal panels the n_r nodes are split into (default 4; must divide n_r) */
     double  t_max;             /* radial contour k_rho = t - i alpha tanh(beta t), t in [0, t_max] (default 10) */
     double  alpha;             /* contour depth (default 1; wide clouds need ~3 / horizontal extent) */
@@ -72,11 +72,12 @@ typedef struct {
 /* Defaults into *o.  NULL is ignored. */
 void ms3_default_options(ms3_options* o);
 
-/* Handle for the geometry, media (Lame pairs of both layers, unit density), omega > 0 and order
+/* Handle for the geometry, media (Lame pairs of both layers, unit density), finite omega > 0 and order
  * 1 <= p <= 10.  Host-side validation (MS_ERR_ARG, MS_ERR_NOT_BURIED, MS_ERR_OVERLAP: centres closer
  * than 1.1 (R_l + R_m)) precedes any device work.  Tables: the sphere matrices, per-node spectral
  * factors of blocks B and C and the reflection matrices (about 16 (2 (T + p(p+2)) + 9) N_S bytes,
- * N_S = n_r n_theta), translation coefficient tables.  *out is NULL on failure. */
+ * N_S = n_r n_theta), translation coefficient tables.  MS_ERR_ALLOC if a device or host allocation fails.  *out is NULL on
+ * failure. */
 int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
               ms3_handle** out);
 

@@ -47,7 +47,7 @@ extern "C" {
 #define MS_ERR_NOT_BURIED       -4    /* a particle with y_m + 1.1 R_m > 0 (must lie in x2 < 0, Sec. 2) */
 #define MS_ERR_UNSUPPORTED      -5    /* request outside what this build implements */
 #define MS_ERR_RECEIVER_INSIDE  -6    /* a receiver inside some particle's enclosing disc, or above y = 0 */
-#define MS_ERR_ALLOC            -7    /* device allocation failed */
+#define MS_ERR_ALLOC            -7    /* device or host allocation failed */
 #define MS_ERR_NONFINITE        -9    /* NaN or Inf met in a right-hand side or residual */
 #define MS_ERR_BREAKDOWN       -10    /* GMRES breakdown with a non-zero residual */
 #define MS_ERR_TOO_LARGE       -11    /* request exceeds the fixed scratch of ms_fields_noalloc */
@@ -96,7 +96,8 @@ typedef struct {
 typedef struct {
     int32_t n_panels;          /* uniform Gauss-Legendre panels on [-t_max, t_max] (default 32) */
     int32_t nodes_per_panel;   /* nodes per panel (default 16); N_S = panels * nodes_per_panel, the panels
-                                  being the uniform ones split at the graded edges (see grade) */
+                                  being the uniform ones split at the graded edges (see grade);
+                                  n_panels * nodes_per_panel <= 2^20 */
     double  t_max;             /* contour xi(t) = t - i tanh(t)/2, |t| <= t_max (Sec. 5.1; default 20) */
     int32_t restart;           /* GMRES restart length (default 50; block iterations with block_krylov) */
     int32_t max_iters;         /* total GMRES iteration cap per solve (default 2000) */
@@ -164,7 +165,7 @@ typedef struct ms_handle ms_handle;
 /* Fill *o with the defaults listed above. */
 void ms_default_options(ms_options* o);
 
-/* Build a handle for one geometry, medium, frequency omega > 0 and expansion order 0 <= p <= 30
+/* Build a handle for one geometry, medium, finite frequency omega > 0 and expansion order 0 <= p <= 30
  * (truncation Z_p of Sec. 4.1): wavenumbers (Sec. 2), scattering matrices (closed-form discs,
  * Sec. 4.1; caller prototypes, Sec. 4.3), the Sommerfeld contour and the 2x2 reflection table per
  * node (Sec. 3, 5.1), and device workspace.  Errors: MS_ERR_ARG, MS_ERR_OVERLAP,

@@ -5,7 +5,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <complex>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -270,11 +272,15 @@ static std::vector<double> contour_edges(const ms_handle* h, const ms_options& o
     return out;
 }
 
-extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
-                        const ms_options* o, ms_handle** out) {
+constexpr long long MS_MAX_NODES = 1LL << 20;   // Sommerfeld nodes n_panels x nodes_per_panel
+
+// The body of ms_setup; `made` receives the handle as soon as it exists, so that the C entry point can
+// release it if a host allocation throws.
+static int ms_setup_impl(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
+                         const ms_options* o, ms_handle** out, ms_handle*& made) {
     if (!out) return MS_ERR_ARG;
     *out = nullptr;
-    if (!g || !md || !g->centres || !g->radius || !g->bc || g->M < 1 || !(omega > 0) || p < 0 ||
+    if (!g || !md || !g->centres || !g->radius || !g->bc || g->M < 1 || !(omega > 0) || !std::isfinite(omega) || p < 0 ||
         p > 30)
         return MS_ERR_ARG;
     if (!(md->mu_u > 0) || !(md->mu_l > 0) || !(md->lam_u + md->mu_u > 0) || !(md->lam_l + md->mu_l > 0))
@@ -282,7 +288,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     ms_options opt;
     ms_default_options(&opt);
     if (o) opt = *o;
-    if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || opt.restart < 1 || opt.max_iters < 1 ||
+    if (opt.n_panels < 1 || opt.nodes_per_panel < 1 || !(opt.t_max > 0) || !std::isfinite(opt.t_max) ||
+        (long long)opt.n_panels * opt.nodes_per_panel > MS_MAX_NODES || opt.restart < 1 || opt.max_iters < 1 ||
         opt.leaf_target < 1 || !(opt.depth > 0) || opt.grade < 0 || opt.grade > 30 ||
         (opt.tensor_cores != 0 && opt.tensor_cores != 1) || !(opt.inner_tol >= 0.0 && opt.inner_tol < 1.0) ||
         opt.tc_wait_test < 0 || opt.tc_wait_test > 1000000 || (opt.block_krylov != 0 && opt.block_krylov != 1) ||
@@ -291,7 +298,8 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
         return MS_ERR_ARG;
     const int M = g->M, nc = 2 * p + 1;
     for (int m = 0; m < M; ++m) {
-        if (!(g->radius[m] > 0) || !std::isfinite(g->centres[2 * m]) || !std::isfinite(g->centres[2 * m + 1]))
+        if (!(g->radius[m] > 0) || !std::isfinite(g->radius[m]) || !std::isfinite(g->centres[2 * m]) ||
+            !std::isfinite(g->centres[2 * m + 1]))
             return MS_ERR_ARG;
         if (g->bc[m] != 0 && g->bc[m] != 1) return MS_ERR_ARG;
         if (g->proto && (g->proto[m] >= g->n_proto || g->proto[m] < -1)) return MS_ERR_ARG;
@@ -336,6 +344,7 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     }
 
     ms_handle* h = new ms_handle();
+    made = h;
     h->M = M;
     h->p = p;
     h->nc = nc;
@@ -530,4 +539,17 @@ extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, 
     }
     *out = h;
     return MS_OK;
+}
+
+extern "C" int ms_setup(const ms_geometry* g, const ms_media* md, double omega, int32_t p,
+                        const ms_options* o, ms_handle** out) {
+    ms_handle* made = nullptr;
+    try {
+        const int rc = ms_setup_impl(g, md, omega, p, o, out, made);
+        return rc;
+    } catch (const std::bad_alloc&) {
+        if (made) ms_destroy(made);
+        if (out) *out = nullptr;
+        return MS_ERR_ALLOC;
+    }
 }

@@ -33,6 +33,7 @@
 #include <cmath>
 #include <complex>
 #include <functional>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -1040,22 +1041,29 @@ extern "C" void ms3_default_options(ms3_options* o) {
     o->max_iters = 1000;
 }
 
-extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
-                         ms3_handle** out) {
+constexpr long long MS3_MAX_NODES = 1LL << 18;   // Sommerfeld nodes n_r n_theta (the tables hold 3 T per node)
+
+// The body of ms3_setup; `made` receives the handle as soon as it exists, so that the C entry point can
+// release it if a host allocation throws.
+static int ms3_setup_impl(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
+                   ms3_handle** out, ms3_handle*& made) {
     if (!out) return MS_ERR_ARG;
     *out = nullptr;
-    if (!g || !md || !g->centres || !g->radius || !g->bc || g->M < 1 || !(omega > 0) || p < 1 || p > P3MAX)
+    if (!g || !md || !g->centres || !g->radius || !g->bc || g->M < 1 || !(omega > 0) || !std::isfinite(omega) ||
+        p < 1 || p > P3MAX)
         return MS_ERR_ARG;
     if (!(md->mu_u > 0) || !(md->mu_l > 0) || !(md->lam_u + md->mu_u > 0) || !(md->lam_l + md->mu_l > 0)) return MS_ERR_ARG;
     ms3_options opt;
     ms3_default_options(&opt);
     if (o) opt = *o;
     if (opt.n_r < 1 || opt.n_theta < 1 || opt.n_panels < 1 || opt.n_r % opt.n_panels || !(opt.t_max > 0) ||
-        !(opt.alpha >= 0) || !(opt.beta > 0) || opt.restart < 1 || opt.max_iters < 1)
+        !(opt.alpha >= 0) || !(opt.beta > 0) || !std::isfinite(opt.t_max) || !std::isfinite(opt.alpha) ||
+        !std::isfinite(opt.beta) || opt.restart < 1 || opt.max_iters < 1 ||
+        (long long)opt.n_r * opt.n_theta > MS3_MAX_NODES)
         return MS_ERR_ARG;
     const int M = g->M;
     for (int m = 0; m < M; ++m) {
-        if (!(g->radius[m] > 0) || (g->bc[m] != 0 && g->bc[m] != 1)) return MS_ERR_ARG;
+        if (!(g->radius[m] > 0) || !std::isfinite(g->radius[m]) || (g->bc[m] != 0 && g->bc[m] != 1)) return MS_ERR_ARG;
         for (int i = 0; i < 3; ++i)
             if (!std::isfinite(g->centres[3 * m + i])) return MS_ERR_ARG;
         if (g->centres[3 * m + 2] + 1.1 * g->radius[m] > 0.0) return MS_ERR_NOT_BURIED;
@@ -1067,6 +1075,7 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
             if (sqrt(d2) < 1.1 * (g->radius[m] + g->radius[l])) return MS_ERR_OVERLAP;
         }
     ms3_handle* h = new ms3_handle;
+    made = h;
     h->herr = new ms_handle;
     h->M = M;
     h->p = p;
@@ -1087,6 +1096,7 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
         free_all(h);
         delete h->herr;
         delete h;
+        made = nullptr;
         return code;
     };
     // sphere matrices
@@ -1204,6 +1214,22 @@ extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega
         return fail(MS_ERR_CUDA);
     *out = h;
     return MS_OK;
+}
+
+extern "C" int ms3_setup(const ms3_geometry* g, const ms_media* md, double omega, int32_t p, const ms3_options* o,
+                         ms3_handle** out) {
+    ms3_handle* made = nullptr;
+    try {
+        return ms3_setup_impl(g, md, omega, p, o, out, made);
+    } catch (const std::bad_alloc&) {
+        if (made) {
+            free_all(made);
+            delete made->herr;
+            delete made;
+        }
+        if (out) *out = nullptr;
+        return MS_ERR_ALLOC;
+    }
 }
 
 extern "C" int ms3_operator(ms3_handle* h, const void* x, void* y, int32_t nrhs, int32_t parts, int32_t prec,

@@ -151,6 +151,10 @@ def _raw_setup(lib, case):
         g.n_proto = int(value)                 # tables announced, none passed
     elif field == "p":
         p = int(value)
+    elif field == "omega":
+        omega = float(value)
+    elif field == "radius":
+        r[3] = float(value)
     else:
         raise AssertionError(case)
     h = ctypes.c_void_p(12345)
@@ -163,7 +167,8 @@ def _raw_setup(lib, case):
     "leaf_target=0", "restart=0", "max_iters=0", "n_panels=0", "nodes_per_panel=0", "t_max=0",
     "depth=0", "depth=nan", "grade=-1", "grade=31", "mu_u=0", "mu_l=-1", "lam_l=-1.5", "M=0",
     "centre=nan", "centre=inf", "proto=0", "proto=-2", "n_proto=2", "p=-1", "store_near=-1",
-    "store_near=1025", "precond_group=-1", "precond_group=65"])
+    "store_near=1025", "precond_group=-1", "precond_group=65", "t_max=inf", "omega=inf", "omega=nan",
+    "radius=inf", "nodes_per_panel=65536"])
 def test_invalid_options_and_media_are_refused_before_device_work(lib, case):
     """Every ms_options field, the media and the geometry arrays are checked on the host: an
     invalid value returns MS_ERR_ARG and leaves the handle NULL (the call never reaches CUDA, so
@@ -229,7 +234,8 @@ def test_tensor_peak_refuses_invalid_arguments(lib):
     assert lib.ms_tensor_peak(1, 10, None, None) == nat.MS_ERR_ARG
 
 
-@pytest.mark.parametrize("case", ["p=0", "p=11", "not_buried", "overlap", "bc=2", "panels", "M=0", "nan"])
+@pytest.mark.parametrize("case", ["p=0", "p=11", "not_buried", "overlap", "bc=2", "panels", "M=0", "nan",
+                                  "omega=inf", "t_max=inf", "alpha=nan", "radius=inf", "nodes"])
 def test_3d_setup_refuses_invalid_input_before_device_work(lib, case):
     """ms3_setup validates geometry, order and rule on the host (no device needed)."""
     from paper_2608_26875_b300 import _native as nat
@@ -259,10 +265,19 @@ def test_3d_setup_refuses_invalid_input_before_device_work(lib, case):
         M = 0
     elif case == "nan":
         c[0, 0] = np.nan
+    elif case == "t_max=inf":
+        o.t_max = np.inf
+    elif case == "alpha=nan":
+        o.alpha = np.nan
+    elif case == "radius=inf":
+        r[0] = np.inf
+    elif case == "nodes":
+        o.n_r, o.n_theta = 1024, 512     # 2^19 Sommerfeld nodes, above the 2^18 limit
+    omega = np.inf if case == "omega=inf" else 2.0
     g = nat.Geometry3(M, c.ctypes.data_as(nat.c_dp), r.ctypes.data_as(nat.c_dp), bc.ctypes.data_as(nat.c_ip))
     md = nat.Media(1.0, 0.5, 2.0, 1.0)
     h = ctypes.c_void_p()
-    st = lib.ms3_setup(ctypes.byref(g), ctypes.byref(md), 2.0, p, ctypes.byref(o), ctypes.byref(h))
+    st = lib.ms3_setup(ctypes.byref(g), ctypes.byref(md), omega, p, ctypes.byref(o), ctypes.byref(h))
     assert st == want, (case, st)
     assert not h.value
 
