@@ -143,7 +143,8 @@ typedef struct {
                                   about n particles (a fuller cell cut into runs of at most 2n), each group's
                                   block I - S T (free-space translations inside the group) inverted in FP64
                                   at setup; costs 24 (2 (2p+1) n_g)^2 bytes per group.  0 = none (default).
-                                  Valid range 0..64. */
+                                  Valid range 0..64; ms_setup returns MS_ERR_UNSUPPORTED for more than 65535
+                                  groups or a group block wider than 12800 unknowns. */
 } ms_options;
 
 typedef struct {

@@ -190,7 +190,7 @@ __global__ void k_pc_to_f32(const double2* __restrict__ a, float2* __restrict__ 
 }
 
 // y_g = Binv_g x_g (adj = 0) or Binv_g^H x_g (adj = 1) for every group, x and y in the operator layout
-// [M][2][nc][nrhs] (y != x).  CTA = (64-row tile, group); K staged in tiles of 32.
+// [M][2][nc][nrhs] (y != x).  CTA = (64-row tile, group); K staged in tiles of AP_K.
 constexpr int AP_ROWS = 64, AP_K = 16;
 
 template <typename T>
@@ -327,8 +327,9 @@ int ms_precond_build(ms_handle* h) {
         poff[g + 1] = poff[g] + D;
         dmax = std::max(dmax, (int)D);
     }
-    // the inversion keeps one pivot column of the largest block in shared memory
-    if ((size_t)dmax * sizeof(double2) > (size_t)200 * 1024) return MS_ERR_UNSUPPORTED;
+    // the inversion keeps one pivot column of the largest block in shared memory; groups index grid z
+    // (assembly) and grid y (apply), at most 65535
+    if ((size_t)dmax * sizeof(double2) > (size_t)200 * 1024 || ng > 65535) return MS_ERR_UNSUPPORTED;
     PrecondDev& P = h->pc;
     P.ng = ng;
     P.total = goff[ng];
@@ -360,12 +361,15 @@ int ms_precond_build(ms_handle* h) {
         ms_precond_free(h);
         return MS_ERR_ALLOC;
     }
-    cudaMemcpy(dxy, c, 2 * M * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(dpoff, poff.data(), (ng + 1) * sizeof(long long), cudaMemcpyHostToDevice);
-    cudaMemset(sing, 0, sizeof(int));
+    rc = ms_check(h, cudaMemcpy(dxy, c, 2 * M * sizeof(double), cudaMemcpyHostToDevice));
+    if (!rc) rc = ms_check(h, cudaMemcpy(dpoff, poff.data(), (ng + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    if (!rc) rc = ms_check(h, cudaMemset(sing, 0, sizeof(int)));
     const int gm = gmax;
-    k_pc_graf<<<dim3(2 * gm, gm, ng), 256>>>(P.inv64, P.goff, P.gptr, P.gpart, dxy, h->d.expo, h->kp_l, h->ks_l, h->p, gm);
-    rc = ms_check(h, cudaGetLastError());
+    if (!rc) {
+        k_pc_graf<<<dim3(2 * gm, gm, ng), 256>>>(P.inv64, P.goff, P.gptr, P.gpart, dxy, h->d.expo, h->kp_l, h->ks_l,
+                                                 h->p, gm);
+        rc = ms_check(h, cudaGetLastError());
+    }
     for (int c0 = 0; !rc && c0 < dmax; c0 += 64) {
         k_pc_gather<<<nblk((long long)vec, 256), 256>>>(P.inv64, P.goff, P.pgrp, P.ppos, P.gptr, xg, M, nc, c0);
         if ((rc = ms_check(h, cudaGetLastError()))) break;
@@ -374,9 +378,12 @@ int ms_precond_build(ms_handle* h) {
         rc = ms_check(h, cudaGetLastError());
     }
     if (!rc) {
-        cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax * (int)sizeof(double2));
-        k_pc_invert<<<ng, PC_THREADS, dmax * sizeof(double2)>>>(P.inv64, P.goff, P.gptr, nc, ipiv, dpoff, sing);
-        rc = ms_check(h, cudaGetLastError());
+        rc = ms_check(h, cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              dmax * (int)sizeof(double2)));
+        if (!rc) {
+            k_pc_invert<<<ng, PC_THREADS, dmax * sizeof(double2)>>>(P.inv64, P.goff, P.gptr, nc, ipiv, dpoff, sing);
+            rc = ms_check(h, cudaGetLastError());
+        }
     }
     if (!rc) {
         k_pc_to_f32<<<nblk(P.total, 256), 256>>>(P.inv64, P.inv32, P.total);
