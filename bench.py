@@ -175,7 +175,10 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": wl.name, "M": wl.M, "p": wl.p, "nrhs": 64,
                                             "n_nodes": nodes},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "projected": True,
+            "projection": ("value and ms_per_step are projected linearly from each step's bounded sample to one "
+                           "full 64-column mat-vec; the run itself lasts steps x the sample's time")}
     print(json.dumps(line), flush=True)
 
 
