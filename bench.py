@@ -545,6 +545,9 @@ def run_3d(args):
                         "free_space": {"achieved": 8 * cmac_T / t_T / 1e12, "frac": 8 * cmac_T / t_T / fp64_peak},
                         "reflected": {"achieved": 8 * cmac_R / t_R / 1e12, "frac": 8 * cmac_R / t_R / fp64_peak},
                         "flops": "complex MACs of the contractions x 8 (translation-coefficient generation not counted)"}}
+    if args.no_solve:
+        print(json.dumps(out), flush=True)
+        return
     gm, info_m = s.solve(wl.inc_kind, wl.inc_theta, wl.inc_phi, tol=args.tol, prec=P.MS_PREC_FP32)
     out["solve_mixed"] = info_m
     if not args.skip_fp64:
@@ -613,6 +616,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8, help="--mode grad: solve tolerance")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="--mode solve: inner GMRES tolerance (0: default)")
     ap.add_argument("--skip-fp64", action="store_true", help="--mode solve: mixed form only")
+    ap.add_argument("--no-solve", action="store_true", help="--mode 3d: mat-vec timings only")
     ap.add_argument("--far-diag", action="store_true", help="--mode solve: FP32-vs-FP64 far-field discrepancy")
     ap.add_argument("--iter-sweep", type=str, default="", help="--mode solve: comma-separated iteration caps; "
                     "reports the mixed solve's FP64 residual after each cap (a fresh handle per cap)")
