@@ -45,7 +45,7 @@ extern "C" {
 #define MS_ERR_CUDA             -2    /* a CUDA runtime call failed; see ms_last_cuda_error */
 #define MS_ERR_OVERLAP          -3    /* two enclosing discs closer than 1.1 (R_l + R_m) (Sec. 2) */
 #define MS_ERR_NOT_BURIED       -4    /* a particle with y_m + 1.1 R_m > 0 (must lie in x2 < 0, Sec. 2) */
-#define MS_ERR_UNSUPPORTED      -5    /* request outside what this build implements */
+#define MS_ERR_UNSUPPORTED      -5    /* request outside what this library implements */
 #define MS_ERR_RECEIVER_INSIDE  -6    /* a receiver inside some particle's enclosing disc, or above y = 0 */
 #define MS_ERR_ALLOC            -7    /* device or host allocation failed */
 #define MS_ERR_NONFINITE        -9    /* NaN or Inf met in a right-hand side or residual */
