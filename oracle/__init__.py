@@ -51,7 +51,8 @@ multiple-scattering solve against the brute-force layered boundary integral solv
 and the fixed contour rule against adaptive Gauss-Kronrod quadrature.  For 3D (tests/test_oracle_3d.py):
 orthonormality and the addition theorem of the harmonics, differences of the harmonics and of the wave
 functions' curls, the exponential itself for the plane-wave coefficients at real and complex
-directions, sphere boundary conditions, the local expansion reproducing the sources' field, the polar
+directions, sphere boundary conditions, the local expansion reproducing the sources' field, the projection
+translation against the scalar addition-theorem series written out with Gaunt integrals, the polar
 quadrature of the spectral representation reproducing the outgoing field, zero reflection between
 identical layers, energy balance, and the solved system's boundary residual falling with the order.
 """
