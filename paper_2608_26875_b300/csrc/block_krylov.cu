@@ -29,6 +29,12 @@
 
 typedef std::complex<double> cd;
 
+using dense::apply_step;
+using dense::chol_upper;
+using dense::matmul;
+using dense::StepQR;
+using dense::tri_inv_upper;
+
 namespace {
 
 using tcp::KCC;
@@ -303,72 +309,6 @@ __global__ void k_fill_random(typename CT<T>::c* __restrict__ dst, long long N, 
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     dst[row * s + c] = to_c<T>(make_double2(((z & 0xffffffff) * 0x1p-31 - 1.0) * scale, ((z >> 32) * 0x1p-31 - 1.0) * scale));
-}
-
-// ------------------------------------------------------------------ host: small dense FP64 algebra
-// Upper-triangular R with G = R^H R (G Hermitian positive definite, s x s row-major); a diagonal
-// shift of shift * max diag(G) keeps the factorisation defined for (nearly) dependent blocks.
-bool chol_upper(const std::vector<cd>& G, int s, double shift, std::vector<cd>& R) {
-    double dmax = 0;
-    for (int i = 0; i < s; ++i) dmax = std::max(dmax, G[i * s + i].real());
-    const double add = shift * dmax + 1e-300;
-    R.assign((size_t)s * s, cd(0));
-    for (int i = 0; i < s; ++i) {
-        cd d = G[i * s + i] + add;
-        for (int k = 0; k < i; ++k) d -= std::conj(R[k * s + i]) * R[k * s + i];
-        if (!(d.real() > 0)) return false;
-        const double rii = sqrt(d.real());
-        R[i * s + i] = rii;
-        for (int j = i + 1; j < s; ++j) {
-            cd v = G[i * s + j];
-            for (int k = 0; k < i; ++k) v -= std::conj(R[k * s + i]) * R[k * s + j];
-            R[i * s + j] = v / rii;
-        }
-    }
-    return true;
-}
-
-// inverse of an upper-triangular s x s matrix
-void tri_inv_upper(const std::vector<cd>& R, int s, std::vector<cd>& Ri) {
-    Ri.assign((size_t)s * s, cd(0));
-    for (int j = 0; j < s; ++j) {
-        Ri[j * s + j] = 1.0 / R[j * s + j];
-        for (int i = j - 1; i >= 0; --i) {
-            cd v = 0;
-            for (int k = i + 1; k <= j; ++k) v += R[i * s + k] * Ri[k * s + j];
-            Ri[i * s + j] = -v / R[i * s + i];
-        }
-    }
-}
-
-// C = A B (s x s, row-major)
-std::vector<cd> matmul(const std::vector<cd>& A, const std::vector<cd>& B, int s) {
-    std::vector<cd> C((size_t)s * s, cd(0));
-    for (int i = 0; i < s; ++i)
-        for (int k = 0; k < s; ++k) {
-            const cd a = A[i * s + k];
-            if (a == 0.0) continue;
-            for (int j = 0; j < s; ++j) C[i * s + j] += a * B[k * s + j];
-        }
-    return C;
-}
-
-// Householder reflectors of one block step: acting on rows [j s, (j+2) s) of the block Hessenberg
-// matrix; reflector k has vector v_k (2s entries, zero above k) and factor tau_k: (I - tau v v^H).
-struct StepQR {
-    std::vector<cd> v;      // [s][2s]
-    std::vector<double> tau;
-};
-
-// y (2s entries with stride ys) -= tau v (v^H y) for every reflector of the step, in order
-void apply_step(const StepQR& q, int s, cd* y, long long ys) {
-    for (int k = 0; k < s; ++k) {
-        const cd* v = &q.v[(size_t)k * 2 * s];
-        cd d = 0;
-        for (int i = k; i < 2 * s; ++i) d += std::conj(v[i]) * y[i * ys];
-        d *= q.tau[k];
-        for (int i = k; i < 2 * s; ++i) y[i * ys] -= v[i] * d;
-    }
 }
 
 }  // namespace
@@ -686,30 +626,7 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
             for (int c = 0; c < s; ++c)
                 for (int i = 0; i < j; ++i) apply_step(qr[i], s, &hcol[(size_t)(i * s) * s + c], s);
             StepQR q;
-            q.v.assign((size_t)s * 2 * s, cd(0));
-            q.tau.assign(s, 0.0);
-            cd* P = &hcol[(size_t)(j * s) * s];                     // 2s x s panel, row stride s
-            for (int k = 0; k < s; ++k) {
-                double nx = 0;
-                for (int i = k; i < 2 * s; ++i) nx += std::norm(P[(size_t)i * s + k]);
-                nx = sqrt(nx);
-                cd* v = &q.v[(size_t)k * 2 * s];
-                if (nx == 0) continue;
-                const cd x0 = P[(size_t)k * s + k];
-                const cd alpha = -(std::abs(x0) > 0 ? x0 / std::abs(x0) : cd(1.0)) * nx;
-                for (int i = k; i < 2 * s; ++i) v[i] = P[(size_t)i * s + k];
-                v[k] -= alpha;
-                double vn = 0;
-                for (int i = k; i < 2 * s; ++i) vn += std::norm(v[i]);
-                if (vn == 0) continue;
-                q.tau[k] = 2.0 / vn;
-                for (int c = k; c < s; ++c) {
-                    cd d = 0;
-                    for (int i = k; i < 2 * s; ++i) d += std::conj(v[i]) * P[(size_t)i * s + c];
-                    d *= q.tau[k];
-                    for (int i = k; i < 2 * s; ++i) P[(size_t)i * s + c] -= v[i] * d;
-                }
-            }
+            dense::step_qr(&hcol[(size_t)(j * s) * s], s, q);      // the 2s x s panel, row stride s
 #pragma omp parallel for schedule(static)
             for (int c = 0; c < s; ++c) apply_step(q, s, &g[(size_t)(j * s) * s + c], s);
             qr.push_back(std::move(q));
@@ -730,30 +647,8 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
         // x += V_{0:j} Y with R Y = g[0 : j s] (block upper-triangular back substitution per column)
         const int nbj = j * s;
         if (nbj > 0) {
-            std::vector<cd> Y((size_t)nbj * s, cd(0));
-            // truncated back substitution: a diagonal entry below the floor times the largest is a direction
-            // the basis cannot resolve (deflated or stagnant), and its component is left at zero
-            double dmax = 0;
-            for (int row = 0; row < nbj; ++row) dmax = std::max(dmax, std::abs(Rcol[row / s][(size_t)row * s + (row % s)]));
-            const double dfloor = K.floor_rel() * dmax;
-#pragma omp parallel for schedule(static)
-            for (int c = 0; c < s; ++c) {
-                for (int row = nbj - 1; row >= 0; --row) {
-                    cd v = g[(size_t)row * s + c];
-                    // entries of row `row` in block columns jj >= its own block
-                    const int jb = row / s;
-                    for (int jj = jb; jj < j; ++jj) {
-                        const std::vector<cd>& Rc = Rcol[jj];
-                        for (int cc = 0; cc < s; ++cc) {
-                            const int col = jj * s + cc;
-                            if (col <= row) continue;
-                            v -= Rc[(size_t)row * s + cc] * Y[(size_t)col * s + c];
-                        }
-                    }
-                    const cd d = Rcol[jb][(size_t)row * s + (row - jb * s)];
-                    Y[(size_t)row * s + c] = std::abs(d) > dfloor ? v / d : cd(0);
-                }
-            }
+            std::vector<cd> Y;
+            dense::block_back_substitute(Rcol, g, s, j, K.floor_rel(), Y);
             if ((rc = ms_check(K.h, cudaMemcpyAsync(K.Xprev, x, (size_t)K.N * s * sizeof(C), cudaMemcpyDeviceToDevice,
                                                     K.st))))
                 return rc;
