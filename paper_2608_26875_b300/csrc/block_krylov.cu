@@ -29,7 +29,6 @@
 
 typedef std::complex<double> cd;
 
-using dense::apply_step;
 using dense::chol_upper;
 using dense::matmul;
 using dense::StepQR;
@@ -621,15 +620,12 @@ int block_gmres(BlockKrylov<T>& K, Op op, const typename CT<T>::c* b, typename C
             for (int i = 0; i < s; ++i)
                 for (int c = 0; c < s; ++c) hcol[(size_t)(nb + i) * s + c] = Rn[(size_t)i * s + c];
             ++total;
-            // previous steps' reflectors on the new block column, then this step's QR
-#pragma omp parallel for schedule(static)
-            for (int c = 0; c < s; ++c)
-                for (int i = 0; i < j; ++i) apply_step(qr[i], s, &hcol[(size_t)(i * s) * s + c], s);
+            // previous steps' reflectors on the new block column, then this step's QR, applied to g too
+            dense::apply_steps(qr, 0, j, s, hcol.data());
             StepQR q;
             dense::step_qr(&hcol[(size_t)(j * s) * s], s, q);      // the 2s x s panel, row stride s
-#pragma omp parallel for schedule(static)
-            for (int c = 0; c < s; ++c) apply_step(q, s, &g[(size_t)(j * s) * s + c], s);
             qr.push_back(std::move(q));
+            dense::apply_steps(qr, j, j + 1, s, g.data());
             Rcol.emplace_back(hcol.begin(), hcol.begin() + (size_t)nb * s);
             all = true;
             for (int c = 0; c < s; ++c) {

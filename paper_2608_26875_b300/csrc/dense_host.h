@@ -117,17 +117,6 @@ struct StepQR {
     std::vector<double> tau;
 };
 
-// y (2s entries with stride ys) -= tau v (v^H y) for every reflector of the step, in order
-inline void apply_step(const StepQR& q, int s, cd* y, long long ys) {
-    for (int k = 0; k < s; ++k) {
-        const cd* v = &q.v[(size_t)k * 2 * s];
-        cd d = 0;
-        for (int i = k; i < 2 * s; ++i) d += std::conj(v[i]) * y[i * ys];
-        d *= q.tau[k];
-        for (int i = k; i < 2 * s; ++i) y[i * ys] -= v[i] * d;
-    }
-}
-
 // Householder QR in place of the 2s x s panel P (row stride s): on return its upper s x s block is R
 // (up to rounding, zeros below), and q holds the s reflectors, reflector k zeroing column k below row k
 // (a zero column gets tau_k = 0, the identity).
@@ -157,33 +146,74 @@ inline void step_qr(cd* P, int s, StepQR& q) {
     }
 }
 
+// Steps i0 .. i1-1 of qr, in order, on all s columns of the block column H (row-major, row stride s):
+// step i acts on rows [i s, (i+2) s), and each of its reflectors k in order maps a column y (those 2s
+// rows) to y - tau_k v_k (v_k^H y).  The columns are processed in chunks of 8 adjacent ones (one chunk
+// per thread), so that the rows are read contiguously and no two threads write the same cache line.
+inline void apply_steps(const std::vector<StepQR>& qr, int i0, int i1, int s, cd* H) {
+    constexpr int CH = 8;
+    const int nch = (s + CH - 1) / CH;
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < nch; ++ch) {
+        const int c0 = ch * CH, w = std::min(CH, s - c0);
+        for (int i = i0; i < i1; ++i) {
+            cd* Y = H + (size_t)i * s * s + c0;
+            const StepQR& q = qr[i];
+            for (int k = 0; k < s; ++k) {
+                const cd* v = &q.v[(size_t)k * 2 * s];
+                cd d[CH];
+                for (int c = 0; c < w; ++c) d[c] = 0;
+                for (int r = k; r < 2 * s; ++r) {
+                    const cd vr = std::conj(v[r]);
+                    const cd* y = Y + (size_t)r * s;
+                    for (int c = 0; c < w; ++c) d[c] += vr * y[c];
+                }
+                for (int c = 0; c < w; ++c) d[c] *= q.tau[k];
+                for (int r = k; r < 2 * s; ++r) {
+                    const cd vr = v[r];
+                    cd* y = Y + (size_t)r * s;
+                    for (int c = 0; c < w; ++c) y[c] -= vr * d[c];
+                }
+            }
+        }
+    }
+}
+
 // Y (j s x s, row-major: Y[row * s + c]) with R Y = g[0 : j s] for the block upper-triangular R whose
 // block column jj is Rcol[jj] ((jj + 1) s x s, row-major), g[row * s + c] the transformed right-hand
 // side.  Truncated: a diagonal entry at or below floor_rel times the largest is a direction the basis
-// cannot resolve (deflated or stagnant), and its component is left at zero.  Parallel over the columns.
+// cannot resolve (deflated or stagnant), and its component is left at zero.  The columns go in chunks
+// of 8 adjacent ones (one chunk per thread), each column with the operations of a plain per-column
+// back substitution in the same order.
 inline void block_back_substitute(const std::vector<std::vector<cd>>& Rcol, const std::vector<cd>& g, int s, int j,
                                   double floor_rel, std::vector<cd>& Y) {
+    constexpr int CH = 8;
     const int nbj = j * s;
     Y.assign((size_t)nbj * s, cd(0));
     double dmax = 0;
     for (int row = 0; row < nbj; ++row) dmax = std::max(dmax, std::abs(Rcol[row / s][(size_t)row * s + (row % s)]));
     const double dfloor = floor_rel * dmax;
+    const int nch = (s + CH - 1) / CH;
 #pragma omp parallel for schedule(static)
-    for (int c = 0; c < s; ++c) {
+    for (int ch = 0; ch < nch; ++ch) {
+        const int c0 = ch * CH, w = std::min(CH, s - c0);
         for (int row = nbj - 1; row >= 0; --row) {
-            cd v = g[(size_t)row * s + c];
+            cd v[CH];
+            for (int c = 0; c < w; ++c) v[c] = g[(size_t)row * s + c0 + c];
             // entries of row `row` in block columns jj >= its own block
             const int jb = row / s;
             for (int jj = jb; jj < j; ++jj) {
-                const std::vector<cd>& Rc = Rcol[jj];
+                const cd* Rr = &Rcol[jj][(size_t)row * s];
                 for (int cc = 0; cc < s; ++cc) {
                     const int col = jj * s + cc;
                     if (col <= row) continue;
-                    v -= Rc[(size_t)row * s + cc] * Y[(size_t)col * s + c];
+                    const cd r = Rr[cc];
+                    const cd* y = &Y[(size_t)col * s + c0];
+                    for (int c = 0; c < w; ++c) v[c] -= r * y[c];
                 }
             }
             const cd d = Rcol[jb][(size_t)row * s + (row - jb * s)];
-            Y[(size_t)row * s + c] = std::abs(d) > dfloor ? v / d : cd(0);
+            for (int c = 0; c < w; ++c) Y[(size_t)row * s + c0 + c] = std::abs(d) > dfloor ? v[c] / d : cd(0);
         }
     }
 }

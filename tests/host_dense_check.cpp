@@ -96,12 +96,11 @@ int main(int argc, char** argv) {
                 std::vector<cd> hcol((size_t)(nb + s) * s);
                 for (int r = 0; r < nb + s; ++r)
                     for (int c = 0; c < s; ++c) hcol[(size_t)r * s + c] = H[(size_t)r * cols + j * s + c];
-                for (int c = 0; c < s; ++c)
-                    for (int i = 0; i < j; ++i) dense::apply_step(qr[i], s, &hcol[(size_t)(i * s) * s + c], s);
+                dense::apply_steps(qr, 0, j, s, hcol.data());
                 dense::StepQR q;
                 dense::step_qr(&hcol[(size_t)(j * s) * s], s, q);
-                for (int c = 0; c < s; ++c) dense::apply_step(q, s, &g[(size_t)(j * s) * s + c], s);
                 qr.push_back(std::move(q));
+                dense::apply_steps(qr, j, j + 1, s, g.data());
                 Rcol.emplace_back(hcol.begin(), hcol.begin() + (size_t)nb * s);
                 for (int c = 0; c < s; ++c) {
                     double r2 = 0;
